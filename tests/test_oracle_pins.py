@@ -1,0 +1,440 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: moment
+identities, closed-form flows, exactness of the compact interpolation on
+polynomial fields, conservation laws, the convergence order reported in the
+paper, and finite differences for the dual-number twin.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_06984_gb300 import workloads as W
+
+C9 = np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [0, -1], [1, 1], [-1, -1], [1, -1], [-1, 1]])
+C19 = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1], [1, 0, -1],
+                [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]])
+
+
+def lattice(Q):
+    return C9 if Q == 9 else C19
+
+
+def sym_to_mat(Sv, d):
+    n = Sv.shape[0]
+    S = np.zeros((n, d, d))
+    if d == 2:
+        S[:, 0, 0], S[:, 1, 1] = Sv[:, 0], Sv[:, 1]
+        S[:, 0, 1] = S[:, 1, 0] = Sv[:, 2]
+    else:
+        for k, (a, b) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2)]):
+            S[:, a, b] = S[:, b, a] = Sv[:, k]
+    return S
+
+
+def mat_to_sym(S, d):
+    if d == 2:
+        return np.stack([S[:, 0, 0], S[:, 1, 1], S[:, 0, 1]], axis=1)
+    return np.stack([S[:, 0, 0], S[:, 1, 1], S[:, 2, 2], S[:, 0, 1], S[:, 1, 2], S[:, 0, 2]], axis=1)
+
+
+# ---------------------------------------------------------------- lattice / equilibrium
+@pytest.mark.parametrize("Q", [9, 19])
+def test_equilibrium_moments(oracle_mod, Q):
+    """Sec. 2.1, Eq. (feq) with the u.u term subtracted: the zeroth, first and
+    second moments of f^eq are rho, rho u and rho (c_s^2 I + u u).  The printed
+    '+' sign would fail the zeroth moment."""
+    d = 2 if Q == 9 else 3
+    mesh = W.uniform(d, 2, (4,) * d, (0,) * (2 * d))
+    rng = np.random.default_rng(1)
+    rho = 1.0 + 0.05 * rng.standard_normal(mesh.n)
+    u = 0.05 * rng.standard_normal((mesh.n, d))
+    o = oracle_mod.Oracle(mesh, Q, 1.7)
+    o.init(rho, u)
+    f = o.get_f()
+    c = lattice(Q)
+    assert np.abs(f.sum(1) - rho).max() < 1e-15
+    assert np.abs(f @ c - rho[:, None] * u).max() < 1e-15
+    P = np.einsum("ni,ia,ib->nab", f, c, c)
+    P_ref = rho[:, None, None] * (np.eye(d)[None] / 3.0 + np.einsum("na,nb->nab", u, u))
+    assert np.abs(P - P_ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_strain_rate_roundtrip(oracle_mod, Q):
+    """Sec. 4.1 initial f^neq with the strain-rate equation of Sec. 2.1: the
+    strain rate read back from the initial state equals the one put in, and the
+    non-equilibrium part carries no mass or momentum (4th-order isotropy)."""
+    d = 2 if Q == 9 else 3
+    mesh = W.uniform(d, 2, (4,) * d, (0,) * (2 * d))
+    rng = np.random.default_rng(2)
+    n = mesh.n
+    rho = 1.0 + 0.02 * rng.standard_normal(n)
+    u = 0.02 * rng.standard_normal((n, d))
+    S = 1e-3 * rng.standard_normal((n, 3 if d == 2 else 6))
+    o = oracle_mod.Oracle(mesh, Q, 1.3)
+    o.init(rho, u, S)
+    r1, u1, S1 = o.moments()
+    assert np.abs(r1 - rho).max() < 1e-15
+    assert np.abs(u1 - u).max() < 1e-15
+    assert np.abs(S1 - S).max() < 1e-14 * max(1.0, np.abs(S).max() * 1e3)
+
+
+# ---------------------------------------------------------------- compact interpolation
+def quadratic_field(d, rng, scale=1.0):
+    A = rng.standard_normal(d)
+    B = rng.standard_normal((d, d))
+    C = rng.standard_normal((d, d, d))
+    C = (C + C.transpose(0, 2, 1)) / 2
+
+    def u(x):
+        x = np.atleast_2d(x)
+        return scale * (A + x @ B.T + np.einsum("abc,nb,nc->na", C, x, x))
+
+    def S(x):
+        x = np.atleast_2d(x)
+        g = B[None] + 2 * np.einsum("abc,nc->nab", C, x)
+        return scale * mat_to_sym(0.5 * (g + g.transpose(0, 2, 1)), d)
+
+    return u, S, C
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_compact_velocity_quadratic_exact(oracle_mod, d):
+    """Sec. 2.2, Eqs. (compact_3D_s), (compact_3D_u): the 30 coefficients are
+    determined by the four sources, so any quadratic velocity field (with its
+    exact strain rate) is reproduced exactly at the ghost position, in every
+    octant.  2D uses the same construction on the unit square."""
+    rng = np.random.default_rng(3)
+    offs = [(0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)] if d == 3 else [(0, 0), (1, 0), (0, 1), (1, 1)]
+    worst = 0.0
+    for trial in range(5):
+        u, S, _ = quadratic_field(d, rng)
+        for s in itertools.product((-1, 1), repeat=d):
+            s = np.array(s)
+            P = rng.standard_normal(d) * 3
+            src = np.array([P + s * np.array(o[:d]) for o in offs])
+            out = oracle_mod.compact_velocity(d, np.array(list(s) + [1] * (3 - d)), u(src), S(src))
+            exact = u(P + 0.25 * s)[0]
+            worst = max(worst, np.abs(out - exact).max() / np.abs(exact).max())
+    assert worst < 1e-12
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_compact_velocity_uses_strain_rate(oracle_mod, d):
+    """A plausible slip, dropping the strain-rate terms, is not quadratic exact:
+    with zero source velocities and nonzero strain rates the interpolant is
+    nonzero and equals the quadratic's value."""
+    rng = np.random.default_rng(4)
+    u, S, _ = quadratic_field(d, rng)
+    offs = [(0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)] if d == 3 else [(0, 0), (1, 0), (0, 1), (1, 1)]
+    s = np.ones(d, dtype=int)
+    src = np.array([np.array(o[:d], float) for o in offs])
+    base = oracle_mod.compact_velocity(d, np.ones(3, dtype=np.int32), u(src), np.zeros((4, 3 if d == 2 else 6)))
+    full = oracle_mod.compact_velocity(d, np.ones(3, dtype=np.int32), u(src), S(src))
+    assert np.abs(full - u(0.25 * s)[0]).max() < 1e-12
+    assert np.abs(full - base).max() > 1e-3
+
+
+def exact_level_fields(mesh, ufun, Sfun, level):
+    """Exact (rho=1, u, S) on a uniform mesh at the given level; S in that
+    level's lattice units."""
+    fac = 1 << (level - mesh.lmin)
+    um = W.uniform(mesh.d, level, tuple(e * fac for e in mesh.extent), mesh.bc)
+    x = um.centres() / fac
+    return um, ufun(x), Sfun(x) / fac
+
+
+@pytest.mark.parametrize("d,mode", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_ghost_fill_exact_on_quadratic_field(oracle_mod, d, mode):
+    """Sec. 2.2 steps 1-5 on a two-level mesh: with a quadratic velocity, linear
+    strain rate and constant density on both levels, every GhostFromCoarser and
+    GhostFromFiner element holds exactly the pdfs an element of its own level
+    would be initialised with from the exact field at its centre.  This pins the
+    source choice and octant signs, the f^neq rescale with the factor 1/m, the
+    quadratic GFF velocity and f = f^eq + (1-omega) f^neq."""
+    Q = 9 if d == 2 else 19
+    n = 16 if d == 2 else 8
+    mesh = W.two_level_block(d, n, n // 4, 3 * n // 4)
+    rng = np.random.default_rng(5)
+    u, S, _ = quadratic_field(d, rng, scale=1e-3)
+    ufun = lambda x: u(x / n)
+    Sfun = lambda x: S(x / n) / n
+    x = mesh.centres()
+    lvl_scale = np.ldexp(1.0, -(mesh.levels.astype(np.int64) - mesh.lmin))
+    o = oracle_mod.Oracle(mesh, Q, 1.6, time_mode=mode)
+    o.init(np.ones(mesh.n), ufun(x), Sfun(x) * lvl_scale[:, None])
+    o.fill_ghosts()
+    info, fg = o.ghosts()
+    assert len(info) > 0
+    ref = {}
+    for li, L in enumerate((mesh.lmin, mesh.lmin + 1)):
+        um, uu, SS = exact_level_fields(mesh, ufun, Sfun, L)
+        r = oracle_mod.Oracle(um, Q, o.level_omega(li))
+        r.init(np.ones(um.n), uu, SS)
+        ref[L] = (r.get_f(), {tuple(c): i for i, c in enumerate(um.coords)})
+    kinds = set()
+    for k in range(len(info)):
+        L, kind = int(info[k, 0]), int(info[k, 1])
+        fr, lut = ref[L]
+        j = lut[tuple(int(v) for v in info[k, 3:3 + d])]
+        assert np.abs(fg[k] - fr[j]).max() < 1e-12, (L, kind, info[k])
+        kinds.add(kind)
+    assert kinds == {1, 2}
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("d,mode", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_uniform_state_is_stationary(oracle_mod, d, mode):
+    """A constant (rho0, u) equilibrium is a fixed point of the whole multilevel
+    step: stream, collide, both ghost fills and the time interpolation."""
+    Q = 9 if d == 2 else 19
+    n = 16 if d == 2 else 8
+    mesh = W.two_level_block(d, n, n // 4, 3 * n // 4)
+    U = (0.03, -0.02, 0.01)[:d]
+    rho, u, S = W.uniform_fields(mesh, 1.0, U)
+    o = oracle_mod.Oracle(mesh, Q, 1.6, time_mode=mode)
+    o.init(rho, u, S)
+    o.step(10)
+    r1, u1, S1 = o.moments()
+    assert np.abs(r1 - 1).max() < 1e-13
+    assert np.abs(u1 - u).max() < 1e-14
+    assert np.abs(S1).max() < 1e-14
+
+
+def test_single_level_conservation(oracle_mod):
+    """Periodic single-level BGK conserves mass and momentum exactly (up to
+    round-off) over 200 steps, with the seeded pdf perturbation."""
+    mesh = W.uniform(2, 5, (32, 32), (0,) * 4)
+    rho, u, S = W.tgv_fields(mesh, 0.02)
+    o = oracle_mod.Oracle(mesh, 9, 1.6)
+    o.init(rho, u, S, W.pdf_perturbation(mesh, 9, 1e-6))
+    m0 = o.reduce()
+    o.step(200)
+    m1 = o.reduce()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-12
+    assert np.abs(m1[1:3] - m0[1:3]).max() / m0[0] < 1e-12
+
+
+def test_user_order_does_not_matter(oracle_mod):
+    """The element order handed in is arbitrary: a shuffled mesh gives the same
+    per-element result."""
+    mesh = W.config_tgv2d()
+    sh = W.shuffled(mesh)
+    out = []
+    for m in (mesh, sh):
+        o = oracle_mod.Oracle(m, 9, 1.6)
+        rho, u, S = W.tgv_fields(m, 0.01)
+        o.init(rho, u, S)
+        o.step(5)
+        r, uu, _ = o.moments()
+        key = np.argsort(m.tree_ids)
+        out.append((r[key], uu[key]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+# ---------------------------------------------------------------- closed-form flows
+def test_tgv_config1_decay(oracle_mod):
+    """Sec. 4.1 Eq. (tgv): on the two-level 32x32 / 16x16-block mesh with
+    u0=0.01, omega_c=1.6 (nu_c=1/24), the velocity amplitude after 200 coarse
+    steps follows exp(-2 nu k^2 t) with k = 2 pi / 32 (about 0.526)."""
+    mesh = W.config_tgv2d()
+    nu = (1 / 1.6 - 0.5) / 3
+    k = 2 * math.pi / 32
+    vol = np.ldexp(1.0, -2 * (mesh.levels.astype(np.int64) - mesh.lmin))
+    for mode in (0, 1):
+        o = oracle_mod.Oracle(mesh, 9, 1.6, time_mode=mode)
+        assert abs(o.level_omega(1) - 4.0 / 3.0) < 1e-15   # Eq. (fneq_scale)
+        rho, u, S = W.tgv_fields(mesh, 0.01)
+        o.init(rho, u, S)
+        o.step(200)
+        _, u1, _ = o.moments()
+        amp = math.sqrt((vol[:, None] * u1 ** 2).sum() / (vol[:, None] * u ** 2).sum())
+        assert abs(amp / math.exp(-2 * nu * k * k * 200) - 1) < 1e-3
+
+
+def tgv_errors(oracle_mod, N, mode, u0_16=0.0025, omega=1.6):
+    mesh = W.half_refined_2d(N)
+    nu = (1 / omega - 0.5) / 3
+    k = 2 * math.pi / N
+    steps = int(round(0.25 / (2 * nu * k * k)))
+    u0 = u0_16 * 16 / N  # diffusive scaling: Ma -> 0 with the mesh
+    o = oracle_mod.Oracle(mesh, 9, omega, time_mode=mode)
+    rho, u, S = W.tgv_fields(mesh, u0)
+    o.init(rho, u, S)
+    o.step(steps)
+    _, u1, S1 = o.moments()
+    _, ua, Sa = W.tgv_fields(mesh, u0, t=steps, nu=nu)
+    sc = np.ldexp(1.0, mesh.levels.astype(np.int64) - mesh.lmin)  # S to coarse units
+    eu = math.sqrt(((u1[:, 0] - ua[:, 0]) ** 2).sum() / (ua[:, 0] ** 2).sum())
+    eS = math.sqrt((((S1[:, 0] - Sa[:, 0]) * sc) ** 2).sum() / ((Sa[:, 0] * sc) ** 2).sum())
+    return eu, eS
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tgv_second_order_convergence(oracle_mod, mode):
+    """Sec. 4.1, Fig. tgv_conv: with the left half at level L and the right half
+    one level finer, the l2 errors of u_x and S_xx (Eq. error norm) converge at
+    second order.  Diffusive scaling (u0 ~ dx, omega fixed) so the Ma^2 error
+    converges too; errors at t = t_D/4."""
+    errs = [tgv_errors(oracle_mod, N, mode) for N in (16, 32, 64)]
+    for a, b in zip(errs[:-1], errs[1:]):
+        su = math.log2(a[0] / b[0])
+        sS = math.log2(a[1] / b[1])
+        assert 1.8 < su < 2.8, (mode, errs)
+        assert 1.8 < sS < 2.8, (mode, errs)
+
+
+def test_poiseuille_exact_at_magic_relaxation(oracle_mod):
+    """Half-way bounce-back walls with Guo body forcing: for BGK with
+    (1/omega - 1/2)^2 = 3/16 the steady Poiseuille profile is the exact parabola
+    u(y) = F y (H - y) / (2 nu) with the walls half way between nodes."""
+    H = 8
+    mesh = W.uniform(2, 3, (4, H), (W.BC_PERIODIC, W.BC_PERIODIC, W.BC_WALL, W.BC_WALL))
+    tau = 0.5 + math.sqrt(3.0 / 16.0)
+    omega = 1.0 / tau
+    nu = (tau - 0.5) / 3
+    F = 1e-6
+    o = oracle_mod.Oracle(mesh, 9, omega, use_force=True)
+    rho, u, S = W.uniform_fields(mesh)
+    o.init(rho, u, S)
+    force = np.zeros((mesh.n, 2))
+    force[:, 0] = F
+    o.set_force(force)
+    o.step(6000)
+    _, u1, _ = o.moments()
+    y = mesh.centres()[:, 1]
+    exact = F * y * (H - y) / (2 * nu)
+    assert np.abs(u1[:, 0] - exact).max() / exact.max() < 1e-9
+    assert np.abs(u1[:, 1]).max() < 1e-15
+
+
+def test_couette_moving_wall(oracle_mod):
+    """Sec. 2.3 velocity bounce-back (Ladd) on a face moving tangentially with U
+    over a resting half-way wall: the steady profile is exactly linear."""
+    H = 8
+    U = 0.02
+    mesh = W.uniform(2, 3, (4, H), (W.BC_PERIODIC, W.BC_PERIODIC, W.BC_WALL, W.BC_VELOCITY_IN))
+    o = oracle_mod.Oracle(mesh, 9, 1.4, u_in=(U, 0.0, 0.0))
+    rho, u, S = W.uniform_fields(mesh)
+    o.init(rho, u, S)
+    o.step(4000)
+    r1, u1, _ = o.moments()
+    y = mesh.centres()[:, 1]
+    assert np.abs(u1[:, 0] - U * y / H).max() < 1e-10
+    assert np.abs(r1 - 1).max() < 1e-10
+
+
+def test_uniform_inflow_is_stationary(oracle_mod):
+    """Velocity inlet at x-, pressure outlet at x+: the uniform state
+    (rho0, U) is a fixed point of both boundary rules (a sign slip in the
+    inlet term or in the outlet correction breaks it)."""
+    U = 0.05
+    mesh = W.uniform(2, 4, (16, 8), (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_PERIODIC, W.BC_PERIODIC))
+    o = oracle_mod.Oracle(mesh, 9, 1.5, u_in=(U, 0.0, 0.0))
+    rho, u, S = W.uniform_fields(mesh, 1.0, (U, 0.0))
+    o.init(rho, u, S)
+    o.step(50)
+    r1, u1, _ = o.moments()
+    assert np.abs(r1 - 1).max() < 1e-14
+    assert np.abs(u1 - u).max() < 1e-14
+
+
+def test_obstacle_force_balances_body_force(oracle_mod):
+    """Sec. 2.3 momentum exchange: in a periodic box driven by a uniform body
+    force, the steady drag on a bounce-back obstacle equals the total body
+    force (momentum balance)."""
+    N = 16
+    def solid(L, cen):
+        return (np.abs(cen[:, 0] - 8) < 2.5) & (np.abs(cen[:, 1] - 8) < 2.5)
+    mesh = W.uniform(2, 4, (N, N), (0,) * 4, solid=solid)
+    F = 1e-6
+    o = oracle_mod.Oracle(mesh, 9, 1.2, use_force=True)
+    rho, u, S = W.uniform_fields(mesh)
+    o.init(rho, u, S)
+    force = np.zeros((mesh.n, 2))
+    force[:, 0] = F
+    o.set_force(force)
+    o.step(8000)
+    red = o.reduce()
+    total = F * mesh.n
+    assert abs(red[4] - total) / total < 1e-8
+    assert abs(red[5]) < 1e-12
+
+
+def test_tgv3d_decay_two_level(oracle_mod):
+    """3D two-level Taylor-Green (extruded in z) on a small 16^3 / 8^3 mesh
+    decays like exp(-2 nu k^2 t)."""
+    mesh = W.config_tgv3d(16)
+    nu = (1 / 1.6 - 0.5) / 3
+    k = 2 * math.pi / 16
+    vol = np.ldexp(1.0, -3 * (mesh.levels.astype(np.int64) - mesh.lmin))
+    o = oracle_mod.Oracle(mesh, 19, 1.6)
+    rho, u, S = W.tgv_fields(mesh, 0.01)
+    o.init(rho, u, S)
+    o.step(40)
+    _, u1, _ = o.moments()
+    amp = math.sqrt((vol[:, None] * u1 ** 2).sum() / (vol[:, None] * u ** 2).sum())
+    assert abs(amp / math.exp(-2 * nu * k * k * 40) - 1) < 3e-3
+
+
+# ---------------------------------------------------------------- dual numbers
+def test_dual_tangent_matches_central_differences(oracle_mod):
+    """The dual-number oracle's tangent of the kinetic energy along a random
+    direction in (body force, omega_c) equals a central finite difference of
+    the plain oracle."""
+    mesh = W.two_level_block(2, 8, 2, 6)
+    rng_dir = W.random_direction((mesh.n, 2), W.SEED, 7)
+    F0 = W.gaussian_force(mesh, 1e-5)
+    om, om_dot = 1.6, 0.3
+    rho, u, S = W.tgv_fields(mesh, 0.02)
+
+    def J(h):
+        o = oracle_mod.Oracle(mesh, 9, om + h * om_dot, use_force=True)
+        o.init(rho, u, S)
+        o.set_force(F0 + h * 1e-5 * rng_dir)
+        o.step(6)
+        return o.reduce()[7]
+
+    h = 1e-4
+    fd = (J(h) - J(-h)) / (2 * h)
+    od = oracle_mod.Oracle(mesh, 9, om, use_force=True, dual=True, omega_dot=om_dot)
+    od.init(rho, u, S)
+    od.set_force(F0, 1e-5 * rng_dir)
+    od.step(6)
+    val, dot = od.reduce()
+    assert abs(val[7] - J(0.0)) < 1e-18
+    assert abs(dot[7] - fd) / abs(fd) < 1e-6
+
+
+# ---------------------------------------------------------------- mesh checks
+def _raises(oracle_mod, mesh, Q=9, match=None):
+    with pytest.raises(oracle_mod.OracleError, match=match):
+        oracle_mod.Oracle(mesh, Q, 1.6)
+
+
+def test_mesh_validation(oracle_mod):
+    good = W.config_tgv2d()
+    # duplicate treeID
+    dup = W.Mesh(good.d, good.extent, good.bc, np.concatenate([good.tree_ids, good.tree_ids[:1]]),
+                 np.concatenate([good.levels, good.levels[:1]]), np.concatenate([good.coords, good.coords[:1]]),
+                 good.lmin)
+    _raises(oracle_mod, dup, match="duplicate")
+    # a coarse element overlapping its own children
+    fine = good.levels > good.lmin
+    parent = good.coords[fine][0] // 2
+    ov = W.Mesh(good.d, good.extent, good.bc,
+                np.concatenate([good.tree_ids, W.tree_ids(parent[None], good.lmin, 2)]),
+                np.concatenate([good.levels, [good.lmin]]).astype(np.int8),
+                np.concatenate([good.coords, parent[None]]), good.lmin)
+    _raises(oracle_mod, ov, match="overlapping")
+    # a level jump of two (2:1 violation) has no valid ghost layer
+    jump = W.nested_boxes(2, 5, (32, 32), [((16, 16), (48, 48)), ((48, 48), (80, 80))], (0,) * 4)
+    _raises(oracle_mod, jump)
+    # treeIDs beyond the box
+    far = W.Mesh(2, (4, 4), (0,) * 4, W.tree_ids(np.array([[5, 5]]), 3, 2), np.array([3], np.int8),
+                 np.array([[5, 5]]), 3)
+    _raises(oracle_mod, far)
