@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the multilevel D3Q19 lattice Boltzmann hot path on GB300.
+
+Default workload: the sphere flow at Re = 100 (box 32D x 16D x 16D, sphere
+D = 64 finest elements, five levels D/4 .. D/64, about 8.6e7 fluid elements,
+velocity inlet / pressure outlet), FP32-deviation storage.  A "step" is one
+coarse time step of the whole hierarchy (31 stream-collide launches plus the
+ghost fills).  The metric is fine-substep weighted MLUPS,
+U = sum_L N_L 2^{L - Lmin} element updates per coarse step.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 (launched by torch.distributed.run): independent replicas, one per GPU
+(the method is not sharded here), value = total updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "multilevel D3Q19 MLUPS & % HBM peak, FP32-dev vs FP64 at stated error"
+SMI_FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "tgv3d"])
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP64/BF16 and TGV side measurements")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- workloads
+def make_workload(name):
+    from paper_1601_06984_gb300 import workloads as W
+    if name == "sphere":
+        mesh = W.config_sphere(1)
+        U = 0.04
+        om_f = W.omega_for_re(U, 64, 100.0)
+        om_c = W.omega_coarse_from_finest(om_f, 5)
+        desc = {"workload": "sphere_re100_d3q19_5level", "box": "32D x 16D x 16D", "D_finest": 64,
+                "levels": 5, "u_in": U, "omega_finest": round(om_f, 6), "omega_coarsest": round(om_c, 6),
+                "boundaries": "velocity inlet x-, pressure outlet x+, periodic y/z, half-way bounce-back sphere"}
+        fields = lambda m: W.uniform_fields(m, 1.0, (U, 0.0, 0.0))
+        return mesh, 19, om_c, (U, 0.0, 0.0), fields, desc
+    mesh = W.config_tgv3d(64)
+    desc = {"workload": "tgv3d_two_level_64", "box": "64^3 periodic, 32^3 block refined", "levels": 2,
+            "u0": 0.01, "omega_coarse": 1.6}
+    fields = lambda m: W.tgv_fields(m, 0.01)
+    return mesh, 19, 1.6, (0.0, 0.0, 0.0), fields, desc
+
+
+def small_sample():
+    """Bounded sample of the sphere workload for the CPU oracle: the reduced
+    three-level sphere case (about 1.75e4 elements)."""
+    from paper_1601_06984_gb300 import workloads as W
+    m = W.config_sphere_small()
+    om = W.omega_coarse_from_finest(W.omega_for_re(0.04, 64, 100.0), 3)
+    return m, om, (0.04, 0.0, 0.0)
+
+
+def bytes_per_update(Q, prec):
+    s = {0: 8, 1: 4, 2: 2}[prec]
+    return 2 * Q * s + 4 * (Q - 1)
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, uuid=None, index=0):
+        self.uuid, self.index = uuid, index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={SMI_FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                r = [x.strip() for x in line.split(",")]
+                if len(r) < 10:
+                    continue
+                if self.uuid and self.uuid not in r[1]:
+                    continue
+                if not self.uuid and r[0] != str(self.index):
+                    continue
+                rows.append(r)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        pw = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def gpu_uuid(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle(seconds, min_steps=2):
+    """Time the CPU oracle (single thread) on the bounded sample."""
+    from oracle.oracle import Oracle
+    from paper_1601_06984_gb300 import workloads as W
+    m, om, uin = small_sample()
+    o = Oracle(m, 19, om, u_in=uin)
+    o.init(*W.uniform_fields(m, 1.0, uin))
+    o.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < seconds:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    U = m.updates_per_coarse_step()
+    return {"value": steps * U / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"reduced 3-level D3Q19 sphere ({m.n} elements, {U} updates/coarse step), "
+                      f"{steps} coarse steps, single-threaded FP64 oracle",
+            "seconds": round(dt, 2), "ms_per_step": 1e3 * dt / steps}
+
+
+# ---------------------------------------------------------------- GPU runs
+def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_moments=False):
+    import torch
+
+    from paper_1601_06984_gb300 import lbm
+    U = mesh.updates_per_coarse_step()
+    t_build = time.perf_counter()
+    sim = lbm.Sim(mesh, Q, om, precision=prec, u_in=uin, device=device)
+    t_build = time.perf_counter() - t_build
+    rho, u, S = fields(mesh)
+    sim.init(rho, u, S)
+    sim.step(W_)
+    info = sim.mesh_info()
+    stream = sim.stream
+    torch.cuda.synchronize(device)
+    sim.timing_enable(True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    n0 = sim.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(K)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.kernel_launches() - n0
+    nl, kms = sim.timing_read()
+    if dist is not None:
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    finest = len(info) - 1
+    units = int(info[finest, 1])  # fluid updates per finest launch
+    avg_ms = kms[finest] / max(nl[finest], 1)
+    bpu = bytes_per_update(Q, prec)
+    res = {"ms_total": ms, "ms_per_step": ms / K, "mlups": K * U / (ms * 1e-3) / 1e6, "launches": launches,
+           "finest_launch_ms": avg_ms, "finest_launches": int(nl[finest]), "finest_units": units,
+           "finest_bytes": units * bpu, "finest_gbs": units * bpu / (avg_ms * 1e-3) / 1e9,
+           "level_ms": [float(x) for x in kms], "level_launches": [int(x) for x in nl],
+           "bytes_per_update": bpu, "build_s": t_build, "device_gb": sim.device_bytes() / 1e9,
+           "reduce": sim.reduce().tolist()}
+    if want_moments:
+        res["moments"] = sim.moments()
+    return sim, res
+
+
+def e2e_run(sim, mesh, fields, K):
+    """End to end through the C ABI: initial fields from pinned host memory,
+    then K coarse steps each followed by the FP64 reduction (mass, momentum,
+    drag, kinetic energy) read back to the host."""
+    import torch
+    rho, u, _ = fields(mesh)
+    rho_p = torch.from_numpy(rho).pin_memory()
+    u_p = torch.from_numpy(u).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.init(rho_p.numpy(), u_p.numpy())
+    n0 = sim.kernel_launches()
+    for _ in range(K):
+        sim.step(1)
+        sim.reduce()
+    dt = time.perf_counter() - t0
+    U = mesh.updates_per_coarse_step()
+    return {"value": K * U / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": int((rho_p.numel() + u_p.numel()) * 8 / K), "d2h_bytes_per_step": 64,
+            "seconds": round(dt, 3), "launches": sim.kernel_launches() - n0}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    K, W_ = args.steps, args.warmup
+    assert W_ >= 3, "at least 3 warm-up steps"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_oracle(max(5.0, min(args.cpu_seconds, 20.0)), min_steps=K)
+        desc = {"workload": "sphere_re100_d3q19_5level" if args.workload == "sphere" else "tgv3d_two_level_64"}
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": K, "warmup": W_, "ms_per_step": cb["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": dict(desc, sample="bounded: reduced 3-level D3Q19 sphere run by the CPU oracle"),
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1601_06984_gb300 import lbm
+
+    mesh, Q, om, uin, fields, desc = make_workload(args.workload)
+    U = mesh.updates_per_coarse_step()
+    peak, peak_src = measured_peaks()
+
+    clk = Clocks(uuid=gpu_uuid(device), index=local)
+    sim, r = run_gpu(mesh, Q, om, uin, fields, lbm.FP32DEV, K, W_, device, dist,
+                     want_moments=not args.no_variants)
+    clocks = clk.stop()
+    e2e = e2e_run(sim, mesh, fields, K)
+    if dist is not None:
+        t = torch.tensor([e2e["seconds"]], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e["value"] = world * K * U / float(t.item()) / 1e6
+    mom32 = r.pop("moments", None)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    variants, errors, tgv = {}, {}, None
+    if not args.no_variants and rank == 0 and world == 1:
+        mom = {}
+        for name, prec in (("fp64", lbm.FP64), ("bf16dev", lbm.BF16DEV)):
+            s2, r2 = run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, None, want_moments=True)
+            mom[name] = r2.pop("moments")
+            variants[name] = {"mlups": r2["mlups"], "ms_per_step": r2["ms_per_step"],
+                              "finest_kernel_gbs": r2["finest_gbs"], "finest_kernel_frac": r2["finest_gbs"] / peak,
+                              "bytes_per_update": r2["bytes_per_update"], "device_gb": r2["device_gb"],
+                              "reduce": r2["reduce"]}
+            s2.close()
+            del s2
+            torch.cuda.empty_cache()
+        ref_u = mom["fp64"][1]
+        ref_red = variants["fp64"]["reduce"]
+        for name, m_ in (("fp32dev", mom32), ("bf16dev", mom["bf16dev"])):
+            if m_ is None:
+                continue
+            du = m_[1] - ref_u
+            red = r["reduce"] if name == "fp32dev" else variants["bf16dev"]["reduce"]
+            errors[name] = {
+                "u_l2_rel_vs_fp64": float(math.sqrt((du ** 2).sum() / (ref_u ** 2).sum())),
+                "u_max_abs_vs_fp64": float(np.abs(du).max()),
+                "drag_rel_vs_fp64": float(abs(red[4] - ref_red[4]) / abs(ref_red[4])) if ref_red[4] else None,
+                "after_coarse_steps": W_ + K}
+        del mom
+        # secondary: the 64^3 / 32^3 two-level Taylor-Green (working set fits in L2)
+        from paper_1601_06984_gb300 import workloads as Wk
+        tm, tQ, tom, tuin, tfields, tdesc = make_workload("tgv3d")
+        tgv = {"config": tdesc, "note": "working set (~0.13 GB) fits in the 129 MB L2 plus HBM; L2 not flushed"}
+        for name, prec in (("fp32dev", lbm.FP32DEV), ("fp64", lbm.FP64)):
+            st, rt = run_gpu(tm, tQ, tom, tuin, tfields, prec, 50, 3, device, None, want_moments=True)
+            _, ut, _ = rt.pop("moments")
+            nu = (1 / 1.6 - 0.5) / 3
+            _, ua, _ = Wk.tgv_fields(tm, 0.01, t=53, nu=nu)
+            tgv[name] = {"mlups": rt["mlups"], "ms_per_step": rt["ms_per_step"],
+                         "u_l2_rel_vs_closed_form": float(math.sqrt(((ut - ua) ** 2).sum() / (ua ** 2).sum()))}
+            st.close()
+            del st
+            torch.cuda.empty_cache()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cb = cpu_oracle(args.cpu_seconds) if world == 1 else None
+    value = world * r["mlups"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W_,
+        "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": dict(desc, elements=mesh.n, updates_per_coarse_step=U, storage="fp32 deviation g=f-w*rho0",
+                       time_mode="linear", parallelism="replicas" if world > 1 else "single GPU",
+                       l2="inputs larger than L2 (%.1f GB workspace)" % r["device_gb"]),
+        "roofline": {"bound": "hbm", "achieved": r["finest_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": r["finest_gbs"] / peak, "traffic": None,
+                     "kernel": "k_stream_collide<19,float> on the finest level",
+                     "units_per_launch": r["finest_units"], "bytes_per_unit": r["bytes_per_update"],
+                     "avg_launch_ms": r["finest_launch_ms"], "peak_source": peak_src},
+        "step_gbs_algorithmic": U * r["bytes_per_update"] / (r["ms_per_step"] * 1e-3) / 1e9,
+        "cpu_baseline": cb if cb is None else {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
+        "gpu_launches": r["launches"], "clocks": clocks,
+        "level_stream_collide_ms": r["level_ms"], "level_stream_collide_launches": r["level_launches"],
+        "drag_force_fp32dev": r["reduce"][4],
+    }
+    if variants:
+        line["variants"] = variants
+        line["error_vs_fp64"] = errors
+    if tgv:
+        line["tgv3d"] = tgv
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

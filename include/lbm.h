@@ -1,0 +1,195 @@
+/*
+ * lbm.h -- C ABI of the GB300 multilevel octree lattice Boltzmann library.
+ *
+ * The library runs the data-parallel hot path of the method of Qi, Klimach &
+ * Roller, "Implementation of the compact interpolation within the octree based
+ * Lattice Boltzmann solver Musubi" (arXiv:1601.06984): per-level pull
+ * stream + BGK collide over level-wise, space-filling-curve ordered element
+ * arrays (D2Q9 / D3Q19), ghost filling between levels by compact interpolation
+ * (GhostFromCoarser) and by restriction from the children (GhostFromFiner), and
+ * the recursive level time stepping with two fine substeps per coarse step.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an lbm_status; on error lbm_last_error() gives a
+ *    one-line message.  No exception crosses the ABI.  After LBM_ERR_ARG,
+ *    LBM_ERR_MESH or LBM_ERR_STATE the context stays usable; after
+ *    LBM_ERR_CUDA it must be destroyed.
+ *  - Host arrays passed in are borrowed for the duration of the call and
+ *    copied; host arrays passed out are written before the call returns.
+ *  - Element order at the boundary is always the caller's order of the
+ *    treeIDs given to lbm_build_mesh.  The internal order (per level,
+ *    z-curve sorted, ghosts appended) is hidden.
+ *  - Device memory is owned by the caller: lbm_device_bytes() says how much,
+ *    the caller allocates it (e.g. with PyTorch) and hands it to lbm_bind()
+ *    together with the CUDA stream every kernel is enqueued on.  The library
+ *    never allocates or frees device memory itself.
+ *  - Calls that produce host results synchronise the bound stream; lbm_step,
+ *    lbm_fill_ghosts and lbm_set_force return once their work is enqueued.
+ *  - Units: lattice units of each element's own level (dx_L = 1, dt_L = 1);
+ *    positions, volumes and forces in reductions as stated per function.
+ *  - Direction order of per-direction arrays:
+ *      D2Q9 : 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 (+x+y), 6 (-x-y), 7 (+x-y), 8 (-x+y)
+ *      D3Q19: 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z, 7 (+x+y), 8 (-x-y),
+ *             9 (+x-y), 10 (-x+y), 11 (+x+z), 12 (-x-z), 13 (+x-z), 14 (-x+z),
+ *             15 (+y+z), 16 (-y-z), 17 (+y-z), 18 (-y+z)
+ *    Strain-rate components: 2D xx, yy, xy; 3D xx, yy, zz, xy, yz, xz.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; created by lbm_build_mesh, freed by lbm_destroy */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,      /* bad argument (null pointer, out-of-range value)        */
+  LBM_ERR_MESH = -2,     /* mesh rejected (see lbm_last_error for the rule broken) */
+  LBM_ERR_CUDA = -3,     /* a CUDA runtime call failed                             */
+  LBM_ERR_OOM = -4,      /* host allocation failed                                 */
+  LBM_ERR_STATE = -5,    /* wrong call order (e.g. lbm_step before lbm_bind)       */
+  LBM_ERR_NUMERIC = -6,  /* non-finite mass found by the optional mass check       */
+  LBM_ERR_INTERNAL = -7
+} lbm_status;
+
+enum { LBM_FP64 = 0, LBM_FP32DEV = 1, LBM_BF16DEV = 2 };
+enum { LBM_TIME_LINEAR = 0, LBM_TIME_TWO_LAYER = 1 };
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_VELOCITY_IN = 2, LBM_BC_PRESSURE_OUT = 3 };
+
+/* Simulation parameters.
+ *  stencil       9 (D2Q9) or 19 (D3Q19); Sec. 2.1.
+ *  precision     LBM_FP64: pdfs stored and computed in double.
+ *                LBM_FP32DEV: each pdf stored as float deviation g_i = f_i - w_i rho0,
+ *                             arithmetic in float.
+ *                LBM_BF16DEV: same deviation stored as bfloat16, arithmetic in float.
+ *  time_mode     LBM_TIME_LINEAR: fine ghosts refilled before the second fine substep
+ *                from the mean of the coarse source moments at t and t+1.
+ *                LBM_TIME_TWO_LAYER: two fine ghost layers filled at the synchronous
+ *                step and advanced by the fine kernel (Sec. 2.2, last paragraph).
+ *  extent        domain box in elements of the coarsest level present (unused axes 1).
+ *  bc            per face x-, x+, y-, y+, z-, z+; PERIODIC must be set on both faces of
+ *                an axis.  WALL = half-way bounce-back, VELOCITY_IN = velocity
+ *                bounce-back with u_in, PRESSURE_OUT = extrapolation outlet with the
+ *                normal pdf pressure-corrected to rho0 (Sec. 2.3).
+ *  omega_coarse  BGK relaxation rate on the coarsest level, in (0,2); finer levels
+ *                follow 1/omega_f - 1/2 = 2 (1/omega_c - 1/2) (Sec. 2.2, Eq. fneq_scale).
+ *  rho0          reference density (outlet density, deviation offset).
+ *  u_in          inlet velocity (lattice units).
+ *  use_force     nonzero: a per-element body force (Guo forcing) is applied. */
+typedef struct {
+  int32_t stencil;
+  int32_t precision;
+  int32_t time_mode;
+  int32_t extent[3];
+  int32_t bc[6];
+  double omega_coarse;
+  double rho0;
+  double u_in[3];
+  int32_t use_force;
+  int32_t reserved;
+} lbm_params;
+
+/* Build the multilevel mesh on the host (no device work).
+ * Sec. 3.1: every element is a treeID (int64): level L holds ids
+ * off(L) .. off(L+1)-1 with off(L) = (2^{dL}-1)/(2^d-1), the remainder being the
+ * z-curve (Morton) index at that level, x bit lowest.  levels[k] must equal the
+ * level encoded in tree_ids[k].  Boxes not covered by any element inside the
+ * domain are solid (half-way bounce-back; their links count toward the
+ * obstacle force).  Level interfaces may differ by one level only (Sec. 2.2) and
+ * must leave room for the ghost layers; violations return LBM_ERR_MESH.
+ * Sec. 3.2: per level the elements are stored as GhostFromCoarser | fluid |
+ * GhostFromFiner (inner) | GhostFromFiner (outer), each z-curve sorted.
+ * On success *out owns a new context. */
+lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t n,
+                          const lbm_params* params, lbm_ctx** out);
+
+/* Per level, 8 int64 each: level, fluid, GFC, GFF inner, GFF outer, padded
+ * element count, outlet links, obstacle links.  cap = rows available in info. */
+lbm_status lbm_mesh_info(const lbm_ctx* ctx, int64_t* info, int32_t cap, int32_t* nlevels);
+
+/* Bytes of the single device workspace the caller must allocate (256-byte
+ * aligned start) before lbm_bind. */
+lbm_status lbm_device_bytes(const lbm_ctx* ctx, uint64_t* bytes);
+
+/* Bind the device workspace and CUDA stream (cudaStream_t passed as void*; NULL =
+ * legacy default stream) and upload the static mesh tables.  The workspace
+ * must stay allocated until lbm_destroy.  All pdfs start at rest equilibrium
+ * w_i rho0. */
+lbm_status lbm_bind(lbm_ctx* ctx, void* device_workspace, uint64_t bytes, void* stream);
+
+/* Initial state from macroscopic fields (Sec. 4.1):
+ *   f*_i = f^eq_i(rho, u) + (1 - omega_L) f^neq_i + df_i,
+ *   f^neq_i = -(w_i rho / (c_s^2 omega_L)) (c_i c_i - c_s^2 I) : S,
+ * stored as the post-collision state at t = 0.  rho[n], u[n][d], S[n][nS] (level
+ * lattice units; may be NULL for S = 0), df[n][Q] (may be NULL).  Host
+ * arrays, caller order.  Ghost elements are filled on the next step. */
+lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const double* S,
+                    const double* df);
+
+/* Body force F[n][d] per fluid element (level lattice units), Guo forcing.
+ * Requires params.use_force. */
+lbm_status lbm_set_force(lbm_ctx* ctx, const double* F);
+
+/* Advance n_coarse coarse time steps (Sec. 2.2 recursive level stepping:
+ * GhostFromFiner, then GhostFromCoarser, then stream+collide on the level, then
+ * two substeps of the next finer level). */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n_coarse);
+
+/* Fill every ghost element from the current state (the synchronous-time part
+ * of a step without stream/collide), coarsest interface first. */
+lbm_status lbm_fill_ghosts(lbm_ctx* ctx);
+
+/* Macroscopic fields of every element from the stored post-collision state:
+ * rho = sum f*, rho u = sum c f* - F/2, S_ab = -(3 omega / 2 rho) sum c_a c_b f^neq
+ * (Sec. 2.1) with f^neq = (f* - f^eq - F_i)/(1 - omega).  rho[n], u[n][d],
+ * S[n][nS]; any may be NULL.  Caller order, level lattice units. */
+lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* S);
+
+/* FP64 reductions over fluid elements, deterministic order:
+ * out[0] mass sum rho vol, out[1..3] momentum sum rho u vol, out[4..6] force on
+ * solid obstacles by momentum exchange (Sec. 2.3, half-way bounce-back: each
+ * link carries 2 c f*), in finest-level lattice units, out[7] kinetic energy
+ * sum rho |u|^2 vol / 2; vol = 2^{-d (L - Lmin)}. */
+lbm_status lbm_reduce(lbm_ctx* ctx, double out[8]);
+
+/* Post-collision pdfs f*[n][Q] of the fluid elements as FP64 (deviation storage
+ * converted back to f), caller order. */
+lbm_status lbm_get_state(lbm_ctx* ctx, double* f);
+
+/* Ghost elements: count, then info[n][6] (level, kind 1=GFC 2=GFF, layer, x, y, z
+ * at the element's level) and f[n][Q] (FP64) of the current state. */
+lbm_status lbm_ghost_count(const lbm_ctx* ctx, int64_t* n);
+lbm_status lbm_get_ghosts(lbm_ctx* ctx, int64_t* info, double* f);
+
+/* Host utility, Sec. 3.1 (weight based domain decomposition): z-curve order of
+ * the elements, workload weights w = 2^{L - Lmin} (Eq. weight), cumulative
+ * weights W, and the part of each sorted element when W is split into nparts
+ * equal shares.  order[n] (indices into tree_ids), weights[n], cumulative[n],
+ * part[n] in sorted order; any output may be NULL. */
+lbm_status lbm_sfc_partition(const int64_t* tree_ids, int64_t n, int32_t d, int32_t nparts,
+                             int64_t* order, int64_t* weights, int64_t* cumulative,
+                             int32_t* part);
+
+/* Launches of library kernels enqueued by this context since it was bound. */
+lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
+
+/* Device timing of the stream-collide kernel: while enabled, every
+ * stream-collide launch is bracketed by CUDA events recorded on the bound
+ * stream.  lbm_timing_read synchronises the stream and returns, per level
+ * (rows 0..cap-1, coarsest first), the number of timed launches and their
+ * summed device time in milliseconds, then clears the record.  Enabling
+ * clears it too. */
+lbm_status lbm_timing_enable(lbm_ctx* ctx, int32_t on);
+lbm_status lbm_timing_read(lbm_ctx* ctx, int64_t* launches, double* ms, int32_t cap);
+
+const char* lbm_last_error(const lbm_ctx* ctx);
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

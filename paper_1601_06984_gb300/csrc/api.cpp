@@ -1,0 +1,673 @@
+// C ABI of liblbm (include/lbm.h): context, device workspace layout, the
+// recursive level time stepping driver (Sec. 2.2) and the host<->device
+// transfers of the public calls.
+#include <cuda_runtime_api.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// device lattice weights and velocities for the inlet term (lbm.h order)
+void lattice_host(int Q, int c[19][3], double w[19]) {
+  static const int c9[9][3] = {{0, 0, 0}, {1, 0, 0},  {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                               {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+  static const int c19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                 {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                 {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                 {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+  for (int i = 0; i < Q; ++i) {
+    int n2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      c[i][a] = Q == 9 ? c9[i][a] : c19[i][a];
+      n2 += c[i][a] * c[i][a];
+    }
+    if (Q == 9) w[i] = n2 == 0 ? 4.0 / 9.0 : (n2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+    else w[i] = n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+}
+
+struct LevelDev {
+  size_t gff_child0 = 0, gfc_src = 0, gfc_oct = 0, src_elem = 0, momA = 0, momB = 0;
+  int64_t nsrc = 0;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_params p{};
+  HostMesh M;
+  const Ops* ops = nullptr;
+  std::string err;
+  int d = 2, Q = 9, nS = 3, nlev = 1;
+  double rho_off = 0.0;
+  double inlet[19] = {};
+  // layout (byte offsets into the workspace)
+  size_t oA = 0, oB = 0, oNbr = 0, oF = 0, oOutElem = 0, oOutA = 0, oOutB = 0, oOutDir = 0, oOutKind = 0,
+         oSide = 0, oObsElem = 0, oObsDir = 0, oUslot = 0, oUlev = 0, oStage = 0, oPartial = 0, oRed = 0;
+  std::vector<LevelDev> ld;
+  size_t bytes = 0;
+  int64_t chunk = 0;
+  // bound state
+  bool bound = false;
+  char* ws = nullptr;
+  cudaStream_t st = nullptr;
+  std::vector<int> parity;
+  int64_t launches = 0;
+  // stream-collide timing (events recorded around each launch when enabled)
+  bool timing = false;
+  struct Timed {
+    int li;
+    cudaEvent_t a, b;
+  };
+  std::vector<Timed> timed;
+  std::vector<cudaEvent_t> event_pool;
+  cudaEvent_t get_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void recycle_timed() {
+    for (auto& t : timed) {
+      event_pool.push_back(t.a);
+      event_pool.push_back(t.b);
+    }
+    timed.clear();
+  }
+  ~lbm_ctx() {
+    recycle_timed();
+    for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+  }
+
+  template <class T = void>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(ws + off);
+  }
+  void* cur(int li) const { return parity[li] ? at(oB) : at(oA); }
+  void* nxt(int li) const { return parity[li] ? at(oA) : at(oB); }
+  uint32_t parity_mask() const {
+    uint32_t m = 0;
+    for (int li = 0; li < nlev; ++li) m |= (uint32_t)(parity[li] & 1) << li;
+    return m;
+  }
+  const void* force_ptr() const { return p.use_force ? at(oF) : nullptr; }
+
+  lbm_status fail(lbm_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  lbm_status cuda_check(cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return LBM_OK;
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return LBM_ERR_CUDA;
+  }
+  lbm_status launched(const char* where) { return cuda_check(cudaGetLastError(), where); }
+
+  void layout();
+  // driver pieces
+  void fill_gff(int li);
+  void source_moments(int li, size_t mom_off);
+  void fill_gfc(int li_fine, bool two_times);
+  void stream_collide(int li);
+  void advance(int li);
+};
+
+void lbm_ctx::layout() {
+  const HostMesh& m = M;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t r = o;
+    o += align_up(std::max<size_t>(b, 1));
+    return r;
+  };
+  const size_t sb = ops->storage_bytes, cb = ops->compute_bytes;
+  const size_t N = (size_t)m.Ntot;
+  oA = take(Q * N * sb);
+  oB = take(Q * N * sb);
+  oNbr = take((size_t)(Q - 1) * N * 4);
+  oF = p.use_force ? take((size_t)d * N * cb) : 0;
+  ld.assign(nlev, LevelDev());
+  const size_t M_ = 1 + d + nS + Q;
+  for (int li = 0; li < nlev; ++li) {
+    const HostLevel& H = m.lv[li];
+    LevelDev& L = ld[li];
+    L.gff_child0 = take(H.gff_child0.size() * 4);
+    L.gfc_src = take(H.gfc_src.size() * 4);
+    L.gfc_oct = take(H.gfc_oct.size());
+    L.src_elem = take(H.src_elem.size() * 4);
+    L.nsrc = (int64_t)H.src_elem.size();
+    L.momA = take(M_ * L.nsrc * cb);
+    L.momB = take(M_ * L.nsrc * cb);
+  }
+  const size_t nout = m.out_elem.size(), nobs = m.obs_elem.size();
+  oOutElem = take(nout * 4);
+  oOutA = take(nout * 4);
+  oOutB = take(nout * 4);
+  oOutDir = take(nout);
+  oOutKind = take(nout);
+  oSide = take(nout * cb);
+  oObsElem = take(nobs * 4);
+  oObsDir = take(nobs);
+  oUslot = take((size_t)m.n_user * 4);
+  oUlev = take((size_t)m.n_user);
+  chunk = std::min<int64_t>(m.n_user, (int64_t)1 << 20);
+  oStage = take((size_t)chunk * (1 + d + nS + Q + Q) * 8);
+  oPartial = take((size_t)nlev * kReduceBlocks * 8 * 8);
+  oRed = take(8 * 8);
+  bytes = o;
+}
+
+// ---------------------------------------------------------------- driver
+void lbm_ctx::fill_gff(int li) {
+  const HostLevel& H = M.lv[li];
+  const HostLevel& Hf = M.lv[li + 1];
+  if (H.nG1 + H.nG2 == 0) return;
+  GffArgs a{};
+  a.src_fine = cur(li + 1);
+  a.force = force_ptr();
+  a.child0 = at<int32_t>(ld[li].gff_child0);
+  a.ng = H.nG1 + H.nG2;
+  a.n_inner = H.nG1;
+  a.dest0 = H.base + H.oG1;
+  a.dest_outer = H.base + H.oG2;
+  a.dst = cur(li);
+  a.Ntot = M.Ntot;
+  a.omega_c = H.omega;
+  a.omega_f = Hf.omega;
+  a.rho_off = rho_off;
+  ops->fill_gff(Q, a, st);
+  ++launches;
+}
+
+void lbm_ctx::source_moments(int li, size_t mom_off) {
+  if (ld[li].nsrc == 0) return;
+  MomentsArgs a{};
+  a.src = cur(li);
+  a.force = force_ptr();
+  a.elem = at<int32_t>(ld[li].src_elem);
+  a.mom = at(mom_off);
+  a.Ntot = M.Ntot;
+  a.nsrc = ld[li].nsrc;
+  a.omega = M.lv[li].omega;
+  a.rho_off = rho_off;
+  ops->source_moments(Q, a, st);
+  ++launches;
+}
+
+void lbm_ctx::fill_gfc(int lf, bool two_times) {
+  const HostLevel& H = M.lv[lf];
+  if (H.nC == 0) return;
+  const int lc = lf - 1;
+  GfcArgs a{};
+  a.momA = at(ld[lc].momA);
+  a.momB = two_times ? at(ld[lc].momB) : nullptr;
+  a.nsrc = ld[lc].nsrc;
+  a.gsrc = at<int32_t>(ld[lf].gfc_src);
+  a.oct = at<uint8_t>(ld[lf].gfc_oct);
+  a.ng = H.nC;
+  a.dest0 = H.base + H.oC;
+  a.dst = cur(lf);
+  a.Ntot = M.Ntot;
+  a.omega_c = M.lv[lc].omega;
+  a.omega_f = H.omega;
+  a.rho_off = rho_off;
+  ops->fill_gfc(Q, a, st);
+  ++launches;
+}
+
+void lbm_ctx::stream_collide(int li) {
+  const HostLevel& H = M.lv[li];
+  if (H.out_end > H.out_begin) {
+    OutletArgs o{};
+    o.src = cur(li);
+    o.side = at(oSide);
+    o.elem = at<int32_t>(oOutElem);
+    o.a = at<int32_t>(oOutA);
+    o.b = at<int32_t>(oOutB);
+    o.dir = at<int8_t>(oOutDir);
+    o.kind = at<int8_t>(oOutKind);
+    o.force = force_ptr();
+    o.Ntot = M.Ntot;
+    o.begin = H.out_begin;
+    o.end = H.out_end;
+    o.omega = H.omega;
+    o.rho_off = rho_off;
+    o.rho0 = p.rho0;
+    ops->outlet(Q, o, st);
+    ++launches;
+  }
+  StreamCollideArgs a{};
+  a.src = cur(li);
+  a.dst = nxt(li);
+  a.nbr = at<uint32_t>(oNbr);
+  a.force = force_ptr();
+  a.side = at(oSide);
+  a.Ntot = M.Ntot;
+  // processed range: TWO_LAYER [GFC | fluid], LINEAR [fluid | GFF inner]
+  if (p.time_mode == LBM_TIME_TWO_LAYER) {
+    a.begin = H.base + H.oC;
+    a.end = H.base + H.oG1;
+  } else {
+    a.begin = H.base + H.oF;
+    a.end = H.base + H.oG2;
+  }
+  a.omega = H.omega;
+  a.rho_off = rho_off;
+  std::memcpy(a.inlet, inlet, sizeof(inlet));
+  if (timing) {
+    Timed t{li, get_event(), get_event()};
+    cudaEventRecord(t.a, st);
+    ops->stream_collide(Q, p.use_force != 0, a, st);
+    cudaEventRecord(t.b, st);
+    timed.push_back(t);
+  } else {
+    ops->stream_collide(Q, p.use_force != 0, a, st);
+  }
+  ++launches;
+  parity[li] ^= 1;
+}
+
+void lbm_ctx::advance(int li) {
+  const bool has_finer = li + 1 < nlev;
+  if (has_finer) {
+    fill_gff(li);
+    source_moments(li, ld[li].momA);
+    fill_gfc(li + 1, false);
+  }
+  stream_collide(li);
+  if (has_finer) {
+    advance(li + 1);
+    if (p.time_mode == LBM_TIME_LINEAR) {
+      source_moments(li, ld[li].momB);
+      fill_gfc(li + 1, true);
+    }
+    advance(li + 1);
+  }
+}
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t n, const lbm_params* params,
+                          lbm_ctx** out) {
+  if (!out || !params) return LBM_ERR_ARG;
+  *out = nullptr;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_OOM;
+  c->p = *params;
+  if (params->precision == LBM_FP64) c->ops = ops_fp64();
+  else if (params->precision == LBM_FP32DEV) c->ops = ops_fp32dev();
+  else if (params->precision == LBM_BF16DEV) c->ops = ops_bf16dev();
+  else {
+    c->err = "bad precision";
+    *out = c;
+    return LBM_ERR_ARG;
+  }
+  lbm_status s;
+  try {
+    s = build_host_mesh(tree_ids, levels, n, c->p, &c->M, &c->err);
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    s = LBM_ERR_OOM;
+  }
+  *out = c;
+  if (s != LBM_OK) return s;
+  c->Q = c->M.Q;
+  c->d = c->M.d;
+  c->nS = c->M.nS;
+  c->nlev = (int)c->M.lv.size();
+  c->rho_off = params->precision == LBM_FP64 ? 0.0 : params->rho0;
+  int cc[19][3];
+  double w[19];
+  lattice_host(c->Q, cc, w);
+  for (int i = 0; i < c->Q; ++i) {
+    double cu = 0;
+    for (int a = 0; a < c->d; ++a) cu += cc[i][a] * params->u_in[a];
+    c->inlet[i] = 6.0 * w[i] * params->rho0 * cu;
+  }
+  c->layout();
+  c->parity.assign(c->nlev, 0);
+  return LBM_OK;
+}
+
+lbm_status lbm_mesh_info(const lbm_ctx* c, int64_t* info, int32_t cap, int32_t* nlevels) {
+  if (!c || !info) return LBM_ERR_ARG;
+  int n = 0;
+  for (const HostLevel& H : c->M.lv) {
+    if (n >= cap) break;
+    int64_t r[8] = {H.L, H.nF, H.nC, H.nG1, H.nG2, H.N, H.out_end - H.out_begin, H.obs_end - H.obs_begin};
+    std::memcpy(info + 8 * n, r, sizeof(r));
+    ++n;
+  }
+  if (nlevels) *nlevels = (int32_t)c->M.lv.size();
+  return LBM_OK;
+}
+
+lbm_status lbm_device_bytes(const lbm_ctx* c, uint64_t* bytes) {
+  if (!c || !bytes || !c->ops || c->M.lv.empty()) return LBM_ERR_ARG;
+  *bytes = c->bytes;
+  return LBM_OK;
+}
+
+lbm_status lbm_bind(lbm_ctx* c, void* ws, uint64_t bytes, void* stream) {
+  if (!c || !ws) return LBM_ERR_ARG;
+  if (c->M.lv.empty()) return c->fail(LBM_ERR_STATE, "no mesh");
+  if (bytes < c->bytes) return c->fail(LBM_ERR_ARG, "device workspace too small");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return c->fail(LBM_ERR_ARG, "device workspace not 256-byte aligned");
+  c->ws = static_cast<char*>(ws);
+  c->st = static_cast<cudaStream_t>(stream);
+  const HostMesh& m = c->M;
+  auto up = [&](size_t off, const void* src, size_t b) -> lbm_status {
+    if (b == 0) return LBM_OK;
+    return c->cuda_check(cudaMemcpyAsync(c->ws + off, src, b, cudaMemcpyHostToDevice, c->st), "upload");
+  };
+  lbm_status s = up(c->oNbr, m.nbr.data(), m.nbr.size() * 4);
+  for (int li = 0; li < c->nlev && s == LBM_OK; ++li) {
+    const HostLevel& H = m.lv[li];
+    s = up(c->ld[li].gff_child0, H.gff_child0.data(), H.gff_child0.size() * 4);
+    if (s == LBM_OK) s = up(c->ld[li].gfc_src, H.gfc_src.data(), H.gfc_src.size() * 4);
+    if (s == LBM_OK) s = up(c->ld[li].gfc_oct, H.gfc_oct.data(), H.gfc_oct.size());
+    if (s == LBM_OK) s = up(c->ld[li].src_elem, H.src_elem.data(), H.src_elem.size() * 4);
+  }
+  if (s == LBM_OK) s = up(c->oOutElem, m.out_elem.data(), m.out_elem.size() * 4);
+  if (s == LBM_OK) s = up(c->oOutA, m.out_a.data(), m.out_a.size() * 4);
+  if (s == LBM_OK) s = up(c->oOutB, m.out_b.data(), m.out_b.size() * 4);
+  if (s == LBM_OK) s = up(c->oOutDir, m.out_dir.data(), m.out_dir.size());
+  if (s == LBM_OK) s = up(c->oOutKind, m.out_kind.data(), m.out_kind.size());
+  if (s == LBM_OK) s = up(c->oObsElem, m.obs_elem.data(), m.obs_elem.size() * 4);
+  if (s == LBM_OK) s = up(c->oObsDir, m.obs_dir.data(), m.obs_dir.size());
+  if (s == LBM_OK) s = up(c->oUslot, m.uslot.data(), m.uslot.size() * 4);
+  if (s == LBM_OK) s = up(c->oUlev, m.ulev.data(), m.ulev.size());
+  if (s != LBM_OK) return s;
+  if (c->p.use_force) {
+    s = c->cuda_check(cudaMemsetAsync(c->ws + c->oF, 0, (size_t)c->d * m.Ntot * c->ops->compute_bytes, c->st),
+                      "force clear");
+    if (s != LBM_OK) return s;
+  }
+  for (size_t off : {c->oA, c->oB}) {
+    FillArgs f{c->ws + off, m.Ntot, c->p.rho0, c->rho_off};
+    c->ops->fill_rest(c->Q, f, c->st);
+    ++c->launches;
+  }
+  s = c->launched("bind");
+  if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "bind sync");
+  if (s != LBM_OK) return s;
+  std::fill(c->parity.begin(), c->parity.end(), 0);
+  c->bound = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* S, const double* df) {
+  if (!c || !rho || !u) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_init before lbm_bind");
+  const int64_t n = c->M.n_user, CH = c->chunk;
+  const int d = c->d, nS = c->nS, Q = c->Q;
+  double* sr = c->at<double>(c->oStage);
+  double* su = sr + CH;
+  double* sS = su + CH * d;
+  double* sdf = sS + CH * nS;
+  for (int64_t first = 0; first < n; first += CH) {
+    const int64_t cnt = std::min(CH, n - first);
+    lbm_status s = c->cuda_check(cudaMemcpyAsync(sr, rho + first, cnt * 8, cudaMemcpyHostToDevice, c->st), "init copy");
+    if (s == LBM_OK)
+      s = c->cuda_check(cudaMemcpyAsync(su, u + first * d, cnt * d * 8, cudaMemcpyHostToDevice, c->st), "init copy");
+    if (s == LBM_OK && S)
+      s = c->cuda_check(cudaMemcpyAsync(sS, S + first * nS, cnt * nS * 8, cudaMemcpyHostToDevice, c->st), "init copy");
+    if (s == LBM_OK && df)
+      s = c->cuda_check(cudaMemcpyAsync(sdf, df + first * Q, cnt * Q * 8, cudaMemcpyHostToDevice, c->st), "init copy");
+    if (s != LBM_OK) return s;
+    InitArgs a{};
+    a.A = c->at(c->oA);
+    a.B = c->at(c->oB);
+    a.uslot = c->at<int32_t>(c->oUslot);
+    a.ulev = c->at<uint8_t>(c->oUlev);
+    a.parity = c->parity_mask();
+    a.rho = sr;
+    a.u = su;
+    a.S = S ? sS : nullptr;
+    a.df = df ? sdf : nullptr;
+    a.first = first;
+    a.cnt = cnt;
+    a.Ntot = c->M.Ntot;
+    for (int li = 0; li < c->nlev; ++li) a.omega[li] = c->M.lv[li].omega;
+    a.rho_off = c->rho_off;
+    c->ops->init(Q, a, c->st);
+    ++c->launches;
+  }
+  lbm_status s = c->launched("init");
+  if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "init sync");
+  return s;
+}
+
+lbm_status lbm_set_force(lbm_ctx* c, const double* F) {
+  if (!c || !F) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_set_force before lbm_bind");
+  if (!c->p.use_force) return c->fail(LBM_ERR_STATE, "params.use_force is 0");
+  const int64_t n = c->M.n_user, CH = c->chunk;
+  double* sf = c->at<double>(c->oStage);
+  for (int64_t first = 0; first < n; first += CH) {
+    const int64_t cnt = std::min(CH, n - first);
+    lbm_status s = c->cuda_check(
+        cudaMemcpyAsync(sf, F + first * c->d, cnt * c->d * 8, cudaMemcpyHostToDevice, c->st), "force copy");
+    if (s != LBM_OK) return s;
+    ForceArgs a{c->at(c->oF), c->at<int32_t>(c->oUslot), sf, first, cnt, c->M.Ntot, c->d};
+    launch_scatter_force(c->p.precision == LBM_FP64, a, c->st);
+    ++c->launches;
+  }
+  lbm_status s = c->launched("set_force");
+  if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "force sync");
+  return s;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t n_coarse) {
+  if (!c || n_coarse < 0) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_step before lbm_bind");
+  for (int64_t k = 0; k < n_coarse; ++k) c->advance(0);
+  return c->launched("step");
+}
+
+lbm_status lbm_fill_ghosts(lbm_ctx* c) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_fill_ghosts before lbm_bind");
+  for (int li = 0; li + 1 < c->nlev; ++li) {
+    c->fill_gff(li);
+    c->source_moments(li, c->ld[li].momA);
+    c->fill_gfc(li + 1, false);
+  }
+  return c->launched("fill_ghosts");
+}
+
+static lbm_status out_chunks(lbm_ctx* c, double* rho, double* u, double* S, double* f) {
+  const int64_t n = c->M.n_user, CH = c->chunk;
+  const int d = c->d, nS = c->nS, Q = c->Q;
+  double* sr = c->at<double>(c->oStage);
+  double* su = sr + CH;
+  double* sS = su + CH * d;
+  double* sf = sS + CH * nS;
+  for (int64_t first = 0; first < n; first += CH) {
+    const int64_t cnt = std::min(CH, n - first);
+    OutArgs a{};
+    a.A = c->at(c->oA);
+    a.B = c->at(c->oB);
+    a.force = c->force_ptr();
+    a.uslot = c->at<int32_t>(c->oUslot);
+    a.ulev = c->at<uint8_t>(c->oUlev);
+    a.parity = c->parity_mask();
+    a.rho = rho ? sr : nullptr;
+    a.u = u ? su : nullptr;
+    a.S = S ? sS : nullptr;
+    a.f = f ? sf : nullptr;
+    a.first = first;
+    a.cnt = cnt;
+    a.Ntot = c->M.Ntot;
+    for (int li = 0; li < c->nlev; ++li) a.omega[li] = c->M.lv[li].omega;
+    a.rho_off = c->rho_off;
+    c->ops->out(Q, a, c->st);
+    ++c->launches;
+    lbm_status s = c->launched("output");
+    auto down = [&](double* dst, const double* src, size_t b) {
+      if (s == LBM_OK) s = c->cuda_check(cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, c->st), "output copy");
+    };
+    if (rho) down(rho + first, sr, cnt * 8);
+    if (u) down(u + first * d, su, cnt * d * 8);
+    if (S) down(S + first * nS, sS, cnt * nS * 8);
+    if (f) down(f + first * Q, sf, cnt * Q * 8);
+    if (s != LBM_OK) return s;
+  }
+  return c->cuda_check(cudaStreamSynchronize(c->st), "output sync");
+}
+
+lbm_status lbm_moments(lbm_ctx* c, double* rho, double* u, double* S) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_moments before lbm_bind");
+  return out_chunks(c, rho, u, S, nullptr);
+}
+
+lbm_status lbm_get_state(lbm_ctx* c, double* f) {
+  if (!c || !f) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_get_state before lbm_bind");
+  return out_chunks(c, nullptr, nullptr, nullptr, f);
+}
+
+lbm_status lbm_reduce(lbm_ctx* c, double out[8]) {
+  if (!c || !out) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_reduce before lbm_bind");
+  const int d = c->d;
+  for (int li = 0; li < c->nlev; ++li) {
+    const HostLevel& H = c->M.lv[li];
+    ReduceArgs a{};
+    a.pdf = c->cur(li);
+    a.force = c->force_ptr();
+    a.Ntot = c->M.Ntot;
+    a.begin = H.base + H.oF;
+    a.end = H.base + H.oF + H.nF;
+    a.omega = H.omega;
+    a.rho_off = c->rho_off;
+    a.vol = std::ldexp(1.0, -d * li);
+    a.partial = c->at<double>(c->oPartial) + (size_t)li * kReduceBlocks * 8;
+    a.nblocks = kReduceBlocks;
+    a.obs_elem = c->at<int32_t>(c->oObsElem) + H.obs_begin;
+    a.obs_dir = c->at<int8_t>(c->oObsDir) + H.obs_begin;
+    a.obs_n = H.obs_end - H.obs_begin;
+    a.fscale = std::ldexp(1.0, (d - 1) * (c->nlev - 1 - li));
+    c->ops->reduce(c->Q, a, c->st);
+    ++c->launches;
+  }
+  FinalArgs fa{c->at<double>(c->oPartial), (int64_t)c->nlev * kReduceBlocks, c->at<double>(c->oRed)};
+  launch_final_reduce(fa, c->st);
+  ++c->launches;
+  lbm_status s = c->launched("reduce");
+  if (s == LBM_OK) s = c->cuda_check(cudaMemcpyAsync(out, c->at(c->oRed), 64, cudaMemcpyDeviceToHost, c->st), "reduce copy");
+  if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "reduce sync");
+  return s;
+}
+
+lbm_status lbm_ghost_count(const lbm_ctx* c, int64_t* n) {
+  if (!c || !n) return LBM_ERR_ARG;
+  int64_t t = 0;
+  for (const HostLevel& H : c->M.lv) t += H.nC + H.nG1 + H.nG2;
+  *n = t;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_ghosts(lbm_ctx* c, int64_t* info, double* f) {
+  if (!c || !info || !f) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_get_ghosts before lbm_bind");
+  const int Q = c->Q;
+  int64_t row = 0;
+  double* stage = c->at<double>(c->oStage);
+  for (int li = 0; li < c->nlev; ++li) {
+    const HostLevel& H = c->M.lv[li];
+    const int64_t ng = H.nC + H.nG1 + H.nG2;
+    for (int64_t k = 0; k < ng; ++k) {
+      int64_t* r = info + 6 * (row + k);
+      r[0] = H.L;
+      r[1] = k < H.nC ? 1 : 2;
+      r[2] = H.ghost_layer[k];
+      for (int a = 0; a < 3; ++a) r[3 + a] = H.ghost_xyz[3 * k + a];
+    }
+    const int64_t seg_first[3] = {H.base + H.oC, H.base + H.oG1, H.base + H.oG2};
+    const int64_t seg_cnt[3] = {H.nC, H.nG1, H.nG2};
+    for (int sgi = 0; sgi < 3; ++sgi) {
+      for (int64_t done = 0; done < seg_cnt[sgi]; done += c->chunk) {
+        const int64_t cnt = std::min<int64_t>(c->chunk, seg_cnt[sgi] - done);
+        GatherGhostArgs a{c->cur(li), seg_first[sgi] + done, cnt, c->M.Ntot, stage, c->rho_off};
+        c->ops->gather_ghosts(Q, a, c->st);
+        ++c->launches;
+        lbm_status s = c->launched("ghosts");
+        if (s == LBM_OK)
+          s = c->cuda_check(cudaMemcpyAsync(f + (row + done) * Q, stage, cnt * Q * 8, cudaMemcpyDeviceToHost, c->st),
+                            "ghost copy");
+        if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "ghost sync");
+        if (s != LBM_OK) return s;
+      }
+      row += seg_cnt[sgi];
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_sfc_partition(const int64_t* tree_ids, int64_t n, int32_t d, int32_t nparts, int64_t* order,
+                             int64_t* weights, int64_t* cumulative, int32_t* part) {
+  std::string msg;
+  return sfc_partition(tree_ids, n, d, nparts, order, weights, cumulative, part, &msg);
+}
+
+lbm_status lbm_kernel_launches(const lbm_ctx* c, int64_t* count) {
+  if (!c || !count) return LBM_ERR_ARG;
+  *count = c->launches;
+  return LBM_OK;
+}
+
+lbm_status lbm_timing_enable(lbm_ctx* c, int32_t on) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_timing_enable before lbm_bind");
+  lbm_status s = c->cuda_check(cudaStreamSynchronize(c->st), "timing sync");
+  c->recycle_timed();
+  c->timing = on != 0;
+  return s;
+}
+
+lbm_status lbm_timing_read(lbm_ctx* c, int64_t* launches, double* ms, int32_t cap) {
+  if (!c || !launches || !ms) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_timing_read before lbm_bind");
+  lbm_status s = c->cuda_check(cudaStreamSynchronize(c->st), "timing sync");
+  if (s != LBM_OK) return s;
+  for (int k = 0; k < cap; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  for (auto& t : c->timed) {
+    float e = 0.f;
+    s = c->cuda_check(cudaEventElapsedTime(&e, t.a, t.b), "timing read");
+    if (s != LBM_OK) break;
+    if (t.li < cap) {
+      launches[t.li] += 1;
+      ms[t.li] += e;
+    }
+  }
+  c->recycle_timed();
+  return s;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void lbm_destroy(lbm_ctx* c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,728 @@
+// Device kernels of the multilevel lattice Boltzmann hot path (sm_103a).
+//
+// Storage S is double (LBM_FP64), float or bfloat16 (deviation storage
+// g_i = f_i - w_i rho0, arithmetic in float).  Every kernel is written in the
+// deviation form with an offset rho_off (0 for FP64, rho0 otherwise):
+//   rho = rho_off + sum g,  g^eq_i = w_i [ (rho - rho_off) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ],
+// which is Eq. (feq) of Sec. 2.1 minus w_i rho_off.
+//
+// Memory layout: pdfs A, B as [Q][Ntot] structure-of-arrays over all levels
+// (each level a contiguous, padded index range); pull neighbour indices
+// nbr[Q-1][Ntot] (uint32, see lbm_internal.h).  One thread per element; the
+// direction loops are fully unrolled so every load/store of a warp touches 32
+// consecutive elements of one direction array (coalesced), except the pull
+// gathers, whose locality comes from the z-curve order.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace dev {
+
+// ----------------------------------------------------------------- lattices
+template <int Q>
+struct Lat;
+
+template <>
+struct Lat<9> {
+  static constexpr int D = 2, NS = 3;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    return a == 0   ? ((i == 1 || i == 5 || i == 7) ? 1 : (i == 2 || i == 6 || i == 8) ? -1 : 0)
+           : a == 1 ? ((i == 3 || i == 5 || i == 8) ? 1 : (i == 4 || i == 6 || i == 7) ? -1 : 0)
+                    : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+};
+
+template <>
+struct Lat<19> {
+  static constexpr int D = 3, NS = 6;
+  __host__ __device__ static constexpr int c(int i, int a) {
+    return a == 0   ? ((i == 1 || i == 7 || i == 9 || i == 11 || i == 13)    ? 1
+                       : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1
+                                                                               : 0)
+           : a == 1 ? ((i == 3 || i == 7 || i == 10 || i == 15 || i == 17)   ? 1
+                       : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18)  ? -1
+                                                                               : 0)
+                    : ((i == 5 || i == 11 || i == 14 || i == 15 || i == 18)  ? 1
+                       : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1
+                                                                                : 0);
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// index of S_ab in the packed strain-rate vector (xx,yy,xy | xx,yy,zz,xy,yz,xz)
+template <int D>
+__host__ __device__ constexpr int sidx(int a, int b) {
+  return a == b ? a
+                : (D == 2 ? 2
+                          : ((a + b == 1) ? 3 : ((a + b == 3) ? 4 : 5)));
+}
+
+// ----------------------------------------------------------------- storage
+template <class S>
+struct Sto;
+template <>
+struct Sto<double> {
+  using R = double;
+  __device__ static __forceinline__ R ld(const double* p) { return *p; }
+  __device__ static __forceinline__ double cv(R v) { return v; }
+};
+template <>
+struct Sto<float> {
+  using R = float;
+  __device__ static __forceinline__ R ld(const float* p) { return *p; }
+  __device__ static __forceinline__ float cv(R v) { return v; }
+};
+template <>
+struct Sto<__nv_bfloat16> {
+  using R = float;
+  __device__ static __forceinline__ R ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ static __forceinline__ __nv_bfloat16 cv(R v) { return __float2bfloat16_rn(v); }
+};
+
+// ----------------------------------------------------------------- physics
+// g^eq_i for density deviation rp = rho - rho_off
+template <int Q, class R>
+__device__ __forceinline__ R geq(int i, R rp, R rho, const R* u, R usq) {
+  using LT = Lat<Q>;
+  R cu = R(0);
+#pragma unroll
+  for (int a = 0; a < LT::D; ++a) cu += R(LT::c(i, a)) * u[a];
+  return R(LT::w(i)) * (rp + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
+}
+
+// Guo forcing term (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F
+template <int Q, class R>
+__device__ __forceinline__ R guo(int i, R omega, const R* u, const R* F) {
+  using LT = Lat<Q>;
+  R cu = R(0), cF = R(0), uF = R(0);
+#pragma unroll
+  for (int a = 0; a < LT::D; ++a) {
+    cu += R(LT::c(i, a)) * u[a];
+    cF += R(LT::c(i, a)) * F[a];
+    uF += u[a] * F[a];
+  }
+  return (R(1) - R(0.5) * omega) * R(LT::w(i)) * (R(3) * (cF - uF) + R(9) * cu * cF);
+}
+
+// rho deviation and first moment of a pdf set
+template <int Q, class R>
+__device__ __forceinline__ void raw_moments(const R* g, R& rp, R* j) {
+  using LT = Lat<Q>;
+  rp = R(0);
+  j[0] = j[1] = j[2] = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    rp += g[i];
+#pragma unroll
+    for (int a = 0; a < LT::D; ++a) {
+      if (LT::c(i, a) > 0) j[a] += g[i];
+      if (LT::c(i, a) < 0) j[a] -= g[i];
+    }
+  }
+}
+
+// Pre-collision moments from a stored post-collision set: u = (j - F/2)/rho,
+// f^neq = (g - g^eq - F_i) / (1 - omega), S_ab = -(3 omega / 2 rho) sum c_a c_b f^neq.
+template <int Q, class R, bool WANT_S>
+__device__ __forceinline__ void post_moments(const R* g, R omega, R rho_off, const R* F, R& rp, R* u,
+                                             R* fneq, R* S) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  R j[3];
+  raw_moments<Q, R>(g, rp, j);
+  const R rho = rho_off + rp;
+  const R inv = R(1) / rho;
+  u[0] = u[1] = u[2] = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) u[a] = (j[a] - R(0.5) * F[a]) * inv;
+  R usq = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) usq += u[a] * u[a];
+  const R r1w = R(1) / (R(1) - omega);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) fneq[i] = (g[i] - geq<Q, R>(i, rp, rho, u, usq) - guo<Q, R>(i, omega, u, F)) * r1w;
+  if (WANT_S) {
+    const R pre = -R(1.5) * omega * inv;
+#pragma unroll
+    for (int s = 0; s < LT::NS; ++s) S[s] = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b) {
+          const int cc = LT::c(i, a) * LT::c(i, b);
+          if (cc > 0) S[sidx<D>(a, b)] += fneq[i];
+          if (cc < 0) S[sidx<D>(a, b)] -= fneq[i];
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < LT::NS; ++s) S[s] *= pre;
+  }
+}
+
+// ----------------------------------------------------------------- stream + collide
+// Pull streaming f_i(x) = f*_i(x - c_i) through the neighbour list (Sec. 2.1,
+// Eq. lbe) fused with the BGK collision (Eq. bgk) and Guo forcing.
+template <int Q, class S, bool FORCE>
+__global__ void __launch_bounds__(256) k_stream_collide(const StreamCollideArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int64_t e = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.end) return;
+  const S* __restrict__ src = static_cast<const S*>(a.src);
+  S* __restrict__ dst = static_cast<S*>(a.dst);
+  const uint32_t* __restrict__ nbr = a.nbr;
+  const size_t N = (size_t)a.Ntot;
+  R g[Q];
+  g[0] = Sto<S>::ld(src + e);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const uint32_t nb = __ldg(nbr + (size_t)(i - 1) * N + e);
+    R v;
+    if (nb < NB_FLAG30) {
+      v = Sto<S>::ld(src + (size_t)i * N + nb);
+    } else if (nb & NB_BOUNCE) {
+      v = Sto<S>::ld(src + (size_t)opp(i) * N + e);
+      if (nb & NB_FLAG30) v += R(a.inlet[i]);
+    } else {
+      v = static_cast<const R*>(a.side)[nb & NB_INDEX];
+    }
+    g[i] = v;
+  }
+  R F[3] = {R(0), R(0), R(0)};
+  if (FORCE) {
+    const R* __restrict__ fp = static_cast<const R*>(a.force);
+#pragma unroll
+    for (int b = 0; b < D; ++b) F[b] = fp[(size_t)b * N + e];
+  }
+  R rp, j[3];
+  raw_moments<Q, R>(g, rp, j);
+  const R rho = R(a.rho_off) + rp;
+  const R inv = R(1) / rho;
+  R u[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int b = 0; b < D; ++b) u[b] = (j[b] + R(0.5) * F[b]) * inv;
+  R usq = R(0);
+#pragma unroll
+  for (int b = 0; b < D; ++b) usq += u[b] * u[b];
+  const R om = R(a.omega);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R gi = g[i] - om * (g[i] - geq<Q, R>(i, rp, rho, u, usq));
+    if (FORCE) gi += guo<Q, R>(i, om, u, F);
+    dst[(size_t)i * N + e] = Sto<S>::cv(gi);
+  }
+}
+
+// ----------------------------------------------------------------- outlet values
+// Sec. 2.3 outflow: for an incoming direction i whose upstream element lies
+// beyond the outlet, either extrapolate that element's f_i linearly along -n
+// (2 f_i(x - c_i - n) - f_i(x - c_i - 2n)), or, for c_i = -n, correct the
+// pressure: f^eq_i(rho0, u) + f^neq_opp(i)(x).
+template <int Q, class S>
+__global__ void k_outlet(const OutletArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const int64_t k = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.end) return;
+  const S* __restrict__ src = static_cast<const S*>(a.src);
+  const size_t N = (size_t)a.Ntot;
+  const int i = a.dir[k];
+  R* side = static_cast<R*>(a.side);
+  if (a.kind[k] == OUT_EXTRAP) {
+    side[k] = R(2) * Sto<S>::ld(src + (size_t)i * N + a.a[k]) - Sto<S>::ld(src + (size_t)i * N + a.b[k]);
+    return;
+  }
+  const int64_t e = a.elem[k];
+  R g[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(src + (size_t)q * N + e);
+  R F[3] = {R(0), R(0), R(0)};
+  if (a.force)
+#pragma unroll
+    for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(a.force)[(size_t)b * N + e];
+  R rp, j[3];
+  raw_moments<Q, R>(g, rp, j);
+  const R rho = R(a.rho_off) + rp;
+  R u[3] = {R(0), R(0), R(0)};
+  R usq = R(0);
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    u[b] = (j[b] - R(0.5) * F[b]) / rho;
+    usq += u[b] * u[b];
+  }
+  const int ib = opp(i);
+  R gib = R(0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    if (q == ib) gib = g[q];
+  const R r0 = R(a.rho0);
+  side[k] = geq<Q, R>(i, r0 - R(a.rho_off), r0, u, usq) + gib - geq<Q, R>(ib, rp, rho, u, usq);
+}
+
+// ----------------------------------------------------------------- GFC source moments
+// Interpolation step 1 (Sec. 2.2): density, velocity, strain rate and f^neq of
+// every coarse element that feeds a GhostFromCoarser, into mom[M][nsrc].
+template <int Q, class S>
+__global__ void k_source_moments(const MomentsArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D, NS = LT::NS;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.nsrc) return;
+  const S* __restrict__ src = static_cast<const S*>(a.src);
+  const size_t N = (size_t)a.Ntot;
+  const int64_t e = a.elem[k];
+  R g[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(src + (size_t)q * N + e);
+  R F[3] = {R(0), R(0), R(0)};
+  if (a.force)
+#pragma unroll
+    for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(a.force)[(size_t)b * N + e];
+  R rp, u[3], fneq[Q], Sv[NS];
+  post_moments<Q, R, true>(g, R(a.omega), R(a.rho_off), F, rp, u, fneq, Sv);
+  R* m = static_cast<R*>(a.mom);
+  const size_t ns = (size_t)a.nsrc;
+  m[k] = rp;
+#pragma unroll
+  for (int b = 0; b < D; ++b) m[(1 + b) * ns + k] = u[b];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) m[(1 + D + s) * ns + k] = Sv[s];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) m[(1 + D + NS + q) * ns + k] = fneq[q];
+}
+
+// ----------------------------------------------------------------- GhostFromCoarser
+// Interpolation steps 2-5 (Sec. 2.2) for one fine ghost from its four coarse
+// sources.  The velocity is the compact quadratic interpolant evaluated at the
+// ghost, written in the octant's local frame (signs s_a) in closed form:
+// 3D (H, K, M, N at (0,0,0), (1,1,0), (1,0,1), (0,1,1); ghost at (1/4,1/4,1/4)),
+//   u_a = 5/8 u_H + 1/8 (u_K + u_M + u_N) - 3/16 (q_xx + q_yy + q_zz)_a
+//         - 1/16 (q_xy + q_yz + q_xz)_a,
+// with the quadratic coefficients q from the strain-rate differences of
+// Eqs. (compact_3D_s); 2D (H, E, N, NE on the unit square, ghost at (1/4,1/4)),
+//   u_a = 1/2 u_H + 1/4 (u_E + u_N) - 3/16 (q_xx + q_yy)_a + 1/16 q_xy,a,
+// the least-squares linear part over the square.  Density and f^neq are
+// linear (weights 5/8,1/8,1/8,1/8 resp. 9/16,3/16,3/16,1/16), f^neq is
+// rescaled by omega_c / (m omega_f), and f = f^eq + (1 - omega_f) f^neq is
+// stored as the ghost's post-collision state.
+template <int Q, class S>
+__global__ void k_fill_gfc(const GfcArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D, NS = LT::NS;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.ng) return;
+  const R* __restrict__ mA = static_cast<const R*>(a.momA);
+  const R* __restrict__ mB = static_cast<const R*>(a.momB);
+  const size_t ns = (size_t)a.nsrc;
+  int32_t sp[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) sp[s] = a.gsrc[(size_t)s * a.ng + k];
+  auto mom = [&](int field, int s) -> R {
+    const size_t o = (size_t)field * ns + sp[s];
+    return mB ? R(0.5) * (mA[o] + mB[o]) : mA[o];
+  };
+  const uint8_t oct = a.oct[k];
+  R sg[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) sg[b] = ((oct >> b) & 1) ? R(1) : R(-1);
+  // local-frame velocity and strain rate of the sources
+  R ul[4][3], Sl[4][NS];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+#pragma unroll
+    for (int b = 0; b < D; ++b) ul[s][b] = sg[b] * mom(1 + b, s);
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+#pragma unroll
+      for (int c = b; c < D; ++c) Sl[s][sidx<D>(b, c)] = sg[b] * sg[c] * mom(1 + D + sidx<D>(b, c), s);
+  }
+  R uloc[3] = {R(0), R(0), R(0)};
+  if (D == 3) {
+    auto Dx = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] + Sl[2][c] - Sl[3][c]); };
+    auto Dy = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] - Sl[2][c] + Sl[3][c]); };
+    auto Dz = [&](int c) { return R(0.5) * (-Sl[0][c] - Sl[1][c] + Sl[2][c] + Sl[3][c]); };
+    constexpr int XX = 0, YY = 1, ZZ = 2, XY = 3, YZ = 4, XZ = NS - 1;
+    const R h3 = Dz(XY) + Dx(YZ) + Dy(XZ);
+    const R sd[3] = {R(0.5) * Dx(XX) + Dy(XY) - R(0.5) * Dx(YY) + Dz(XZ) - R(0.5) * Dx(ZZ),
+                     Dx(XY) - R(0.5) * Dy(XX) + R(0.5) * Dy(YY) + Dz(YZ) - R(0.5) * Dy(ZZ),
+                     Dx(XZ) - R(0.5) * Dz(XX) + Dy(YZ) - R(0.5) * Dz(YY) + R(0.5) * Dz(ZZ)};
+    const R so[3] = {Dy(XX) + Dz(XX) + h3 - R(2) * Dx(YZ), Dx(YY) + Dz(YY) + h3 - R(2) * Dy(XZ),
+                     Dx(ZZ) + Dy(ZZ) + h3 - R(2) * Dz(XY)};
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      uloc[b] = R(0.625) * ul[0][b] + R(0.125) * (ul[1][b] + ul[2][b] + ul[3][b]) - R(0.1875) * sd[b] -
+                R(0.0625) * so[b];
+  } else {
+    auto Dx = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] - Sl[2][c] + Sl[3][c]); };
+    auto Dy = [&](int c) { return R(0.5) * (-Sl[0][c] - Sl[1][c] + Sl[2][c] + Sl[3][c]); };
+    const R axx = R(0.5) * Dx(0), axy = Dy(0), ayy = Dy(2) - R(0.5) * Dx(1);
+    const R bxx = Dx(2) - R(0.5) * Dy(0), byy = R(0.5) * Dy(1), bxy = Dx(1);
+    uloc[0] = R(0.5) * ul[0][0] + R(0.25) * (ul[1][0] + ul[2][0]) - R(0.1875) * (axx + ayy) + R(0.0625) * axy;
+    uloc[1] = R(0.5) * ul[0][1] + R(0.25) * (ul[1][1] + ul[2][1]) - R(0.1875) * (bxx + byy) + R(0.0625) * bxy;
+  }
+  R u[3] = {R(0), R(0), R(0)};
+  R usq = R(0);
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    u[b] = sg[b] * uloc[b];
+    usq += u[b] * u[b];
+  }
+  const R lw0 = D == 3 ? R(0.625) : R(0.5625);
+  const R lw1 = D == 3 ? R(0.125) : R(0.1875);
+  const R lw2 = D == 3 ? R(0.125) : R(0.1875);
+  const R lw3 = D == 3 ? R(0.125) : R(0.0625);
+  const R rp = lw0 * mom(0, 0) + lw1 * mom(0, 1) + lw2 * mom(0, 2) + lw3 * mom(0, 3);
+  const R rho = R(a.rho_off) + rp;
+  const R wf = R(a.omega_f);
+  const R scale = (R(1) - wf) * R(a.omega_c) / (R(2) * wf);
+  S* __restrict__ dst = static_cast<S*>(a.dst);
+  const size_t N = (size_t)a.Ntot;
+  const int64_t e = a.dest0 + k;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int fld = 1 + D + NS + q;
+    const R fn = lw0 * mom(fld, 0) + lw1 * mom(fld, 1) + lw2 * mom(fld, 2) + lw3 * mom(fld, 3);
+    dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rp, rho, u, usq) + scale * fn);
+  }
+}
+
+// ----------------------------------------------------------------- GhostFromFiner
+// Coarse ghost from its 2^d children (Sec. 2.2 steps 1-5 with the children as
+// sources; they surround the ghost symmetrically at +-1/4 coarse cell).
+// Density and f^neq: the children's mean.  Velocity: the children's mean minus
+// (1/32) lap u, with lap u_a = 2 d_c S_ac - d_a S_cc from the children's strain
+// rates (differences across the children's cube).  f^neq is rescaled by
+// m omega_f / omega_c; f = f^eq + (1 - omega_c) f^neq.
+template <int Q, class S>
+__global__ void k_fill_gff(const GffArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D, NS = LT::NS, NCH = 1 << D;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.ng) return;
+  const S* __restrict__ src = static_cast<const S*>(a.src_fine);
+  const size_t N = (size_t)a.Ntot;
+  const int64_t c0 = a.child0[k];
+  const R wf = R(a.omega_f), rho_off = R(a.rho_off);
+  R rps = R(0), us[3] = {R(0), R(0), R(0)}, fns[Q], dS[3][NS];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) fns[q] = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dS[c][s] = R(0);
+#pragma unroll 1
+  for (int b = 0; b < NCH; ++b) {
+    const int64_t e = c0 + b;
+    R g[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(src + (size_t)q * N + e);
+    R F[3] = {R(0), R(0), R(0)};
+    if (a.force)
+#pragma unroll
+      for (int c = 0; c < D; ++c) F[c] = static_cast<const R*>(a.force)[(size_t)c * N + e];
+    R rp, u[3], fneq[Q], Sv[NS];
+    post_moments<Q, R, true>(g, wf, rho_off, F, rp, u, fneq, Sv);
+    rps += rp;
+#pragma unroll
+    for (int c = 0; c < D; ++c) us[c] += u[c];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fns[q] += fneq[q];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const R sgn = ((b >> c) & 1) ? R(1) : R(-1);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) dS[c][s] += sgn * Sv[s];
+    }
+  }
+  const R inv = R(1) / R(NCH);
+  // d_c S (coarse units): S_coarse = 2 S_fine; difference of the two half-cubes
+  // over a distance of 1/2 coarse cell -> factor 2 * 2^{2-D}
+  const R dfac = R(2) * R(D == 3 ? 0.5 : 1.0);
+  const R rp = rps * inv;
+  R u[3] = {R(0), R(0), R(0)};
+  R usq = R(0);
+#pragma unroll
+  for (int aa = 0; aa < D; ++aa) {
+    R lap = R(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) lap += dfac * (R(2) * dS[c][sidx<D>(aa, c)] - dS[aa][sidx<D>(c, c)]);
+    u[aa] = us[aa] * inv - lap * R(1.0 / 32.0);
+    usq += u[aa] * u[aa];
+  }
+  const R wc = R(a.omega_c);
+  const R rho = rho_off + rp;
+  const R scale = (R(1) - wc) * R(2) * wf / wc * inv;
+  S* __restrict__ dst = static_cast<S*>(a.dst);
+  const int64_t e = k < a.n_inner ? a.dest0 + k : a.dest_outer + (k - a.n_inner);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rp, rho, u, usq) + scale * fns[q]);
+}
+
+// ----------------------------------------------------------------- set-up / output (FP64 arithmetic)
+template <int Q, class S>
+__global__ void k_fill_rest(const FillArgs a) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.Ntot) return;
+  S* p = static_cast<S*>(a.pdf);
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    p[(size_t)q * a.Ntot + e] = Sto<S>::cv(typename Sto<S>::R(Lat<Q>::w(q) * (a.rho0 - a.rho_off)));
+}
+
+// Initial state, Sec. 4.1: f = f^eq + (1 - omega) f^neq + df with
+// f^neq_i = -(3 w_i rho / omega) (c_i c_i - I/3) : S.
+template <int Q, class S>
+__global__ void k_init(const InitArgs a) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D, NS = LT::NS;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.cnt) return;
+  const int64_t k = a.first + t;
+  const int li = a.ulev[k];
+  S* cur = static_cast<S*>(((a.parity >> li) & 1) ? a.B : a.A);
+  const int64_t e = a.uslot[k];
+  const double rho = a.rho[t];
+  double u[3] = {0, 0, 0}, usq = 0;
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    u[b] = a.u[t * D + b];
+    usq += u[b] * u[b];
+  }
+  const double* Sv = a.S ? a.S + t * NS : nullptr;
+  const double* df = a.df ? a.df + t * Q : nullptr;
+  const double om = a.omega[li];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    double cu = 0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) cu += LT::c(q, b) * u[b];
+    double f = LT::w(q) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+    if (Sv) {
+      double qs = 0, tr = 0;
+#pragma unroll
+      for (int b = 0; b < D; ++b)
+#pragma unroll
+        for (int c = b; c < D; ++c) {
+          const double w2 = b == c ? 1.0 : 2.0;
+          qs += w2 * LT::c(q, b) * LT::c(q, c) * Sv[sidx<D>(b, c)];
+          if (b == c) tr += Sv[sidx<D>(b, b)];
+        }
+      f += (1.0 - om) * (-(3.0 * LT::w(q) * rho / om) * (qs - tr / 3.0));
+    }
+    if (df) f += df[q];
+    cur[(size_t)q * a.Ntot + e] = Sto<S>::cv(typename Sto<S>::R(f - LT::w(q) * a.rho_off));
+  }
+}
+
+template <int Q, class S>
+__global__ void k_out(const OutArgs a) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D, NS = LT::NS;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.cnt) return;
+  const int64_t k = a.first + t;
+  const int li = a.ulev[k];
+  const S* cur = static_cast<const S*>(((a.parity >> li) & 1) ? a.B : a.A);
+  const int64_t e = a.uslot[k];
+  double g[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) g[q] = (double)Sto<S>::ld(cur + (size_t)q * a.Ntot + e);
+  if (a.f) {
+    double* o = a.f + t * Q;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) o[q] = g[q] + LT::w(q) * a.rho_off;
+  }
+  if (!a.rho && !a.u && !a.S) return;
+  double F[3] = {0, 0, 0};
+  if (a.force) {
+    // force is stored in the compute type
+    if (sizeof(typename Sto<S>::R) == 8)
+      for (int b = 0; b < D; ++b) F[b] = static_cast<const double*>(a.force)[(size_t)b * a.Ntot + e];
+    else
+      for (int b = 0; b < D; ++b) F[b] = static_cast<const float*>(a.force)[(size_t)b * a.Ntot + e];
+  }
+  double rp, u[3], fneq[Q], Sv[NS];
+  post_moments<Q, double, true>(g, a.omega[li], a.rho_off, F, rp, u, fneq, Sv);
+  if (a.rho) a.rho[t] = a.rho_off + rp;
+  if (a.u)
+#pragma unroll
+    for (int b = 0; b < D; ++b) a.u[t * D + b] = u[b];
+  if (a.S)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) a.S[t * NS + s] = Sv[s];
+}
+
+template <int Q, class S>
+__global__ void k_gather_ghosts(const GatherGhostArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.cnt) return;
+  const S* p = static_cast<const S*>(a.pdf);
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    a.stage[t * Q + q] = (double)Sto<S>::ld(p + (size_t)q * a.Ntot + a.first_global + t) + Lat<Q>::w(q) * a.rho_off;
+}
+
+// ----------------------------------------------------------------- FP64 reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    const double s = warp_sum(v[c]);
+    if (lane == 0) sh[c][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double s = lane < nw ? sh[c][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) out[c] = s;
+    }
+  }
+}
+
+// mass, momentum, obstacle force (momentum exchange, Sec. 2.3) and kinetic energy
+// of one level; one partial row per block, fixed grid -> deterministic order.
+template <int Q, class S>
+__global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const S* p = static_cast<const S*>(a.pdf);
+  const size_t N = (size_t)a.Ntot;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.end; e += stride) {
+    double g[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) g[q] = (double)Sto<S>::ld(p + (size_t)q * N + e);
+    double rp, j[3];
+    raw_moments<Q, double>(g, rp, j);
+    double F[3] = {0, 0, 0};
+    if (a.force) {
+      if (sizeof(typename Sto<S>::R) == 8)
+        for (int b = 0; b < D; ++b) F[b] = static_cast<const double*>(a.force)[(size_t)b * N + e];
+      else
+        for (int b = 0; b < D; ++b) F[b] = static_cast<const float*>(a.force)[(size_t)b * N + e];
+    }
+    const double rho = a.rho_off + rp;
+    double uu = 0;
+    acc[0] += a.vol * rho;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const double m = j[b] - 0.5 * F[b];  // rho u
+      acc[1 + b] += a.vol * m;
+      uu += m * m;
+    }
+    acc[7] += 0.5 * a.vol * uu / rho;
+  }
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < a.obs_n; l += stride) {
+    const int i = a.obs_dir[l];
+    const int ib = opp(i);
+    const int64_t e = a.obs_elem[l];
+    const double fib = (double)Sto<S>::ld(p + (size_t)ib * N + e) + LT::w(ib) * a.rho_off;
+#pragma unroll
+    for (int b = 0; b < D; ++b) acc[4 + b] += 2.0 * a.fscale * LT::c(ib, b) * fib;
+  }
+  block_sum_store<8>(acc, a.partial + (size_t)blockIdx.x * 8);
+}
+
+// ----------------------------------------------------------------- launchers
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <class S>
+struct Launch {
+  static void stream_collide(int Q, bool force, const StreamCollideArgs& a, cudaStream_t st) {
+    const int64_t n = a.end - a.begin;
+    if (n <= 0) return;
+    const unsigned g = blocks_for(n, 256);
+    if (Q == 9) {
+      if (force) k_stream_collide<9, S, true><<<g, 256, 0, st>>>(a);
+      else k_stream_collide<9, S, false><<<g, 256, 0, st>>>(a);
+    } else {
+      if (force) k_stream_collide<19, S, true><<<g, 256, 0, st>>>(a);
+      else k_stream_collide<19, S, false><<<g, 256, 0, st>>>(a);
+    }
+  }
+  static void outlet(int Q, const OutletArgs& a, cudaStream_t st) {
+    const int64_t n = a.end - a.begin;
+    if (n <= 0) return;
+    if (Q == 9) k_outlet<9, S><<<blocks_for(n, 128), 128, 0, st>>>(a);
+    else k_outlet<19, S><<<blocks_for(n, 128), 128, 0, st>>>(a);
+  }
+  static void source_moments(int Q, const MomentsArgs& a, cudaStream_t st) {
+    if (a.nsrc <= 0) return;
+    if (Q == 9) k_source_moments<9, S><<<blocks_for(a.nsrc, 128), 128, 0, st>>>(a);
+    else k_source_moments<19, S><<<blocks_for(a.nsrc, 128), 128, 0, st>>>(a);
+  }
+  static void fill_gfc(int Q, const GfcArgs& a, cudaStream_t st) {
+    if (a.ng <= 0) return;
+    if (Q == 9) k_fill_gfc<9, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a);
+    else k_fill_gfc<19, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a);
+  }
+  static void fill_gff(int Q, const GffArgs& a, cudaStream_t st) {
+    if (a.ng <= 0) return;
+    if (Q == 9) k_fill_gff<9, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a);
+    else k_fill_gff<19, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a);
+  }
+  static void fill_rest(int Q, const FillArgs& a, cudaStream_t st) {
+    if (Q == 9) k_fill_rest<9, S><<<blocks_for(a.Ntot, 256), 256, 0, st>>>(a);
+    else k_fill_rest<19, S><<<blocks_for(a.Ntot, 256), 256, 0, st>>>(a);
+  }
+  static void init(int Q, const InitArgs& a, cudaStream_t st) {
+    if (a.cnt <= 0) return;
+    if (Q == 9) k_init<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    else k_init<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+  }
+  static void out(int Q, const OutArgs& a, cudaStream_t st) {
+    if (a.cnt <= 0) return;
+    if (Q == 9) k_out<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    else k_out<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+  }
+  static void gather_ghosts(int Q, const GatherGhostArgs& a, cudaStream_t st) {
+    if (a.cnt <= 0) return;
+    if (Q == 9) k_gather_ghosts<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    else k_gather_ghosts<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+  }
+  static void reduce(int Q, const ReduceArgs& a, cudaStream_t st) {
+    if (Q == 9) k_reduce<9, S><<<a.nblocks, 256, 0, st>>>(a);
+    else k_reduce<19, S><<<a.nblocks, 256, 0, st>>>(a);
+  }
+};
+
+template <class S>
+const Ops* make_ops() {
+  static const Ops ops = {&Launch<S>::stream_collide, &Launch<S>::outlet,     &Launch<S>::source_moments,
+                          &Launch<S>::fill_gfc,       &Launch<S>::fill_gff,   &Launch<S>::fill_rest,
+                          &Launch<S>::init,           &Launch<S>::out,        &Launch<S>::gather_ghosts,
+                          &Launch<S>::reduce,         sizeof(S),              sizeof(typename Sto<S>::R)};
+  return &ops;
+}
+
+}  // namespace dev
+}  // namespace lbm

@@ -1,0 +1,221 @@
+// Internal structures of liblbm: host mesh tables, the device workspace layout
+// and the kernel launch interface.  Not part of the public ABI (include/lbm.h).
+#pragma once
+
+#include <cuda_runtime_api.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+
+namespace lbm {
+
+// Neighbour (pull) index encoding, one uint32 per element and direction i >= 1:
+//   bit31=0 bit30=0 : pull f_i from global element index (bits 0..29) of the same level
+//   bit31=1 bit30=0 : half-way bounce-back, read the element's own f_opp(i)
+//   bit31=1 bit30=1 : velocity bounce-back (inlet): own f_opp(i) + 6 w_i rho0 (c_i . u_in)
+//   bit31=0 bit30=1 : precomputed incoming value (outlet), index into the boundary values
+constexpr uint32_t NB_BOUNCE = 0x80000000u;
+constexpr uint32_t NB_FLAG30 = 0x40000000u;
+constexpr uint32_t NB_INDEX = 0x3FFFFFFFu;
+constexpr int kPad = 32;  // every level segment is padded to a multiple of this
+
+enum { K_FLUID = 0, K_GFC = 1, K_GFF = 2, K_PAD = 3 };
+enum { OUT_NORMAL = 0, OUT_EXTRAP = 1 };
+
+struct HostLevel {
+  int L = 0;
+  double omega = 1.0;
+  int64_t nC = 0, nF = 0, nG1 = 0, nG2 = 0;  // GFC, fluid, GFF inner layer, GFF outer layer
+  int64_t oC = 0, oF = 0, oG1 = 0, oG2 = 0;  // padded segment offsets (local)
+  int64_t N = 0;                             // padded local size
+  int64_t base = 0;                          // global index of local element 0
+  // ghosts (host copies for lbm_get_ghosts): coords and layer per ghost, GFC then GFF
+  std::vector<int32_t> ghost_xyz;  // [nC + nG1 + nG2][3]
+  std::vector<int8_t> ghost_layer;
+  // GhostFromFiner of this level: global index of the first child on level L+1
+  std::vector<int32_t> gff_child0;  // [nG1 + nG2]
+  // GhostFromCoarser of this level: 4 positions in the source list of level L-1, octant bits
+  std::vector<int32_t> gfc_src;  // [4][nC]
+  std::vector<uint8_t> gfc_oct;  // [nC], bit a set: ghost on the + side of its parent along a
+  // sources (global indices on this level) feeding the GFC of level L+1
+  std::vector<int32_t> src_elem;
+  // outlet links processed before this level's stream-collide: global range in the outlet list
+  int64_t out_begin = 0, out_end = 0;
+  // obstacle links of this level: global range in the obstacle list
+  int64_t obs_begin = 0, obs_end = 0;
+};
+
+struct HostMesh {
+  int d = 2, Q = 9, nS = 3;
+  int Lmin = 0, Lmax = 0;
+  int64_t n_user = 0;
+  int64_t Ntot = 0;
+  std::vector<HostLevel> lv;
+  std::vector<uint32_t> nbr;    // [Q-1][Ntot]
+  std::vector<int32_t> uslot;   // [n_user] global element index
+  std::vector<uint8_t> ulev;    // [n_user] level index (L - Lmin)
+  std::vector<uint8_t> kind;    // [Ntot] element kind (K_*)
+  // outlet links (all levels, grouped by level)
+  std::vector<int32_t> out_elem, out_a, out_b;
+  std::vector<int8_t> out_dir, out_kind;
+  // obstacle links (all levels, grouped by level): element, direction i with x - c_i solid
+  std::vector<int32_t> obs_elem;
+  std::vector<int8_t> obs_dir;
+};
+
+// Build the mesh tables; returns LBM_OK or LBM_ERR_MESH / LBM_ERR_ARG with msg.
+lbm_status build_host_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t n,
+                           const lbm_params& p, HostMesh* out, std::string* msg);
+
+// Sec. 3.1 utility (host only).
+lbm_status sfc_partition(const int64_t* tree_ids, int64_t n, int d, int nparts, int64_t* order,
+                         int64_t* weights, int64_t* cumulative, int32_t* part, std::string* msg);
+
+// ----------------------------------------------------------------- kernels
+// Launch arguments are plain data; pointers are device pointers into the
+// workspace.  "src"/"dst" are pdf arrays [Q][Ntot] of the storage type.
+struct StreamCollideArgs {
+  const void* src;
+  void* dst;
+  const uint32_t* nbr;
+  const void* force;  // [d][Ntot] compute type, or null
+  const void* side;   // boundary values, compute type, or null
+  int64_t Ntot, begin, end;
+  double omega, rho_off;
+  double inlet[19];   // 6 w_i rho0 (c_i . u_in)
+};
+
+struct OutletArgs {
+  const void* src;
+  void* side;
+  const int32_t *elem, *a, *b;
+  const int8_t *dir, *kind;
+  const void* force;
+  int64_t Ntot, begin, end;
+  double omega, rho_off, rho0;
+};
+
+struct MomentsArgs {  // GFC source moments
+  const void* src;
+  const void* force;
+  const int32_t* elem;
+  void* mom;  // [M][nsrc] compute type, M = 1 + d + nS + Q
+  int64_t Ntot, nsrc;
+  double omega, rho_off;
+};
+
+struct GfcArgs {
+  const void* momA;
+  const void* momB;  // null unless averaging two time levels
+  int64_t nsrc;
+  const int32_t* gsrc;   // [4][ng]
+  const uint8_t* oct;    // [ng]
+  int64_t ng, dest0;     // global index of the first GFC
+  void* dst;
+  int64_t Ntot;
+  double omega_c, omega_f, rho_off;
+};
+
+struct GffArgs {
+  const void* src_fine;  // pdfs holding the children
+  const void* force;
+  const int32_t* child0; // [ng], inner layer first
+  int64_t ng, n_inner;   // ghosts k < n_inner go to dest0 + k, the rest to dest_outer + (k - n_inner)
+  int64_t dest0, dest_outer;
+  void* dst;             // pdfs holding the coarse ghosts
+  int64_t Ntot;
+  double omega_c, omega_f, rho_off;
+};
+
+struct FillArgs {  // rest equilibrium everywhere
+  void* pdf;
+  int64_t Ntot;
+  double rho0, rho_off;
+};
+
+struct InitArgs {
+  void* A;
+  void* B;
+  const int32_t* uslot;
+  const uint8_t* ulev;
+  uint32_t parity;  // bit li set: level li's current state lives in B
+  const double *rho, *u, *S, *df;  // staged chunk: rho[cnt], u[cnt][d], S[cnt][nS] or null, df[cnt][Q] or null
+  int64_t first, cnt, Ntot;
+  double omega[16];
+  double rho_off;
+};
+
+struct OutArgs {  // moments / state to FP64 staging in user order
+  const void* A;
+  const void* B;
+  const void* force;
+  const int32_t* uslot;
+  const uint8_t* ulev;
+  uint32_t parity;
+  double *rho, *u, *S, *f;  // staged chunk outputs (any may be null)
+  int64_t first, cnt, Ntot;
+  double omega[16];
+  double rho_off;
+};
+
+struct ForceArgs {  // scatter user force to [d][Ntot]
+  void* force;
+  const int32_t* uslot;
+  const double* stage;  // [cnt][d]
+  int64_t first, cnt, Ntot;
+  int dim;
+};
+
+struct GatherGhostArgs {  // ghost pdfs -> FP64 [cnt][Q]
+  const void* pdf;
+  int64_t first_global, cnt, Ntot;
+  double* stage;
+  double rho_off;
+};
+
+struct ReduceArgs {
+  const void* pdf;       // current state of the level
+  const void* force;
+  int64_t Ntot, begin, end;  // fluid range of the level
+  double omega, rho_off, vol;
+  double* partial;       // [nblocks][8]
+  int nblocks;
+  // obstacle links of the level
+  const int32_t* obs_elem;
+  const int8_t* obs_dir;
+  int64_t obs_n;
+  double fscale;
+};
+
+struct FinalArgs {
+  const double* partial;
+  int64_t n;  // partial rows
+  double* out;
+};
+
+struct Ops {
+  void (*stream_collide)(int Q, bool force, const StreamCollideArgs&, cudaStream_t);
+  void (*outlet)(int Q, const OutletArgs&, cudaStream_t);
+  void (*source_moments)(int Q, const MomentsArgs&, cudaStream_t);
+  void (*fill_gfc)(int Q, const GfcArgs&, cudaStream_t);
+  void (*fill_gff)(int Q, const GffArgs&, cudaStream_t);
+  void (*fill_rest)(int Q, const FillArgs&, cudaStream_t);
+  void (*init)(int Q, const InitArgs&, cudaStream_t);
+  void (*out)(int Q, const OutArgs&, cudaStream_t);
+  void (*gather_ghosts)(int Q, const GatherGhostArgs&, cudaStream_t);
+  void (*reduce)(int Q, const ReduceArgs&, cudaStream_t);
+  size_t storage_bytes;  // bytes per stored pdf
+  size_t compute_bytes;  // bytes of the compute type
+};
+
+const Ops* ops_fp64();
+const Ops* ops_fp32dev();
+const Ops* ops_bf16dev();
+void launch_scatter_force(bool fp64, const ForceArgs&, cudaStream_t);
+void launch_final_reduce(const FinalArgs&, cudaStream_t);
+constexpr int kReduceBlocks = 512;  // blocks per reduce launch (fixed: deterministic order)
+
+}  // namespace lbm

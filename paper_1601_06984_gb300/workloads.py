@@ -33,14 +33,29 @@ def level_offset(L: int, d: int) -> int:
     return ((1 << (d * L)) - 1) // ((1 << d) - 1)
 
 
+def _spread(v: np.ndarray, d: int) -> np.ndarray:
+    """Insert d-1 zero bits between the bits of v (v < 2^21 for d=3, < 2^31 for d=2)."""
+    v = v.astype(np.uint64)
+    if d == 2:
+        for shift, mask in ((16, 0x0000FFFF0000FFFF), (8, 0x00FF00FF00FF00FF), (4, 0x0F0F0F0F0F0F0F0F),
+                            (2, 0x3333333333333333), (1, 0x5555555555555555)):
+            v = (v | (v << np.uint64(shift))) & np.uint64(mask)
+    else:
+        for shift, mask in ((32, 0x001F00000000FFFF), (16, 0x001F0000FF0000FF), (8, 0x100F00F00F00F00F),
+                            (4, 0x10C30C30C30C30C3), (2, 0x1249249249249249)):
+            v = (v | (v << np.uint64(shift))) & np.uint64(mask)
+    return v
+
+
 def morton(coords: np.ndarray, L: int, d: int) -> np.ndarray:
-    """Interleave the bits of integer coordinates [n, d] at level L."""
+    """Interleave the bits of integer coordinates [n, d] at level L (x bit lowest)."""
     coords = np.asarray(coords, dtype=np.int64)
-    m = np.zeros(coords.shape[0], dtype=np.int64)
-    for b in range(L):
-        for a in range(d):
-            m |= ((coords[:, a] >> b) & 1) << (d * b + a)
-    return m
+    if coords.shape[0] == 0:
+        return np.zeros(0, dtype=np.int64)
+    m = np.zeros(coords.shape[0], dtype=np.uint64)
+    for a in range(d):
+        m |= _spread(coords[:, a], d) << np.uint64(a)
+    return m.astype(np.int64)
 
 
 def tree_ids(coords: np.ndarray, L: int, d: int) -> np.ndarray:
@@ -302,3 +317,29 @@ def gaussian_force(mesh: Mesh, sigma: float = 1e-6, seed: int = SEED) -> np.ndar
 def random_direction(shape, seed: int, stream: int) -> np.ndarray:
     """Seeded direction for directional-derivative checks."""
     return np.random.default_rng([seed, stream]).standard_normal(shape)
+
+
+def config_sphere_small():
+    """Reduced sphere-like case for oracle parity (about 17k elements): box
+    24 x 12 x 12 coarse cells, three levels with nested boxes
+    [4,20)x[2,10)^2 (coarse cells) and [7,15)x[4,8)^2 (coarse cells), a sphere
+    of diameter 8 finest cells at the finest box centre, velocity inlet x-,
+    pressure outlet x+, periodic lateral faces."""
+    boxes = [((8, 4, 4), (40, 20, 20)), ((28, 16, 16), (60, 32, 32))]
+
+    def solid(L, cen):
+        return ((cen - np.array([44.0, 24.0, 24.0])) ** 2).sum(axis=1) < 16.0
+
+    bc = (BC_VELOCITY_IN, BC_PRESSURE_OUT, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
+    return nested_boxes(3, 5, (24, 12, 12), boxes, bc, solid)
+
+
+def omega_coarse_from_finest(omega_f: float, nlev: int) -> float:
+    """Coarsest-level relaxation rate for a finest-level one under
+    1/omega_f - 1/2 = m (1/omega_c - 1/2), m = 2 per level."""
+    return 1.0 / (0.5 + (1.0 / omega_f - 0.5) / (1 << (nlev - 1)))
+
+
+def omega_for_re(U: float, D: float, Re: float) -> float:
+    """Finest-level relaxation rate for Re = U D / nu (lattice units)."""
+    return 1.0 / (3.0 * U * D / Re + 0.5)

@@ -1,0 +1,138 @@
+"""Host-side checks of the C ABI (no GPU): the library loads and exports every
+entry point declared in include/lbm.h, the host mesh builder agrees with the
+oracle's own mesh code on ghost counts and on rejected meshes, and the
+z-curve / weight utility reproduces the paper's worked example."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1601_06984_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_1601_06984_gb300 import build, lbm as L
+    build.build()
+    return L
+
+
+def test_exports_every_declared_symbol(lbm):
+    header = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    declared = set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", header))
+    declared.discard("lbm_params")
+    lib = lbm.lib()
+    missing = [s for s in sorted(declared) if not hasattr(lib, s)]
+    assert not missing, missing
+    assert declared == set(lbm.EXPORTS)
+
+
+MESHES = [
+    ("tgv2d", W.config_tgv2d, 9, 1.6),
+    ("tgv3d", lambda: W.config_tgv3d(16), 19, 1.6),
+    ("half", lambda: W.half_refined_2d(16), 9, 1.6),
+    ("cylinder", W.config_cylinder, 9, 1.8605),
+]
+
+
+@pytest.mark.parametrize("name,make,Q,omega", MESHES)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_mesh_counts_match_oracle(lbm, oracle_mod, name, make, Q, omega, mode):
+    """Level-wise fluid / GhostFromCoarser / GhostFromFiner counts of the
+    library's builder equal those of the oracle's independent mesh code."""
+    mesh = make()
+    s = lbm.Sim(mesh, Q, omega, time_mode=mode, device=None)
+    info = s.mesh_info()
+    oc = oracle_mod.Oracle(mesh, Q, omega, time_mode=mode).counts()
+    assert len(info) == len(oc)
+    for a, b in zip(info, oc):
+        assert a[0] == b[0]
+        assert a[1] == b[1]              # fluid
+        assert a[2] == b[2]              # GFC
+        assert a[3] + a[4] == b[3]       # GFF
+        assert a[3] == b[5]              # inner GFF layer
+    assert s.ghost_count() == int(oc[:, 2].sum() + oc[:, 3].sum())
+
+
+def test_config1_counts(lbm):
+    """Config-1 figures: 768 coarse and 1024 fine fluid elements, 272 fine
+    GhostFromCoarser, 60 coarse GhostFromFiner (112 with the second layer)."""
+    mesh = W.config_tgv2d()
+    lin = lbm.Sim(mesh, 9, 1.6, time_mode=0, device=None).mesh_info()
+    two = lbm.Sim(mesh, 9, 1.6, time_mode=1, device=None).mesh_info()
+    assert lin[0, 1] == 768 and lin[1, 1] == 1024 and lin[1, 2] == 272
+    assert two[0, 3] + two[0, 4] == 60 and lin[0, 3] + lin[0, 4] == 112
+
+
+def _bad_meshes():
+    good = W.config_tgv2d()
+    dup = W.Mesh(2, good.extent, good.bc, np.concatenate([good.tree_ids, good.tree_ids[:1]]),
+                 np.concatenate([good.levels, good.levels[:1]]), np.concatenate([good.coords, good.coords[:1]]),
+                 good.lmin)
+    fine = good.levels > good.lmin
+    parent = good.coords[fine][0] // 2
+    ov = W.Mesh(2, good.extent, good.bc, np.concatenate([good.tree_ids, W.tree_ids(parent[None], good.lmin, 2)]),
+                np.concatenate([good.levels, [good.lmin]]).astype(np.int8),
+                np.concatenate([good.coords, parent[None]]), good.lmin)
+    jump = W.nested_boxes(2, 5, (32, 32), [((16, 16), (48, 48)), ((48, 48), (80, 80))], (0,) * 4)
+    far = W.Mesh(2, (4, 4), (0,) * 4, W.tree_ids(np.array([[5, 5]]), 3, 2), np.array([3], np.int8),
+                 np.array([[5, 5]]), 3)
+    return [("duplicate", dup), ("overlap", ov), ("level jump", jump), ("outside", far)]
+
+
+@pytest.mark.parametrize("name,mesh", _bad_meshes())
+def test_invalid_meshes_rejected_like_the_oracle(lbm, oracle_mod, name, mesh):
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.Oracle(mesh, 9, 1.6)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.Sim(mesh, 9, 1.6, device=None)
+    assert ei.value.status in (-1, -2)
+
+
+def test_level_list_must_match_tree_ids(lbm):
+    mesh = W.config_tgv2d()
+    lv = mesh.levels.copy()
+    lv[0] += 1
+    bad = W.Mesh(2, mesh.extent, mesh.bc, mesh.tree_ids, lv, mesh.coords, mesh.lmin)
+    with pytest.raises(lbm.LBMError, match="level"):
+        lbm.Sim(bad, 9, 1.6, device=None)
+
+
+def test_bad_arguments(lbm):
+    mesh = W.config_tgv2d()
+    with pytest.raises(lbm.LBMError):
+        lbm.Sim(mesh, 9, 2.5, device=None)          # omega outside (0,2)
+    with pytest.raises(lbm.LBMError):
+        lbm.Sim(mesh, 7, 1.6, device=None)          # unknown stencil
+    half_periodic = W.Mesh(2, mesh.extent, (0, 1, 0, 0), mesh.tree_ids, mesh.levels, mesh.coords, mesh.lmin)
+    with pytest.raises(lbm.LBMError, match="periodic"):
+        lbm.Sim(half_periodic, 9, 1.6, device=None)
+
+
+def test_sfc_worked_example(lbm):
+    """Sec. 3.1, Fig. partition: z-curve order, weights, cumulative weights and
+    the split over three processes of the 10-element quadtree."""
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "worked_example.json")))
+    el = g["elements"]
+    # treeIDs of the figure agree with the encoding used by the workloads
+    for e in el:
+        assert W.tree_ids(np.array([[e["x"], e["y"]]]), e["level"], 2)[0] == e["tree_id"]
+    # hand the elements over in a scrambled order
+    tids = np.array([e["tree_id"] for e in el], np.int64)[[3, 9, 0, 5, 7, 1, 8, 2, 6, 4]]
+    order, w, cum, part = lbm.lbm_sfc_partition(tids, 2, g["processes"])
+    assert tids[order].tolist() == g["sfc_order"]
+    assert w.tolist() == g["weights"]
+    assert cum.tolist() == g["cumulative_weights"]
+    assert np.bincount(part, minlength=g["processes"]).tolist() == g["partition_sizes"]
+
+
+def test_updates_weighting():
+    """Fine-substep weighted updates per coarse step, sum_L N_L 2^{L-Lmin}."""
+    m = W.config_tgv2d()
+    assert m.updates_per_coarse_step() == 768 + 2 * 1024
+    m3 = W.config_tgv3d(64)
+    assert m3.updates_per_coarse_step() == 229376 + 2 * 262144

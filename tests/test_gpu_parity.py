@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+FP64 must match the oracle to 1e-11 relative max-norm on the post-collision
+pdfs and on the moments, element by element, on meshes that span several
+levels, ghost layers, boundaries and forces, in both time-coupling modes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_06984_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1601_06984_gb300 import build, lbm as L
+    build.build()
+    return L
+
+
+def rel(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def make_case(name):
+    """mesh, stencil, omega_c, u_in, fields(mesh) -> (rho, u, S, df), force or None, steps"""
+    if name == "tgv2d":
+        m = W.config_tgv2d()
+        return m, 9, 1.6, (0, 0, 0), lambda m: (*W.tgv_fields(m, 0.01), W.pdf_perturbation(m, 9)), None, 50
+    if name == "tgv2d_half":
+        m = W.half_refined_2d(16)
+        return m, 9, 1.6, (0, 0, 0), lambda m: (*W.tgv_fields(m, 0.02), W.pdf_perturbation(m, 9)), None, 20
+    if name == "tgv3d":
+        m = W.config_tgv3d(16)
+        return m, 19, 1.6, (0, 0, 0), lambda m: (*W.tgv_fields(m, 0.01), W.pdf_perturbation(m, 19)), None, 8
+    if name == "tgv3d_force":
+        m = W.config_tgv3d(16)
+        return (m, 19, 1.6, (0, 0, 0), lambda m: (*W.tgv_fields(m, 0.01), None),
+                W.gaussian_force(m, 1e-5), 6)
+    if name == "cylinder":
+        m = W.config_cylinder()
+        om = W.omega_coarse_from_finest(W.omega_for_re(0.05, 40, 20), 4)
+        return (m, 9, om, (0.05, 0, 0),
+                lambda m: (*W.uniform_fields(m, 1.0, (0.05, 0.0)), W.pdf_perturbation(m, 9, 1e-4)), None, 2)
+    if name == "sphere_small":
+        m = W.config_sphere_small()
+        om = W.omega_coarse_from_finest(1.6, 3)
+        return (m, 19, om, (0.04, 0, 0),
+                lambda m: (*W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), W.pdf_perturbation(m, 19, 1e-4)), None, 3)
+    raise KeyError(name)
+
+
+def run_both(lbm, oracle_mod, name, mode, precision=0):
+    m, Q, om, uin, fields, force, steps = make_case(name)
+    rho, u, S, df = fields(m)
+    o = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin, use_force=force is not None)
+    o.init(rho, u, S, df)
+    g = lbm.Sim(m, Q, om, precision=precision, time_mode=mode, u_in=uin, use_force=force is not None)
+    g.init(rho, u, S, df)
+    if force is not None:
+        o.set_force(force)
+        g.set_force(force)
+    o.step(steps)
+    g.step(steps)
+    return m, o, g
+
+
+CASES = ["tgv2d", "tgv2d_half", "tgv3d", "tgv3d_force", "cylinder", "sphere_small"]
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp64_matches_oracle(lbm, oracle_mod, name, mode):
+    m, o, g = run_both(lbm, oracle_mod, name, mode)
+    assert rel(g.get_state(), o.get_f()) < TOL
+    r_o, u_o, S_o = o.moments()
+    r_g, u_g, S_g = g.moments()
+    assert rel(r_g, r_o) < TOL
+    assert rel(u_g, u_o) < TOL
+    assert rel(S_g, S_o) < 1e-10
+    red_o, red_g = o.reduce(), g.reduce()
+    assert abs(red_g[0] - red_o[0]) / red_o[0] < TOL
+    mom_scale = max(np.abs(red_o[1:4]).max(), 1e-300)
+    assert np.abs(red_g[1:4] - red_o[1:4]).max() / max(mom_scale, red_o[0] * 1e-6) < 1e-9
+    assert abs(red_g[7] - red_o[7]) / max(red_o[7], 1e-300) < 1e-10
+    if np.abs(red_o[4:7]).max() > 0:
+        assert np.abs(red_g[4:7] - red_o[4:7]).max() / np.abs(red_o[4:7]).max() < 1e-10
+
+
+@pytest.mark.parametrize("name", ["tgv2d", "tgv3d", "sphere_small"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ghost_fill_matches_oracle(lbm, oracle_mod, name, mode):
+    """GhostFromFiner and GhostFromCoarser values after one synchronous fill."""
+    m, Q, om, uin, fields, force, _ = make_case(name)
+    rho, u, S, df = fields(m)
+    o = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin)
+    g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin)
+    o.init(rho, u, S, df)
+    g.init(rho, u, S, df)
+    o.fill_ghosts()
+    g.fill_ghosts()
+    io, fo = o.ghosts()
+    ig, fg = g.ghosts()
+    assert len(io) == len(ig) > 0
+    key = lambda info: {(int(r[0]), int(r[1]), int(r[3]), int(r[4]), int(r[5])): k for k, r in enumerate(info)}
+    ko, kg = key(io), key(ig)
+    assert ko.keys() == kg.keys()
+    idx_o = np.array([ko[k] for k in ko])
+    idx_g = np.array([kg[k] for k in ko])
+    assert rel(fg[idx_g], fo[idx_o]) < 1e-12
+    # layers agree too
+    assert np.array_equal(ig[idx_g, 2], io[idx_o, 2])
+
+
+def test_fp64_full_size_tgv3d(lbm, oracle_mod):
+    """The 64^3 / 32^3-block D3Q19 mesh at full size (about 0.5M elements),
+    two coarse steps, every element against the oracle."""
+    m = W.config_tgv3d(64)
+    rho, u, S = W.tgv_fields(m, 0.01)
+    df = W.pdf_perturbation(m, 19)
+    o = oracle_mod.Oracle(m, 19, 1.6)
+    o.init(rho, u, S, df)
+    o.step(2)
+    g = lbm.Sim(m, 19, 1.6)
+    g.init(rho, u, S, df)
+    g.step(2)
+    assert rel(g.get_state(), o.get_f()) < TOL
+
+
+def test_shuffled_user_order_is_bitwise_identical(lbm):
+    m = W.config_tgv3d(16)
+    sh = W.shuffled(m)
+    res = []
+    for mesh in (m, sh):
+        g = lbm.Sim(mesh, 19, 1.6)
+        rho, u, S = W.tgv_fields(mesh, 0.01)
+        g.init(rho, u, S, W.pdf_perturbation(mesh, 19))
+        g.step(4)
+        key = np.argsort(mesh.tree_ids)
+        res.append(g.get_state()[key])
+    assert np.array_equal(res[0], res[1])
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_deterministic(lbm, precision):
+    """No atomics on the forward path: two identical runs give identical bits,
+    reductions included."""
+    m = W.config_sphere_small()
+    om = W.omega_coarse_from_finest(1.6, 3)
+    out = []
+    for _ in range(2):
+        g = lbm.Sim(m, 19, om, precision=precision, u_in=(0.04, 0, 0))
+        g.init(*W.uniform_fields(m, 1.0, (0.04, 0, 0)), W.pdf_perturbation(m, 19, 1e-4))
+        g.step(3)
+        out.append((g.get_state(), g.reduce()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_precision_variants_error(lbm, oracle_mod, mode):
+    """FP32-deviation and BF16-deviation storage against the FP64 oracle on the
+    2D two-level Taylor-Green (200 coarse steps, u0 = 0.01): velocity l2 error
+    and mass drift stay within the stated bounds."""
+    m = W.config_tgv2d()
+    rho, u, S = W.tgv_fields(m, 0.01)
+    o = oracle_mod.Oracle(m, 9, 1.6, time_mode=mode)
+    o.init(rho, u, S)
+    o.step(200)
+    _, u_o, S_o = o.moments()
+    bounds = {1: 1e-4, 2: 5e-2}
+    for prec, bound in bounds.items():
+        g = lbm.Sim(m, 9, 1.6, precision=prec, time_mode=mode)
+        g.init(rho, u, S)
+        g.step(200)
+        _, u_g, _ = g.moments()
+        err = math.sqrt(((u_g - u_o) ** 2).sum() / (u_o ** 2).sum())
+        assert err < bound, (prec, err)
+
+
+def test_kernel_launches_counted(lbm):
+    m = W.config_tgv2d()
+    g = lbm.Sim(m, 9, 1.6)
+    g.init(*W.tgv_fields(m, 0.01))
+    n0 = g.kernel_launches()
+    g.step(1)
+    # LINEAR two-level step: GFF, source moments, GFC, coarse stream-collide,
+    # fine stream-collide, source moments, GFC, fine stream-collide
+    assert g.kernel_launches() - n0 == 8
