@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "tgv3d"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "sphere_half", "tgv3d"],
+                    help="sphere_half: every length halved (about 1.1e7 elements), for profiling captures")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64/BF16 and TGV side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
     return ap.parse_args()
@@ -49,12 +50,14 @@ def parse():
 # ---------------------------------------------------------------- workloads
 def make_workload(name):
     from paper_1601_06984_gb300 import workloads as W
-    if name == "sphere":
-        mesh = W.config_sphere(1)
+    if name in ("sphere", "sphere_half"):
+        scale = 1 if name == "sphere" else 2
+        mesh = W.config_sphere(scale)
         U = 0.04
         om_f = W.omega_for_re(U, 64, 100.0)
         om_c = W.omega_coarse_from_finest(om_f, 5)
-        desc = {"workload": "sphere_re100_d3q19_5level", "box": "32D x 16D x 16D", "D_finest": 64,
+        desc = {"workload": "sphere_re100_d3q19_5level" + ("" if scale == 1 else "_half"),
+                "box": "32D x 16D x 16D", "D_finest": 64 // scale,
                 "levels": 5, "u_in": U, "omega_finest": round(om_f, 6), "omega_coarsest": round(om_c, 6),
                 "boundaries": "velocity inlet x-, pressure outlet x+, periodic y/z, half-way bounce-back sphere"}
         fields = lambda m: W.uniform_fields(m, 1.0, (U, 0.0, 0.0))
