@@ -156,6 +156,28 @@ lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* S);
  * sum rho |u|^2 vol / 2; vol = 2^{-d (L - Lmin)}. */
 lbm_status lbm_reduce(lbm_ctx* ctx, double out[8]);
 
+/* lbm_reduce_noalloc: the same eight FP64 values as lbm_reduce, computed by the
+ * same kernels in the same order (identical results), for callers that cannot
+ * allocate device memory when they ask for them -- for instance code running
+ * under a host framework that owns every device allocation and forbids raw
+ * cudaMalloc, or a monitor that must not grow device memory mid-run.  It
+ * allocates nothing and uses no caller scratch: the block partial sums and the
+ * result live in a static device array of the library (4096 x 8 + 8 doubles,
+ * about 256 KiB), held on every GPU that loads the library until the process
+ * exits.  The caller passes the bound context (input) and out[8] (host output).
+ *  - Limit: meshes with at most 8 levels (512 partial rows per level); deeper
+ *    hierarchies get LBM_ERR_ARG with a message naming lbm_reduce instead.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device made current for the lookup);
+ *    make that first call before any CUDA stream capture.
+ *  - All calls share the one array and every call overwrites what it reads,
+ *    so nothing carries over between calls; calls that overlap on the GPU
+ *    (other streams, other threads, other contexts on the same device) race
+ *    and must be serialised by the caller.
+ * The paper has no counterpart: this is an interface convenience of the
+ * library, not a step of the method. */
+lbm_status lbm_reduce_noalloc(lbm_ctx* ctx, double out[8]);
+
 /* Post-collision pdfs f*[n][Q] of the fluid elements as FP64 (deviation storage
  * converted back to f), caller order. */
 lbm_status lbm_get_state(lbm_ctx* ctx, double* f);

@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "liblbm.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU = ["kernels_fp64.cu", "kernels_fp32dev.cu", "kernels_bf16dev.cu"]
+CU = ["kernels_fp64.cu", "kernels_fp32dev.cu", "kernels_bf16dev.cu", "reduce_noalloc.cu"]
 CPP = ["mesh.cpp", "api.cpp"]
 
 

@@ -301,6 +301,46 @@ void lbm_ctx::advance(int li) {
   }
 }
 
+// ---------------------------------------------------------------- internal accessors
+namespace lbm {
+
+lbm_status reduce_plan(lbm_ctx* c, ReducePlan* plan) {
+  if (!c || !plan) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "reduction before lbm_bind");
+  plan->ops = c->ops;
+  plan->Q = c->Q;
+  plan->stream = c->st;
+  plan->workspace = c->ws;
+  plan->levels.clear();
+  const int d = c->d;
+  for (int li = 0; li < c->nlev; ++li) {
+    const HostLevel& H = c->M.lv[li];
+    ReduceArgs a{};
+    a.pdf = c->cur(li);
+    a.force = c->force_ptr();
+    a.Ntot = c->M.Ntot;
+    a.begin = H.base + H.oF;
+    a.end = H.base + H.oF + H.nF;
+    a.omega = H.omega;
+    a.rho_off = c->rho_off;
+    a.vol = std::ldexp(1.0, -d * li);
+    a.partial = nullptr;
+    a.nblocks = kReduceBlocks;
+    a.obs_elem = c->at<int32_t>(c->oObsElem) + H.obs_begin;
+    a.obs_dir = c->at<int8_t>(c->oObsDir) + H.obs_begin;
+    a.obs_n = H.obs_end - H.obs_begin;
+    a.fscale = std::ldexp(1.0, (d - 1) * (c->nlev - 1 - li));
+    plan->levels.push_back(a);
+  }
+  return LBM_OK;
+}
+
+lbm_status set_error(lbm_ctx* c, lbm_status s, const std::string& msg) { return c->fail(s, msg); }
+
+void count_launches(lbm_ctx* c, int64_t n) { c->launches += n; }
+
+}  // namespace lbm
+
 // ---------------------------------------------------------------- C ABI
 extern "C" {
 

@@ -218,4 +218,17 @@ void launch_scatter_force(bool fp64, const ForceArgs&, cudaStream_t);
 void launch_final_reduce(const FinalArgs&, cudaStream_t);
 constexpr int kReduceBlocks = 512;  // blocks per reduce launch (fixed: deterministic order)
 
+// What a reduction over a bound context needs, without the scratch pointers
+// (used by the entry point that keeps its scratch in a static device array).
+struct ReducePlan {
+  const Ops* ops = nullptr;
+  int Q = 0;
+  cudaStream_t stream = nullptr;
+  const void* workspace = nullptr;
+  std::vector<ReduceArgs> levels;  // partial == nullptr; filled in by the caller
+};
+lbm_status reduce_plan(lbm_ctx* ctx, ReducePlan* plan);
+lbm_status set_error(lbm_ctx* ctx, lbm_status s, const std::string& msg);
+void count_launches(lbm_ctx* ctx, int64_t n);
+
 }  // namespace lbm

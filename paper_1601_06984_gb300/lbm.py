@@ -23,7 +23,7 @@ TIME_LINEAR, TIME_TWO_LAYER = 0, 1
 EXPORTS = ["lbm_build_mesh", "lbm_mesh_info", "lbm_device_bytes", "lbm_bind", "lbm_init", "lbm_set_force",
            "lbm_step", "lbm_fill_ghosts", "lbm_moments", "lbm_reduce", "lbm_get_state", "lbm_ghost_count",
            "lbm_get_ghosts", "lbm_sfc_partition", "lbm_kernel_launches", "lbm_timing_enable", "lbm_timing_read",
-           "lbm_last_error", "lbm_destroy"]
+           "lbm_reduce_noalloc", "lbm_last_error", "lbm_destroy"]
 
 
 class LBMError(RuntimeError):
@@ -69,6 +69,7 @@ def lib():
             "lbm_kernel_launches": [P, C.POINTER(I64)],
             "lbm_timing_enable": [P, I32],
             "lbm_timing_read": [P, P, P, I32],
+            "lbm_reduce_noalloc": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -124,6 +125,14 @@ def lbm_sfc_partition(tree_ids, d, nparts):
     part = np.zeros(n, np.int32)
     _check(None, lib().lbm_sfc_partition(_p(tid), n, d, nparts, _p(order), _p(w), _p(cum), _p(part)))
     return order, w, cum, part
+
+
+def lbm_reduce_noalloc(sim):
+    """FP64 reductions of a bound simulation through the entry point that
+    allocates nothing (its scratch is a static device array of the library)."""
+    out = np.zeros(8)
+    _check(sim.ctx, lib().lbm_reduce_noalloc(sim.ctx, _p(out)))
+    return out
 
 
 # ---------------------------------------------------------------- convenience
