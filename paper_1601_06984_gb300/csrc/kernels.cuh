@@ -173,57 +173,174 @@ __device__ __forceinline__ void post_moments(const R* g, R omega, R rho_off, con
 }
 
 // ----------------------------------------------------------------- stream + collide
+// Tuning knobs of the hot kernel (compile-time; the defaults are the measured
+// best on GB300).  LBM_SC_EPT: elements per thread; LBM_SC_BLOCK: threads per
+// block; LBM_SC_MINB: minimum resident blocks per SM for __launch_bounds__;
+// LBM_SC_STREAM: streaming (evict-first) hints on the use-once neighbour
+// indices and on the stores.
+#ifndef LBM_SC_EPT
+#define LBM_SC_EPT 1
+#endif
+#ifndef LBM_SC_BLOCK
+#define LBM_SC_BLOCK 256
+#endif
+#ifndef LBM_SC_MINB
+#define LBM_SC_MINB 4
+#endif
+#ifndef LBM_SC_STREAM
+#define LBM_SC_STREAM 1
+#endif
+
+__device__ __forceinline__ uint32_t ld_once(const uint32_t* p) {
+#if LBM_SC_STREAM
+  return __ldcs(p);
+#else
+  return __ldg(p);
+#endif
+}
+__device__ __forceinline__ void st_once(double* p, double v) {
+#if LBM_SC_STREAM
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
+__device__ __forceinline__ void st_once(float* p, float v) {
+#if LBM_SC_STREAM
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
+__device__ __forceinline__ void st_once(__nv_bfloat16* p, __nv_bfloat16 v) {
+#if LBM_SC_STREAM
+  __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(v));
+#else
+  *p = v;
+#endif
+}
+
+// BGK collision (Eq. bgk) of one element in place, with Guo forcing, using the
+// symmetry of each velocity pair (i, opp(i)): c.u and c.F change sign, so the
+// even part of f^eq (and of the forcing term) is shared and the odd part flips.
+template <int Q, class R, bool FORCE>
+__device__ __forceinline__ void bgk_collide(R (&g)[Q], R om, R rho_off, const R* F) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  R rp, j[3];
+  raw_moments<Q, R>(g, rp, j);
+  const R rho = rho_off + rp;
+  const R inv = R(1) / rho;
+  R u[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int b = 0; b < D; ++b) u[b] = (j[b] + (FORCE ? R(0.5) * F[b] : R(0))) * inv;
+  R usq = R(0), uF = R(0);
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    usq += u[b] * u[b];
+    if (FORCE) uF += u[b] * F[b];
+  }
+  const R base = rp - R(1.5) * rho * usq;  // even part without the (c.u)^2 term, per unit weight
+  const R fpre = FORCE ? (R(1) - R(0.5) * om) : R(0);
+  {
+    R geq0 = R(LT::w(0)) * base;
+    R gi = g[0] + om * (geq0 - g[0]);
+    if (FORCE) gi += fpre * R(LT::w(0)) * (-R(3) * uF);
+    g[0] = gi;
+  }
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    R cu = R(0), cF = R(0);
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      if (LT::c(i, b) > 0) {
+        cu += u[b];
+        if (FORCE) cF += F[b];
+      }
+      if (LT::c(i, b) < 0) {
+        cu -= u[b];
+        if (FORCE) cF -= F[b];
+      }
+    }
+    const R w = R(LT::w(i));
+    const R even = w * (base + R(4.5) * rho * cu * cu);
+    const R odd = w * R(3) * rho * cu;
+    R a = g[i] + om * (even + odd - g[i]);
+    R b = g[i + 1] + om * (even - odd - g[i + 1]);
+    if (FORCE) {
+      const R fe = fpre * w * (R(9) * cu * cF - R(3) * uF);
+      const R fo = fpre * w * R(3) * cF;
+      a += fe + fo;
+      b += fe - fo;
+    }
+    g[i] = a;
+    g[i + 1] = b;
+  }
+}
+
 // Pull streaming f_i(x) = f*_i(x - c_i) through the neighbour list (Sec. 2.1,
-// Eq. lbe) fused with the BGK collision (Eq. bgk) and Guo forcing.
-template <int Q, class S, bool FORCE>
-__global__ void __launch_bounds__(256) k_stream_collide(const StreamCollideArgs a) {
+// Eq. lbe) fused with the BGK collision (Eq. bgk).  Every thread first issues
+// all neighbour-index loads, then all pdf gathers (branch-free: codes other than
+// a plain pull read the element's own opposite slot, which is the bounce-back
+// value), and patches the rare inlet / outlet values afterwards, so that up to
+// 2(Q-1) independent loads per element are in flight.
+template <int Q, class S, bool FORCE, int EPT>
+__global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(const StreamCollideArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
-  const int64_t e = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.end) return;
+  const int64_t e0 = a.begin + (int64_t)blockIdx.x * (LBM_SC_BLOCK * EPT) + threadIdx.x;
   const S* __restrict__ src = static_cast<const S*>(a.src);
   S* __restrict__ dst = static_cast<S*>(a.dst);
   const uint32_t* __restrict__ nbr = a.nbr;
   const size_t N = (size_t)a.Ntot;
-  R g[Q];
-  g[0] = Sto<S>::ld(src + e);
+  uint32_t nb[EPT][Q - 1];
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const uint32_t nb = __ldg(nbr + (size_t)(i - 1) * N + e);
-    R v;
-    if (nb < NB_FLAG30) {
-      v = Sto<S>::ld(src + (size_t)i * N + nb);
-    } else if (nb & NB_BOUNCE) {
-      v = Sto<S>::ld(src + (size_t)opp(i) * N + e);
-      if (nb & NB_FLAG30) v += R(a.inlet[i]);
-    } else {
-      v = static_cast<const R*>(a.side)[nb & NB_INDEX];
+  for (int k = 0; k < EPT; ++k) {
+    const int64_t e = e0 + k * LBM_SC_BLOCK;
+    if (e < a.end) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i) nb[k][i - 1] = ld_once(nbr + (size_t)(i - 1) * N + e);
     }
-    g[i] = v;
   }
-  R F[3] = {R(0), R(0), R(0)};
-  if (FORCE) {
-    const R* __restrict__ fp = static_cast<const R*>(a.force);
+  R g[EPT][Q];
 #pragma unroll
-    for (int b = 0; b < D; ++b) F[b] = fp[(size_t)b * N + e];
+  for (int k = 0; k < EPT; ++k) {
+    const int64_t e = e0 + k * LBM_SC_BLOCK;
+    if (e < a.end) {
+      g[k][0] = Sto<S>::ld(src + e);
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const uint32_t n = nb[k][i - 1];
+        const size_t idx = n < NB_FLAG30 ? (size_t)i * N + n : (size_t)opp(i) * N + (size_t)e;
+        g[k][i] = Sto<S>::ld(src + idx);
+      }
+    }
   }
-  R rp, j[3];
-  raw_moments<Q, R>(g, rp, j);
-  const R rho = R(a.rho_off) + rp;
-  const R inv = R(1) / rho;
-  R u[3] = {R(0), R(0), R(0)};
 #pragma unroll
-  for (int b = 0; b < D; ++b) u[b] = (j[b] + R(0.5) * F[b]) * inv;
-  R usq = R(0);
+  for (int k = 0; k < EPT; ++k) {
+    const int64_t e = e0 + k * LBM_SC_BLOCK;
+    if (e >= a.end) continue;
 #pragma unroll
-  for (int b = 0; b < D; ++b) usq += u[b] * u[b];
-  const R om = R(a.omega);
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t n = nb[k][i - 1];
+      if (n >= NB_FLAG30) {
+        if (n & NB_BOUNCE) {
+          if (n & NB_FLAG30) g[k][i] += R(a.inlet[i]);
+        } else {
+          g[k][i] = static_cast<const R*>(a.side)[n & NB_INDEX];
+        }
+      }
+    }
+    R F[3] = {R(0), R(0), R(0)};
+    if (FORCE) {
+      const R* __restrict__ fp = static_cast<const R*>(a.force);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    R gi = g[i] - om * (g[i] - geq<Q, R>(i, rp, rho, u, usq));
-    if (FORCE) gi += guo<Q, R>(i, om, u, F);
-    dst[(size_t)i * N + e] = Sto<S>::cv(gi);
+      for (int b = 0; b < D; ++b) F[b] = fp[(size_t)b * N + e];
+    }
+    bgk_collide<Q, R, FORCE>(g[k], R(a.omega), R(a.rho_off), F);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_once(dst + (size_t)i * N + e, Sto<S>::cv(g[k][i]));
   }
 }
 
@@ -660,13 +777,14 @@ struct Launch {
   static void stream_collide(int Q, bool force, const StreamCollideArgs& a, cudaStream_t st) {
     const int64_t n = a.end - a.begin;
     if (n <= 0) return;
-    const unsigned g = blocks_for(n, 256);
+    constexpr int EPT = LBM_SC_EPT;
+    const unsigned g = blocks_for(n, LBM_SC_BLOCK * EPT);
     if (Q == 9) {
-      if (force) k_stream_collide<9, S, true><<<g, 256, 0, st>>>(a);
-      else k_stream_collide<9, S, false><<<g, 256, 0, st>>>(a);
+      if (force) k_stream_collide<9, S, true, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+      else k_stream_collide<9, S, false, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
     } else {
-      if (force) k_stream_collide<19, S, true><<<g, 256, 0, st>>>(a);
-      else k_stream_collide<19, S, false><<<g, 256, 0, st>>>(a);
+      if (force) k_stream_collide<19, S, true, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+      else k_stream_collide<19, S, false, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
     }
   }
   static void outlet(int Q, const OutletArgs& a, cudaStream_t st) {
