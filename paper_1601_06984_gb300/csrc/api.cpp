@@ -122,7 +122,7 @@ struct lbm_ctx {
   void layout();
   // driver pieces
   void fill_gff(int li);
-  void source_moments(int li, size_t mom_off);
+  void source_moments(int li, size_t mom_off, size_t prev_off = 0);
   void fill_gfc(int li_fine, bool two_times);
   void stream_collide(int li);
   void advance(int li);
@@ -143,7 +143,7 @@ void lbm_ctx::layout() {
   oNbr = take((size_t)(Q - 1) * N * 4);
   oF = p.use_force ? take((size_t)d * N * cb) : 0;
   ld.assign(nlev, LevelDev());
-  const size_t M_ = 1 + d + nS + Q;
+  const size_t M_ = kMomStride;
   for (int li = 0; li < nlev; ++li) {
     const HostLevel& H = m.lv[li];
     LevelDev& L = ld[li];
@@ -195,13 +195,14 @@ void lbm_ctx::fill_gff(int li) {
   ++launches;
 }
 
-void lbm_ctx::source_moments(int li, size_t mom_off) {
+void lbm_ctx::source_moments(int li, size_t mom_off, size_t prev_off) {
   if (ld[li].nsrc == 0) return;
   MomentsArgs a{};
   a.src = cur(li);
   a.force = force_ptr();
   a.elem = at<int32_t>(ld[li].src_elem);
   a.mom = at(mom_off);
+  a.prev = prev_off ? at(prev_off) : nullptr;
   a.Ntot = M.Ntot;
   a.nsrc = ld[li].nsrc;
   a.omega = M.lv[li].omega;
@@ -215,8 +216,7 @@ void lbm_ctx::fill_gfc(int lf, bool two_times) {
   if (H.nC == 0) return;
   const int lc = lf - 1;
   GfcArgs a{};
-  a.momA = at(ld[lc].momA);
-  a.momB = two_times ? at(ld[lc].momB) : nullptr;
+  a.mom = two_times ? at(ld[lc].momB) : at(ld[lc].momA);
   a.nsrc = ld[lc].nsrc;
   a.gsrc = at<int32_t>(ld[lf].gfc_src);
   a.oct = at<uint8_t>(ld[lf].gfc_oct);
@@ -294,7 +294,8 @@ void lbm_ctx::advance(int li) {
   if (has_finer) {
     advance(li + 1);
     if (p.time_mode == LBM_TIME_LINEAR) {
-      source_moments(li, ld[li].momB);
+      // source moments at t+1/2: mean of those at t (momA) and at t+1
+      source_moments(li, ld[li].momB, ld[li].momA);
       fill_gfc(li + 1, true);
     }
     advance(li + 1);

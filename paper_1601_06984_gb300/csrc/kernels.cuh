@@ -392,12 +392,51 @@ __global__ void k_outlet(const OutletArgs a) {
 }
 
 // ----------------------------------------------------------------- GFC source moments
+// Record of one source (compute type, kMomStride values, 16-byte aligned
+// groups): f^neq[Q] padded to a multiple of 4, then rho - rho_off, u[D], S[nS],
+// padding.  Vector loads/stores move a record in 8 (float) or 16 (double) pieces.
+template <int Q>
+struct RecLayout {
+  static constexpr int D = Lat<Q>::D, NS = Lat<Q>::NS;
+  static constexpr int FN = 0;
+  static constexpr int RP = (Q + 3) / 4 * 4;
+  static constexpr int U = RP + 1;
+  static constexpr int SS = U + D;
+  static constexpr int END = SS + NS;
+  static_assert(END <= kMomStride, "moment record too long");
+};
+
+__device__ __forceinline__ void ld4(const float* p, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* o) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = b.x;
+  o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // Interpolation step 1 (Sec. 2.2): density, velocity, strain rate and f^neq of
-// every coarse element that feeds a GhostFromCoarser, into mom[M][nsrc].
+// every coarse element that feeds a GhostFromCoarser, one record per source.
+// With prev set, the record is the mean of prev and the moments now (the
+// source moments at t+1/2 of the linear-in-time mode).
 template <int Q, class S>
-__global__ void k_source_moments(const MomentsArgs a) {
+__global__ void __launch_bounds__(128) k_source_moments(const MomentsArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
+  using RL = RecLayout<Q>;
   constexpr int D = LT::D, NS = LT::NS;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.nsrc) return;
@@ -411,17 +450,31 @@ __global__ void k_source_moments(const MomentsArgs a) {
   if (a.force)
 #pragma unroll
     for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(a.force)[(size_t)b * N + e];
+  R rec[kMomStride];
+#pragma unroll
+  for (int f = 0; f < kMomStride; ++f) rec[f] = R(0);
   R rp, u[3], fneq[Q], Sv[NS];
   post_moments<Q, R, true>(g, R(a.omega), R(a.rho_off), F, rp, u, fneq, Sv);
-  R* m = static_cast<R*>(a.mom);
-  const size_t ns = (size_t)a.nsrc;
-  m[k] = rp;
 #pragma unroll
-  for (int b = 0; b < D; ++b) m[(1 + b) * ns + k] = u[b];
+  for (int q = 0; q < Q; ++q) rec[RL::FN + q] = fneq[q];
+  rec[RL::RP] = rp;
 #pragma unroll
-  for (int s = 0; s < NS; ++s) m[(1 + D + s) * ns + k] = Sv[s];
+  for (int b = 0; b < D; ++b) rec[RL::U + b] = u[b];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) m[(1 + D + NS + q) * ns + k] = fneq[q];
+  for (int s = 0; s < NS; ++s) rec[RL::SS + s] = Sv[s];
+  R* out = static_cast<R*>(a.mom) + (size_t)k * kMomStride;
+  const R* prev = a.prev ? static_cast<const R*>(a.prev) + (size_t)k * kMomStride : nullptr;
+#pragma unroll
+  for (int f = 0; f < kMomStride; f += 4) {
+    if (f >= RL::END) break;
+    if (prev) {
+      R pv[4];
+      ld4(prev + f, pv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rec[f + c] = R(0.5) * (pv[c] + rec[f + c]);
+    }
+    st4(out + f, rec + f);
+  }
 }
 
 // ----------------------------------------------------------------- GhostFromCoarser
@@ -439,36 +492,38 @@ __global__ void k_source_moments(const MomentsArgs a) {
 // rescaled by omega_c / (m omega_f), and f = f^eq + (1 - omega_f) f^neq is
 // stored as the ghost's post-collision state.
 template <int Q, class S>
-__global__ void k_fill_gfc(const GfcArgs a) {
+__global__ void __launch_bounds__(128) k_fill_gfc(const GfcArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
+  using RL = RecLayout<Q>;
   constexpr int D = LT::D, NS = LT::NS;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.ng) return;
-  const R* __restrict__ mA = static_cast<const R*>(a.momA);
-  const R* __restrict__ mB = static_cast<const R*>(a.momB);
-  const size_t ns = (size_t)a.nsrc;
-  int32_t sp[4];
+  const R* __restrict__ mom = static_cast<const R*>(a.mom);
+  const R* rec[4];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) sp[s] = a.gsrc[(size_t)s * a.ng + k];
-  auto mom = [&](int field, int s) -> R {
-    const size_t o = (size_t)field * ns + sp[s];
-    return mB ? R(0.5) * (mA[o] + mB[o]) : mA[o];
-  };
+  for (int s = 0; s < 4; ++s) rec[s] = mom + (size_t)a.gsrc[(size_t)s * a.ng + k] * kMomStride;
   const uint8_t oct = a.oct[k];
   R sg[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) sg[b] = ((oct >> b) & 1) ? R(1) : R(-1);
-  // local-frame velocity and strain rate of the sources
-  R ul[4][3], Sl[4][NS];
+  // local-frame velocity and strain rate of the sources (vector loads of the
+  // record tail: rho, u, S)
+  R ul[4][3], Sl[4][NS], rps[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
+    R h[kMomStride - RL::RP];
 #pragma unroll
-    for (int b = 0; b < D; ++b) ul[s][b] = sg[b] * mom(1 + b, s);
+    for (int f = RL::RP; f < kMomStride; f += 4)
+      if (f < RL::END) ld4(rec[s] + f, h + (f - RL::RP));
+    rps[s] = h[0];
+#pragma unroll
+    for (int b = 0; b < D; ++b) ul[s][b] = sg[b] * h[RL::U - RL::RP + b];
 #pragma unroll
     for (int b = 0; b < D; ++b)
 #pragma unroll
-      for (int c = b; c < D; ++c) Sl[s][sidx<D>(b, c)] = sg[b] * sg[c] * mom(1 + D + sidx<D>(b, c), s);
+      for (int c = b; c < D; ++c)
+        Sl[s][sidx<D>(b, c)] = sg[b] * sg[c] * h[RL::SS - RL::RP + sidx<D>(b, c)];
   }
   R uloc[3] = {R(0), R(0), R(0)};
   if (D == 3) {
@@ -505,7 +560,7 @@ __global__ void k_fill_gfc(const GfcArgs a) {
   const R lw1 = D == 3 ? R(0.125) : R(0.1875);
   const R lw2 = D == 3 ? R(0.125) : R(0.1875);
   const R lw3 = D == 3 ? R(0.125) : R(0.0625);
-  const R rp = lw0 * mom(0, 0) + lw1 * mom(0, 1) + lw2 * mom(0, 2) + lw3 * mom(0, 3);
+  const R rp = lw0 * rps[0] + lw1 * rps[1] + lw2 * rps[2] + lw3 * rps[3];
   const R rho = R(a.rho_off) + rp;
   const R wf = R(a.omega_f);
   const R scale = (R(1) - wf) * R(a.omega_c) / (R(2) * wf);
@@ -513,10 +568,20 @@ __global__ void k_fill_gfc(const GfcArgs a) {
   const size_t N = (size_t)a.Ntot;
   const int64_t e = a.dest0 + k;
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int fld = 1 + D + NS + q;
-    const R fn = lw0 * mom(fld, 0) + lw1 * mom(fld, 1) + lw2 * mom(fld, 2) + lw3 * mom(fld, 3);
-    dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rp, rho, u, usq) + scale * fn);
+  for (int q0 = 0; q0 < Q; q0 += 4) {
+    R f0[4], f1[4], f2[4], f3[4];
+    ld4(rec[0] + RL::FN + q0, f0);
+    ld4(rec[1] + RL::FN + q0, f1);
+    ld4(rec[2] + RL::FN + q0, f2);
+    ld4(rec[3] + RL::FN + q0, f3);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int q = q0 + c;
+      if (q < Q) {
+        const R fn = lw0 * f0[c] + lw1 * f1[c] + lw2 * f2[c] + lw3 * f3[c];
+        dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rp, rho, u, usq) + scale * fn);
+      }
+    }
   }
 }
 
@@ -527,27 +592,28 @@ __global__ void k_fill_gfc(const GfcArgs a) {
 // (1/32) lap u, with lap u_a = 2 d_c S_ac - d_a S_cc from the children's strain
 // rates (differences across the children's cube).  f^neq is rescaled by
 // m omega_f / omega_c; f = f^eq + (1 - omega_c) f^neq.
+// One group of 2^d consecutive lanes per ghost: lane b loads child b (siblings
+// are contiguous, so the group's loads are coalesced), and the sums over the
+// children are butterfly shuffles inside the group.
 template <int Q, class S>
-__global__ void k_fill_gff(const GffArgs a) {
+__global__ void __launch_bounds__(256) k_fill_gff(const GffArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D, NS = LT::NS, NCH = 1 << D;
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.ng) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t k = t / NCH;
+  const int b = (int)(t % NCH);
+  const bool active = k < a.ng;
   const S* __restrict__ src = static_cast<const S*>(a.src_fine);
   const size_t N = (size_t)a.Ntot;
-  const int64_t c0 = a.child0[k];
   const R wf = R(a.omega_f), rho_off = R(a.rho_off);
-  R rps = R(0), us[3] = {R(0), R(0), R(0)}, fns[Q], dS[3][NS];
+  R rp = R(0), u[3] = {R(0), R(0), R(0)}, fneq[Q], Sv[NS];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) fns[q] = R(0);
+  for (int q = 0; q < Q; ++q) fneq[q] = R(0);
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int s = 0; s < NS; ++s) dS[c][s] = R(0);
-#pragma unroll 1
-  for (int b = 0; b < NCH; ++b) {
-    const int64_t e = c0 + b;
+  for (int s = 0; s < NS; ++s) Sv[s] = R(0);
+  if (active) {
+    const int64_t e = (int64_t)a.child0[k] + b;
     R g[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(src + (size_t)q * N + e);
@@ -555,42 +621,54 @@ __global__ void k_fill_gff(const GffArgs a) {
     if (a.force)
 #pragma unroll
       for (int c = 0; c < D; ++c) F[c] = static_cast<const R*>(a.force)[(size_t)c * N + e];
-    R rp, u[3], fneq[Q], Sv[NS];
     post_moments<Q, R, true>(g, wf, rho_off, F, rp, u, fneq, Sv);
-    rps += rp;
-#pragma unroll
-    for (int c = 0; c < D; ++c) us[c] += u[c];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) fns[q] += fneq[q];
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const R sgn = ((b >> c) & 1) ? R(1) : R(-1);
-#pragma unroll
-      for (int s = 0; s < NS; ++s) dS[c][s] += sgn * Sv[s];
-    }
   }
+  // signed strain rates for the derivatives across the children's cube
+  R dS[3][NS];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const R sgn = ((b >> c) & 1) ? R(1) : R(-1);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dS[c][s] = sgn * Sv[s];
+  }
+  // butterfly sums over the NCH lanes of the group (all lanes take part)
+#pragma unroll
+  for (int o = 1; o < NCH; o <<= 1) {
+    rp += __shfl_xor_sync(0xffffffffu, rp, o);
+#pragma unroll
+    for (int c = 0; c < D; ++c) u[c] += __shfl_xor_sync(0xffffffffu, u[c], o);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) fneq[q] += __shfl_xor_sync(0xffffffffu, fneq[q], o);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) dS[c][s] += __shfl_xor_sync(0xffffffffu, dS[c][s], o);
+  }
+  if (!active) return;
   const R inv = R(1) / R(NCH);
   // d_c S (coarse units): S_coarse = 2 S_fine; difference of the two half-cubes
   // over a distance of 1/2 coarse cell -> factor 2 * 2^{2-D}
   const R dfac = R(2) * R(D == 3 ? 0.5 : 1.0);
-  const R rp = rps * inv;
-  R u[3] = {R(0), R(0), R(0)};
+  const R rpm = rp * inv;
+  R uP[3] = {R(0), R(0), R(0)};
   R usq = R(0);
 #pragma unroll
   for (int aa = 0; aa < D; ++aa) {
     R lap = R(0);
 #pragma unroll
     for (int c = 0; c < D; ++c) lap += dfac * (R(2) * dS[c][sidx<D>(aa, c)] - dS[aa][sidx<D>(c, c)]);
-    u[aa] = us[aa] * inv - lap * R(1.0 / 32.0);
-    usq += u[aa] * u[aa];
+    uP[aa] = u[aa] * inv - lap * R(1.0 / 32.0);
+    usq += uP[aa] * uP[aa];
   }
   const R wc = R(a.omega_c);
-  const R rho = rho_off + rp;
+  const R rho = rho_off + rpm;
   const R scale = (R(1) - wc) * R(2) * wf / wc * inv;
   S* __restrict__ dst = static_cast<S*>(a.dst);
   const int64_t e = k < a.n_inner ? a.dest0 + k : a.dest_outer + (k - a.n_inner);
+  // the group's lanes share the Q stores
 #pragma unroll
-  for (int q = 0; q < Q; ++q) dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rp, rho, u, usq) + scale * fns[q]);
+  for (int q = 0; q < Q; ++q)
+    if (q % NCH == b) dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rpm, rho, uP, usq) + scale * fneq[q]);
 }
 
 // ----------------------------------------------------------------- set-up / output (FP64 arithmetic)
@@ -805,8 +883,8 @@ struct Launch {
   }
   static void fill_gff(int Q, const GffArgs& a, cudaStream_t st) {
     if (a.ng <= 0) return;
-    if (Q == 9) k_fill_gff<9, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a);
-    else k_fill_gff<19, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a);
+    if (Q == 9) k_fill_gff<9, S><<<blocks_for(a.ng * 4, 256), 256, 0, st>>>(a);
+    else k_fill_gff<19, S><<<blocks_for(a.ng * 8, 256), 256, 0, st>>>(a);
   }
   static void fill_rest(int Q, const FillArgs& a, cudaStream_t st) {
     if (Q == 9) k_fill_rest<9, S><<<blocks_for(a.Ntot, 256), 256, 0, st>>>(a);

@@ -98,18 +98,21 @@ struct OutletArgs {
   double omega, rho_off, rho0;
 };
 
-struct MomentsArgs {  // GFC source moments
+// GFC source moments: one record of kMomStride values per source (compute
+// type): rho - rho_off, u[d], S[nS], f^neq[Q], zero padding.
+constexpr int kMomStride = 32;
+struct MomentsArgs {
   const void* src;
   const void* force;
   const int32_t* elem;
-  void* mom;  // [M][nsrc] compute type, M = 1 + d + nS + Q
+  void* mom;         // [nsrc][kMomStride]
+  const void* prev;  // if set: mom = (prev + moments now) / 2 (mean of two time levels)
   int64_t Ntot, nsrc;
   double omega, rho_off;
 };
 
 struct GfcArgs {
-  const void* momA;
-  const void* momB;  // null unless averaging two time levels
+  const void* mom;       // [nsrc][kMomStride] source records
   int64_t nsrc;
   const int32_t* gsrc;   // [4][ng]
   const uint8_t* oct;    // [ng]
