@@ -135,6 +135,24 @@ def gpu_uuid(dev):
         return None
 
 
+def stream_collide_traffic():
+    """DRAM bytes per element update of the finest-level stream-collide from the
+    committed ncu capture, if that kernel's source is unchanged since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "stream_collide_fp32_sphere.json")) as fh:
+            rec = json.load(fh)
+        with open(os.path.join(ROOT, "paper_1601_06984_gb300", "csrc", "kernels.cuh")) as fh:
+            src = fh.read()
+        a = src.index("// ----------------------------------------------------------------- physics")
+        b = src.index("// ----------------------------------------------------------------- outlet values")
+        if hashlib.sha256(src[a:b].encode()).hexdigest()[:16] != rec["kernel_source_sha256_16"]:
+            return None
+        return float(rec["dram_bytes_per_unit"])
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -275,6 +293,7 @@ def main():
     mesh, Q, om, uin, fields, desc = make_workload(args.workload)
     U = mesh.updates_per_coarse_step()
     peak, peak_src = measured_peaks()
+    traffic_per_unit = stream_collide_traffic()
 
     clk = Clocks(uuid=gpu_uuid(device), index=local)
     sim, r = run_gpu(mesh, Q, om, uin, fields, lbm.FP32DEV, K, W_, device, dist,
@@ -345,7 +364,10 @@ def main():
                        time_mode="linear", parallelism="replicas" if world > 1 else "single GPU",
                        l2="inputs larger than L2 (%.1f GB workspace)" % r["device_gb"]),
         "roofline": {"bound": "hbm", "achieved": r["finest_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": r["finest_gbs"] / peak, "traffic": None,
+                     "frac": r["finest_gbs"] / peak,
+                     "traffic": None if traffic_per_unit is None else traffic_per_unit * r["finest_units"],
+                     "traffic_source": "ncu capture on the half-scale sphere scaled by units "
+                                       "(profiles/stream_collide_fp32_sphere.md)",
                      "kernel": "k_stream_collide<19,float> on the finest level",
                      "units_per_launch": r["finest_units"], "bytes_per_unit": r["bytes_per_update"],
                      "avg_launch_ms": r["finest_launch_ms"], "peak_source": peak_src},
