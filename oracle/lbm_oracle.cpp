@@ -190,6 +190,7 @@ struct Sim {
   int bc[6] = {0, 0, 0, 0, 0, 0};
   double rho0 = 1.0;
   double uin[3] = {0.0, 0.0, 0.0};
+  T uinT[3] = {T(0.0), T(0.0), T(0.0)};  // inlet velocity carried in T (tangent for the dual twin)
   bool use_force = false;
   T omega_c = T(1.0);
   int Lmin = 0, Lmax = 0;
@@ -552,9 +553,9 @@ struct Sim {
         return e.f[ib];
       case LK_INLET: {
         // velocity bounce-back (Ladd): f_i = f*_ib + 2 w_i rho0 (c_i.U) / c_s^2
-        double cu = 0.0;
-        for (int a = 0; a < d; ++a) cu += lat.c[i][a] * uin[a];
-        return e.f[ib] + T(6.0 * lat.w[i] * rho0 * cu);
+        T cu = T(0.0);
+        for (int a = 0; a < d; ++a) cu += T((double)lat.c[i][a]) * uinT[a];
+        return e.f[ib] + T(6.0 * lat.w[i] * rho0) * cu;
       }
       case LK_OUT_NORMAL: {
         // pressure-corrected outlet along the normal: f^eq_i(rho0, u) + f^neq_ib
@@ -861,7 +862,7 @@ struct Handle {
 
 template <class T>
 Sim<T>* create_sim(int stencil, int time_mode, const int* extent, const int* bc, double omega_c,
-                   double omega_dot, double rho0, const double* u_in, int use_force,
+                   double omega_dot, double rho0, const double* u_in, const double* u_in_dot, int use_force,
                    const int64_t* tree_ids, int64_t n, char* err, int errlen) {
   auto* s = new Sim<T>();
   auto bail = [&](const char* m) -> Sim<T>* {
@@ -884,7 +885,11 @@ Sim<T>* create_sim(int stencil, int time_mode, const int* extent, const int* bc,
   s->omega_c = T(omega_c);
   if constexpr (std::is_same<T, Dual>::value) s->omega_c = Dual(omega_c, omega_dot);
   s->rho0 = rho0;
-  for (int a = 0; a < 3; ++a) s->uin[a] = u_in ? u_in[a] : 0.0;
+  for (int a = 0; a < 3; ++a) {
+    s->uin[a] = u_in ? u_in[a] : 0.0;
+    s->uinT[a] = T(s->uin[a]);
+    if constexpr (std::is_same<T, Dual>::value) s->uinT[a] = Dual(s->uin[a], u_in_dot ? u_in_dot[a] : 0.0);
+  }
   s->use_force = use_force != 0;
   if (!s->build(tree_ids, n)) return bail(s->err.c_str());
   for (auto& l : s->lv)
@@ -966,7 +971,7 @@ extern "C" {
 void* orc_create(int stencil, int time_mode, const int* extent, const int* bc, double omega_c,
                  double rho0, const double* u_in, int use_force, const int64_t* tree_ids, int64_t n,
                  char* err, int errlen) {
-  return create_sim<double>(stencil, time_mode, extent, bc, omega_c, 0.0, rho0, u_in, use_force,
+  return create_sim<double>(stencil, time_mode, extent, bc, omega_c, 0.0, rho0, u_in, nullptr, use_force,
                             tree_ids, n, err, errlen);
 }
 
@@ -1110,13 +1115,14 @@ int orc_compact_velocity(int d, const int* s, const double* u4, const double* S4
 
 // ---------------------------------------------------------- dual-number twin
 // Same oracle with every value carrying a tangent: omega_c has tangent
-// omega_dot and the body force field has tangent F_dot, so every output's
-// tangent is its directional derivative along (F_dot, omega_dot).
+// omega_dot, the inlet velocity u_in_dot and the body force field F_dot, so
+// every output's tangent is its directional derivative along
+// (F_dot, omega_dot, u_in_dot).
 void* orc_dual_create(int stencil, int time_mode, const int* extent, const int* bc, double omega_c,
-                      double omega_dot, double rho0, const double* u_in, int use_force,
-                      const int64_t* tree_ids, int64_t n, char* err, int errlen) {
-  return create_sim<Dual>(stencil, time_mode, extent, bc, omega_c, omega_dot, rho0, u_in, use_force,
-                          tree_ids, n, err, errlen);
+                      double omega_dot, double rho0, const double* u_in, const double* u_in_dot,
+                      int use_force, const int64_t* tree_ids, int64_t n, char* err, int errlen) {
+  return create_sim<Dual>(stencil, time_mode, extent, bc, omega_c, omega_dot, rho0, u_in, u_in_dot,
+                          use_force, tree_ids, n, err, errlen);
 }
 
 void orc_dual_destroy(void* h) { delete static_cast<Sim<Dual>*>(h); }

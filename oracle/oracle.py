@@ -40,7 +40,7 @@ def lib():
         L.orc_create.restype = P
         L.orc_create.argtypes = [I, I, P, P, D, D, P, I, P, I64, C.c_char_p, I]
         L.orc_dual_create.restype = P
-        L.orc_dual_create.argtypes = [I, I, P, P, D, D, D, P, I, P, I64, C.c_char_p, I]
+        L.orc_dual_create.argtypes = [I, I, P, P, D, D, D, P, P, I, P, I64, C.c_char_p, I]
         L.orc_destroy.argtypes = [P]
         L.orc_dual_destroy.argtypes = [P]
         L.orc_counts.argtypes = [P, P, I]
@@ -88,7 +88,7 @@ class Oracle:
     carries a tangent (forward-mode derivative along omega_dot and F_dot)."""
 
     def __init__(self, mesh, stencil, omega_c, time_mode=0, rho0=1.0, u_in=(0.0, 0.0, 0.0),
-                 use_force=False, dual=False, omega_dot=0.0):
+                 use_force=False, dual=False, omega_dot=0.0, u_in_dot=(0.0, 0.0, 0.0)):
         L = lib()
         self.mesh, self.stencil, self.dual = mesh, stencil, dual
         self.d = 2 if stencil == 9 else 3
@@ -98,12 +98,13 @@ class Oracle:
         self._keep = [np.ascontiguousarray(mesh.tree_ids, dtype=np.int64),
                       np.array(list(mesh.extent) + [1] * (3 - len(mesh.extent)), dtype=np.int32),
                       np.array(list(mesh.bc) + [0] * (6 - len(mesh.bc)), dtype=np.int32),
-                      np.array(list(u_in) + [0.0] * (3 - len(u_in)), dtype=np.float64)]
-        tid, ext, bc, uin = self._keep
+                      np.array(list(u_in) + [0.0] * (3 - len(u_in)), dtype=np.float64),
+                      np.array(list(u_in_dot) + [0.0] * (3 - len(u_in_dot)), dtype=np.float64)]
+        tid, ext, bc, uin, uin_dot = self._keep
         err = C.create_string_buffer(512)
         if dual:
             h = L.orc_dual_create(stencil, time_mode, _p(ext), _p(bc), omega_c, omega_dot, rho0, _p(uin),
-                                  int(use_force), _p(tid), self.n, err, 512)
+                                  _p(uin_dot), int(use_force), _p(tid), self.n, err, 512)
         else:
             h = L.orc_create(stencil, time_mode, _p(ext), _p(bc), omega_c, rho0, _p(uin), int(use_force),
                              _p(tid), self.n, err, 512)

@@ -438,3 +438,29 @@ def test_mesh_validation(oracle_mod):
     far = W.Mesh(2, (4, 4), (0,) * 4, W.tree_ids(np.array([[5, 5]]), 3, 2), np.array([3], np.int8),
                  np.array([[5, 5]]), 3)
     _raises(oracle_mod, far)
+
+
+def test_dual_inlet_tangent_matches_central_differences(oracle_mod):
+    """The dual twin's tangent of the kinetic energy along the inlet velocity
+    (Sec. 2.3 velocity bounce-back) equals a central difference of the plain
+    oracle."""
+    mesh = W.config_sphere_small()
+    om = W.omega_coarse_from_finest(1.6, 3)
+    U = np.array([0.04, 0.0, 0.0])
+    dU = np.array([1.0, 0.3, -0.2])
+    base = W.uniform_fields(mesh, 1.0, (0.04, 0.0, 0.0))
+
+    def J(h):
+        o = oracle_mod.Oracle(mesh, 19, om, u_in=tuple(U + h * dU))
+        o.init(*base)
+        o.step(2)
+        return o.reduce()[7]
+
+    h = 1e-5
+    fd = (J(h) - J(-h)) / (2 * h)
+    od = oracle_mod.Oracle(mesh, 19, om, u_in=tuple(U), dual=True, u_in_dot=tuple(dU))
+    od.init(*base)
+    od.step(2)
+    _, dot = od.reduce()
+    assert abs(fd) > 0
+    assert abs(dot[7] - fd) / abs(fd) < 1e-6
