@@ -196,6 +196,37 @@ lbm_status lbm_sfc_partition(const int64_t* tree_ids, int64_t n, int32_t d, int3
                              int64_t* order, int64_t* weights, int64_t* cumulative,
                              int32_t* part);
 
+/* Change the coarsest relaxation rate (finer levels follow Eq. fneq_scale) and,
+ * if u_in is not NULL, the inlet velocity, without rebuilding the mesh.  The
+ * state is kept. */
+lbm_status lbm_set_params(lbm_ctx* ctx, double omega_coarse, const double* u_in);
+
+/* Discrete adjoint of n_coarse coarse steps (reverse mode, hand-written
+ * kernels for every forward op: pull stream + BGK collide with Guo forcing,
+ * outlet values, GhostFromCoarser source moments and compact interpolation,
+ * GhostFromFiner restriction; Sec. 2.1-2.3 forward, the paper has no
+ * adjoint).  Starting from the current state it runs the n_coarse forward steps
+ * (the same arithmetic as lbm_step), evaluates the objective at the end,
+ *   objective 0: kinetic energy  sum_fluid vol rho |u|^2 / 2,
+ *   objective 1..d: obstacle force component (momentum exchange, as lbm_reduce),
+ * and returns J and its gradients with respect to the body-force field
+ * dJ_dF[n][d] (caller order, level lattice units), omega_coarse (dJ_domega) and
+ * u_in (dJ_duin[3]), all at fixed initial pdfs, and the gradient with respect to
+ * those initial post-collision pdfs dJ_df0[n][Q] (caller order; chain it with
+ * the derivative of whatever produced the initial state, e.g. the omega
+ * dependence of the lbm_init non-equilibrium part); any output may be NULL.
+ * Checkpoints: the state every K
+ * coarse steps; each segment is recomputed once, and every step once more while
+ * its op inputs are recorded.  adj_ws is a device workspace of
+ * lbm_adjoint_bytes(n_coarse, K) bytes owned by the caller.  Afterwards the
+ * simulation is at the final state, as after lbm_step(n_coarse).  The
+ * gradient with respect to F is that of the forced scheme (also when
+ * use_force is 0, where it is taken at F = 0). */
+lbm_status lbm_adjoint_bytes(lbm_ctx* ctx, int64_t n_coarse, int32_t K, uint64_t* bytes);
+lbm_status lbm_adjoint(lbm_ctx* ctx, int64_t n_coarse, int32_t K, int32_t objective, void* adj_ws,
+                       uint64_t bytes, double* J, double* dJ_dF, double* dJ_domega, double* dJ_duin,
+                       double* dJ_df0);
+
 /* Launches of library kernels enqueued by this context since it was bound. */
 lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
 

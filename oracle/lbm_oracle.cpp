@@ -1141,6 +1141,16 @@ int orc_dual_set_force(void* h, const double* F, const double* F_dot) {
   return 0;
 }
 
+// set the fluid pdfs f*[n][Q] (caller order) with tangents f_dot (NULL: zero)
+int orc_dual_set_f(void* h, const double* f, const double* f_dot) {
+  auto* s = static_cast<Sim<Dual>*>(h);
+  for (size_t k = 0; k < s->upos.size(); ++k) {
+    auto& e = s->lv[s->upos[k].first].e[s->upos[k].second];
+    for (int i = 0; i < s->Q; ++i) e.f[i] = Dual(f[k * s->Q + i], f_dot ? f_dot[k * s->Q + i] : 0.0);
+  }
+  return 0;
+}
+
 int orc_dual_step(void* h, int64_t n) {
   auto* s = static_cast<Sim<Dual>*>(h);
   for (int64_t k = 0; k < n; ++k) s->advance(0);

@@ -56,6 +56,7 @@ def lib():
         L.orc_moments.argtypes = [P, P, P, P]
         L.orc_get_f.argtypes = [P, P]
         L.orc_set_f.argtypes = [P, P]
+        L.orc_dual_set_f.argtypes = [P, P, P]
         L.orc_ghost_count.restype = I64
         L.orc_ghost_count.argtypes = [P]
         L.orc_ghosts.argtypes = [P, P, P]
@@ -160,9 +161,13 @@ class Oracle:
         lib().orc_get_f(self.h, _p(f))
         return f
 
-    def set_f(self, f):
+    def set_f(self, f, f_dot=None):
+        """Set the fluid pdfs (dual twin: with tangents f_dot, default zero)."""
         f = _f64(f, (self.n, self.Q))
-        lib().orc_set_f(self.h, _p(f))
+        if self.dual:
+            lib().orc_dual_set_f(self.h, _p(f), _p(_f64(f_dot, (self.n, self.Q))))
+        else:
+            lib().orc_set_f(self.h, _p(f))
 
     def ghosts(self):
         n = lib().orc_ghost_count(self.h)

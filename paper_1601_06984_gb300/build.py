@@ -16,8 +16,9 @@ OUT = os.path.join(HERE, "liblbm.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU = ["kernels_fp64.cu", "kernels_fp32dev.cu", "kernels_bf16dev.cu", "reduce_noalloc.cu"]
-CPP = ["mesh.cpp", "api.cpp"]
+CU = ["kernels_fp64.cu", "kernels_fp32dev.cu", "kernels_bf16dev.cu", "reduce_noalloc.cu",
+      "adjoint_fp64.cu", "adjoint_fp32dev.cu", "adjoint_bf16dev.cu"]
+CPP = ["mesh.cpp", "api.cpp", "adjoint.cpp"]
 
 
 def _cuda_home() -> str:
@@ -28,7 +29,8 @@ def _cuda_home() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in CU + CPP + ["kernels.cuh", "lbm_internal.h"]] + [
+    return [os.path.join(CSRC, f) for f in CU + CPP + ["kernels.cuh", "adjoint.cuh", "lbm_internal.h",
+                                                      "lbm_ctx.h"]] + [
         os.path.join(INCLUDE, "lbm.h")]
 
 

@@ -1,0 +1,765 @@
+// Discrete adjoint of the multilevel step (reverse mode, hand-written).
+//
+// Every forward kernel of the path has a reverse here: pull stream + BGK
+// collide (Sec. 2.1), the outlet values (Sec. 2.3), the GhostFromCoarser
+// source moments and compact interpolation and the GhostFromFiner restriction
+// (Sec. 2.2).  A reverse kernel reads the forward state the op saw (a snapshot),
+// consumes the adjoint of the op's outputs (and zeroes it: those slots were
+// overwritten by the op), and adds the transposed Jacobian times that adjoint
+// to the adjoint of the op's inputs.  Scatter targets are unique within one
+// launch (each pdf slot is pulled by exactly one element; each ghost has its
+// own children; each source element appears once), so plain read-modify-write
+// is race-free; the ghost-to-source sums of GhostFromCoarser go through a
+// transposed (CSR) list so that they are deterministic too.  Derivatives with
+// respect to the relaxation rates and the inlet velocity are summed per block
+// and then added in launch order (deterministic); body-force derivatives are
+// accumulated per element in FP64.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace lbm {
+namespace dev {
+
+// ----------------------------------------------------------------- reverse helpers
+// Reverse of g^eq_i(rp, rho = rho_off + rp, u) for all i, weighted by lam[i]:
+// adds to lam_rp and lam_u.
+template <int Q, class R>
+__device__ __forceinline__ void geq_rev(const R* lam, R rho, const R* u, R usq, R& lam_rp, R* lam_u) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R cu = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) cu += R(LT::c(i, a)) * u[a];
+    const R wl = R(LT::w(i)) * lam[i];
+    lam_rp += wl * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+    const R t = wl * rho;
+#pragma unroll
+    for (int a = 0; a < D; ++a) lam_u[a] += t * (R(3) * R(LT::c(i, a)) + R(9) * cu * R(LT::c(i, a)) - R(3) * u[a]);
+  }
+}
+
+// Reverse of the Guo term (1 - omega/2) w_i [3 (c_i.F - u.F) + 9 (c_i.u)(c_i.F)].
+template <int Q, class R>
+__device__ __forceinline__ void guo_rev(const R* lam, R om, const R* u, const R* F, R& lam_om, R* lam_u, R* lam_F) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const R pre = R(1) - R(0.5) * om;
+  R uF = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) uF += u[a] * F[a];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R cu = R(0), cF = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      cu += R(LT::c(i, a)) * u[a];
+      cF += R(LT::c(i, a)) * F[a];
+    }
+    const R wl = R(LT::w(i)) * lam[i];
+    lam_om += -R(0.5) * wl * (R(3) * (cF - uF) + R(9) * cu * cF);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const R ca = R(LT::c(i, a));
+      lam_u[a] += pre * wl * (-R(3) * F[a] + R(9) * ca * cF);
+      lam_F[a] += pre * wl * (R(3) * (ca - u[a]) + R(9) * cu * ca);
+    }
+  }
+}
+
+// Reverse of post_moments (stored post-collision pdfs -> rp, u, f^neq, S).
+// Inputs: the pdfs g, the adjoints of the outputs (lam_fneq is overwritten).
+// Outputs: lam_g (assigned), lam_F and lam_om (accumulated).
+template <int Q, class R>
+__device__ __forceinline__ void post_moments_rev(const R* g, R om, R rho_off, const R* F, R lam_rp_in,
+                                                 const R* lam_u_in, R* lam_fneq, const R* lam_S, R* lam_g,
+                                                 R* lam_F, R& lam_om) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D, NS = LT::NS;
+  R rp, j[3];
+  raw_moments<Q, R>(g, rp, j);
+  const R rho = rho_off + rp;
+  const R inv = R(1) / rho;
+  R u[3] = {R(0), R(0), R(0)};
+  R usq = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    u[a] = (j[a] - R(0.5) * F[a]) * inv;
+    usq += u[a] * u[a];
+  }
+  const R r1w = R(1) / (R(1) - om);
+  R fneq[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) fneq[i] = (g[i] - geq<Q, R>(i, rp, rho, u, usq) - guo<Q, R>(i, om, u, F)) * r1w;
+  const R pre = -R(1.5) * om * inv;
+  R lam_pre = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R add = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = a; b < D; ++b) {
+        const int cc = LT::c(i, a) * LT::c(i, b);
+        if (cc != 0) {
+          const R ls = lam_S[sidx<D>(a, b)];
+          add += R(cc) * ls;
+          lam_pre += R(cc) * ls * fneq[i];
+        }
+      }
+    lam_fneq[i] += pre * add;
+  }
+  R lam_rho = lam_pre * R(1.5) * om * inv * inv;
+  lam_om += lam_pre * (-R(1.5) * inv);
+  R lam_rp = lam_rp_in;
+  R lam_u[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int a = 0; a < D; ++a) lam_u[a] = lam_u_in[a];
+  R lam_q[Q];
+  R lam_r1w = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    lam_g[i] = lam_fneq[i] * r1w;
+    lam_q[i] = -lam_fneq[i] * r1w;
+    lam_r1w += lam_fneq[i] * fneq[i];  // fneq = (...) r1w, so d/dr1w = fneq / r1w
+  }
+  lam_om += lam_r1w * r1w;  // d r1w / d omega = r1w^2; times fneq/r1w gives fneq * r1w
+  guo_rev<Q, R>(lam_q, om, u, F, lam_om, lam_u, lam_F);
+  geq_rev<Q, R>(lam_q, rho, u, usq, lam_rp, lam_u);
+  R lam_j[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    lam_j[a] = lam_u[a] * inv;
+    lam_F[a] += -R(0.5) * lam_u[a] * inv;
+    lam_rho += -lam_u[a] * u[a] * inv;
+  }
+  lam_rp += lam_rho;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R v = lam_g[i] + lam_rp;
+#pragma unroll
+    for (int a = 0; a < D; ++a) v += R(LT::c(i, a)) * lam_j[a];
+    lam_g[i] = v;
+  }
+}
+
+// Reverse of the BGK collision with Guo forcing (u = (j + F/2) / rho).
+template <int Q, class R>
+__device__ __forceinline__ void bgk_rev(const R* g, R om, R rho_off, const R* F, const R* lam_out, R* lam_g,
+                                        R* lam_F, R& lam_om) {
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  R rp, j[3];
+  raw_moments<Q, R>(g, rp, j);
+  const R rho = rho_off + rp;
+  const R inv = R(1) / rho;
+  R u[3] = {R(0), R(0), R(0)};
+  R usq = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    u[a] = (j[a] + R(0.5) * F[a]) * inv;
+    usq += u[a] * u[a];
+  }
+  R lam_geq[Q];
+  R lam_rp = R(0);
+  R lam_u[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    lam_g[i] = (R(1) - om) * lam_out[i];
+    lam_geq[i] = om * lam_out[i];
+    lam_om += lam_out[i] * (geq<Q, R>(i, rp, rho, u, usq) - g[i]);
+  }
+  guo_rev<Q, R>(lam_out, om, u, F, lam_om, lam_u, lam_F);
+  geq_rev<Q, R>(lam_geq, rho, u, usq, lam_rp, lam_u);
+  R lam_j[3] = {R(0), R(0), R(0)};
+  R lam_rho = R(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    lam_j[a] = lam_u[a] * inv;
+    lam_F[a] += R(0.5) * lam_u[a] * inv;
+    lam_rho += -lam_u[a] * u[a] * inv;
+  }
+  lam_rp += lam_rho;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R v = lam_g[i] + lam_rp;
+#pragma unroll
+    for (int a = 0; a < D; ++a) v += R(LT::c(i, a)) * lam_j[a];
+    lam_g[i] = v;
+  }
+}
+
+template <class R, int NV>
+__device__ __forceinline__ void store_partials(R (&v)[NV], double* partial) {
+  double d[kPartCols];
+#pragma unroll
+  for (int c = 0; c < kPartCols; ++c) d[c] = c < NV ? (double)v[c] : 0.0;
+  block_sum_store<kPartCols>(d, partial + (size_t)blockIdx.x * kPartCols);
+}
+
+template <class R>
+__device__ __forceinline__ void add_force(double* lam_force, int64_t Ntot, int64_t e, const R* lF, int D) {
+  if (!lam_force) return;
+  for (int b = 0; b < D; ++b) lam_force[(size_t)b * Ntot + e] += (double)lF[b];
+}
+
+template <class S, class R>
+__device__ __forceinline__ void load_force(const void* force, int64_t Ntot, int64_t e, R* F, int D) {
+  F[0] = F[1] = F[2] = R(0);
+  if (force)
+    for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(force)[(size_t)b * Ntot + e];
+}
+
+// ----------------------------------------------------------------- objective seeds
+// Kinetic energy J = sum vol rho |u|^2 / 2 with rho u = j - F/2: dJ/dg_i =
+// vol (c_i.u - |u|^2/2), dJ/dF = -vol u / 2.  Obstacle force component k:
+// J = sum_links 2 fscale c_opp,k f*_opp  ->  dJ/dg_opp = 2 fscale c_opp,k.
+template <int Q, class S>
+__global__ void __launch_bounds__(256) k_adj_seed(const AdjSeedArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const S* __restrict__ x = static_cast<const S*>(a.c.fsrc);
+  R* lam = static_cast<R*>(a.c.lam_b);
+  const size_t N = (size_t)a.c.Ntot;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a.objective == 0) {
+    for (int64_t e = a.begin + t0; e < a.end; e += stride) {
+      R g[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(x + (size_t)q * N + e);
+      R F[3];
+      load_force<S, R>(a.c.force, a.c.Ntot, e, F, D);
+      R rp, j[3];
+      raw_moments<Q, R>(g, rp, j);
+      const R rho = R(a.c.rho_off) + rp;
+      R u[3] = {R(0), R(0), R(0)}, usq = R(0);
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        u[b] = (j[b] - R(0.5) * F[b]) / rho;
+        usq += u[b] * u[b];
+      }
+      const R vol = R(a.vol);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        R cu = R(0);
+#pragma unroll
+        for (int b = 0; b < D; ++b) cu += R(LT::c(q, b)) * u[b];
+        lam[(size_t)q * N + e] += vol * (cu - R(0.5) * usq);
+      }
+      R lF[3];
+#pragma unroll
+      for (int b = 0; b < D; ++b) lF[b] = -R(0.5) * vol * u[b];
+      add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
+    }
+  } else {
+    const int k = a.objective - 1;
+    for (int64_t l = t0; l < a.obs_n; l += stride) {
+      const int ib = opp(a.obs_dir[l]);
+      const int64_t e = a.obs_elem[l];
+      int cb = 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (q == ib) cb = LT::c(q, k < D ? k : 0);
+      if (k < D) lam[(size_t)ib * N + e] += R(2.0 * a.fscale) * R(cb);
+    }
+  }
+}
+
+// ----------------------------------------------------------------- stream + collide
+template <int Q, class S>
+__global__ void __launch_bounds__(256) k_adj_sc(const AdjSCArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const S* __restrict__ x = static_cast<const S*>(a.c.fsrc);
+  R* lam_out = static_cast<R*>(a.c.lam_a);
+  R* lam_in = static_cast<R*>(a.c.lam_b);
+  const size_t N = (size_t)a.c.Ntot;
+  const R om = R(a.omega), rho_off = R(a.c.rho_off);
+  R part[5] = {R(0), R(0), R(0), R(0), R(0)};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.end; e += stride) {
+    uint32_t nb[Q];
+    R g[Q];
+    nb[0] = (uint32_t)e;
+    g[0] = Sto<S>::ld(x + e);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t n = a.nbr[(size_t)(i - 1) * N + e];
+      nb[i] = n;
+      if (n < NB_FLAG30) {
+        g[i] = Sto<S>::ld(x + (size_t)i * N + n);
+      } else if (n & NB_BOUNCE) {
+        g[i] = Sto<S>::ld(x + (size_t)opp(i) * N + e);
+        if (n & NB_FLAG30) g[i] += R(a.inlet[i]);
+      } else {
+        g[i] = static_cast<const R*>(a.side_fwd)[n & NB_INDEX];
+      }
+    }
+    R lam_o[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      lam_o[i] = lam_out[(size_t)i * N + e];
+      lam_out[(size_t)i * N + e] = R(0);
+    }
+    R F[3];
+    load_force<S, R>(a.c.force, a.c.Ntot, e, F, D);
+    R lam_g[Q], lF[3] = {R(0), R(0), R(0)}, lom = R(0);
+    bgk_rev<Q, R>(g, om, rho_off, F, lam_o, lam_g, lF, lom);
+    part[0] += lom;
+    add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
+    // reverse streaming: every pulled value's adjoint goes back to its source slot
+    lam_in[e] += lam_g[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t n = nb[i];
+      if (n < NB_FLAG30) {
+        lam_in[(size_t)i * N + n] += lam_g[i];
+      } else if (n & NB_BOUNCE) {
+        lam_in[(size_t)opp(i) * N + e] += lam_g[i];
+        if (n & NB_FLAG30) {
+          // d f_i / d u_in = 6 w_i rho0 c_i
+#pragma unroll
+          for (int b = 0; b < D; ++b) part[2 + b] += lam_g[i] * R(6.0 * LT::w(i) * a.c.rho0 * LT::c(i, b));
+        }
+      } else {
+        static_cast<R*>(a.lam_side)[n & NB_INDEX] = lam_g[i];
+      }
+    }
+  }
+  store_partials<R, 5>(part, a.c.partial);
+}
+
+// ----------------------------------------------------------------- outlet values
+template <int Q, class S>
+__global__ void __launch_bounds__(256) k_adj_outlet(const AdjOutletArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  const S* __restrict__ x = static_cast<const S*>(a.c.fsrc);
+  R* lam_in = static_cast<R*>(a.c.lam_b);
+  const R* lam_side = static_cast<const R*>(a.lam_side);
+  const size_t N = (size_t)a.c.Ntot;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.end; k += stride) {
+    const int i = a.dir[k];
+    const R ls = lam_side[k];
+    if (a.kind[k] == OUT_EXTRAP) {
+      if (a.which == 1) lam_in[(size_t)i * N + a.a[k]] += R(2) * ls;
+      if (a.which == 2) lam_in[(size_t)i * N + a.b[k]] -= ls;
+      continue;
+    }
+    if (a.which != 0) continue;
+    // side = g^eq_i(rho0, u) + g_ib - g^eq_ib(rho, u), u = (j - F/2)/rho
+    const int64_t e = a.elem[k];
+    R g[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(x + (size_t)q * N + e);
+    R F[3];
+    load_force<S, R>(a.c.force, a.c.Ntot, e, F, D);
+    R rp, j[3];
+    raw_moments<Q, R>(g, rp, j);
+    const R rho = R(a.c.rho_off) + rp, inv = R(1) / rho;
+    R u[3] = {R(0), R(0), R(0)}, usq = R(0);
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      u[b] = (j[b] - R(0.5) * F[b]) * inv;
+      usq += u[b] * u[b];
+    }
+    const int ib = opp(i);
+    R lq[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lq[q] = R(0);
+    // term g^eq_i(rho0, u): depends on u only
+    R lam_rp_dummy = R(0), lam_u[3] = {R(0), R(0), R(0)};
+    R l1[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) l1[q] = q == i ? ls : R(0);
+    geq_rev<Q, R>(l1, R(a.c.rho0), u, usq, lam_rp_dummy, lam_u);
+    // term -g^eq_ib(rho, u)
+    R l2[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) l2[q] = q == ib ? -ls : R(0);
+    R lam_rp = R(0);
+    geq_rev<Q, R>(l2, rho, u, usq, lam_rp, lam_u);
+    R lam_j[3], lam_rho = R(0), lF[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      lam_j[b] = lam_u[b] * inv;
+      lF[b] = -R(0.5) * lam_u[b] * inv;
+      lam_rho += -lam_u[b] * u[b] * inv;
+    }
+    lam_rp += lam_rho;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      R v = lam_rp + (q == ib ? ls : R(0));
+#pragma unroll
+      for (int b = 0; b < D; ++b) v += R(LT::c(q, b)) * lam_j[b];
+      lam_in[(size_t)q * N + e] += v;
+    }
+    add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
+  }
+}
+
+// ----------------------------------------------------------------- source moments
+template <int Q, class S>
+__global__ void __launch_bounds__(128) k_adj_moments(const AdjMomArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  using RL = RecLayout<Q>;
+  constexpr int D = LT::D, NS = LT::NS;
+  const S* __restrict__ x = static_cast<const S*>(a.c.fsrc);
+  R* lam_in = static_cast<R*>(a.c.lam_b);
+  const size_t N = (size_t)a.c.Ntot;
+  R part[1] = {R(0)};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.nsrc; k += stride) {
+    R* lr = static_cast<R*>(a.lam_rec) + (size_t)k * kMomStride;
+    R rec[kMomStride];
+#pragma unroll
+    for (int f = 0; f < kMomStride; ++f) {
+      rec[f] = lr[f];
+      lr[f] = R(0);
+    }
+    if (a.lam_rec_prev) {
+      R* lp = static_cast<R*>(a.lam_rec_prev) + (size_t)k * kMomStride;
+#pragma unroll
+      for (int f = 0; f < kMomStride; ++f) {
+        rec[f] *= R(0.5);
+        lp[f] += rec[f];
+      }
+    }
+    const int64_t e = a.elem[k];
+    R g[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(x + (size_t)q * N + e);
+    R F[3];
+    load_force<S, R>(a.c.force, a.c.Ntot, e, F, D);
+    R lfn[Q], lS[NS], lu[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lfn[q] = rec[RL::FN + q];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) lS[s] = rec[RL::SS + s];
+#pragma unroll
+    for (int b = 0; b < D; ++b) lu[b] = rec[RL::U + b];
+    R lg[Q], lF[3] = {R(0), R(0), R(0)}, lom = R(0);
+    post_moments_rev<Q, R>(g, R(a.omega), R(a.c.rho_off), F, rec[RL::RP], lu, lfn, lS, lg, lF, lom);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lam_in[(size_t)q * N + e] += lg[q];
+    add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
+    part[0] += lom;
+  }
+  store_partials<R, 1>(part, a.c.partial);
+}
+
+// ----------------------------------------------------------------- GhostFromCoarser
+template <int Q, class S>
+__global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  using RL = RecLayout<Q>;
+  constexpr int D = LT::D, NS = LT::NS;
+  R* lam = static_cast<R*>(a.c.lam_a);
+  const R* __restrict__ mom = static_cast<const R*>(a.rec);
+  const size_t N = (size_t)a.c.Ntot;
+  R part[2] = {R(0), R(0)};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.ng; k += stride) {
+    const R* rec[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) rec[s] = mom + (size_t)a.gsrc[(size_t)s * a.ng + k] * kMomStride;
+    const uint8_t oct = a.oct[k];
+    R sg[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) sg[b] = ((oct >> b) & 1) ? R(1) : R(-1);
+    R ul[4][3], Sl[4][NS], rps[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      ul[s][0] = ul[s][1] = ul[s][2] = R(0);
+      rps[s] = rec[s][RL::RP];
+#pragma unroll
+      for (int b = 0; b < D; ++b) ul[s][b] = sg[b] * rec[s][RL::U + b];
+#pragma unroll
+      for (int b = 0; b < D; ++b)
+#pragma unroll
+        for (int c = b; c < D; ++c) Sl[s][sidx<D>(b, c)] = sg[b] * sg[c] * rec[s][RL::SS + sidx<D>(b, c)];
+    }
+    R uloc[3];
+    compact_uloc<Q, R>(ul, Sl, uloc);
+    R u[3] = {R(0), R(0), R(0)}, usq = R(0);
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      u[b] = sg[b] * uloc[b];
+      usq += u[b] * u[b];
+    }
+    const R lw[4] = {D == 3 ? R(0.625) : R(0.5625), D == 3 ? R(0.125) : R(0.1875), D == 3 ? R(0.125) : R(0.1875),
+                     D == 3 ? R(0.125) : R(0.0625)};
+    const R rp = lw[0] * rps[0] + lw[1] * rps[1] + lw[2] * rps[2] + lw[3] * rps[3];
+    const R rho = R(a.c.rho_off) + rp;
+    const R wf = R(a.omega_f), wc = R(a.omega_c);
+    const R scale = (R(1) - wf) * wc / (R(2) * wf);
+    const int64_t e = a.dest0 + k;
+    R lo[Q];
+    R lam_scale = R(0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      lo[q] = lam[(size_t)q * N + e];
+      lam[(size_t)q * N + e] = R(0);
+      const R fn = lw[0] * rec[0][RL::FN + q] + lw[1] * rec[1][RL::FN + q] + lw[2] * rec[2][RL::FN + q] +
+                   lw[3] * rec[3][RL::FN + q];
+      lam_scale += lo[q] * fn;
+    }
+    part[0] += lam_scale * (R(1) - wf) / (R(2) * wf);  // d scale / d omega_c
+    part[1] += lam_scale * (-wc / (R(2) * wf * wf));    // d scale / d omega_f
+    R lam_rp = R(0), lam_u[3] = {R(0), R(0), R(0)};
+    geq_rev<Q, R>(lo, rho, u, usq, lam_rp, lam_u);
+    R lam_uloc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int b = 0; b < D; ++b) lam_uloc[b] = sg[b] * lam_u[b];
+    // transpose of the linear compact map: column m of its Jacobian by
+    // evaluating it on the m-th unit input
+    R lul[4][3], lSl[4][NS];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        R eu[4][3] = {}, eS[4][NS] = {}, o[3];
+        eu[s][b] = R(1);
+        compact_uloc<Q, R>(eu, eS, o);
+        lul[s][b] = o[0] * lam_uloc[0] + o[1] * lam_uloc[1] + o[2] * lam_uloc[2];
+      }
+#pragma unroll
+      for (int c = 0; c < NS; ++c) {
+        R eu[4][3] = {}, eS[4][NS] = {}, o[3];
+        eS[s][c] = R(1);
+        compact_uloc<Q, R>(eu, eS, o);
+        lSl[s][c] = o[0] * lam_uloc[0] + o[1] * lam_uloc[1] + o[2] * lam_uloc[2];
+      }
+    }
+    R* out = static_cast<R*>(a.contrib) + (size_t)k * 4 * kMomStride;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      R v[kMomStride];
+#pragma unroll
+      for (int f = 0; f < kMomStride; ++f) v[f] = R(0);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[RL::FN + q] = lw[s] * scale * lo[q];
+      v[RL::RP] = lw[s] * lam_rp;
+#pragma unroll
+      for (int b = 0; b < D; ++b) v[RL::U + b] = sg[b] * lul[s][b];
+#pragma unroll
+      for (int b = 0; b < D; ++b)
+#pragma unroll
+        for (int c = b; c < D; ++c) v[RL::SS + sidx<D>(b, c)] = sg[b] * sg[c] * lSl[s][sidx<D>(b, c)];
+#pragma unroll
+      for (int f = 0; f < kMomStride; f += 4) st4(out + s * kMomStride + f, v + f);
+    }
+  }
+  store_partials<R, 2>(part, a.c.partial);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k_adj_gather(const AdjGatherArgs a) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.nsrc) return;
+  const R* c = static_cast<const R*>(a.contrib);
+  R acc[kMomStride];
+  R* lr = static_cast<R*>(a.lam_rec) + (size_t)k * kMomStride;
+#pragma unroll
+  for (int f = 0; f < kMomStride; ++f) acc[f] = lr[f];
+  for (int j = a.off[k]; j < a.off[k + 1]; ++j) {
+    const R* p = c + (size_t)a.item[j] * kMomStride;
+#pragma unroll
+    for (int f = 0; f < kMomStride; f += 4) {
+      R v[4];
+      ld4(p + f, v);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[f + t] += v[t];
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < kMomStride; f += 4) st4(lr + f, acc + f);
+}
+
+// ----------------------------------------------------------------- GhostFromFiner
+template <int Q, class S>
+__global__ void __launch_bounds__(256) k_adj_gff(const AdjGffArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D, NS = LT::NS, NCH = 1 << D;
+  const S* __restrict__ x = static_cast<const S*>(a.c.fsrc);
+  R* lam_c = static_cast<R*>(a.c.lam_a);
+  R* lam_f = static_cast<R*>(a.c.lam_b);
+  const size_t N = (size_t)a.c.Ntot;
+  const R wf = R(a.omega_f), wc = R(a.omega_c), rho_off = R(a.c.rho_off);
+  R part[2] = {R(0), R(0)};
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  // every lane of a warp runs the same number of iterations (the shuffles need the whole warp)
+  const int64_t total = (a.ng * NCH + 31) / 32 * 32;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t - threadIdx.x % 32 < total; t += gstride) {
+    const int64_t k = t / NCH;
+    const int b = (int)(t % NCH);
+    const bool active = k < a.ng;
+    R g[Q], F[3] = {R(0), R(0), R(0)};
+    R rp = R(0), u[3] = {R(0), R(0), R(0)}, fneq[Q], Sv[NS];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      g[q] = R(0);
+      fneq[q] = R(0);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Sv[s] = R(0);
+    int64_t ec = 0;
+    if (active) {
+      ec = (int64_t)a.child0[k] + b;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(x + (size_t)q * N + ec);
+      load_force<S, R>(a.c.force, a.c.Ntot, ec, F, D);
+      post_moments<Q, R, true>(g, wf, rho_off, F, rp, u, fneq, Sv);
+    }
+    R dS[3][NS];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const R sgn = ((b >> c) & 1) ? R(1) : R(-1);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) dS[c][s] = sgn * Sv[s];
+    }
+    R RP = rp, U[3] = {u[0], u[1], u[2]}, FN[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) FN[q] = fneq[q];
+#pragma unroll
+    for (int o = 1; o < NCH; o <<= 1) {
+      RP += __shfl_xor_sync(0xffffffffu, RP, o);
+#pragma unroll
+      for (int c = 0; c < D; ++c) U[c] += __shfl_xor_sync(0xffffffffu, U[c], o);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) FN[q] += __shfl_xor_sync(0xffffffffu, FN[q], o);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) dS[c][s] += __shfl_xor_sync(0xffffffffu, dS[c][s], o);
+    }
+    // adjoint of the ghost's pdfs: every lane of the group reads all of them,
+    // then (after the warp barrier) each lane clears its share of the slots
+    const int64_t kk = active ? k : 0;
+    const int64_t eg = kk < a.n_inner ? a.dest0 + kk : a.dest_outer + (kk - a.n_inner);
+    R lo[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lo[q] = active ? lam_c[(size_t)q * N + eg] : R(0);
+    __syncwarp();
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (q % NCH == b) lam_c[(size_t)q * N + eg] = R(0);
+    }
+    if (!active) continue;
+    const R inv = R(1) / R(NCH);
+    const R dfac = R(2) * R(D == 3 ? 0.5 : 1.0);
+    const R rpm = RP * inv;
+    R uP[3] = {R(0), R(0), R(0)}, usq = R(0);
+#pragma unroll
+    for (int aa = 0; aa < D; ++aa) {
+      R lap = R(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) lap += dfac * (R(2) * dS[c][sidx<D>(aa, c)] - dS[aa][sidx<D>(c, c)]);
+      uP[aa] = U[aa] * inv - lap * R(1.0 / 32.0);
+      usq += uP[aa] * uP[aa];
+    }
+    const R rho = rho_off + rpm;
+    const R scale = (R(1) - wc) * R(2) * wf / wc * inv;
+    R lam_scale = R(0);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lam_scale += lo[q] * FN[q];
+    if (b == 0) {
+      part[0] += lam_scale * (R(2) * wf * inv) * (-R(1) / (wc * wc));  // d scale / d omega_c
+      part[1] += lam_scale * (R(1) - wc) * R(2) / wc * inv;            // d scale / d omega_f
+    }
+    R lam_rpm = R(0), lam_uP[3] = {R(0), R(0), R(0)};
+    geq_rev<Q, R>(lo, rho, uP, usq, lam_rpm, lam_uP);
+    R ldS[3][NS];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) ldS[c][s] = R(0);
+#pragma unroll
+    for (int aa = 0; aa < D; ++aa) {
+      const R lap_l = -lam_uP[aa] * R(1.0 / 32.0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        ldS[c][sidx<D>(aa, c)] += dfac * R(2) * lap_l;
+        ldS[aa][sidx<D>(c, c)] -= dfac * lap_l;
+      }
+    }
+    // this lane's child
+    R lS[NS], lu[3] = {R(0), R(0), R(0)}, lfn[Q];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      R v = R(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) v += (((b >> c) & 1) ? R(1) : R(-1)) * ldS[c][s];
+      lS[s] = v;
+    }
+#pragma unroll
+    for (int aa = 0; aa < D; ++aa) lu[aa] = lam_uP[aa] * inv;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lfn[q] = scale * lo[q];
+    R lg[Q], lF[3] = {R(0), R(0), R(0)}, lom = R(0);
+    post_moments_rev<Q, R>(g, wf, rho_off, F, lam_rpm * inv, lu, lfn, lS, lg, lF, lom);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lam_f[(size_t)q * N + ec] += lg[q];
+    add_force<R>(a.c.lam_force, a.c.Ntot, ec, lF, D);
+    part[1] += lom;
+  }
+  store_partials<R, 2>(part, a.c.partial);
+}
+
+// ----------------------------------------------------------------- launchers
+inline unsigned adj_grid(int64_t n, int threads) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : (b > kAdjBlocks ? kAdjBlocks : b));
+}
+
+template <class S>
+struct AdjLaunch {
+  static void seed(int Q, const AdjSeedArgs& a, cudaStream_t st) {
+    const int64_t n = a.objective == 0 ? a.end - a.begin : a.obs_n;
+    if (Q == 9) k_adj_seed<9, S><<<adj_grid(n, 256), 256, 0, st>>>(a);
+    else k_adj_seed<19, S><<<adj_grid(n, 256), 256, 0, st>>>(a);
+  }
+  static void sc(int Q, const AdjSCArgs& a, cudaStream_t st) {
+    if (Q == 9) k_adj_sc<9, S><<<kAdjBlocks, 256, 0, st>>>(a);
+    else k_adj_sc<19, S><<<kAdjBlocks, 256, 0, st>>>(a);
+  }
+  static void outlet(int Q, const AdjOutletArgs& a, cudaStream_t st) {
+    if (a.end <= a.begin) return;
+    if (Q == 9) k_adj_outlet<9, S><<<adj_grid(a.end - a.begin, 256), 256, 0, st>>>(a);
+    else k_adj_outlet<19, S><<<adj_grid(a.end - a.begin, 256), 256, 0, st>>>(a);
+  }
+  static void moments(int Q, const AdjMomArgs& a, cudaStream_t st) {
+    if (Q == 9) k_adj_moments<9, S><<<kAdjBlocks, 128, 0, st>>>(a);
+    else k_adj_moments<19, S><<<kAdjBlocks, 128, 0, st>>>(a);
+  }
+  static void gfc(int Q, const AdjGfcArgs& a, cudaStream_t st) {
+    if (Q == 9) k_adj_gfc<9, S><<<kAdjBlocks, 128, 0, st>>>(a);
+    else k_adj_gfc<19, S><<<kAdjBlocks, 128, 0, st>>>(a);
+  }
+  static void gff(int Q, const AdjGffArgs& a, cudaStream_t st) {
+    if (Q == 9) k_adj_gff<9, S><<<kAdjBlocks, 256, 0, st>>>(a);
+    else k_adj_gff<19, S><<<kAdjBlocks, 256, 0, st>>>(a);
+  }
+};
+
+template <class S>
+const AdjOps* make_adj_ops() {
+  static const AdjOps ops = {&AdjLaunch<S>::seed, &AdjLaunch<S>::sc,  &AdjLaunch<S>::outlet,
+                             &AdjLaunch<S>::moments, &AdjLaunch<S>::gfc, &AdjLaunch<S>::gff,
+                             sizeof(typename Sto<S>::R)};
+  return &ops;
+}
+
+}  // namespace dev
+}  // namespace lbm

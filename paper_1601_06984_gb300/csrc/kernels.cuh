@@ -477,6 +477,38 @@ __global__ void __launch_bounds__(128) k_source_moments(const MomentsArgs a) {
   }
 }
 
+// Compact quadratic velocity at the ghost in the octant's local frame, a linear
+// map of the sources' local-frame velocities ul and strain rates Sl (see the
+// GhostFromCoarser comment below for the closed form).
+template <int Q, class R>
+__device__ __forceinline__ void compact_uloc(const R (&ul)[4][3], const R (&Sl)[4][Lat<Q>::NS], R (&uloc)[3]) {
+  constexpr int D = Lat<Q>::D, NS = Lat<Q>::NS;
+  uloc[0] = uloc[1] = uloc[2] = R(0);
+  if (D == 3) {
+    auto Dx = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] + Sl[2][c] - Sl[3][c]); };
+    auto Dy = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] - Sl[2][c] + Sl[3][c]); };
+    auto Dz = [&](int c) { return R(0.5) * (-Sl[0][c] - Sl[1][c] + Sl[2][c] + Sl[3][c]); };
+    constexpr int XX = 0, YY = 1, ZZ = 2, XY = 3, YZ = 4, XZ = NS - 1;
+    const R h3 = Dz(XY) + Dx(YZ) + Dy(XZ);
+    const R sd[3] = {R(0.5) * Dx(XX) + Dy(XY) - R(0.5) * Dx(YY) + Dz(XZ) - R(0.5) * Dx(ZZ),
+                     Dx(XY) - R(0.5) * Dy(XX) + R(0.5) * Dy(YY) + Dz(YZ) - R(0.5) * Dy(ZZ),
+                     Dx(XZ) - R(0.5) * Dz(XX) + Dy(YZ) - R(0.5) * Dz(YY) + R(0.5) * Dz(ZZ)};
+    const R so[3] = {Dy(XX) + Dz(XX) + h3 - R(2) * Dx(YZ), Dx(YY) + Dz(YY) + h3 - R(2) * Dy(XZ),
+                     Dx(ZZ) + Dy(ZZ) + h3 - R(2) * Dz(XY)};
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      uloc[b] = R(0.625) * ul[0][b] + R(0.125) * (ul[1][b] + ul[2][b] + ul[3][b]) - R(0.1875) * sd[b] -
+                R(0.0625) * so[b];
+  } else {
+    auto Dx = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] - Sl[2][c] + Sl[3][c]); };
+    auto Dy = [&](int c) { return R(0.5) * (-Sl[0][c] - Sl[1][c] + Sl[2][c] + Sl[3][c]); };
+    const R axx = R(0.5) * Dx(0), axy = Dy(0), ayy = Dy(2) - R(0.5) * Dx(1);
+    const R bxx = Dx(2) - R(0.5) * Dy(0), byy = R(0.5) * Dy(1), bxy = Dx(1);
+    uloc[0] = R(0.5) * ul[0][0] + R(0.25) * (ul[1][0] + ul[2][0]) - R(0.1875) * (axx + ayy) + R(0.0625) * axy;
+    uloc[1] = R(0.5) * ul[0][1] + R(0.25) * (ul[1][1] + ul[2][1]) - R(0.1875) * (bxx + byy) + R(0.0625) * bxy;
+  }
+}
+
 // ----------------------------------------------------------------- GhostFromCoarser
 // Interpolation steps 2-5 (Sec. 2.2) for one fine ghost from its four coarse
 // sources.  The velocity is the compact quadratic interpolant evaluated at the
@@ -525,30 +557,8 @@ __global__ void __launch_bounds__(128) k_fill_gfc(const GfcArgs a) {
       for (int c = b; c < D; ++c)
         Sl[s][sidx<D>(b, c)] = sg[b] * sg[c] * h[RL::SS - RL::RP + sidx<D>(b, c)];
   }
-  R uloc[3] = {R(0), R(0), R(0)};
-  if (D == 3) {
-    auto Dx = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] + Sl[2][c] - Sl[3][c]); };
-    auto Dy = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] - Sl[2][c] + Sl[3][c]); };
-    auto Dz = [&](int c) { return R(0.5) * (-Sl[0][c] - Sl[1][c] + Sl[2][c] + Sl[3][c]); };
-    constexpr int XX = 0, YY = 1, ZZ = 2, XY = 3, YZ = 4, XZ = NS - 1;
-    const R h3 = Dz(XY) + Dx(YZ) + Dy(XZ);
-    const R sd[3] = {R(0.5) * Dx(XX) + Dy(XY) - R(0.5) * Dx(YY) + Dz(XZ) - R(0.5) * Dx(ZZ),
-                     Dx(XY) - R(0.5) * Dy(XX) + R(0.5) * Dy(YY) + Dz(YZ) - R(0.5) * Dy(ZZ),
-                     Dx(XZ) - R(0.5) * Dz(XX) + Dy(YZ) - R(0.5) * Dz(YY) + R(0.5) * Dz(ZZ)};
-    const R so[3] = {Dy(XX) + Dz(XX) + h3 - R(2) * Dx(YZ), Dx(YY) + Dz(YY) + h3 - R(2) * Dy(XZ),
-                     Dx(ZZ) + Dy(ZZ) + h3 - R(2) * Dz(XY)};
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-      uloc[b] = R(0.625) * ul[0][b] + R(0.125) * (ul[1][b] + ul[2][b] + ul[3][b]) - R(0.1875) * sd[b] -
-                R(0.0625) * so[b];
-  } else {
-    auto Dx = [&](int c) { return R(0.5) * (-Sl[0][c] + Sl[1][c] - Sl[2][c] + Sl[3][c]); };
-    auto Dy = [&](int c) { return R(0.5) * (-Sl[0][c] - Sl[1][c] + Sl[2][c] + Sl[3][c]); };
-    const R axx = R(0.5) * Dx(0), axy = Dy(0), ayy = Dy(2) - R(0.5) * Dx(1);
-    const R bxx = Dx(2) - R(0.5) * Dy(0), byy = R(0.5) * Dy(1), bxy = Dx(1);
-    uloc[0] = R(0.5) * ul[0][0] + R(0.25) * (ul[1][0] + ul[2][0]) - R(0.1875) * (axx + ayy) + R(0.0625) * axy;
-    uloc[1] = R(0.5) * ul[0][1] + R(0.25) * (ul[1][1] + ul[2][1]) - R(0.1875) * (bxx + byy) + R(0.0625) * bxy;
-  }
+  R uloc[3];
+  compact_uloc<Q, R>(ul, Sl, uloc);
   R u[3] = {R(0), R(0), R(0)};
   R usq = R(0);
 #pragma unroll

@@ -1,0 +1,110 @@
+// The library context (opaque at the ABI): host mesh, workspace layout, bound
+// device state and the driver.  Shared by api.cpp and adjoint.cpp.
+#pragma once
+
+#include <cuda_runtime_api.h>
+
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+// Ops of the recursive level step, in the order lbm_ctx::advance issues them.
+enum StepOp { OP_GFF = 0, OP_MOM_A = 1, OP_GFC_A = 2, OP_SC = 3, OP_MOM_B = 4, OP_GFC_B = 5 };
+
+struct LevelDev {
+  size_t gff_child0 = 0, gfc_src = 0, gfc_oct = 0, src_elem = 0, momA = 0, momB = 0;
+  int64_t nsrc = 0;
+};
+
+}  // namespace lbm
+
+struct lbm_ctx {
+  lbm_params p{};
+  lbm::HostMesh M;
+  const lbm::Ops* ops = nullptr;
+  std::string err;
+  int d = 2, Q = 9, nS = 3, nlev = 1;
+  double rho_off = 0.0;
+  double inlet[19] = {};
+  // layout (byte offsets into the workspace)
+  size_t oA = 0, oB = 0, oNbr = 0, oF = 0, oOutElem = 0, oOutA = 0, oOutB = 0, oOutDir = 0, oOutKind = 0,
+         oSide = 0, oObsElem = 0, oObsDir = 0, oUslot = 0, oUlev = 0, oStage = 0, oPartial = 0, oRed = 0;
+  std::vector<lbm::LevelDev> ld;
+  size_t bytes = 0;
+  int64_t chunk = 0;
+  // bound state
+  bool bound = false;
+  char* ws = nullptr;
+  cudaStream_t st = nullptr;
+  std::vector<int> parity;
+  int64_t launches = 0;
+  // observer called before every op of advance() (records the adjoint tape);
+  // with dry set, advance() only walks the op sequence and flips parities
+  std::function<void(int op, int level)> hook;
+  bool dry = false;
+  // stream-collide timing (events recorded around each launch when enabled)
+  bool timing = false;
+  struct Timed {
+    int li;
+    cudaEvent_t a, b;
+  };
+  std::vector<Timed> timed;
+  std::vector<cudaEvent_t> event_pool;
+  cudaEvent_t get_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void recycle_timed() {
+    for (auto& t : timed) {
+      event_pool.push_back(t.a);
+      event_pool.push_back(t.b);
+    }
+    timed.clear();
+  }
+  ~lbm_ctx() {
+    recycle_timed();
+    for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+  }
+
+  template <class T = void>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(ws + off);
+  }
+  void* cur(int li) const { return parity[li] ? at(oB) : at(oA); }
+  void* nxt(int li) const { return parity[li] ? at(oA) : at(oB); }
+  uint32_t parity_mask() const {
+    uint32_t m = 0;
+    for (int li = 0; li < nlev; ++li) m |= (uint32_t)(parity[li] & 1) << li;
+    return m;
+  }
+  const void* force_ptr() const { return p.use_force ? at(oF) : nullptr; }
+
+  lbm_status fail(lbm_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  lbm_status cuda_check(cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return LBM_OK;
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return LBM_ERR_CUDA;
+  }
+  lbm_status launched(const char* where) { return cuda_check(cudaGetLastError(), where); }
+
+  void layout();
+  // driver pieces
+  void fill_gff(int li);
+  void source_moments(int li, size_t mom_off, size_t prev_off = 0);
+  void fill_gfc(int li_fine, bool two_times);
+  void stream_collide(int li);
+  void advance(int li);
+};
+

@@ -214,6 +214,117 @@ struct Ops {
   size_t compute_bytes;  // bytes of the compute type
 };
 
+// ----------------------------------------------------------------- adjoint kernels
+// lam* are adjoint pdf buffers [Q][Ntot] in the compute type; lam_force is
+// [d][Ntot] FP64; partial rows hold per-block sums of parameter derivatives:
+// col 0 d/d omega of level la, col 1 d/d omega of level lb, cols 2..4 d/d u_in.
+constexpr int kAdjBlocks = 1024;  // fixed grid of the adjoint kernels (deterministic partials)
+constexpr int kPartCols = 8;
+
+struct AdjCommon {
+  const void* fsrc;   // forward state the op read (full [Q][Ntot] snapshot, storage type)
+  const void* force;  // [d][Ntot] compute type or null (treated as zero force)
+  void* lam_a;        // adjoint buffer the op's outputs live in (consumed, zeroed)
+  void* lam_b;        // adjoint buffer of the op's inputs (accumulated)
+  double* lam_force;  // [d][Ntot] FP64 accumulated (null: not wanted)
+  double* partial;    // [kAdjBlocks][kPartCols]
+  int64_t Ntot;
+  double rho_off, rho0;
+};
+
+struct AdjSCArgs {
+  AdjCommon c;
+  const uint32_t* nbr;
+  const void* side_fwd;  // outlet values the forward used (compute type)
+  void* lam_side;        // adjoint of the outlet values (written)
+  int64_t begin, end;
+  double omega;
+  double inlet[19];      // 6 w_i rho0 (c_i . u_in) of the forward
+};
+
+struct AdjOutletArgs {
+  AdjCommon c;
+  const int32_t *elem, *a, *b;
+  const int8_t *dir, *kind;
+  const void* lam_side;
+  int64_t begin, end;
+  int which;  // 0: normal links, 1: extrapolation term of source a, 2: of source b
+  double omega;
+};
+
+struct AdjMomArgs {  // reverse of the source moments
+  AdjCommon c;       // lam_b: adjoint of the coarse state
+  const int32_t* elem;
+  void* lam_rec;       // [nsrc][kMomStride] adjoint of the records (consumed, zeroed)
+  void* lam_rec_prev;  // averaging mode: receives half of lam_rec (else null)
+  int64_t nsrc;
+  double omega;
+};
+
+struct AdjGfcArgs {  // reverse of the GhostFromCoarser fill, per ghost
+  AdjCommon c;       // lam_a: adjoint of the fine state holding the ghosts
+  const void* rec;   // forward source records [nsrc][kMomStride]
+  const int32_t* gsrc;
+  const uint8_t* oct;
+  void* contrib;     // [ng][4][kMomStride] per-ghost adjoint of each source record
+  int64_t ng, dest0;
+  double omega_c, omega_f;
+};
+
+struct AdjGatherArgs {  // deterministic sum of the per-ghost contributions per source
+  const void* contrib;
+  const int32_t* off;   // [nsrc+1]
+  const int32_t* item;  // ghost*4 + source slot
+  void* lam_rec;        // [nsrc][kMomStride] accumulated
+  int64_t nsrc;
+};
+
+struct AdjGffArgs {
+  AdjCommon c;       // fsrc: fine state (children); lam_a: coarse adjoint; lam_b: fine adjoint
+  const int32_t* child0;
+  int64_t ng, n_inner, dest0, dest_outer;
+  double omega_c, omega_f;
+};
+
+struct AdjSeedArgs {
+  AdjCommon c;  // lam_b receives the seed
+  int objective;  // 0 kinetic energy; 1..3 obstacle force x, y, z
+  int64_t begin, end;  // fluid range (kinetic energy)
+  double vol;
+  const int32_t* obs_elem;
+  const int8_t* obs_dir;
+  int64_t obs_n;
+  double fscale;
+};
+
+struct AccumArgs {
+  const double* partial;
+  int rows;
+  double* acc_omega;  // [16]
+  double* acc_uin;    // [3]
+  int la, lb;
+};
+
+struct AdjOps {
+  void (*seed)(int Q, const AdjSeedArgs&, cudaStream_t);
+  void (*sc)(int Q, const AdjSCArgs&, cudaStream_t);
+  void (*outlet)(int Q, const AdjOutletArgs&, cudaStream_t);
+  void (*moments)(int Q, const AdjMomArgs&, cudaStream_t);
+  void (*gfc)(int Q, const AdjGfcArgs&, cudaStream_t);
+  void (*gff)(int Q, const AdjGffArgs&, cudaStream_t);
+  size_t lam_bytes;  // bytes per adjoint value (compute type)
+};
+const AdjOps* adj_ops_fp64();
+const AdjOps* adj_ops_fp32dev();
+const AdjOps* adj_ops_bf16dev();
+void launch_adj_gather(bool fp64, const AdjGatherArgs&, cudaStream_t);
+void launch_accum(const AccumArgs&, cudaStream_t);
+void launch_gather_lam_user(bool fp64, const void* lamA, const void* lamB, uint32_t parity, const int32_t* uslot,
+                            const uint8_t* ulev, double* stage, int64_t first, int64_t cnt, int64_t Ntot, int Q,
+                            cudaStream_t);
+void launch_gather_force_user(const double* lam_force, const int32_t* uslot, double* stage, int64_t first,
+                              int64_t cnt, int64_t Ntot, int d, cudaStream_t);
+
 const Ops* ops_fp64();
 const Ops* ops_fp32dev();
 const Ops* ops_bf16dev();

@@ -584,7 +584,10 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
         // ghosts whose pulled values reach fluid must find every neighbour
         const bool strict_ghost = (k == K_GFC && layer[e] == 1) || k == K_GFF;
         for (int i = 1; i < Q; ++i) {
-          uint32_t code = (uint32_t)ge;  // default: pull from itself (value unused)
+          // default for links whose value never reaches a fluid element: read the
+          // element's own opposite slot (each pdf slot keeps a single reader, so
+          // the reverse of the streaming has no write conflicts)
+          uint32_t code = proc ? NB_BOUNCE : (uint32_t)ge;
           if (proc) {
             int64_t q[3] = {pos[3 * e] - B.dr.c[i][0], pos[3 * e + 1] - B.dr.c[i][1], pos[3 * e + 2] - B.dr.c[i][2]};
             const int fc = B.wrap(li, q);

@@ -23,7 +23,8 @@ TIME_LINEAR, TIME_TWO_LAYER = 0, 1
 EXPORTS = ["lbm_build_mesh", "lbm_mesh_info", "lbm_device_bytes", "lbm_bind", "lbm_init", "lbm_set_force",
            "lbm_step", "lbm_fill_ghosts", "lbm_moments", "lbm_reduce", "lbm_get_state", "lbm_ghost_count",
            "lbm_get_ghosts", "lbm_sfc_partition", "lbm_kernel_launches", "lbm_timing_enable", "lbm_timing_read",
-           "lbm_reduce_noalloc", "lbm_last_error", "lbm_destroy"]
+           "lbm_reduce_noalloc", "lbm_set_params", "lbm_adjoint_bytes", "lbm_adjoint", "lbm_last_error",
+           "lbm_destroy"]
 
 
 class LBMError(RuntimeError):
@@ -70,6 +71,9 @@ def lib():
             "lbm_timing_enable": [P, I32],
             "lbm_timing_read": [P, P, P, I32],
             "lbm_reduce_noalloc": [P, P],
+            "lbm_set_params": [P, C.c_double, P],
+            "lbm_adjoint_bytes": [P, I64, I32, C.POINTER(U64)],
+            "lbm_adjoint": [P, I64, I32, I32, P, U64, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -258,3 +262,33 @@ class Sim:
         out = np.zeros(8)
         _check(self.ctx, lib().lbm_reduce(self.ctx, _p(out)))
         return out
+
+    def set_params(self, omega_c, u_in=None):
+        uin = None if u_in is None else _arr(list(u_in) + [0.0] * (3 - len(u_in)), np.float64)
+        _check(self.ctx, lib().lbm_set_params(self.ctx, float(omega_c), _p(uin)))
+
+    def adjoint_bytes(self, n_coarse, K=20):
+        nbytes = C.c_uint64()
+        _check(self.ctx, lib().lbm_adjoint_bytes(self.ctx, int(n_coarse), int(K), C.byref(nbytes)))
+        return int(nbytes.value)
+
+    def adjoint(self, n_coarse, K=20, objective=0, want_force=True, want_f0=False):
+        """Discrete adjoint of n_coarse steps from the current state (gradients
+        at fixed initial pdfs).  Returns (J, dJ/dF [n, d] or None, dJ/domega_c,
+        dJ/du_in [3]) and, with want_f0, dJ/d(initial pdfs) [n, Q] last."""
+        import torch
+        nbytes = C.c_uint64()
+        _check(self.ctx, lib().lbm_adjoint_bytes(self.ctx, int(n_coarse), int(K), C.byref(nbytes)))
+        ws = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.ws.device)
+        J = C.c_double()
+        dF = np.zeros((self.n, self.d)) if want_force else None
+        dw = C.c_double()
+        du = np.zeros(3)
+        df0 = np.zeros((self.n, self.Q)) if want_f0 else None
+        _check(self.ctx, lib().lbm_adjoint(self.ctx, int(n_coarse), int(K), int(objective),
+                                           C.c_void_p(ws.data_ptr()), nbytes.value, C.byref(J), _p(dF),
+                                           C.byref(dw), _p(du), _p(df0)))
+        del ws
+        if want_f0:
+            return J.value, dF, dw.value, du, df0
+        return J.value, dF, dw.value, du
