@@ -162,6 +162,23 @@ def measured_peaks():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(value, dist=None, device="cpu"):
+    """Largest value over all ranks (the slowest replica sets the job time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(updates_per_rank, seconds_per_rank, world, dist=None, device="cpu"):
+    """Whole-job MLUPS of independent replicas: all ranks' updates over the
+    slowest rank's time."""
+    return world * updates_per_rank / max_over_ranks(seconds_per_rank, dist, device) / 1e6
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_oracle(seconds, min_steps=2):
     """Time the CPU oracle (single thread) on the bounded sample."""
@@ -211,10 +228,7 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     ms = ev0.elapsed_time(ev1)
     launches = sim.kernel_launches() - n0
     nl, kms = sim.timing_read()
-    if dist is not None:
-        t = torch.tensor([ms], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, device)
     finest = len(info) - 1
     units = int(info[finest, 1])  # fluid updates per finest launch
     avg_ms = kms[finest] / max(nl[finest], 1)
@@ -228,6 +242,62 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     if want_moments:
         res["moments"] = sim.moments()
     return sim, res
+
+
+def adjoint_run(device):
+    """Adjoint configuration: periodic 64^3 coarse with the central 32^3 block
+    refined, Gaussian body force N(0, 1e-6) per component, 400 coarse steps,
+    final kinetic energy, checkpoints every 20 steps.  FP32 deviation: time of
+    the adjoint (forward with checkpoints + reverse sweep) over the forward
+    alone.  FP64: gradient along a random force direction and along omega
+    against central differences."""
+    import torch
+    from paper_1601_06984_gb300 import lbm, workloads as W
+    m = W.config_tgv3d(64)
+    rho, u, S = W.uniform_fields(m)
+    F = W.gaussian_force(m, 1e-6)
+    n, K = 400, 20
+    out = {"config": "tgv3d 64^3/32^3 two-level, force N(0,1e-6), 400 coarse steps, K=20, objective KE"}
+    for name, prec in (("fp32dev", lbm.FP32DEV), ("fp64", lbm.FP64)):
+        g = lbm.Sim(m, 19, 1.6, precision=prec, use_force=True, device=device)
+        g.init(rho, u, S)
+        g.set_force(F)
+        g.step(3)
+        g.init(rho, u, S)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        g.step(n)
+        g.reduce()
+        tf = time.perf_counter() - t0
+        g.init(rho, u, S)
+        t0 = time.perf_counter()
+        J, dF, dw, _ = g.adjoint(n, K, 0)
+        ta = time.perf_counter() - t0
+        rec = {"forward_s": tf, "adjoint_s": ta, "adjoint_to_forward": ta / tf, "J": J,
+               "adjoint_workspace_gb": g.adjoint_bytes(n, K) / 1e9}
+        if prec == lbm.FP64:
+            vF = W.random_direction((m.n, 3), W.SEED, 51) * 1e-6
+            vw = 0.1
+
+            def run(h):
+                gg = lbm.Sim(m, 19, 1.6, precision=prec, use_force=True, device=device)
+                gg.init(rho, u, S)
+                gg.set_params(1.6 + h * vw)
+                gg.set_force(F + h * vF)
+                gg.step(n)
+                return gg.reduce()[7]
+
+            h = 1e-3
+            fd = (run(h) - run(-h)) / (2 * h)
+            adj = float((dF * vF).sum() + dw * vw)
+            rec["directional_derivative_adjoint"] = adj
+            rec["directional_derivative_central_fd"] = fd
+            rec["rel_error_vs_fd"] = abs(adj - fd) / abs(fd)
+        out[name] = rec
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    return out
 
 
 def e2e_run(sim, mesh, fields, K):
@@ -301,15 +371,13 @@ def main():
     clocks = clk.stop()
     e2e = e2e_run(sim, mesh, fields, K)
     if dist is not None:
-        t = torch.tensor([e2e["seconds"]], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * K * U / float(t.item()) / 1e6
+        e2e["value"] = job_throughput(K * U, e2e["seconds"], world, dist, device)
     mom32 = r.pop("moments", None)
     sim.close()
     del sim
     torch.cuda.empty_cache()
 
-    variants, errors, tgv = {}, {}, None
+    variants, errors, tgv, adj = {}, {}, None, None
     if not args.no_variants and rank == 0 and world == 1:
         mom = {}
         for name, prec in (("fp64", lbm.FP64), ("bf16dev", lbm.BF16DEV)):
@@ -349,6 +417,7 @@ def main():
             st.close()
             del st
             torch.cuda.empty_cache()
+        adj = adjoint_run(device)
 
     if rank != 0:
         if dist is not None:
@@ -383,6 +452,8 @@ def main():
         line["error_vs_fp64"] = errors
     if tgv:
         line["tgv3d"] = tgv
+    if adj:
+        line["adjoint"] = adj
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -77,7 +77,7 @@ __device__ __forceinline__ void post_moments_rev(const R* g, R om, R rho_off, co
                                                  const R* lam_u_in, R* lam_fneq, const R* lam_S, R* lam_g,
                                                  R* lam_F, R& lam_om) {
   using LT = Lat<Q>;
-  constexpr int D = LT::D, NS = LT::NS;
+  constexpr int D = LT::D;
   R rp, j[3];
   raw_moments<Q, R>(g, rp, j);
   const R rho = rho_off + rp;
@@ -270,8 +270,15 @@ __global__ void __launch_bounds__(256) k_adj_seed(const AdjSeedArgs a) {
 }
 
 // ----------------------------------------------------------------- stream + collide
+// Reverse of one element's pull + BGK collide.  The collision Jacobian is the
+// identity times (1-omega) plus a rank-(1+d) part: with
+//   A_i = d g^eq_i / d rp,  B_ia = d g^eq_i / d u_a,  G_ia = d guo_i / d u_a,
+//   S0 = sum_i lam_i A_i,   S_a = sum_i lam_i (omega B_ia + G_ia),
+// the adjoint of the pulled pdf k is
+//   lam_g_k = (1-omega) lam_k + omega S0 + sum_a S_a (c_ka - u_a) / rho,
+// so only a handful of scalars are carried (few registers, more warps).
 template <int Q, class S>
-__global__ void __launch_bounds__(256) k_adj_sc(const AdjSCArgs a) {
+__global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -284,50 +291,108 @@ __global__ void __launch_bounds__(256) k_adj_sc(const AdjSCArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.end; e += stride) {
     uint32_t nb[Q];
-    R g[Q];
     nb[0] = (uint32_t)e;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) nb[i] = __ldg(a.nbr + (size_t)(i - 1) * N + e);
+    R g[Q];
     g[0] = Sto<S>::ld(x + e);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const uint32_t n = a.nbr[(size_t)(i - 1) * N + e];
-      nb[i] = n;
-      if (n < NB_FLAG30) {
-        g[i] = Sto<S>::ld(x + (size_t)i * N + n);
-      } else if (n & NB_BOUNCE) {
-        g[i] = Sto<S>::ld(x + (size_t)opp(i) * N + e);
-        if (n & NB_FLAG30) g[i] += R(a.inlet[i]);
-      } else {
-        g[i] = static_cast<const R*>(a.side_fwd)[n & NB_INDEX];
-      }
+      const uint32_t n = nb[i];
+      const size_t idx = n < NB_FLAG30 ? (size_t)i * N + n : (size_t)opp(i) * N + (size_t)e;
+      g[i] = Sto<S>::ld(x + idx);
     }
-    R lam_o[Q];
+    R lo[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      lam_o[i] = lam_out[(size_t)i * N + e];
-      lam_out[(size_t)i * N + e] = R(0);
-    }
-    R F[3];
-    load_force<S, R>(a.c.force, a.c.Ntot, e, F, D);
-    R lam_g[Q], lF[3] = {R(0), R(0), R(0)}, lom = R(0);
-    bgk_rev<Q, R>(g, om, rho_off, F, lam_o, lam_g, lF, lom);
-    part[0] += lom;
-    add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
-    // reverse streaming: every pulled value's adjoint goes back to its source slot
-    lam_in[e] += lam_g[0];
+    for (int i = 0; i < Q; ++i) lo[i] = lam_out[(size_t)i * N + e];
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const uint32_t n = nb[i];
-      if (n < NB_FLAG30) {
-        lam_in[(size_t)i * N + n] += lam_g[i];
-      } else if (n & NB_BOUNCE) {
-        lam_in[(size_t)opp(i) * N + e] += lam_g[i];
-        if (n & NB_FLAG30) {
-          // d f_i / d u_in = 6 w_i rho0 c_i
-#pragma unroll
-          for (int b = 0; b < D; ++b) part[2 + b] += lam_g[i] * R(6.0 * LT::w(i) * a.c.rho0 * LT::c(i, b));
+      if (n >= NB_FLAG30) {
+        if (n & NB_BOUNCE) {
+          if (n & NB_FLAG30) g[i] += R(a.inlet[i]);
+        } else {
+          g[i] = static_cast<const R*>(a.side_fwd)[n & NB_INDEX];
         }
-      } else {
-        static_cast<R*>(a.lam_side)[n & NB_INDEX] = lam_g[i];
+      }
+    }
+    R F[3];
+    load_force<S, R>(a.c.force, a.c.Ntot, e, F, D);
+    R rp, j[3];
+    raw_moments<Q, R>(g, rp, j);
+    const R rho = rho_off + rp, inv = R(1) / rho;
+    R u[3] = {R(0), R(0), R(0)}, usq = R(0), uF = R(0);
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      u[b] = (j[b] + R(0.5) * F[b]) * inv;
+      usq += u[b] * u[b];
+      uF += u[b] * F[b];
+    }
+    const R fpre = R(1) - R(0.5) * om;
+    R S0 = R(0), Sa[3] = {R(0), R(0), R(0)}, lF[3] = {R(0), R(0), R(0)}, lom = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      R cu = R(0), cF = R(0);
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        cu += R(LT::c(i, b)) * u[b];
+        cF += R(LT::c(i, b)) * F[b];
+      }
+      const R w = R(LT::w(i));
+      const R Ai = w * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+      const R geqi = w * (rp + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
+      const R Gi = w * (R(3) * (cF - uF) + R(9) * cu * cF);
+      const R l = lo[i];
+      S0 += l * Ai;
+      lom += l * (geqi - g[i] - R(0.5) * Gi);
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        const R cb = R(LT::c(i, b));
+        const R Bib = w * rho * (R(3) * cb + R(9) * cu * cb - R(3) * u[b]);
+        const R Gib = fpre * w * (-R(3) * F[b] + R(9) * cb * cF);
+        Sa[b] += l * (om * Bib + Gib);
+        lF[b] += l * fpre * w * (R(3) * (cb - u[b]) + R(9) * cu * cb);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < D; ++b) lF[b] += R(0.5) * Sa[b] * inv;
+    part[0] += lom;
+    add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
+    R base = om * S0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) base -= Sa[b] * u[b] * inv;
+    // reverse streaming (second phase: indices and output adjoints reloaded,
+    // both coalesced, so they need not stay live through the reductions)
+#pragma unroll
+    for (int i = 1; i < Q; ++i) nb[i] = __ldg(a.nbr + (size_t)(i - 1) * N + e);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lo[i] = lam_out[(size_t)i * N + e];
+    auto target = [&](int i) -> size_t {
+      const uint32_t n = nb[i];
+      return i == 0 ? (size_t)e : (n < NB_FLAG30 ? (size_t)i * N + n : (size_t)opp(i) * N + (size_t)e);
+    };
+    R cur[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const bool side = i > 0 && nb[i] >= NB_FLAG30 && !(nb[i] & NB_BOUNCE);
+      cur[i] = side ? R(0) : lam_in[target(i)];
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      R lg = (R(1) - om) * lo[i] + base;
+#pragma unroll
+      for (int b = 0; b < D; ++b) lg += Sa[b] * R(LT::c(i, b)) * inv;
+      const uint32_t n = nb[i];
+      lam_out[(size_t)i * N + e] = R(0);
+      if (i > 0 && n >= NB_FLAG30 && !(n & NB_BOUNCE)) {
+        static_cast<R*>(a.lam_side)[n & NB_INDEX] = lg;
+        continue;
+      }
+      lam_in[target(i)] = cur[i] + lg;
+      if (i > 0 && (n & NB_BOUNCE) && (n & NB_FLAG30)) {
+        // d f_i / d u_in = 6 w_i rho0 c_i
+#pragma unroll
+        for (int b = 0; b < D; ++b) part[2 + b] += lg * R(6.0 * LT::w(i) * a.c.rho0 * LT::c(i, b));
       }
     }
   }
