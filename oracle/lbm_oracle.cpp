@@ -191,6 +191,7 @@ struct Sim {
   double rho0 = 1.0;
   double uin[3] = {0.0, 0.0, 0.0};
   T uinT[3] = {T(0.0), T(0.0), T(0.0)};  // inlet velocity carried in T (tangent for the dual twin)
+  bool outlet_zero_gradient = false;     // outlet extrapolation order 0 instead of 1
   bool use_force = false;
   T omega_c = T(1.0);
   int Lmin = 0, Lmax = 0;
@@ -558,13 +559,19 @@ struct Sim {
         return e.f[ib] + T(6.0 * lat.w[i] * rho0) * cu;
       }
       case LK_OUT_NORMAL: {
-        // pressure-corrected outlet along the normal: f^eq_i(rho0, u) + f^neq_ib
+        // pressure-corrected outlet along the normal: f^eq_i(rho0, u) + f^neq_ib.
+        // The incoming value is a pre-collision pdf, so f^neq_ib is the
+        // pre-collision non-equilibrium part of the opposite pdf (the same
+        // quantity the interpolation of Sec. 2.2 works with), recovered from
+        // the stored post-collision values by moments().
         Mom<T> m;
         moments(e, l.omega, &m);
-        return feq(i, T(rho0), m.u) + (e.f[ib] - feq(ib, m.rho, m.u));
+        return feq(i, T(rho0), m.u) + m.fneq[ib];
       }
       case LK_OUT_EXTRAP:
-        // linear extrapolation of the missing outside element along -n
+        // extrapolation of the missing outside element along -n: linear
+        // (Sec. 2.3) or, as an option, zero-gradient
+        if (outlet_zero_gradient) return l.e[lk.a].f[i];
         return T(2.0) * l.e[lk.a].f[i] - l.e[lk.b].f[i];
     }
     return e.f[i];
@@ -1004,6 +1011,12 @@ int orc_init(void* h, const double* rho, const double* u, const double* S, const
   return init_sim(static_cast<Sim<double>*>(h), rho, u, S, df);
 }
 
+// Outlet extrapolation: 0 = linear (Sec. 2.3), 1 = zero-gradient.
+int orc_set_outlet(void* h, int mode) {
+  static_cast<Sim<double>*>(h)->outlet_zero_gradient = mode == 1;
+  return mode == 0 || mode == 1 ? 0 : -1;
+}
+
 int orc_set_force(void* h, const double* F) {
   auto* s = static_cast<Sim<double>*>(h);
   for (size_t k = 0; k < s->upos.size(); ++k) {
@@ -1129,6 +1142,11 @@ void orc_dual_destroy(void* h) { delete static_cast<Sim<Dual>*>(h); }
 
 int orc_dual_init(void* h, const double* rho, const double* u, const double* S, const double* df) {
   return init_sim(static_cast<Sim<Dual>*>(h), rho, u, S, df);
+}
+
+int orc_dual_set_outlet(void* h, int mode) {
+  static_cast<Sim<Dual>*>(h)->outlet_zero_gradient = mode == 1;
+  return mode == 0 || mode == 1 ? 0 : -1;
 }
 
 int orc_dual_set_force(void* h, const double* F, const double* F_dot) {

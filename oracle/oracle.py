@@ -49,6 +49,8 @@ def lib():
         for name in ("orc_init", "orc_dual_init"):
             getattr(L, name).argtypes = [P, P, P, P, P]
         L.orc_set_force.argtypes = [P, P]
+        L.orc_set_outlet.argtypes = [P, I]
+        L.orc_dual_set_outlet.argtypes = [P, I]
         L.orc_dual_set_force.argtypes = [P, P, P]
         L.orc_step.argtypes = [P, I64]
         L.orc_dual_step.argtypes = [P, I64]
@@ -89,7 +91,7 @@ class Oracle:
     carries a tangent (forward-mode derivative along omega_dot and F_dot)."""
 
     def __init__(self, mesh, stencil, omega_c, time_mode=0, rho0=1.0, u_in=(0.0, 0.0, 0.0),
-                 use_force=False, dual=False, omega_dot=0.0, u_in_dot=(0.0, 0.0, 0.0)):
+                 use_force=False, dual=False, omega_dot=0.0, u_in_dot=(0.0, 0.0, 0.0), outlet=0):
         L = lib()
         self.mesh, self.stencil, self.dual = mesh, stencil, dual
         self.d = 2 if stencil == 9 else 3
@@ -112,6 +114,9 @@ class Oracle:
         if not h:
             raise OracleError(err.value.decode())
         self.h = h
+        # outlet extrapolation: 0 linear (Sec. 2.3), 1 zero-gradient
+        if (L.orc_dual_set_outlet if dual else L.orc_set_outlet)(h, int(outlet)) != 0:
+            raise OracleError("outlet must be 0 (linear) or 1 (zero-gradient)")
 
     def __del__(self):
         h = getattr(self, "h", None)

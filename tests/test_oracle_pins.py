@@ -328,19 +328,57 @@ def test_couette_moving_wall(oracle_mod):
     assert np.abs(r1 - 1).max() < 1e-10
 
 
-def test_uniform_inflow_is_stationary(oracle_mod):
+@pytest.mark.parametrize("outlet", [0, 1])
+def test_uniform_inflow_is_stationary(oracle_mod, outlet):
     """Velocity inlet at x-, pressure outlet at x+: the uniform state
     (rho0, U) is a fixed point of both boundary rules (a sign slip in the
-    inlet term or in the outlet correction breaks it)."""
+    inlet term or in the outlet correction breaks it), with linear (0) and
+    zero-gradient (1) outlet extrapolation."""
     U = 0.05
     mesh = W.uniform(2, 4, (16, 8), (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_PERIODIC, W.BC_PERIODIC))
-    o = oracle_mod.Oracle(mesh, 9, 1.5, u_in=(U, 0.0, 0.0))
+    o = oracle_mod.Oracle(mesh, 9, 1.5, u_in=(U, 0.0, 0.0), outlet=outlet)
     rho, u, S = W.uniform_fields(mesh, 1.0, (U, 0.0))
     o.init(rho, u, S)
     o.step(50)
     r1, u1, _ = o.moments()
     assert np.abs(r1 - 1).max() < 1e-14
     assert np.abs(u1 - u).max() < 1e-14
+
+
+@pytest.mark.parametrize("outlet", [0, 1])
+def test_outlet_imposes_rho0(oracle_mod, outlet):
+    """Sec. 2.3: the outlet's normal pdf carries the equilibrium at the
+    prescribed density rho0.  A uniform stream started at rho = 1.02 between a
+    velocity inlet and the outlet relaxes to (rho0, U) everywhere (an outlet
+    equilibrium taken at the local density would keep rho = 1.02)."""
+    U = 0.05
+    mesh = W.uniform(2, 4, (16, 8), (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_PERIODIC, W.BC_PERIODIC))
+    o = oracle_mod.Oracle(mesh, 9, 1.5, u_in=(U, 0.0, 0.0), outlet=outlet)
+    rho, u, S = W.uniform_fields(mesh, 1.02, (U, 0.0))
+    o.init(rho, u, S)
+    o.step(2000)
+    r1, u1, _ = o.moments()
+    assert np.abs(r1 - 1).max() < 1e-3
+    assert np.abs(u1[:, 0] - U).max() < 1e-3
+    assert np.abs(u1[:, 1]).max() < 1e-12
+
+
+@pytest.mark.parametrize("outlet,omega,steps", [(0, 1.9, 1500), (1, 1.97, 3000)])
+def test_outlet_bounded_near_omega_two(oracle_mod, outlet, omega, steps):
+    """Walled channel (64 x 32, U = 0.05, seeded 1e-3 pdf noise) at relaxation
+    rates close to 2.  With f^neq of the normal rule taken pre-collision, the
+    linear extrapolation stays bounded at omega = 1.9, and the zero-gradient
+    option at omega = 1.97 (where the linear rule diverges within 6000 steps).
+    Reading f^neq from the post-collision values instead diverges at omega =
+    1.9 within 1500 steps."""
+    U = 0.05
+    mesh = W.uniform(2, 6, (64, 32), (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_WALL, W.BC_WALL))
+    o = oracle_mod.Oracle(mesh, 9, omega, u_in=(U, 0.0, 0.0), outlet=outlet)
+    o.init(*W.uniform_fields(mesh, 1.0, (U, 0.0)), W.pdf_perturbation(mesh, 9, 1e-3))
+    o.step(steps)
+    _, u1, _ = o.moments()
+    umax = np.sqrt((u1 ** 2).sum(1)).max()
+    assert np.isfinite(umax) and umax < 0.1
 
 
 def test_obstacle_force_balances_body_force(oracle_mod):
