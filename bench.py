@@ -59,7 +59,8 @@ def make_workload(name):
         desc = {"workload": "sphere_re100_d3q19_5level" + ("" if scale == 1 else "_half"),
                 "box": "32D x 16D x 16D", "D_finest": 64 // scale,
                 "levels": 5, "u_in": U, "omega_finest": round(om_f, 6), "omega_coarsest": round(om_c, 6),
-                "boundaries": "velocity inlet x-, pressure outlet x+, periodic y/z, half-way bounce-back sphere"}
+                "boundaries": "velocity inlet x-, pressure outlet x+, periodic y/z, half-way bounce-back sphere",
+                "outlet": "zero-gradient"}
         fields = lambda m: W.uniform_fields(m, 1.0, (U, 0.0, 0.0))
         return mesh, 19, om_c, (U, 0.0, 0.0), fields, desc
     mesh = W.config_tgv3d(64)
@@ -78,9 +79,13 @@ def small_sample():
     return m, om, (0.04, 0.0, 0.0)
 
 
-def bytes_per_update(Q, prec):
+def bytes_per_update(Q, prec, brick=False):
+    """Algorithmic HBM bytes of one element update: Q pdf reads and Q writes,
+    plus the 32-bit neighbour list (Q-1 entries) for the neighbour-list kernel
+    or one 27-entry row of neighbour-brick indices per 64 elements for the
+    interior-brick kernel."""
     s = {0: 8, 1: 4, 2: 2}[prec]
-    return 2 * Q * s + 4 * (Q - 1)
+    return 2 * Q * s + (27 * 4 / 64 if brick else 4 * (Q - 1))
 
 
 # ---------------------------------------------------------------- clocks
@@ -185,7 +190,7 @@ def cpu_oracle(seconds, min_steps=2):
     from oracle.oracle import Oracle
     from paper_1601_06984_gb300 import workloads as W
     m, om, uin = small_sample()
-    o = Oracle(m, 19, om, u_in=uin)
+    o = Oracle(m, 19, om, u_in=uin, outlet=1)
     o.init(*W.uniform_fields(m, 1.0, uin))
     o.step(1)
     steps, t0 = 0, time.perf_counter()
@@ -201,13 +206,16 @@ def cpu_oracle(seconds, min_steps=2):
 
 
 # ---------------------------------------------------------------- GPU runs
-def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_moments=False):
+OUTLETS = {"linear": 0, "zero-gradient": 1}
+
+
+def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_moments=False, outlet=0):
     import torch
 
     from paper_1601_06984_gb300 import lbm
     U = mesh.updates_per_coarse_step()
     t_build = time.perf_counter()
-    sim = lbm.Sim(mesh, Q, om, precision=prec, u_in=uin, device=device)
+    sim = lbm.Sim(mesh, Q, om, precision=prec, u_in=uin, device=device, outlet=outlet)
     t_build = time.perf_counter() - t_build
     rho, u, S = fields(mesh)
     sim.init(rho, u, S)
@@ -230,13 +238,26 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     nl, kms = sim.timing_read()
     ms = max_over_ranks(ms, dist, device)
     finest = len(info) - 1
-    units = int(info[finest, 1])  # fluid updates per finest launch
-    avg_ms = kms[finest] / max(nl[finest], 1)
-    bpu = bytes_per_update(Q, prec)
+    # dominant kernel: the interior-brick stream-collide of the finest level
+    # (the neighbour-list kernel when the level has no interior bricks)
+    kb = 0 if info[finest, 8] > 0 else 1
+    units = int(64 * info[finest, 8]) if kb == 0 else int(info[finest, 1])
+    avg_ms = kms[finest, kb] / max(nl[finest, kb], 1)
+    bpu = bytes_per_update(Q, prec, brick=kb == 0)
+    list_units = int(info[finest, 1] - 64 * info[finest, 8])
+    list_ms = kms[finest, 1] / max(nl[finest, 1], 1)
     res = {"ms_total": ms, "ms_per_step": ms / K, "mlups": K * U / (ms * 1e-3) / 1e6, "launches": launches,
-           "finest_launch_ms": avg_ms, "finest_launches": int(nl[finest]), "finest_units": units,
+           "finest_kernel": "k_stream_collide_brick" if kb == 0 else "k_stream_collide",
+           "finest_launch_ms": avg_ms, "finest_launches": int(nl[finest, kb]), "finest_units": units,
            "finest_bytes": units * bpu, "finest_gbs": units * bpu / (avg_ms * 1e-3) / 1e9,
-           "level_ms": [float(x) for x in kms], "level_launches": [int(x) for x in nl],
+           "finest_list_units": list_units, "finest_list_launch_ms": list_ms,
+           "finest_list_gbs": (list_units * bytes_per_update(Q, prec) / (list_ms * 1e-3) / 1e9
+                               if nl[finest, 1] > 0 and list_ms > 0 else None),
+           "level_ms": kms.sum(axis=1).tolist(), "level_launches": nl.sum(axis=1).tolist(),
+           "interior_fraction": float(64 * info[:, 8].sum() / info[:, 1].sum()),
+           "step_bytes": float(sum((1 << li) * (64 * info[li, 8] * bytes_per_update(Q, prec, brick=True)
+                                                + (info[li, 1] - 64 * info[li, 8]) * bytes_per_update(Q, prec))
+                                   for li in range(len(info)))),
            "bytes_per_update": bpu, "build_s": t_build, "device_gb": sim.device_bytes() / 1e9,
            "reduce": sim.reduce().tolist()}
     if want_moments:
@@ -366,8 +387,9 @@ def main():
     traffic_per_unit = stream_collide_traffic()
 
     clk = Clocks(uuid=gpu_uuid(device), index=local)
+    outlet = OUTLETS.get(desc.get("outlet"), 0)
     sim, r = run_gpu(mesh, Q, om, uin, fields, lbm.FP32DEV, K, W_, device, dist,
-                     want_moments=not args.no_variants)
+                     want_moments=not args.no_variants, outlet=outlet)
     clocks = clk.stop()
     e2e = e2e_run(sim, mesh, fields, K)
     if dist is not None:
@@ -381,7 +403,8 @@ def main():
     if not args.no_variants and rank == 0 and world == 1:
         mom = {}
         for name, prec in (("fp64", lbm.FP64), ("bf16dev", lbm.BF16DEV)):
-            s2, r2 = run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, None, want_moments=True)
+            s2, r2 = run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, None, want_moments=True,
+                             outlet=outlet)
             mom[name] = r2.pop("moments")
             variants[name] = {"mlups": r2["mlups"], "ms_per_step": r2["ms_per_step"],
                               "finest_kernel_gbs": r2["finest_gbs"], "finest_kernel_frac": r2["finest_gbs"] / peak,
@@ -437,10 +460,14 @@ def main():
                      "traffic": None if traffic_per_unit is None else traffic_per_unit * r["finest_units"],
                      "traffic_source": "ncu capture on the half-scale sphere scaled by units "
                                        "(profiles/stream_collide_fp32_sphere.md)",
-                     "kernel": "k_stream_collide<19,float> on the finest level",
+                     "kernel": r["finest_kernel"] + "<19,float> on the finest level",
                      "units_per_launch": r["finest_units"], "bytes_per_unit": r["bytes_per_update"],
                      "avg_launch_ms": r["finest_launch_ms"], "peak_source": peak_src},
-        "step_gbs_algorithmic": U * r["bytes_per_update"] / (r["ms_per_step"] * 1e-3) / 1e9,
+        "step_gbs_algorithmic": r["step_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9,
+        "interior_brick_fraction": r["interior_fraction"],
+        "finest_list_kernel": {"units_per_launch": r["finest_list_units"],
+                               "avg_launch_ms": r["finest_list_launch_ms"], "achieved_gbs": r["finest_list_gbs"],
+                               "bytes_per_unit": bytes_per_update(Q, lbm.FP32DEV)},
         "cpu_baseline": cb if cb is None else {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
         "gpu_launches": r["launches"], "clocks": clocks,

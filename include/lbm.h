@@ -59,6 +59,7 @@ typedef enum {
 enum { LBM_FP64 = 0, LBM_FP32DEV = 1, LBM_BF16DEV = 2 };
 enum { LBM_TIME_LINEAR = 0, LBM_TIME_TWO_LAYER = 1 };
 enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_VELOCITY_IN = 2, LBM_BC_PRESSURE_OUT = 3 };
+enum { LBM_OUTLET_LINEAR = 0, LBM_OUTLET_ZERO_GRADIENT = 1 };
 
 /* Simulation parameters.
  *  stencil       9 (D2Q9) or 19 (D3Q19); Sec. 2.1.
@@ -74,12 +75,18 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_VELOCITY_IN = 2, LBM_BC_PRES
  *  bc            per face x-, x+, y-, y+, z-, z+; PERIODIC must be set on both faces of
  *                an axis.  WALL = half-way bounce-back, VELOCITY_IN = velocity
  *                bounce-back with u_in, PRESSURE_OUT = extrapolation outlet with the
- *                normal pdf pressure-corrected to rho0 (Sec. 2.3).
+ *                normal pdf pressure-corrected to rho0: f_i = f^eq_i(rho0, u) +
+ *                f^neq_opp(i), f^neq the pre-collision non-equilibrium part (Sec. 2.3).
  *  omega_coarse  BGK relaxation rate on the coarsest level, in (0,2); finer levels
  *                follow 1/omega_f - 1/2 = 2 (1/omega_c - 1/2) (Sec. 2.2, Eq. fneq_scale).
  *  rho0          reference density (outlet density, deviation offset).
  *  u_in          inlet velocity (lattice units).
- *  use_force     nonzero: a per-element body force (Guo forcing) is applied. */
+ *  use_force     nonzero: a per-element body force (Guo forcing) is applied.
+ *  outlet        extrapolation of the outlet's tangential and oblique pdfs:
+ *                LBM_OUTLET_LINEAR (0): 2 f(x - n) - f(x - 2n), as in Sec. 2.3;
+ *                LBM_OUTLET_ZERO_GRADIENT (1): f(x - n), for relaxation rates
+ *                near 2 where the linear rule is unstable.  Other values:
+ *                LBM_ERR_ARG from lbm_build_mesh. */
 typedef struct {
   int32_t stencil;
   int32_t precision;
@@ -90,7 +97,7 @@ typedef struct {
   double rho0;
   double u_in[3];
   int32_t use_force;
-  int32_t reserved;
+  int32_t outlet;
 } lbm_params;
 
 /* Build the multilevel mesh on the host (no device work).
@@ -107,8 +114,12 @@ typedef struct {
 lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t n,
                           const lbm_params* params, lbm_ctx** out);
 
-/* Per level, 8 int64 each: level, fluid, GFC, GFF inner, GFF outer, padded
- * element count, outlet links, obstacle links.  cap = rows available in info. */
+/* Per level, 10 int64 each: level, fluid, GFC, GFF inner, GFF outer, padded
+ * element count, outlet links, obstacle links, interior bricks, 0.  An
+ * interior brick is an aligned block of 64 fluid elements of the level (4^3
+ * in 3D, 8^2 in 2D) whose stencil neighbours are all such blocks; the
+ * stream-collide locates their pull sources from a per-brick table instead
+ * of the neighbour list.  cap = rows available in info. */
 lbm_status lbm_mesh_info(const lbm_ctx* ctx, int64_t* info, int32_t cap, int32_t* nlevels);
 
 /* Bytes of the single device workspace the caller must allocate (256-byte
@@ -136,7 +147,11 @@ lbm_status lbm_set_force(lbm_ctx* ctx, const double* F);
 
 /* Advance n_coarse coarse time steps (Sec. 2.2 recursive level stepping:
  * GhostFromFiner, then GhostFromCoarser, then stream+collide on the level, then
- * two substeps of the next finer level). */
+ * two substeps of the next finer level).  Pairs of coarse steps replay a CUDA
+ * graph captured on first use (one per A/B parity state; dropped by
+ * lbm_set_params and lbm_bind) on the bound stream; a remaining single step,
+ * and all steps while timing is enabled, are launched kernel by kernel.  Both
+ * paths issue the same kernels in the same order. */
 lbm_status lbm_step(lbm_ctx* ctx, int64_t n_coarse);
 
 /* Fill every ghost element from the current state (the synchronous-time part
@@ -181,6 +196,13 @@ lbm_status lbm_reduce_noalloc(lbm_ctx* ctx, double out[8]);
 /* Post-collision pdfs f*[n][Q] of the fluid elements as FP64 (deviation storage
  * converted back to f), caller order. */
 lbm_status lbm_get_state(lbm_ctx* ctx, double* f);
+
+/* Restore a state written by lbm_get_state: f[n][Q] post-collision pdfs of
+ * the fluid elements (FP64, caller order), converted to the storage type
+ * (deviation storage subtracts w_i rho0).  Ghost elements are refilled on the
+ * next step.  With lbm_get_state this is a checkpoint / restart of the
+ * simulation state; in FP64 the round trip is exact. */
+lbm_status lbm_set_state(lbm_ctx* ctx, const double* f);
 
 /* Ghost elements: count, then info[n][6] (level, kind 1=GFC 2=GFF, layer, x, y, z
  * at the element's level) and f[n][Q] (FP64) of the current state. */
@@ -232,9 +254,10 @@ lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
 
 /* Device timing of the stream-collide kernel: while enabled, every
  * stream-collide launch is bracketed by CUDA events recorded on the bound
- * stream.  lbm_timing_read synchronises the stream and returns, per level
- * (rows 0..cap-1, coarsest first), the number of timed launches and their
- * summed device time in milliseconds, then clears the record.  Enabling
+ * stream.  lbm_timing_read synchronises the stream and returns, in row
+ * 2 L + k for level index L (coarsest 0) and kernel k (0: interior bricks,
+ * 1: neighbour list), the number of timed launches and their summed device
+ * time in milliseconds (rows 0..cap-1), then clears the record.  Enabling
  * clears it too. */
 lbm_status lbm_timing_enable(lbm_ctx* ctx, int32_t on);
 lbm_status lbm_timing_read(lbm_ctx* ctx, int64_t* launches, double* ms, int32_t cap);

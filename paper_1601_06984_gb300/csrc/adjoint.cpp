@@ -206,6 +206,7 @@ lbm_status lbm_set_params(lbm_ctx* c, double omega_coarse, const double* u_in) {
   for (int li = 1; li < c->nlev; ++li) om[li] = 1.0 / (0.5 + 2.0 * (1.0 / om[li - 1] - 0.5));
   for (int li = 0; li < c->nlev; ++li)
     if (std::fabs(1.0 - om[li]) < 1e-3) return c->fail(LBM_ERR_ARG, "omega too close to 1 on some level");
+  c->drop_graphs();  // captured steps carry the old omega and inlet values
   for (int li = 0; li < c->nlev; ++li) c->M.lv[li].omega = om[li];
   c->p.omega_coarse = omega_coarse;
   if (u_in) {
@@ -406,6 +407,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
             o.omega = H.omega;
             o.rho_off = c->rho_off;
             o.rho0 = c->p.rho0;
+            o.zero_gradient = c->p.outlet == LBM_OUTLET_ZERO_GRADIENT;
             c->ops->outlet(c->Q, o, st);
           }
           AdjSCArgs a{};
@@ -438,7 +440,9 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
               o.end = H.out_end;
               o.which = which;
               o.omega = H.omega;
+              o.zero_gradient = c->p.outlet == LBM_OUTLET_ZERO_GRADIENT;
               aops->outlet(c->Q, o, st);
+              if (which == 0) accum(li, -1);  // d/d omega through the normal links' f^neq
             }
           }
         } else if (t.op == OP_MOM_A || t.op == OP_MOM_B) {

@@ -404,22 +404,24 @@ template <int Q, class S>
 __global__ void __launch_bounds__(256) k_adj_outlet(const AdjOutletArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
-  constexpr int D = LT::D;
+  constexpr int D = LT::D, NS = LT::NS;
   const S* __restrict__ x = static_cast<const S*>(a.c.fsrc);
   R* lam_in = static_cast<R*>(a.c.lam_b);
   const R* lam_side = static_cast<const R*>(a.lam_side);
   const size_t N = (size_t)a.c.Ntot;
+  R part[1] = {R(0)};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.end; k += stride) {
     const int i = a.dir[k];
     const R ls = lam_side[k];
     if (a.kind[k] == OUT_EXTRAP) {
-      if (a.which == 1) lam_in[(size_t)i * N + a.a[k]] += R(2) * ls;
-      if (a.which == 2) lam_in[(size_t)i * N + a.b[k]] -= ls;
+      if (a.which == 1) lam_in[(size_t)i * N + a.a[k]] += a.zero_gradient ? ls : R(2) * ls;
+      if (a.which == 2 && !a.zero_gradient) lam_in[(size_t)i * N + a.b[k]] -= ls;
       continue;
     }
     if (a.which != 0) continue;
-    // side = g^eq_i(rho0, u) + g_ib - g^eq_ib(rho, u), u = (j - F/2)/rho
+    // side = g^eq_i(rho0, u) + f^neq_ib, with u and the pre-collision f^neq
+    // taken from the stored pdfs g (post_moments)
     const int64_t e = a.elem[k];
     R g[Q];
 #pragma unroll
@@ -436,38 +438,25 @@ __global__ void __launch_bounds__(256) k_adj_outlet(const AdjOutletArgs a) {
       usq += u[b] * u[b];
     }
     const int ib = opp(i);
-    R lq[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) lq[q] = R(0);
     // term g^eq_i(rho0, u): depends on u only
     R lam_rp_dummy = R(0), lam_u[3] = {R(0), R(0), R(0)};
     R l1[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) l1[q] = q == i ? ls : R(0);
     geq_rev<Q, R>(l1, R(a.c.rho0), u, usq, lam_rp_dummy, lam_u);
-    // term -g^eq_ib(rho, u)
-    R l2[Q];
+    // term f^neq_ib, and u's dependence on g
+    R lfn[Q], lS[NS], lg[Q], lF[3] = {R(0), R(0), R(0)}, lom = R(0);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) l2[q] = q == ib ? -ls : R(0);
-    R lam_rp = R(0);
-    geq_rev<Q, R>(l2, rho, u, usq, lam_rp, lam_u);
-    R lam_j[3], lam_rho = R(0), lF[3] = {R(0), R(0), R(0)};
+    for (int q = 0; q < Q; ++q) lfn[q] = q == ib ? ls : R(0);
 #pragma unroll
-    for (int b = 0; b < D; ++b) {
-      lam_j[b] = lam_u[b] * inv;
-      lF[b] = -R(0.5) * lam_u[b] * inv;
-      lam_rho += -lam_u[b] * u[b] * inv;
-    }
-    lam_rp += lam_rho;
+    for (int s2 = 0; s2 < NS; ++s2) lS[s2] = R(0);
+    post_moments_rev<Q, R>(g, R(a.omega), R(a.c.rho_off), F, R(0), lam_u, lfn, lS, lg, lF, lom);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      R v = lam_rp + (q == ib ? ls : R(0));
-#pragma unroll
-      for (int b = 0; b < D; ++b) v += R(LT::c(q, b)) * lam_j[b];
-      lam_in[(size_t)q * N + e] += v;
-    }
+    for (int q = 0; q < Q; ++q) lam_in[(size_t)q * N + e] += lg[q];
     add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
+    part[0] += lom;
   }
+  if (a.which == 0) store_partials<R, 1>(part, a.c.partial);
 }
 
 // ----------------------------------------------------------------- source moments
@@ -800,9 +789,12 @@ struct AdjLaunch {
     else k_adj_sc<19, S><<<kAdjBlocks, 256, 0, st>>>(a);
   }
   static void outlet(int Q, const AdjOutletArgs& a, cudaStream_t st) {
-    if (a.end <= a.begin) return;
-    if (Q == 9) k_adj_outlet<9, S><<<adj_grid(a.end - a.begin, 256), 256, 0, st>>>(a);
-    else k_adj_outlet<19, S><<<adj_grid(a.end - a.begin, 256), 256, 0, st>>>(a);
+    // the normal-link pass writes one row of omega partials per block, so it
+    // runs on the full kAdjBlocks grid that k_accum sums over
+    if (a.which != 0 && a.end <= a.begin) return;
+    const unsigned g = a.which == 0 ? (unsigned)kAdjBlocks : adj_grid(a.end - a.begin, 256);
+    if (Q == 9) k_adj_outlet<9, S><<<g, 256, 0, st>>>(a);
+    else k_adj_outlet<19, S><<<g, 256, 0, st>>>(a);
   }
   static void moments(int Q, const AdjMomArgs& a, cudaStream_t st) {
     if (Q == 9) k_adj_moments<9, S><<<kAdjBlocks, 128, 0, st>>>(a);

@@ -56,6 +56,8 @@ void lbm_ctx::layout() {
   oA = take(Q * N * sb);
   oB = take(Q * N * sb);
   oNbr = take((size_t)(Q - 1) * N * 4);
+  oBrickNb = take(m.brick_nb.size() * 4);
+  oBrickTab = take(m.brick_tab.size() * 2);
   oF = p.use_force ? take((size_t)d * N * cb) : 0;
   ld.assign(nlev, LevelDev());
   const size_t M_ = kMomStride;
@@ -164,9 +166,25 @@ void lbm_ctx::stream_collide(int li) {
     o.omega = H.omega;
     o.rho_off = rho_off;
     o.rho0 = p.rho0;
+    o.zero_gradient = p.outlet == LBM_OUTLET_ZERO_GRADIENT;
     ops->outlet(Q, o, st);
     ++launches;
   }
+  // interior bricks (the first 64 nB fluid elements) through the brick table
+  const int64_t nbrick = 64 * H.nB;
+  BrickArgs b{};
+  b.src = cur(li);
+  b.dst = nxt(li);
+  b.force = force_ptr();
+  b.nb = at<int32_t>(oBrickNb) + (size_t)H.brick_first * 27;
+  b.tab = at<uint16_t>(oBrickTab);
+  b.Ntot = M.Ntot;
+  b.begin = H.base + H.oF;
+  b.nB = H.nB;
+  b.omega = H.omega;
+  b.rho_off = rho_off;
+  // the rest through the neighbour list; processed range: TWO_LAYER [GFC |
+  // fluid], LINEAR [fluid | GFF inner], minus the interior bricks
   StreamCollideArgs a{};
   a.src = cur(li);
   a.dst = nxt(li);
@@ -174,27 +192,38 @@ void lbm_ctx::stream_collide(int li) {
   a.force = force_ptr();
   a.side = at(oSide);
   a.Ntot = M.Ntot;
-  // processed range: TWO_LAYER [GFC | fluid], LINEAR [fluid | GFF inner]
   if (p.time_mode == LBM_TIME_TWO_LAYER) {
     a.begin = H.base + H.oC;
-    a.end = H.base + H.oG1;
+    a.end = H.base + H.oG1 - nbrick;
+    a.hole_at = H.base + H.oF;
+    a.hole_len = nbrick;
   } else {
-    a.begin = H.base + H.oF;
+    a.begin = H.base + H.oF + nbrick;
     a.end = H.base + H.oG2;
+    a.hole_at = a.end;
+    a.hole_len = 0;
   }
   a.omega = H.omega;
   a.rho_off = rho_off;
   std::memcpy(a.inlet, inlet, sizeof(inlet));
-  if (timing) {
-    Timed t{li, get_event(), get_event()};
-    cudaEventRecord(t.a, st);
-    ops->stream_collide(Q, p.use_force != 0, a, st);
-    cudaEventRecord(t.b, st);
-    timed.push_back(t);
-  } else {
-    ops->stream_collide(Q, p.use_force != 0, a, st);
+  const bool use_force = p.use_force != 0;
+  auto launch = [&](int kernel) {
+    if (kernel == 0) ops->stream_collide_brick(Q, use_force, b, st);
+    else ops->stream_collide(Q, use_force, a, st);
+    ++launches;
+  };
+  for (int kernel = 0; kernel < 2; ++kernel) {
+    if (kernel == 0 ? b.nB == 0 : a.end <= a.begin) continue;
+    if (timing) {
+      Timed t{li, kernel, get_event(), get_event()};
+      cudaEventRecord(t.a, st);
+      launch(kernel);
+      cudaEventRecord(t.b, st);
+      timed.push_back(t);
+    } else {
+      launch(kernel);
+    }
   }
-  ++launches;
   parity[li] ^= 1;
 }
 
@@ -220,6 +249,44 @@ void lbm_ctx::advance(int li) {
     }
     advance(li + 1);
   }
+}
+
+const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
+  for (const StepGraph& g : graphs)
+    if (g.parity == parity) return &g;
+  if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    graphs_on = false;
+    return nullptr;
+  }
+  // capture on a private stream (the bound stream may be the legacy default
+  // stream, which cannot be captured); host bookkeeping is restored afterwards
+  const std::vector<int> p0 = parity;
+  const int64_t l0 = launches;
+  cudaStream_t user = st;
+  st = cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    advance(0);
+    advance(0);
+    e = cudaStreamEndCapture(cap_stream, &graph);
+  }
+  st = user;
+  const int64_t nl = launches - l0;
+  launches = l0;
+  const bool same = parity == p0;
+  parity = p0;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess && graph && same) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || !exec || !same) {
+    cudaGetLastError();
+    graphs_on = false;
+    return nullptr;
+  }
+  graphs.push_back({p0, exec, nl});
+  return &graphs.back();
 }
 
 // ---------------------------------------------------------------- internal accessors
@@ -280,6 +347,11 @@ lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t
     *out = c;
     return LBM_ERR_ARG;
   }
+  if (params->outlet != LBM_OUTLET_LINEAR && params->outlet != LBM_OUTLET_ZERO_GRADIENT) {
+    c->err = "bad outlet extrapolation";
+    *out = c;
+    return LBM_ERR_ARG;
+  }
   lbm_status s;
   try {
     s = build_host_mesh(tree_ids, levels, n, c->p, &c->M, &c->err);
@@ -312,8 +384,9 @@ lbm_status lbm_mesh_info(const lbm_ctx* c, int64_t* info, int32_t cap, int32_t* 
   int n = 0;
   for (const HostLevel& H : c->M.lv) {
     if (n >= cap) break;
-    int64_t r[8] = {H.L, H.nF, H.nC, H.nG1, H.nG2, H.N, H.out_end - H.out_begin, H.obs_end - H.obs_begin};
-    std::memcpy(info + 8 * n, r, sizeof(r));
+    int64_t r[10] = {H.L, H.nF, H.nC, H.nG1, H.nG2, H.N, H.out_end - H.out_begin, H.obs_end - H.obs_begin,
+                     H.nB, 0};
+    std::memcpy(info + 10 * n, r, sizeof(r));
     ++n;
   }
   if (nlevels) *nlevels = (int32_t)c->M.lv.size();
@@ -331,6 +404,7 @@ lbm_status lbm_bind(lbm_ctx* c, void* ws, uint64_t bytes, void* stream) {
   if (c->M.lv.empty()) return c->fail(LBM_ERR_STATE, "no mesh");
   if (bytes < c->bytes) return c->fail(LBM_ERR_ARG, "device workspace too small");
   if (reinterpret_cast<uintptr_t>(ws) % kAlign) return c->fail(LBM_ERR_ARG, "device workspace not 256-byte aligned");
+  c->drop_graphs();  // captured steps point into the previous workspace
   c->ws = static_cast<char*>(ws);
   c->st = static_cast<cudaStream_t>(stream);
   const HostMesh& m = c->M;
@@ -339,6 +413,8 @@ lbm_status lbm_bind(lbm_ctx* c, void* ws, uint64_t bytes, void* stream) {
     return c->cuda_check(cudaMemcpyAsync(c->ws + off, src, b, cudaMemcpyHostToDevice, c->st), "upload");
   };
   lbm_status s = up(c->oNbr, m.nbr.data(), m.nbr.size() * 4);
+  if (s == LBM_OK) s = up(c->oBrickNb, m.brick_nb.data(), m.brick_nb.size() * 4);
+  if (s == LBM_OK) s = up(c->oBrickTab, m.brick_tab.data(), m.brick_tab.size() * 2);
   for (int li = 0; li < c->nlev && s == LBM_OK; ++li) {
     const HostLevel& H = m.lv[li];
     s = up(c->ld[li].gff_child0, H.gff_child0.data(), H.gff_child0.size() * 4);
@@ -439,7 +515,20 @@ lbm_status lbm_set_force(lbm_ctx* c, const double* F) {
 lbm_status lbm_step(lbm_ctx* c, int64_t n_coarse) {
   if (!c || n_coarse < 0) return LBM_ERR_ARG;
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_step before lbm_bind");
-  for (int64_t k = 0; k < n_coarse; ++k) c->advance(0);
+  int64_t k = 0;
+  // pairs of coarse steps replay a captured graph; a single step, timed
+  // steps and the adjoint's recorded steps are issued one kernel at a time
+  if (c->graphs_on && !c->timing && !c->hook && !c->dry) {
+    while (n_coarse - k >= 2) {
+      const lbm_ctx::StepGraph* g = c->step_graph();
+      if (!g) break;
+      lbm_status s = c->cuda_check(cudaGraphLaunch(g->exec, c->st), "graph launch");
+      if (s != LBM_OK) return s;
+      c->launches += g->launches;
+      k += 2;
+    }
+  }
+  for (; k < n_coarse; ++k) c->advance(0);
   return c->launched("step");
 }
 
@@ -504,6 +593,26 @@ lbm_status lbm_get_state(lbm_ctx* c, double* f) {
   if (!c || !f) return LBM_ERR_ARG;
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_get_state before lbm_bind");
   return out_chunks(c, nullptr, nullptr, nullptr, f);
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const double* f) {
+  if (!c || !f) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_set_state before lbm_bind");
+  const int64_t n = c->M.n_user, CH = c->chunk;
+  double* sf = c->at<double>(c->oStage);
+  for (int64_t first = 0; first < n; first += CH) {
+    const int64_t cnt = std::min(CH, n - first);
+    lbm_status s = c->cuda_check(
+        cudaMemcpyAsync(sf, f + first * c->Q, cnt * c->Q * 8, cudaMemcpyHostToDevice, c->st), "state copy");
+    if (s != LBM_OK) return s;
+    SetStateArgs a{c->at(c->oA), c->at(c->oB), c->at<int32_t>(c->oUslot), c->at<uint8_t>(c->oUlev),
+                   c->parity_mask(), sf, first, cnt, c->M.Ntot, c->rho_off};
+    c->ops->set_state(c->Q, a, c->st);
+    ++c->launches;
+  }
+  lbm_status s = c->launched("set_state");
+  if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "state sync");
+  return s;
 }
 
 lbm_status lbm_reduce(lbm_ctx* c, double out[8]) {
@@ -618,9 +727,10 @@ lbm_status lbm_timing_read(lbm_ctx* c, int64_t* launches, double* ms, int32_t ca
     float e = 0.f;
     s = c->cuda_check(cudaEventElapsedTime(&e, t.a, t.b), "timing read");
     if (s != LBM_OK) break;
-    if (t.li < cap) {
-      launches[t.li] += 1;
-      ms[t.li] += e;
+    const int row = 2 * t.li + t.kernel;
+    if (row < cap) {
+      launches[row] += 1;
+      ms[row] += e;
     }
   }
   c->recycle_timed();

@@ -289,16 +289,24 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
-  const int64_t e0 = a.begin + (int64_t)blockIdx.x * (LBM_SC_BLOCK * EPT) + threadIdx.x;
+  const int64_t l0 = a.begin + (int64_t)blockIdx.x * (LBM_SC_BLOCK * EPT) + threadIdx.x;
   const S* __restrict__ src = static_cast<const S*>(a.src);
   S* __restrict__ dst = static_cast<S*>(a.dst);
   const uint32_t* __restrict__ nbr = a.nbr;
   const size_t N = (size_t)a.Ntot;
+  // linear position -> element, stepping over the interior bricks; linear
+  // positions at or past a.end are idle
+  int64_t el[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int64_t lin = l0 + k * LBM_SC_BLOCK;
+    el[k] = lin >= a.end ? -1 : lin + (lin >= a.hole_at ? a.hole_len : 0);
+  }
   uint32_t nb[EPT][Q - 1];
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int64_t e = e0 + k * LBM_SC_BLOCK;
-    if (e < a.end) {
+    const int64_t e = el[k];
+    if (e >= 0) {
 #pragma unroll
       for (int i = 1; i < Q; ++i) nb[k][i - 1] = ld_once(nbr + (size_t)(i - 1) * N + e);
     }
@@ -306,8 +314,8 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
   R g[EPT][Q];
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int64_t e = e0 + k * LBM_SC_BLOCK;
-    if (e < a.end) {
+    const int64_t e = el[k];
+    if (e >= 0) {
       g[k][0] = Sto<S>::ld(src + e);
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
@@ -319,8 +327,8 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
   }
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int64_t e = e0 + k * LBM_SC_BLOCK;
-    if (e >= a.end) continue;
+    const int64_t e = el[k];
+    if (e < 0) continue;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const uint32_t n = nb[k][i - 1];
@@ -344,11 +352,61 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
   }
 }
 
+// Stream-collide of interior bricks: the same pull and BGK collision as
+// k_stream_collide, with the pull source of link i located by the brick's
+// neighbour table instead of the per-element neighbour list.  One block holds
+// LBM_BR_BLOCK / 64 bricks; thread l of a brick is its element at z-curve
+// position l.  The link table and the bricks' neighbour rows are staged in
+// shared memory, so the element's HBM traffic is its Q pdf reads and Q writes.
+#ifndef LBM_BR_BLOCK
+#define LBM_BR_BLOCK 256
+#endif
+#ifndef LBM_BR_MINB
+#define LBM_BR_MINB 4
+#endif
+template <int Q, class S, bool FORCE>
+__global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_BR_MINB) k_stream_collide_brick(const BrickArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  constexpr int BPB = LBM_BR_BLOCK / 64;
+  __shared__ uint16_t tab[(Q - 1) * 64];
+  __shared__ int32_t nbs[BPB][27];
+  for (int k = threadIdx.x; k < (Q - 1) * 64; k += LBM_BR_BLOCK) tab[k] = a.tab[k];
+  const int lb = threadIdx.x >> 6, l = threadIdx.x & 63;
+  const int64_t b = (int64_t)blockIdx.x * BPB + lb;
+  if (l < 27 && b < a.nB) nbs[lb][l] = a.nb[b * 27 + l];
+  __syncthreads();
+  if (b >= a.nB) return;
+  const S* __restrict__ src = static_cast<const S*>(a.src);
+  S* __restrict__ dst = static_cast<S*>(a.dst);
+  const size_t N = (size_t)a.Ntot;
+  const int64_t e = a.begin + b * 64 + l;
+  R g[Q];
+  g[0] = Sto<S>::ld(src + e);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const uint32_t v = tab[(i - 1) * 64 + l];
+    const int64_t n = (int64_t)nbs[lb][v >> 6] + (v & 63);
+    g[i] = Sto<S>::ld(src + (size_t)i * N + n);
+  }
+  R F[3] = {R(0), R(0), R(0)};
+  if (FORCE) {
+    const R* __restrict__ fp = static_cast<const R*>(a.force);
+#pragma unroll
+    for (int c = 0; c < D; ++c) F[c] = fp[(size_t)c * N + e];
+  }
+  bgk_collide<Q, R, FORCE>(g, R(a.omega), R(a.rho_off), F);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) st_once(dst + (size_t)i * N + e, Sto<S>::cv(g[i]));
+}
+
 // ----------------------------------------------------------------- outlet values
 // Sec. 2.3 outflow: for an incoming direction i whose upstream element lies
 // beyond the outlet, either extrapolate that element's f_i linearly along -n
-// (2 f_i(x - c_i - n) - f_i(x - c_i - 2n)), or, for c_i = -n, correct the
-// pressure: f^eq_i(rho0, u) + f^neq_opp(i)(x).
+// (2 f_i(x - c_i - n) - f_i(x - c_i - 2n); optionally zero-gradient,
+// f_i(x - c_i - n)), or, for c_i = -n, correct the pressure:
+// f^eq_i(rho0, u) + f^neq_opp(i)(x) with the pre-collision f^neq.
 template <int Q, class S>
 __global__ void k_outlet(const OutletArgs a) {
   using R = typename Sto<S>::R;
@@ -361,7 +419,8 @@ __global__ void k_outlet(const OutletArgs a) {
   const int i = a.dir[k];
   R* side = static_cast<R*>(a.side);
   if (a.kind[k] == OUT_EXTRAP) {
-    side[k] = R(2) * Sto<S>::ld(src + (size_t)i * N + a.a[k]) - Sto<S>::ld(src + (size_t)i * N + a.b[k]);
+    const R fa = Sto<S>::ld(src + (size_t)i * N + a.a[k]);
+    side[k] = a.zero_gradient ? fa : R(2) * fa - Sto<S>::ld(src + (size_t)i * N + a.b[k]);
     return;
   }
   const int64_t e = a.elem[k];
@@ -387,8 +446,12 @@ __global__ void k_outlet(const OutletArgs a) {
 #pragma unroll
   for (int q = 0; q < Q; ++q)
     if (q == ib) gib = g[q];
+  // f^eq_i(rho0, u) + f^neq_ib, f^neq the pre-collision non-equilibrium part
+  // recovered from the stored post-collision pdf: (f* - f^eq - F_ib) / (1 - omega)
+  const R om = R(a.omega);
+  const R fneq_ib = (gib - geq<Q, R>(ib, rp, rho, u, usq) - guo<Q, R>(ib, om, u, F)) * (R(1) / (R(1) - om));
   const R r0 = R(a.rho0);
-  side[k] = geq<Q, R>(i, r0 - R(a.rho_off), r0, u, usq) + gib - geq<Q, R>(ib, rp, rho, u, usq);
+  side[k] = geq<Q, R>(i, r0 - R(a.rho_off), r0, u, usq) + fneq_ib;
 }
 
 // ----------------------------------------------------------------- GFC source moments
@@ -776,6 +839,20 @@ __global__ void k_out(const OutArgs a) {
 }
 
 template <int Q, class S>
+__global__ void k_set_state(const SetStateArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.cnt) return;
+  const int64_t k = a.first + t;
+  const int li = a.ulev[k];
+  S* cur = static_cast<S*>(((a.parity >> li) & 1) ? a.B : a.A);
+  const int64_t e = a.uslot[k];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    cur[(size_t)q * a.Ntot + e] =
+        Sto<S>::cv(typename Sto<S>::R(a.f[t * Q + q] - Lat<Q>::w(q) * a.rho_off));
+}
+
+template <int Q, class S>
 __global__ void k_gather_ghosts(const GatherGhostArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.cnt) return;
@@ -862,6 +939,17 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 template <class S>
 struct Launch {
+  static void stream_collide_brick(int Q, bool force, const BrickArgs& a, cudaStream_t st) {
+    if (a.nB <= 0) return;
+    const unsigned g = blocks_for(a.nB, LBM_BR_BLOCK / 64);
+    if (Q == 9) {
+      if (force) k_stream_collide_brick<9, S, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+      else k_stream_collide_brick<9, S, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+    } else {
+      if (force) k_stream_collide_brick<19, S, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+      else k_stream_collide_brick<19, S, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+    }
+  }
   static void stream_collide(int Q, bool force, const StreamCollideArgs& a, cudaStream_t st) {
     const int64_t n = a.end - a.begin;
     if (n <= 0) return;
@@ -910,6 +998,11 @@ struct Launch {
     if (Q == 9) k_out<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
     else k_out<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
   }
+  static void set_state(int Q, const SetStateArgs& a, cudaStream_t st) {
+    if (a.cnt <= 0) return;
+    if (Q == 9) k_set_state<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    else k_set_state<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+  }
   static void gather_ghosts(int Q, const GatherGhostArgs& a, cudaStream_t st) {
     if (a.cnt <= 0) return;
     if (Q == 9) k_gather_ghosts<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
@@ -923,9 +1016,11 @@ struct Launch {
 
 template <class S>
 const Ops* make_ops() {
-  static const Ops ops = {&Launch<S>::stream_collide, &Launch<S>::outlet,     &Launch<S>::source_moments,
+  static const Ops ops = {&Launch<S>::stream_collide, &Launch<S>::stream_collide_brick,
+                          &Launch<S>::outlet,         &Launch<S>::source_moments,
                           &Launch<S>::fill_gfc,       &Launch<S>::fill_gff,   &Launch<S>::fill_rest,
-                          &Launch<S>::init,           &Launch<S>::out,        &Launch<S>::gather_ghosts,
+                          &Launch<S>::init,           &Launch<S>::out,        &Launch<S>::set_state,
+                          &Launch<S>::gather_ghosts,
                           &Launch<S>::reduce,         sizeof(S),              sizeof(typename Sto<S>::R)};
   return &ops;
 }

@@ -30,7 +30,7 @@ struct lbm_ctx {
   double rho_off = 0.0;
   double inlet[19] = {};
   // layout (byte offsets into the workspace)
-  size_t oA = 0, oB = 0, oNbr = 0, oF = 0, oOutElem = 0, oOutA = 0, oOutB = 0, oOutDir = 0, oOutKind = 0,
+  size_t oA = 0, oB = 0, oNbr = 0, oBrickNb = 0, oBrickTab = 0, oF = 0, oOutElem = 0, oOutA = 0, oOutB = 0, oOutDir = 0, oOutKind = 0,
          oSide = 0, oObsElem = 0, oObsDir = 0, oUslot = 0, oUlev = 0, oStage = 0, oPartial = 0, oRed = 0;
   std::vector<lbm::LevelDev> ld;
   size_t bytes = 0;
@@ -48,7 +48,7 @@ struct lbm_ctx {
   // stream-collide timing (events recorded around each launch when enabled)
   bool timing = false;
   struct Timed {
-    int li;
+    int li, kernel;  // kernel 0: interior bricks, 1: neighbour list
     cudaEvent_t a, b;
   };
   std::vector<Timed> timed;
@@ -70,9 +70,26 @@ struct lbm_ctx {
     }
     timed.clear();
   }
+  // CUDA graphs of two coarse steps (every level's A/B parity is back where it
+  // started after two coarse steps), one per starting parity state; kernel
+  // arguments are baked in, so any change of them drops the graphs
+  struct StepGraph {
+    std::vector<int> parity;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<StepGraph> graphs;
+  cudaStream_t cap_stream = nullptr;
+  bool graphs_on = true;
+  void drop_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
   ~lbm_ctx() {
     recycle_timed();
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+    drop_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 
   template <class T = void>
@@ -106,5 +123,8 @@ struct lbm_ctx {
   void fill_gfc(int li_fine, bool two_times);
   void stream_collide(int li);
   void advance(int li);
+  // graph of two coarse steps from the current parity state, captured on
+  // first use; null when capture is unavailable (the caller steps eagerly)
+  const StepGraph* step_graph();
 };
 

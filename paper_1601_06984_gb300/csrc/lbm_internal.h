@@ -46,6 +46,8 @@ struct HostLevel {
   int64_t out_begin = 0, out_end = 0;
   // obstacle links of this level: global range in the obstacle list
   int64_t obs_begin = 0, obs_end = 0;
+  // interior bricks: the first 64 nB fluid elements; their rows in brick_nb
+  int64_t nB = 0, brick_first = 0;
 };
 
 struct HostMesh {
@@ -64,6 +66,12 @@ struct HostMesh {
   // obstacle links (all levels, grouped by level): element, direction i with x - c_i solid
   std::vector<int32_t> obs_elem;
   std::vector<int8_t> obs_dir;
+  // interior bricks (64 elements each, z-curve order inside): per brick the
+  // global index of the first element of the brick at offset slot
+  // t = (sx+1) + 3 (sy+1) + 9 (sz+1); per link i >= 1 and local position l the
+  // entry (t << 6) | l' locating the pull source f*_i(x - c_i)
+  std::vector<int32_t> brick_nb;    // [sum nB][27]
+  std::vector<uint16_t> brick_tab;  // [Q-1][64]
 };
 
 // Build the mesh tables; returns LBM_OK or LBM_ERR_MESH / LBM_ERR_ARG with msg.
@@ -83,9 +91,23 @@ struct StreamCollideArgs {
   const uint32_t* nbr;
   const void* force;  // [d][Ntot] compute type, or null
   const void* side;   // boundary values, compute type, or null
-  int64_t Ntot, begin, end;
+  int64_t Ntot, begin, end;  // linear range; element = lin + (lin >= hole_at ? hole_len : 0)
+  int64_t hole_at, hole_len;  // interior bricks skipped by this kernel (0 length: none)
   double omega, rho_off;
   double inlet[19];   // 6 w_i rho0 (c_i . u_in)
+};
+
+// Stream-collide of the interior bricks of one level: nB bricks of 64
+// elements from global index begin; neighbour bricks and link table as in
+// HostMesh::brick_nb / brick_tab.
+struct BrickArgs {
+  const void* src;
+  void* dst;
+  const void* force;    // [d][Ntot] compute type, or null
+  const int32_t* nb;    // [nB][27] rows of this level
+  const uint16_t* tab;  // [Q-1][64]
+  int64_t Ntot, begin, nB;
+  double omega, rho_off;
 };
 
 struct OutletArgs {
@@ -96,6 +118,7 @@ struct OutletArgs {
   const void* force;
   int64_t Ntot, begin, end;
   double omega, rho_off, rho0;
+  int zero_gradient;  // extrapolate with f(x - n) instead of 2 f(x - n) - f(x - 2n)
 };
 
 // GFC source moments: one record of kMomStride values per source (compute
@@ -151,6 +174,17 @@ struct InitArgs {
   double rho_off;
 };
 
+struct SetStateArgs {  // FP64 [cnt][Q] in user order -> current pdfs
+  void* A;
+  void* B;
+  const int32_t* uslot;
+  const uint8_t* ulev;
+  uint32_t parity;
+  const double* f;
+  int64_t first, cnt, Ntot;
+  double rho_off;
+};
+
 struct OutArgs {  // moments / state to FP64 staging in user order
   const void* A;
   const void* B;
@@ -201,6 +235,7 @@ struct FinalArgs {
 
 struct Ops {
   void (*stream_collide)(int Q, bool force, const StreamCollideArgs&, cudaStream_t);
+  void (*stream_collide_brick)(int Q, bool force, const BrickArgs&, cudaStream_t);
   void (*outlet)(int Q, const OutletArgs&, cudaStream_t);
   void (*source_moments)(int Q, const MomentsArgs&, cudaStream_t);
   void (*fill_gfc)(int Q, const GfcArgs&, cudaStream_t);
@@ -208,6 +243,7 @@ struct Ops {
   void (*fill_rest)(int Q, const FillArgs&, cudaStream_t);
   void (*init)(int Q, const InitArgs&, cudaStream_t);
   void (*out)(int Q, const OutArgs&, cudaStream_t);
+  void (*set_state)(int Q, const SetStateArgs&, cudaStream_t);
   void (*gather_ghosts)(int Q, const GatherGhostArgs&, cudaStream_t);
   void (*reduce)(int Q, const ReduceArgs&, cudaStream_t);
   size_t storage_bytes;  // bytes per stored pdf
@@ -250,6 +286,7 @@ struct AdjOutletArgs {
   int64_t begin, end;
   int which;  // 0: normal links, 1: extrapolation term of source a, 2: of source b
   double omega;
+  int zero_gradient;
 };
 
 struct AdjMomArgs {  // reverse of the source moments

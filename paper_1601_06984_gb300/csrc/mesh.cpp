@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <unordered_map>
 
 #include "lbm_internal.h"
 
@@ -225,6 +226,108 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     }
   }
 
+  // ---- interior bricks.  A brick is an aligned block of 64 same-level fluid
+  // elements (4^3 in 3D, 8^2 in 2D), i.e. one run of z-curve keys sharing
+  // key >> 6.  A complete brick is interior when every brick its elements pull
+  // from (the face and edge neighbours the stencil reaches) is complete too:
+  // all its links are plain pulls between fluid elements of one level, and the
+  // source of link i at local position l is brick slot t plus local position
+  // l', a table common to all bricks.  Interior bricks move to the front of
+  // the level's fluid list; everything keeps z-curve order within its part
+  // (so GhostFromFiner children stay contiguous).
+  const int bshift = d == 3 ? 2 : 3, bside = 1 << bshift;
+  std::vector<std::vector<std::array<int64_t, 27>>> brick_nbpos(nlev);  // per interior brick: slot -> new position
+  {
+    // brick offsets the stencil needs: s_a in {0, -c_a}, not all zero
+    bool need[27] = {};
+    for (int i = 1; i < Q; ++i)
+      for (int m = 1; m < (1 << d); ++m) {
+        int s3[3] = {0, 0, 0};
+        bool ok = true;
+        for (int a = 0; a < d; ++a)
+          if (m >> a & 1) {
+            if (B.dr.c[i][a] == 0) ok = false;
+            s3[a] = -B.dr.c[i][a];
+          }
+        if (ok) need[(s3[0] + 1) + 3 * (s3[1] + 1) + 9 * (s3[2] + 1)] = true;
+      }
+    for (int li = 0; li < nlev; ++li) {
+      auto& f = fl[li];
+      const int64_t nf = (int64_t)f.size();
+      std::vector<int64_t> cstart;  // original start of each complete brick
+      std::unordered_map<uint64_t, int64_t> cidx;
+      for (int64_t j = 0; j + 63 < nf;) {
+        if ((f[j].first & 63) == 0 && f[j + 63].first == f[j].first + 63) {
+          cidx.emplace(f[j].first >> 6, (int64_t)cstart.size());
+          cstart.push_back(j);
+          j += 64;
+        } else {
+          ++j;
+        }
+      }
+      const int64_t nc = (int64_t)cstart.size();
+      int64_t nbx[3];
+      for (int a = 0; a < 3; ++a) nbx[a] = a < d ? (B.ext(li, a) + bside - 1) >> bshift : 1;
+      std::vector<std::array<int64_t, 27>> nbc(nc);
+      std::vector<uint8_t> interior(nc, 0);
+#pragma omp parallel for schedule(static)
+      for (int64_t b = 0; b < nc; ++b) {
+        const int64_t* x0 = &X[3 * f[cstart[b]].second];
+        int64_t bc[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) bc[a] = x0[a] >> bshift;
+        bool ok = true;
+        for (int t = 0; t < 27 && ok; ++t) {
+          nbc[b][t] = b;
+          if (!need[t]) continue;
+          const int sx[3] = {t % 3 - 1, t / 3 % 3 - 1, t / 9 - 1};
+          int64_t q[3] = {0, 0, 0};
+          for (int a = 0; a < d && ok; ++a) {
+            q[a] = bc[a] + sx[a];
+            if (q[a] < 0 || q[a] >= nbx[a]) {
+              // across the domain edge: only a periodic axis whose extent is a
+              // whole number of bricks keeps the brick structure
+              if (!B.periodic(a) || (B.ext(li, a) & (bside - 1)) != 0) ok = false;
+              else q[a] = (q[a] + nbx[a]) % nbx[a];
+            }
+          }
+          if (!ok) break;
+          auto it = cidx.find(zkey(q, d, B.Lmin + li - bshift));
+          if (it == cidx.end()) ok = false;
+          else nbc[b][t] = it->second;
+        }
+        interior[b] = ok;
+      }
+      // new order: interior bricks, then the rest; new position of every complete brick
+      std::vector<int64_t> cnew(nc);
+      std::vector<std::pair<uint64_t, int64_t>> g;
+      g.reserve(nf);
+      int64_t nint = 0;
+      for (int64_t b = 0; b < nc; ++b)
+        if (interior[b]) {
+          cnew[b] = 64 * nint++;
+          g.insert(g.end(), f.begin() + cstart[b], f.begin() + cstart[b] + 64);
+        }
+      {
+        int64_t b = 0;
+        for (int64_t j = 0; j < nf; ++j) {
+          while (b < nc && cstart[b] + 64 <= j) ++b;
+          const bool in_brick = b < nc && cstart[b] <= j;
+          if (in_brick && interior[b]) continue;
+          if (in_brick && j == cstart[b]) cnew[b] = (int64_t)g.size();
+          g.push_back(f[j]);
+        }
+      }
+      f.swap(g);
+      auto& bn = brick_nbpos[li];
+      bn.resize(nint);
+      for (int64_t b = 0, k = 0; b < nc; ++b)
+        if (interior[b]) {
+          for (int t = 0; t < 27; ++t) bn[k][t] = cnew[nbc[b][t]];
+          ++k;
+        }
+    }
+  }
+
   // ---- bounding boxes and dense lookup grids
   B.grid.resize(nlev);
   B.kind.resize(nlev);
@@ -434,6 +537,41 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
   }
   M.Ntot = base;
   if (M.Ntot >= (int64_t)NB_INDEX) return bad(LBM_ERR_MESH, "too many elements for 30-bit neighbour indices");
+  // interior bricks: global first-element index of each neighbour brick, and
+  // the (slot, local position) table of every link
+  {
+    int64_t rows = 0;
+    for (int li = 0; li < nlev; ++li) {
+      HostLevel& H = M.lv[li];
+      H.nB = (int64_t)brick_nbpos[li].size();
+      H.brick_first = rows;
+      rows += H.nB;
+    }
+    M.brick_nb.resize((size_t)rows * 27);
+    for (int li = 0; li < nlev; ++li) {
+      const HostLevel& H = M.lv[li];
+      for (int64_t b = 0; b < H.nB; ++b)
+        for (int t = 0; t < 27; ++t)
+          M.brick_nb[(size_t)(H.brick_first + b) * 27 + t] = (int32_t)(H.base + H.oF + brick_nbpos[li][b][t]);
+    }
+    M.brick_tab.assign((size_t)(Q - 1) * 64, 0);
+    for (int i = 1; i < Q; ++i)
+      for (int l = 0; l < 64; ++l) {
+        int64_t x[3] = {0, 0, 0};
+        for (int bb = 0; bb < bshift; ++bb)
+          for (int a = 0; a < d; ++a) x[a] |= (int64_t)((l >> (d * bb + a)) & 1) << bb;
+        int t = 0, mul = 1;
+        int64_t y[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) {
+          const int64_t q = a < d ? x[a] - B.dr.c[i][a] : 0;
+          const int sa = q < 0 ? -1 : (q >= bside ? 1 : 0);
+          y[a] = q - sa * bside;
+          t += (sa + 1) * mul;
+          mul *= 3;
+        }
+        M.brick_tab[(size_t)(i - 1) * 64 + l] = (uint16_t)((t << 6) | (int)zkey(y, d, bshift));
+      }
+  }
   // relaxation per level, Eq. (fneq_scale)
   M.lv[0].omega = p.omega_coarse;
   for (int li = 1; li < nlev; ++li) M.lv[li].omega = 1.0 / (0.5 + 2.0 * (1.0 / M.lv[li - 1].omega - 0.5));
@@ -697,6 +835,22 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     H.obs_end = (int64_t)M.obs_elem.size();
   }
   if ((int64_t)M.out_elem.size() >= (int64_t)NB_INDEX) return bad(LBM_ERR_MESH, "too many outlet links");
+  // interior bricks must reproduce the neighbour list exactly
+  for (int li = 0; li < nlev; ++li) {
+    const HostLevel& H = M.lv[li];
+    int mismatch = 0;
+#pragma omp parallel for schedule(static) reduction(| : mismatch)
+    for (int64_t b = 0; b < H.nB; ++b) {
+      const int32_t* nb = &M.brick_nb[(size_t)(H.brick_first + b) * 27];
+      for (int i = 1; i < Q; ++i)
+        for (int l = 0; l < 64; ++l) {
+          const uint16_t v = M.brick_tab[(size_t)(i - 1) * 64 + l];
+          const int64_t e = H.base + H.oF + 64 * b + l;
+          if (M.nbr[(size_t)(i - 1) * M.Ntot + e] != (uint32_t)(nb[v >> 6] + (v & 63))) mismatch = 1;
+        }
+    }
+    if (mismatch) return bad(LBM_ERR_INTERNAL, "interior brick table disagrees with the neighbour list");
+  }
 
   // ---- caller order -> element slots
   M.uslot.resize(n);

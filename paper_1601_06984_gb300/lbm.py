@@ -20,8 +20,9 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_MESH", -3: "LBM_ERR_CUDA"
           -5: "LBM_ERR_STATE", -6: "LBM_ERR_NUMERIC", -7: "LBM_ERR_INTERNAL"}
 FP64, FP32DEV, BF16DEV = 0, 1, 2
 TIME_LINEAR, TIME_TWO_LAYER = 0, 1
+OUTLET_LINEAR, OUTLET_ZERO_GRADIENT = 0, 1
 EXPORTS = ["lbm_build_mesh", "lbm_mesh_info", "lbm_device_bytes", "lbm_bind", "lbm_init", "lbm_set_force",
-           "lbm_step", "lbm_fill_ghosts", "lbm_moments", "lbm_reduce", "lbm_get_state", "lbm_ghost_count",
+           "lbm_step", "lbm_fill_ghosts", "lbm_moments", "lbm_reduce", "lbm_get_state", "lbm_set_state", "lbm_ghost_count",
            "lbm_get_ghosts", "lbm_sfc_partition", "lbm_kernel_launches", "lbm_timing_enable", "lbm_timing_read",
            "lbm_reduce_noalloc", "lbm_set_params", "lbm_adjoint_bytes", "lbm_adjoint", "lbm_last_error",
            "lbm_destroy"]
@@ -37,7 +38,7 @@ class lbm_params(C.Structure):
     _fields_ = [("stencil", C.c_int32), ("precision", C.c_int32), ("time_mode", C.c_int32),
                 ("extent", C.c_int32 * 3), ("bc", C.c_int32 * 6), ("omega_coarse", C.c_double),
                 ("rho0", C.c_double), ("u_in", C.c_double * 3), ("use_force", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("outlet", C.c_int32)]
 
 
 _lib = None
@@ -64,6 +65,7 @@ def lib():
             "lbm_moments": [P, P, P, P],
             "lbm_reduce": [P, P],
             "lbm_get_state": [P, P],
+            "lbm_set_state": [P, P],
             "lbm_ghost_count": [P, C.POINTER(I64)],
             "lbm_get_ghosts": [P, P, P],
             "lbm_sfc_partition": [P, I64, I32, I32, P, P, P, P],
@@ -146,7 +148,7 @@ class Sim:
     the host only (no GPU needed); otherwise a torch CUDA device."""
 
     def __init__(self, mesh, stencil, omega_c, precision=FP64, time_mode=TIME_LINEAR, rho0=1.0,
-                 u_in=(0.0, 0.0, 0.0), use_force=False, device="cuda", stream=None):
+                 u_in=(0.0, 0.0, 0.0), use_force=False, device="cuda", stream=None, outlet=OUTLET_LINEAR):
         self.d = 2 if stencil == 9 else 3
         self.Q = stencil
         self.ns = 3 if self.d == 2 else 6
@@ -161,6 +163,7 @@ class Sim:
         for f in range(6):
             p.bc[f] = int(bc[f])
         p.omega_coarse, p.rho0, p.use_force = float(omega_c), float(rho0), int(bool(use_force))
+        p.outlet = int(outlet)
         self.params = p
         self.ctx = lbm_build_mesh(mesh.tree_ids, mesh.levels, p)
         self.ws = None
@@ -188,7 +191,7 @@ class Sim:
 
     # -- queries
     def mesh_info(self):
-        info = np.zeros((32, 8), np.int64)
+        info = np.zeros((32, 10), np.int64)
         nl = C.c_int32()
         _check(self.ctx, lib().lbm_mesh_info(self.ctx, _p(info), 32, C.byref(nl)))
         return info[: nl.value]
@@ -207,12 +210,13 @@ class Sim:
         _check(self.ctx, lib().lbm_timing_enable(self.ctx, int(bool(on))))
 
     def timing_read(self):
-        """Per level: (stream-collide launches, summed device ms) since enabled."""
-        n = np.zeros(32, np.int64)
-        ms = np.zeros(32)
-        _check(self.ctx, lib().lbm_timing_read(self.ctx, _p(n), _p(ms), 32))
+        """Stream-collide launches and summed device ms since enabled, arrays
+        [level, kernel] with kernel 0 = interior bricks, 1 = neighbour list."""
+        n = np.zeros(64, np.int64)
+        ms = np.zeros(64)
+        _check(self.ctx, lib().lbm_timing_read(self.ctx, _p(n), _p(ms), 64))
         nl = len(self.mesh_info())
-        return n[:nl], ms[:nl]
+        return n[: 2 * nl].reshape(nl, 2), ms[: 2 * nl].reshape(nl, 2)
 
     # -- state
     def init(self, rho, u, S=None, df=None):
@@ -243,6 +247,10 @@ class Sim:
         f = np.empty((self.n, self.Q))
         _check(self.ctx, lib().lbm_get_state(self.ctx, _p(f)))
         return f
+
+    def set_state(self, f):
+        f = _arr(f, np.float64, (self.n, self.Q))
+        _check(self.ctx, lib().lbm_set_state(self.ctx, _p(f)))
 
     def ghosts(self):
         n = C.c_int64()

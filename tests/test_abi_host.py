@@ -2,6 +2,7 @@
 entry point declared in include/lbm.h, the host mesh builder agrees with the
 oracle's own mesh code on ghost counts and on rejected meshes, and the
 z-curve / weight utility reproduces the paper's worked example."""
+import itertools
 import json
 import os
 import re
@@ -108,6 +109,8 @@ def test_bad_arguments(lbm):
         lbm.Sim(mesh, 9, 2.5, device=None)          # omega outside (0,2)
     with pytest.raises(lbm.LBMError):
         lbm.Sim(mesh, 7, 1.6, device=None)          # unknown stencil
+    with pytest.raises(lbm.LBMError, match="outlet"):
+        lbm.Sim(mesh, 9, 1.6, device=None, outlet=2)  # unknown outlet extrapolation
     half_periodic = W.Mesh(2, mesh.extent, (0, 1, 0, 0), mesh.tree_ids, mesh.levels, mesh.coords, mesh.lmin)
     with pytest.raises(lbm.LBMError, match="periodic"):
         lbm.Sim(half_periodic, 9, 1.6, device=None)
@@ -136,3 +139,53 @@ def test_updates_weighting():
     assert m.updates_per_coarse_step() == 768 + 2 * 1024
     m3 = W.config_tgv3d(64)
     assert m3.updates_per_coarse_step() == 229376 + 2 * 262144
+
+
+def _interior_bricks(mesh):
+    """Per level, interior bricks counted from the element coordinates alone:
+    aligned blocks of 64 same-level elements (4^3 / 8^2) whose face and edge
+    neighbour blocks (all eight in 2D) are complete too; periodic axes wrap
+    when their extent is a whole number of blocks."""
+    d = mesh.d
+    side = 4 if d == 3 else 8
+    offs = [o for o in itertools.product((-1, 0, 1), repeat=d) if any(o)]
+    if d == 3:
+        offs = [o for o in offs if sum(map(abs, o)) <= 2]  # D3Q19 reaches no corner block
+    out = []
+    for L in sorted(set(int(v) for v in mesh.levels)):
+        sel = mesh.levels == L
+        xyz = mesh.coords[sel][:, :d] // side
+        keys, cnt = np.unique(xyz, axis=0, return_counts=True)
+        full = {tuple(k) for k, c in zip(keys, cnt) if c == side ** d}
+        ext = [e << (L - mesh.lmin) for e in mesh.extent]
+        nb = [(e + side - 1) // side for e in ext]
+        n = 0
+        for k in full:
+            ok = True
+            for o in offs:
+                q = []
+                for a in range(d):
+                    v = k[a] + o[a]
+                    if v < 0 or v >= nb[a]:
+                        if mesh.bc[2 * a] != W.BC_PERIODIC or ext[a] % side:
+                            ok = False
+                            break
+                        v %= nb[a]
+                    q.append(v)
+                if not ok or tuple(q) not in full:
+                    ok = False
+                    break
+            n += ok
+        out.append(n)
+    return out
+
+
+@pytest.mark.parametrize("name", ["tgv2d", "tgv3d16", "half2d", "cylinder", "sphere_small"])
+def test_interior_brick_counts(lbm, name):
+    """The builder's interior bricks match an independent count, and the
+    builder has checked each brick's link table against the neighbour list."""
+    mesh, Q = {"tgv2d": (W.config_tgv2d(), 9), "tgv3d16": (W.config_tgv3d(16), 19),
+               "half2d": (W.half_refined_2d(32), 9), "cylinder": (W.config_cylinder(), 9),
+               "sphere_small": (W.config_sphere_small(), 19)}[name]
+    info = lbm.Sim(mesh, Q, 1.7, u_in=(0.04, 0, 0), device=None).mesh_info()
+    assert [int(r[8]) for r in info] == _interior_bricks(mesh)

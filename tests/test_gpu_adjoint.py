@@ -41,11 +41,20 @@ def make(name):
         m = W.config_sphere_small()
         return (m, 19, W.omega_coarse_from_finest(1.6, 3), (0.04, 0.0, 0.0),
                 lambda m: W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), 3, 2)
+    if name in ("channel", "channel_zg"):
+        # walled inlet/outlet channel, refined block in the middle; omega near 2
+        # on the coarse level exercises the outlet's f^neq rescale
+        m = W.nested_boxes(2, 5, (32, 16), [((16, 8), (40, 24))],
+                           (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_WALL, W.BC_WALL))
+        return (m, 9, 1.85, (0.05, 0.0, 0.0),
+                lambda m: W.uniform_fields(m, 1.0, (0.05, 0.0)), 6, 2)
     raise KeyError(name)
 
 
+OUTLET = {"channel_zg": 1}
 CASES = [("uni2d", 0, 0), ("tgv2d", 0, 0), ("tgv2d", 1, 0), ("half2d", 0, 0), ("tgv3d", 0, 0), ("tgv3d", 1, 0),
-         ("sphere", 0, 0), ("sphere", 1, 0), ("sphere", 0, 1), ("sphere", 1, 3)]
+         ("sphere", 0, 0), ("sphere", 1, 0), ("sphere", 0, 1), ("sphere", 1, 3),
+         ("channel", 0, 0), ("channel", 1, 0), ("channel_zg", 0, 0)]
 
 
 def J_of(red, objective):
@@ -58,23 +67,25 @@ def test_adjoint_matches_dual_oracle(lbm, oracle_mod, name, mode, objective):
     d = 2 if Q == 9 else 3
     rho, u, S = fields(m)
     F = W.gaussian_force(m, 1e-5)
-    g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True)
+    out = OUTLET.get(name, 0)
+    g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True, outlet=out)
     g.init(rho, u, S, W.pdf_perturbation(m, Q, 1e-5))
     g.set_force(F)
     f0 = g.get_state()
     J, dF, dw, dU, df0 = g.adjoint(n, K, objective, want_f0=True)
     vF = W.random_direction((m.n, d), W.SEED, 21) * 1e-5
     vw = 0.37
-    vU = np.array([0.9, -0.4, 0.25]) if name == "sphere" else np.zeros(3)
+    has_uin = bool(np.any(np.asarray(uin) != 0))
+    vU = np.array([0.9, -0.4, 0.25 if d == 3 else 0.0]) if has_uin else np.zeros(3)
     vf0 = W.random_direction((m.n, Q), W.SEED, 22) * 1e-4
     parts = {"force": (vF, 0.0, np.zeros(3), None), "omega": (0 * vF, vw, np.zeros(3), None),
              "u_in": (0 * vF, 0.0, vU, None), "f0": (0 * vF, 0.0, np.zeros(3), vf0)}
     for key, (a, b, c, fd0) in parts.items():
-        if key == "u_in" and name != "sphere":
+        if key == "u_in" and not has_uin:
             continue
         adj = float((dF * a).sum() + dw * b + (dU * c).sum() + (0.0 if fd0 is None else (df0 * fd0).sum()))
         od = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin, use_force=True, dual=True, omega_dot=b,
-                               u_in_dot=tuple(c))
+                               u_in_dot=tuple(c), outlet=out)
         od.set_f(f0, fd0)
         od.set_force(F, a)
         od.step(n)
@@ -87,7 +98,7 @@ def test_adjoint_matches_dual_oracle(lbm, oracle_mod, name, mode, objective):
         assert abs(adj - exact) <= 1e-9 * scale, (key, adj, exact)
 
 
-@pytest.mark.parametrize("name,mode", [("tgv2d", 0), ("tgv3d", 1), ("sphere", 0)])
+@pytest.mark.parametrize("name,mode", [("tgv2d", 0), ("tgv3d", 1), ("sphere", 0), ("channel_zg", 0)])
 def test_adjoint_matches_central_differences(lbm, name, mode):
     m, Q, om, uin, fields, n, K = make(name)
     d = 2 if Q == 9 else 3
@@ -95,17 +106,18 @@ def test_adjoint_matches_central_differences(lbm, name, mode):
     F = W.gaussian_force(m, 1e-5)
     vF = W.random_direction((m.n, d), W.SEED, 31) * 1e-5
     vw = -0.21
-    vU = np.array([0.5, 0.2, -0.3]) if name == "sphere" else np.zeros(3)
+    vU = np.array([0.5, 0.2, -0.3 if d == 3 else 0.0]) if np.any(np.asarray(uin) != 0) else np.zeros(3)
+    out = OUTLET.get(name, 0)
 
     def run(h):
-        g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True)
+        g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True, outlet=out)
         g.init(rho, u, S)
         g.set_params(om + h * vw, tuple(np.array(uin) + h * vU))
         g.set_force(F + h * vF)
         g.step(n)
         return g, g.reduce()[7]
 
-    g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True)
+    g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True, outlet=out)
     g.init(rho, u, S)
     g.set_force(F)
     J, dF, dw, dU = g.adjoint(n, K, 0)

@@ -49,6 +49,11 @@ def make_case(name):
         om = W.omega_coarse_from_finest(W.omega_for_re(0.05, 40, 20), 4)
         return (m, 9, om, (0.05, 0, 0),
                 lambda m: (*W.uniform_fields(m, 1.0, (0.05, 0.0)), W.pdf_perturbation(m, 9, 1e-4)), None, 2)
+    if name == "channel_zg":
+        m = W.nested_boxes(2, 5, (32, 16), [((16, 8), (40, 24))],
+                           (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_WALL, W.BC_WALL))
+        return (m, 9, 1.85, (0.05, 0, 0),
+                lambda m: (*W.uniform_fields(m, 1.0, (0.05, 0.0)), W.pdf_perturbation(m, 9, 1e-4)), None, 40)
     if name == "sphere_small":
         m = W.config_sphere_small()
         om = W.omega_coarse_from_finest(1.6, 3)
@@ -57,12 +62,17 @@ def make_case(name):
     raise KeyError(name)
 
 
+OUTLET = {"channel_zg": 1}  # zero-gradient outlet extrapolation
+
+
 def run_both(lbm, oracle_mod, name, mode, precision=0):
     m, Q, om, uin, fields, force, steps = make_case(name)
     rho, u, S, df = fields(m)
-    o = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin, use_force=force is not None)
+    out = OUTLET.get(name, 0)
+    o = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin, use_force=force is not None, outlet=out)
     o.init(rho, u, S, df)
-    g = lbm.Sim(m, Q, om, precision=precision, time_mode=mode, u_in=uin, use_force=force is not None)
+    g = lbm.Sim(m, Q, om, precision=precision, time_mode=mode, u_in=uin, use_force=force is not None,
+                outlet=out)
     g.init(rho, u, S, df)
     if force is not None:
         o.set_force(force)
@@ -72,7 +82,7 @@ def run_both(lbm, oracle_mod, name, mode, precision=0):
     return m, o, g
 
 
-CASES = ["tgv2d", "tgv2d_half", "tgv3d", "tgv3d_force", "cylinder", "sphere_small"]
+CASES = ["tgv2d", "tgv2d_half", "tgv3d", "tgv3d_force", "cylinder", "channel_zg", "sphere_small"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -189,8 +199,62 @@ def test_kernel_launches_counted(lbm):
     m = W.config_tgv2d()
     g = lbm.Sim(m, 9, 1.6)
     g.init(*W.tgv_fields(m, 0.01))
+    info = g.mesh_info()
+    assert info[0, 8] == 0 and info[1, 8] == 4  # interior bricks: none coarse, 4 fine
     n0 = g.kernel_launches()
     g.step(1)
     # LINEAR two-level step: GFF, source moments, GFC, coarse stream-collide,
-    # fine stream-collide, source moments, GFC, fine stream-collide
-    assert g.kernel_launches() - n0 == 8
+    # fine stream-collide (bricks + list), source moments, GFC, fine
+    # stream-collide (bricks + list)
+    assert g.kernel_launches() - n0 == 10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_restart(lbm, precision):
+    """lbm_get_state / lbm_set_state: a run interrupted after 3 steps and
+    restarted from the saved state into a fresh context reproduces the
+    uninterrupted run (bitwise in FP64; FP32 within the storage rounding of
+    one round trip)."""
+    m, Q, om, uin, fields, force, _ = make_case("sphere_small")
+    rho, u, S, df = fields(m)
+    a = lbm.Sim(m, Q, om, precision=precision, u_in=uin)
+    a.init(rho, u, S, df)
+    a.step(3)
+    saved = a.get_state()
+    a.step(2)
+    b = lbm.Sim(m, Q, om, precision=precision, u_in=uin)
+    b.set_state(saved)
+    b.step(2)
+    if precision == 0:
+        assert np.array_equal(a.get_state(), b.get_state())
+    else:
+        assert rel(b.get_state(), a.get_state()) < 1e-6
+
+
+@pytest.mark.parametrize("precision,mode", [(0, 0), (1, 1), (2, 0)])
+def test_graph_steps_match_eager_steps(lbm, precision, mode):
+    """lbm_step(n >= 2) replays captured two-step graphs; one step at a time is
+    launched kernel by kernel.  Same kernels, same order: bitwise equal states
+    and equal launch counts, from either parity state, and after set_params
+    (which must drop the captured steps)."""
+    m = W.config_tgv3d(16)
+    rho, u, S = W.tgv_fields(m, 0.01)
+    df = W.pdf_perturbation(m, 19)
+    a = lbm.Sim(m, 19, 1.6, precision=precision, time_mode=mode)
+    b = lbm.Sim(m, 19, 1.6, precision=precision, time_mode=mode)
+    for s_ in (a, b):
+        s_.init(rho, u, S, df)
+    na, nb = a.kernel_launches(), b.kernel_launches()
+    a.step(1)
+    a.step(5)       # graph from the odd parity state, then one eager step
+    a.step(4)       # graph from the even parity state
+    for _ in range(10):
+        b.step(1)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert a.kernel_launches() - na == b.kernel_launches() - nb
+    for s_ in (a, b):
+        s_.set_params(1.5)
+    a.step(4)
+    for _ in range(4):
+        b.step(1)
+    assert np.array_equal(a.get_state(), b.get_state())
