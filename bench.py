@@ -141,11 +141,12 @@ def gpu_uuid(dev):
 
 
 def stream_collide_traffic():
-    """DRAM bytes per element update of the finest-level stream-collide from the
-    committed ncu capture, if that kernel's source is unchanged since."""
+    """DRAM bytes per element update of the finest-level interior-brick
+    stream-collide from the committed ncu capture, if the kernel source is
+    unchanged since."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "stream_collide_fp32_sphere.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", "stream_collide_brick_fp32_sphere.json")) as fh:
             rec = json.load(fh)
         with open(os.path.join(ROOT, "paper_1601_06984_gb300", "csrc", "kernels.cuh")) as fh:
             src = fh.read()
@@ -209,7 +210,12 @@ def cpu_oracle(seconds, min_steps=2):
 OUTLETS = {"linear": 0, "zero-gradient": 1}
 
 
-def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_moments=False, outlet=0):
+def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_moments=False, outlet=0,
+            kernel_timing=True):
+    """Time K coarse steps after W_ warm-up steps.  With kernel_timing the
+    library brackets every stream-collide launch with CUDA events (steps are
+    then launched kernel by kernel); without it the steps replay the library's
+    captured CUDA graphs, as a caller's lbm_step(K) does."""
     import torch
 
     from paper_1601_06984_gb300 import lbm
@@ -223,7 +229,7 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     info = sim.mesh_info()
     stream = sim.stream
     torch.cuda.synchronize(device)
-    sim.timing_enable(True)
+    sim.timing_enable(kernel_timing)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(device)
@@ -242,14 +248,14 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     # (the neighbour-list kernel when the level has no interior bricks)
     kb = 0 if info[finest, 8] > 0 else 1
     units = int(64 * info[finest, 8]) if kb == 0 else int(info[finest, 1])
-    avg_ms = kms[finest, kb] / max(nl[finest, kb], 1)
+    avg_ms = kms[finest, kb] / max(nl[finest, kb], 1) if kernel_timing else float("nan")
     bpu = bytes_per_update(Q, prec, brick=kb == 0)
     list_units = int(info[finest, 1] - 64 * info[finest, 8])
     list_ms = kms[finest, 1] / max(nl[finest, 1], 1)
     res = {"ms_total": ms, "ms_per_step": ms / K, "mlups": K * U / (ms * 1e-3) / 1e6, "launches": launches,
            "finest_kernel": "k_stream_collide_brick" if kb == 0 else "k_stream_collide",
            "finest_launch_ms": avg_ms, "finest_launches": int(nl[finest, kb]), "finest_units": units,
-           "finest_bytes": units * bpu, "finest_gbs": units * bpu / (avg_ms * 1e-3) / 1e9,
+           "finest_bytes": units * bpu, "finest_gbs": units * bpu / (avg_ms * 1e-3) / 1e9 if kernel_timing else None,
            "finest_list_units": list_units, "finest_list_launch_ms": list_ms,
            "finest_list_gbs": (list_units * bytes_per_update(Q, prec) / (list_ms * 1e-3) / 1e9
                                if nl[finest, 1] > 0 and list_ms > 0 else None),
@@ -429,9 +435,11 @@ def main():
         # secondary: the 64^3 / 32^3 two-level Taylor-Green (working set fits in L2)
         from paper_1601_06984_gb300 import workloads as Wk
         tm, tQ, tom, tuin, tfields, tdesc = make_workload("tgv3d")
-        tgv = {"config": tdesc, "note": "working set (~0.13 GB) fits in the 129 MB L2 plus HBM; L2 not flushed"}
+        tgv = {"config": tdesc, "note": "working set (~0.13 GB) fits in the 129 MB L2 plus HBM; L2 not flushed; "
+                                         "steps replay the library's CUDA graphs (launch-bound size)"}
         for name, prec in (("fp32dev", lbm.FP32DEV), ("fp64", lbm.FP64)):
-            st, rt = run_gpu(tm, tQ, tom, tuin, tfields, prec, 50, 3, device, None, want_moments=True)
+            st, rt = run_gpu(tm, tQ, tom, tuin, tfields, prec, 50, 3, device, None, want_moments=True,
+                             kernel_timing=False)
             _, ut, _ = rt.pop("moments")
             nu = (1 / 1.6 - 0.5) / 3
             _, ua, _ = Wk.tgv_fields(tm, 0.01, t=53, nu=nu)
@@ -459,7 +467,7 @@ def main():
                      "frac": r["finest_gbs"] / peak,
                      "traffic": None if traffic_per_unit is None else traffic_per_unit * r["finest_units"],
                      "traffic_source": "ncu capture on the half-scale sphere scaled by units "
-                                       "(profiles/stream_collide_fp32_sphere.md)",
+                                       "(profiles/stream_collide_brick_fp32_sphere.md)",
                      "kernel": r["finest_kernel"] + "<19,float> on the finest level",
                      "units_per_launch": r["finest_units"], "bytes_per_unit": r["bytes_per_update"],
                      "avg_launch_ms": r["finest_launch_ms"], "peak_source": peak_src},

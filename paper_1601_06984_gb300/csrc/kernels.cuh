@@ -354,10 +354,15 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
 
 // Stream-collide of interior bricks: the same pull and BGK collision as
 // k_stream_collide, with the pull source of link i located by the brick's
-// neighbour table instead of the per-element neighbour list.  One block holds
-// LBM_BR_BLOCK / 64 bricks; thread l of a brick is its element at z-curve
-// position l.  The link table and the bricks' neighbour rows are staged in
-// shared memory, so the element's HBM traffic is its Q pdf reads and Q writes.
+// neighbour row instead of the per-element neighbour list.  Each group of 64
+// threads takes one brick, thread l its element at z-curve position l; blocks
+// are issued in brick order, so the bricks in flight stay a compact window of
+// the level and their neighbours' lines are still in L2 when gathered.  The
+// thread's Q-1 link-table entries (slot, position) are loaded into registers,
+// lanes 0..26 of each warp load the brick's 27-entry neighbour row in one
+// coalesced access, and every link takes its row entry by a warp shuffle, so
+// all pdf gathers issue after two loads.  The element's HBM traffic is its Q
+// pdf reads and Q writes.
 #ifndef LBM_BR_BLOCK
 #define LBM_BR_BLOCK 256
 #endif
@@ -370,35 +375,39 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_BR_MINB) k_stream_collide_br
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   constexpr int BPB = LBM_BR_BLOCK / 64;
-  __shared__ uint16_t tab[(Q - 1) * 64];
-  __shared__ int32_t nbs[BPB][27];
-  for (int k = threadIdx.x; k < (Q - 1) * 64; k += LBM_BR_BLOCK) tab[k] = a.tab[k];
-  const int lb = threadIdx.x >> 6, l = threadIdx.x & 63;
-  const int64_t b = (int64_t)blockIdx.x * BPB + lb;
-  if (l < 27 && b < a.nB) nbs[lb][l] = a.nb[b * 27 + l];
-  __syncthreads();
+  constexpr int NW = Q / 2;  // (Q-1)/2 words of two 16-bit entries
+  const int l = threadIdx.x & 63, lane = threadIdx.x & 31;
+  // the brick index is uniform over each warp (64 threads per brick), so the
+  // exit below and the shuffles run with whole warps
+  const int64_t b = (int64_t)blockIdx.x * BPB + (threadIdx.x >> 6);
   if (b >= a.nB) return;
-  const S* __restrict__ src = static_cast<const S*>(a.src);
-  S* __restrict__ dst = static_cast<S*>(a.dst);
+  uint32_t tw[NW];
+#pragma unroll
+  for (int k = 0; k < NW; ++k)
+    tw[k] = (uint32_t)__ldg(a.tab + (2 * k) * 64 + l) | ((uint32_t)__ldg(a.tab + (2 * k + 1) * 64 + l) << 16);
+  const int32_t row = lane < 27 ? __ldg(a.nb + b * 27 + lane) : 0;
   const size_t N = (size_t)a.Ntot;
-  const int64_t e = a.begin + b * 64 + l;
+  // offsets below are relative to the brick's first element
+  const int64_t first = a.begin + b * 64;
+  const S* __restrict__ src = static_cast<const S*>(a.src) + first;
+  S* __restrict__ dst = static_cast<S*>(a.dst) + first + l;
   R g[Q];
-  g[0] = Sto<S>::ld(src + e);
+  g[0] = Sto<S>::ld(src + l);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const uint32_t v = tab[(i - 1) * 64 + l];
-    const int64_t n = (int64_t)nbs[lb][v >> 6] + (v & 63);
-    g[i] = Sto<S>::ld(src + (size_t)i * N + n);
+    const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
+    const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
+    g[i] = Sto<S>::ld(src + (int64_t)(i * N) + r + (v & 63));
   }
   R F[3] = {R(0), R(0), R(0)};
   if (FORCE) {
-    const R* __restrict__ fp = static_cast<const R*>(a.force);
+    const R* __restrict__ fp = static_cast<const R*>(a.force) + first + l;
 #pragma unroll
-    for (int c = 0; c < D; ++c) F[c] = fp[(size_t)c * N + e];
+    for (int c = 0; c < D; ++c) F[c] = fp[c * N];
   }
   bgk_collide<Q, R, FORCE>(g, R(a.omega), R(a.rho_off), F);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) st_once(dst + (size_t)i * N + e, Sto<S>::cv(g[i]));
+  for (int i = 0; i < Q; ++i) st_once(dst + i * N, Sto<S>::cv(g[i]));
 }
 
 // ----------------------------------------------------------------- outlet values

@@ -67,9 +67,10 @@ struct HostMesh {
   std::vector<int32_t> obs_elem;
   std::vector<int8_t> obs_dir;
   // interior bricks (64 elements each, z-curve order inside): per brick the
-  // global index of the first element of the brick at offset slot
-  // t = (sx+1) + 3 (sy+1) + 9 (sz+1); per link i >= 1 and local position l the
-  // entry (t << 6) | l' locating the pull source f*_i(x - c_i)
+  // first element of the brick at offset slot t = (sx+1) + 3 (sy+1) + 9 (sz+1),
+  // relative to the brick's own first element (slot 13, the brick itself, is
+  // 0); per link i >= 1 and local position l the entry (t << 6) | l' locating
+  // the pull source f*_i(x - c_i) at first + brick_nb[t] + l'
   std::vector<int32_t> brick_nb;    // [sum nB][27]
   std::vector<uint16_t> brick_tab;  // [Q-1][64]
 };
@@ -104,7 +105,7 @@ struct BrickArgs {
   const void* src;
   void* dst;
   const void* force;    // [d][Ntot] compute type, or null
-  const int32_t* nb;    // [nB][27] rows of this level
+  const int32_t* nb;    // [nB][27] rows of this level (offsets from the brick's first element)
   const uint16_t* tab;  // [Q-1][64]
   int64_t Ntot, begin, nB;
   double omega, rho_off;

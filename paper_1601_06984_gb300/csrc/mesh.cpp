@@ -552,7 +552,7 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       const HostLevel& H = M.lv[li];
       for (int64_t b = 0; b < H.nB; ++b)
         for (int t = 0; t < 27; ++t)
-          M.brick_nb[(size_t)(H.brick_first + b) * 27 + t] = (int32_t)(H.base + H.oF + brick_nbpos[li][b][t]);
+          M.brick_nb[(size_t)(H.brick_first + b) * 27 + t] = (int32_t)(brick_nbpos[li][b][t] - 64 * b);
     }
     M.brick_tab.assign((size_t)(Q - 1) * 64, 0);
     for (int i = 1; i < Q; ++i)
@@ -845,8 +845,8 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       for (int i = 1; i < Q; ++i)
         for (int l = 0; l < 64; ++l) {
           const uint16_t v = M.brick_tab[(size_t)(i - 1) * 64 + l];
-          const int64_t e = H.base + H.oF + 64 * b + l;
-          if (M.nbr[(size_t)(i - 1) * M.Ntot + e] != (uint32_t)(nb[v >> 6] + (v & 63))) mismatch = 1;
+          const int64_t first = H.base + H.oF + 64 * b;
+          if (M.nbr[(size_t)(i - 1) * M.Ntot + first + l] != (uint32_t)(first + nb[v >> 6] + (v & 63))) mismatch = 1;
         }
     }
     if (mismatch) return bad(LBM_ERR_INTERNAL, "interior brick table disagrees with the neighbour list");

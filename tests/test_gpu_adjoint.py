@@ -196,3 +196,34 @@ def test_adjoint_full_size_config5(lbm):
     h = 1e-3
     fd = (run(h) - run(-h)) / (2 * h)
     assert abs(adj - fd) <= 1e-5 * abs(fd)
+
+
+@pytest.mark.parametrize("outlet", [0, 1])
+def test_adjoint_cylinder_drag(lbm, outlet):
+    """Drag objective on the full 4-level cylinder channel (about 64k elements,
+    coarsest omega 1.86 at Re = 20) with the Sec. 2.3 outlet: the adjoint's
+    derivative of c_D-proportional F_x along (omega_c, u_in) matches central
+    differences of the FP64 forward."""
+    m = W.config_cylinder()
+    U = 0.05
+    om = W.omega_coarse_from_finest(W.omega_for_re(U, 40, 20.0), 4)
+    rho, u, S = W.uniform_fields(m, 1.0, (U, 0.0))
+    df = W.pdf_perturbation(m, 9, 1e-5)
+    n, K = 20, 5
+    vw, vU = 0.05, np.array([0.3, 0.1, 0.0])
+
+    def run(h):
+        g = lbm.Sim(m, 9, om, u_in=(U, 0.0, 0.0), outlet=outlet)
+        g.init(rho, u, S, df)
+        g.set_params(om + h * vw, tuple(np.array([U, 0.0, 0.0]) + h * vU))
+        g.step(n)
+        return g.reduce()[4]
+
+    g = lbm.Sim(m, 9, om, u_in=(U, 0.0, 0.0), outlet=outlet)
+    g.init(rho, u, S, df)
+    J, _, dw, dU = g.adjoint(n, K, 1, want_force=False)
+    assert abs(J - run(0.0)) <= 1e-12 * abs(J)
+    adj = dw * vw + float((dU * vU).sum())
+    h = 1e-4
+    fd = (run(h) - run(-h)) / (2 * h)
+    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
