@@ -159,6 +159,25 @@ def stream_collide_traffic():
         return None
 
 
+def fp64_instruction_record():
+    """FP64 instructions per element update of the interior-brick kernel and
+    the FP64 issue peak, from the committed ncu count, if the kernel source is
+    unchanged since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "stream_collide_brick_fp64_tgv3d.json")) as fh:
+            rec = json.load(fh)
+        with open(os.path.join(ROOT, "paper_1601_06984_gb300", "csrc", "kernels.cuh")) as fh:
+            src = fh.read()
+        a = src.index("// ----------------------------------------------------------------- physics")
+        b = src.index("// ----------------------------------------------------------------- outlet values")
+        if hashlib.sha256(src[a:b].encode()).hexdigest()[:16] != rec["kernel_source_sha256_16"]:
+            return None
+        return rec
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -416,6 +435,16 @@ def main():
                               "finest_kernel_gbs": r2["finest_gbs"], "finest_kernel_frac": r2["finest_gbs"] / peak,
                               "bytes_per_update": r2["bytes_per_update"], "device_gb": r2["device_gb"],
                               "reduce": r2["reduce"]}
+            if name == "fp64":
+                rec = fp64_instruction_record()
+                rate = r2["finest_units"] / (r2["finest_launch_ms"] * 1e-3)  # elements / s
+                variants[name]["alu_roofline"] = None if rec is None else {
+                    "bound": "alu", "unit": "G FP64 inst/s",
+                    "achieved": rate * rec["fp64_inst_per_unit"] / 1e9,
+                    "peak": rec["peak_fp64_inst_per_s"] / 1e9,
+                    "frac": rate * rec["fp64_inst_per_unit"] / rec["peak_fp64_inst_per_s"],
+                    "fp64_inst_per_update": rec["fp64_inst_per_unit"], "flops_per_update": rec["flops_per_unit"],
+                    "peak_source": "152 SMs x 2 FP64 inst/clock x 2.07 GHz (profiles/stream_collide_brick_fp64_tgv3d.md)"}
             s2.close()
             del s2
             torch.cuda.empty_cache()
