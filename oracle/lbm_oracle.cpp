@@ -81,11 +81,16 @@ inline double tangent_of(const Dual& x) { return x.d; }
 //          7 (+x+y), 8 (-x-y), 9 (+x-y), 10 (-x+y),
 //          11 (+x+z), 12 (-x-z), 13 (+x-z), 14 (-x+z),
 //          15 (+y+z), 16 (-y-z), 17 (+y-z), 18 (-y+z)
+//   D3Q27: the D3Q19 set, then 19 (+x+y+z), 20 (-x-y-z), 21 (+x+y-z),
+//          22 (-x-y+z), 23 (+x-y+z), 24 (-x+y-z), 25 (-x+y+z), 26 (+x-y-z)
+// Weights by |c|^2 (Sec. 2.1 uses the standard D2Q9 / D3Q19 / D3Q27 sets):
+//   D2Q9 4/9, 1/9, 1/36;  D3Q19 1/3, 1/18, 1/36;  D3Q27 8/27, 2/27, 1/54, 1/216.
+constexpr int kQmax = 27;
 struct Lattice {
   int d = 0, Q = 0;
-  int c[19][3] = {};
-  double w[19] = {};
-  int opp[19] = {};
+  int c[kQmax][3] = {};
+  double w[kQmax] = {};
+  int opp[kQmax] = {};
 };
 
 Lattice make_lattice(int q) {
@@ -104,18 +109,20 @@ Lattice make_lattice(int q) {
     }
   } else {
     lat.d = 3;
-    lat.Q = 19;
-    const int cc[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
-                           {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
-                           {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                           {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
-    for (int i = 0; i < 19; ++i) {
+    lat.Q = q;
+    const int cc[27][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},
+                           {0, 0, -1},  {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0},  {1, 0, 1},
+                           {-1, 0, -1}, {1, 0, -1},  {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},
+                           {0, -1, 1},  {1, 1, 1},   {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1},
+                           {-1, 1, -1}, {-1, 1, 1},  {1, -1, -1}};
+    for (int i = 0; i < q; ++i) {
       int n2 = 0;
       for (int a = 0; a < 3; ++a) {
         lat.c[i][a] = cc[i][a];
         n2 += cc[i][a] * cc[i][a];
       }
-      lat.w[i] = n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+      if (q == 19) lat.w[i] = n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+      else lat.w[i] = n2 == 0 ? 8.0 / 27.0 : (n2 == 1 ? 2.0 / 27.0 : (n2 == 2 ? 1.0 / 54.0 : 1.0 / 216.0));
     }
   }
   for (int i = 0; i < lat.Q; ++i)
@@ -179,7 +186,7 @@ struct Mom {
   T rho;
   T u[3];
   T S[6];       // xx,yy,zz,xy,yz,xz (3D) or xx,yy,xy (2D)
-  T fneq[19];   // pre-collision non-equilibrium part
+  T fneq[kQmax];  // pre-collision non-equilibrium part
 };
 
 template <class T>
@@ -582,7 +589,7 @@ struct Sim {
     const T omega = l.omega;
     for (auto& e : l.e) {
       if (!e.processed) continue;
-      T fin[19];
+      T fin[kQmax];
       for (int i = 0; i < Q; ++i) fin[i] = pull(l, e, i);
       T rho = T(0.0);
       T j[3] = {T(0.0), T(0.0), T(0.0)};
@@ -620,7 +627,7 @@ struct Sim {
       for (int b = 0; b < nch; ++b) moments(lf.e[g.child[b]], lf.omega, &mk[b]);
       T rho = T(0.0);
       T u[3] = {T(0.0), T(0.0), T(0.0)};
-      T fneq[19];
+      T fneq[kQmax];
       for (int i = 0; i < Q; ++i) fneq[i] = T(0.0);
       for (int b = 0; b < nch; ++b) {
         rho += mk[b].rho;
@@ -877,7 +884,7 @@ Sim<T>* create_sim(int stencil, int time_mode, const int* extent, const int* bc,
     delete s;
     return nullptr;
   };
-  if (stencil != 9 && stencil != 19) return bail("stencil must be 9 or 19");
+  if (stencil != 9 && stencil != 19 && stencil != 27) return bail("stencil must be 9, 19 or 27");
   if (time_mode != TIME_LINEAR && time_mode != TIME_TWO_LAYER) return bail("bad time mode");
   s->lat = make_lattice(stencil);
   s->d = s->lat.d;

@@ -19,8 +19,13 @@ C19 = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 
                 [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]])
 
 
+# D3Q27: the D3Q19 set followed by the 8 corners in opposite pairs
+C27 = np.concatenate([C19, np.array([[1, 1, 1], [-1, -1, -1], [1, 1, -1], [-1, -1, 1], [1, -1, 1],
+                                     [-1, 1, -1], [-1, 1, 1], [1, -1, -1]])])
+
+
 def lattice(Q):
-    return C9 if Q == 9 else C19
+    return {9: C9, 19: C19, 27: C27}[Q]
 
 
 def sym_to_mat(Sv, d):
@@ -42,11 +47,14 @@ def mat_to_sym(S, d):
 
 
 # ---------------------------------------------------------------- lattice / equilibrium
-@pytest.mark.parametrize("Q", [9, 19])
+@pytest.mark.parametrize("Q", [9, 19, 27])
 def test_equilibrium_moments(oracle_mod, Q):
     """Sec. 2.1, Eq. (feq) with the u.u term subtracted: the zeroth, first and
-    second moments of f^eq are rho, rho u and rho (c_s^2 I + u u).  The printed
-    '+' sign would fail the zeroth moment."""
+    second moments of f^eq are rho, rho u and rho (c_s^2 I + u u), and the third
+    moment is rho c_s^2 (u_a d_bc + u_b d_ac + u_c d_ab), which needs the
+    weights' 4th-order isotropy (sum w c c c c = (d d + d d + d d) / 9), so a
+    wrong weight in any velocity shell fails it.  The printed '+' sign would
+    fail the zeroth moment."""
     d = 2 if Q == 9 else 3
     mesh = W.uniform(d, 2, (4,) * d, (0,) * (2 * d))
     rng = np.random.default_rng(1)
@@ -61,9 +69,14 @@ def test_equilibrium_moments(oracle_mod, Q):
     P = np.einsum("ni,ia,ib->nab", f, c, c)
     P_ref = rho[:, None, None] * (np.eye(d)[None] / 3.0 + np.einsum("na,nb->nab", u, u))
     assert np.abs(P - P_ref).max() < 1e-15
+    I = np.eye(d)
+    T3 = np.einsum("ni,ia,ib,ic->nabc", f, c, c, c)
+    T3_ref = rho[:, None, None, None] / 3.0 * (np.einsum("na,bc->nabc", u, I) + np.einsum("nb,ac->nabc", u, I)
+                                               + np.einsum("nc,ab->nabc", u, I))
+    assert np.abs(T3 - T3_ref).max() < 1e-15
 
 
-@pytest.mark.parametrize("Q", [9, 19])
+@pytest.mark.parametrize("Q", [9, 19, 27])
 def test_strain_rate_roundtrip(oracle_mod, Q):
     """Sec. 4.1 initial f^neq with the strain-rate equation of Sec. 2.1: the
     strain rate read back from the initial state equals the one put in, and the
@@ -148,15 +161,14 @@ def exact_level_fields(mesh, ufun, Sfun, level):
     return um, ufun(x), Sfun(x) / fac
 
 
-@pytest.mark.parametrize("d,mode", [(2, 0), (2, 1), (3, 0), (3, 1)])
-def test_ghost_fill_exact_on_quadratic_field(oracle_mod, d, mode):
+@pytest.mark.parametrize("d,mode,Q", [(2, 0, 9), (2, 1, 9), (3, 0, 19), (3, 1, 19), (3, 0, 27), (3, 1, 27)])
+def test_ghost_fill_exact_on_quadratic_field(oracle_mod, d, mode, Q):
     """Sec. 2.2 steps 1-5 on a two-level mesh: with a quadratic velocity, linear
     strain rate and constant density on both levels, every GhostFromCoarser and
     GhostFromFiner element holds exactly the pdfs an element of its own level
     would be initialised with from the exact field at its centre.  This pins the
     source choice and octant signs, the f^neq rescale with the factor 1/m, the
     quadratic GFF velocity and f = f^eq + (1-omega) f^neq."""
-    Q = 9 if d == 2 else 19
     n = 16 if d == 2 else 8
     mesh = W.two_level_block(d, n, n // 4, 3 * n // 4)
     rng = np.random.default_rng(5)
@@ -187,11 +199,10 @@ def test_ghost_fill_exact_on_quadratic_field(oracle_mod, d, mode):
 
 
 # ---------------------------------------------------------------- invariants
-@pytest.mark.parametrize("d,mode", [(2, 0), (2, 1), (3, 0), (3, 1)])
-def test_uniform_state_is_stationary(oracle_mod, d, mode):
+@pytest.mark.parametrize("d,mode,Q", [(2, 0, 9), (2, 1, 9), (3, 0, 19), (3, 1, 19), (3, 0, 27), (3, 1, 27)])
+def test_uniform_state_is_stationary(oracle_mod, d, mode, Q):
     """A constant (rho0, u) equilibrium is a fixed point of the whole multilevel
     step: stream, collide, both ghost fills and the time interpolation."""
-    Q = 9 if d == 2 else 19
     n = 16 if d == 2 else 8
     mesh = W.two_level_block(d, n, n // 4, 3 * n // 4)
     U = (0.03, -0.02, 0.01)[:d]
@@ -205,18 +216,21 @@ def test_uniform_state_is_stationary(oracle_mod, d, mode):
     assert np.abs(S1).max() < 1e-14
 
 
-def test_single_level_conservation(oracle_mod):
+@pytest.mark.parametrize("Q", [9, 27])
+def test_single_level_conservation(oracle_mod, Q):
     """Periodic single-level BGK conserves mass and momentum exactly (up to
-    round-off) over 200 steps, with the seeded pdf perturbation."""
-    mesh = W.uniform(2, 5, (32, 32), (0,) * 4)
+    round-off) over 200 steps (D3Q27: 40 steps on 8^3), with the seeded pdf
+    perturbation."""
+    d = 2 if Q == 9 else 3
+    mesh = W.uniform(2, 5, (32, 32), (0,) * 4) if d == 2 else W.uniform(3, 3, (8, 8, 8), (0,) * 6)
     rho, u, S = W.tgv_fields(mesh, 0.02)
-    o = oracle_mod.Oracle(mesh, 9, 1.6)
-    o.init(rho, u, S, W.pdf_perturbation(mesh, 9, 1e-6))
+    o = oracle_mod.Oracle(mesh, Q, 1.6)
+    o.init(rho, u, S, W.pdf_perturbation(mesh, Q, 1e-6))
     m0 = o.reduce()
-    o.step(200)
+    o.step(200 if d == 2 else 40)
     m1 = o.reduce()
     assert abs(m1[0] - m0[0]) / m0[0] < 1e-12
-    assert np.abs(m1[1:3] - m0[1:3]).max() / m0[0] < 1e-12
+    assert np.abs(m1[1:1 + d] - m0[1:1 + d]).max() / m0[0] < 1e-12
 
 
 def test_user_order_does_not_matter(oracle_mod):
@@ -403,14 +417,15 @@ def test_obstacle_force_balances_body_force(oracle_mod):
     assert abs(red[5]) < 1e-12
 
 
-def test_tgv3d_decay_two_level(oracle_mod):
+@pytest.mark.parametrize("Q", [19, 27])
+def test_tgv3d_decay_two_level(oracle_mod, Q):
     """3D two-level Taylor-Green (extruded in z) on a small 16^3 / 8^3 mesh
-    decays like exp(-2 nu k^2 t)."""
+    decays like exp(-2 nu k^2 t), with D3Q19 and with the paper's D3Q27."""
     mesh = W.config_tgv3d(16)
     nu = (1 / 1.6 - 0.5) / 3
     k = 2 * math.pi / 16
     vol = np.ldexp(1.0, -3 * (mesh.levels.astype(np.int64) - mesh.lmin))
-    o = oracle_mod.Oracle(mesh, 19, 1.6)
+    o = oracle_mod.Oracle(mesh, Q, 1.6)
     rho, u, S = W.tgv_fields(mesh, 0.01)
     o.init(rho, u, S)
     o.step(40)
