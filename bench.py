@@ -448,6 +448,16 @@ def main():
             s2.close()
             del s2
             torch.cuda.empty_cache()
+        # the paper's own 3D stencil on the same mesh, FP32 deviation storage
+        s27, r27 = run_gpu(mesh, 27, om, uin, fields, lbm.FP32DEV, K, W_, device, None, outlet=outlet)
+        variants["d3q27_fp32dev"] = {
+            "mlups": r27["mlups"], "ms_per_step": r27["ms_per_step"], "kernel": r27["finest_kernel"],
+            "finest_kernel_gbs": r27["finest_gbs"], "finest_kernel_frac": r27["finest_gbs"] / peak,
+            "bytes_per_update": r27["bytes_per_update"], "device_gb": r27["device_gb"],
+            "interior_fraction": r27["interior_fraction"], "reduce": r27["reduce"]}
+        s27.close()
+        del s27
+        torch.cuda.empty_cache()
         ref_u = mom["fp64"][1]
         ref_red = variants["fp64"]["reduce"]
         for name, m_ in (("fp32dev", mom32), ("bf16dev", mom["bf16dev"])):

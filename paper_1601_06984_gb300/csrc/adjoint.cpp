@@ -163,16 +163,16 @@ AdjLayout adj_layout(lbm_ctx* c, int64_t n, int K) {
   for (int li = 0; li < c->nlev; ++li) {
     const HostLevel& H = c->M.lv[li];
     const int64_t nsrc = (int64_t)H.src_elem.size();
-    L.lam_recA.push_back(take((size_t)nsrc * kMomStride * lb));
-    L.lam_recB.push_back(take((size_t)nsrc * kMomStride * lb));
-    L.recA.push_back(take((size_t)nsrc * kMomStride * lb));
-    L.recB.push_back(take((size_t)nsrc * kMomStride * lb));
+    L.lam_recA.push_back(take((size_t)nsrc * mom_stride(c->Q) * lb));
+    L.lam_recB.push_back(take((size_t)nsrc * mom_stride(c->Q) * lb));
+    L.recA.push_back(take((size_t)nsrc * mom_stride(c->Q) * lb));
+    L.recB.push_back(take((size_t)nsrc * mom_stride(c->Q) * lb));
     L.csr_off.push_back(take((size_t)(nsrc + 1) * 4));
     const int64_t nfine = li + 1 < c->nlev ? c->M.lv[li + 1].nC : 0;
     L.csr_item.push_back(take((size_t)4 * nfine * 4));
     max_contrib = std::max(max_contrib, nfine);
   }
-  L.contrib = take((size_t)max_contrib * 4 * kMomStride * lb);
+  L.contrib = take((size_t)max_contrib * 4 * mom_stride(c->Q) * lb);
   L.state_bytes = align_up((size_t)c->Q * N * c->ops->storage_bytes);
   L.n_ck = (int)((n + K - 1) / K);
   L.n_steps = K;
@@ -211,20 +211,13 @@ lbm_status lbm_set_params(lbm_ctx* c, double omega_coarse, const double* u_in) {
   c->p.omega_coarse = omega_coarse;
   if (u_in) {
     for (int a = 0; a < 3; ++a) c->p.u_in[a] = u_in[a];
-    static const int c9[9][3] = {{0, 0, 0}, {1, 0, 0},  {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
-                                 {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
-    static const int c19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
-                                   {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
-                                   {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                                   {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    int cc[kQmax][3];
+    double w[kQmax];
+    host_lattice(c->Q, cc, w);
     for (int i = 0; i < c->Q; ++i) {
-      const int* ci = c->Q == 9 ? c9[i] : c19[i];
-      const int n2 = ci[0] * ci[0] + ci[1] * ci[1] + ci[2] * ci[2];
-      const double w = c->Q == 9 ? (n2 == 0 ? 4.0 / 9.0 : (n2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0))
-                                 : (n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0));
       double cu = 0;
-      for (int a = 0; a < c->d; ++a) cu += ci[a] * u_in[a];
-      c->inlet[i] = 6.0 * w * c->p.rho0 * cu;
+      for (int a = 0; a < c->d; ++a) cu += cc[i][a] * u_in[a];
+      c->inlet[i] = 6.0 * w[i] * c->p.rho0 * cu;
     }
   }
   return LBM_OK;
@@ -474,7 +467,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
           accum(lc, li);
           AdjGatherArgs g{W + L.contrib, reinterpret_cast<const int32_t*>(W + L.csr_off[lc]),
                           reinterpret_cast<const int32_t*>(W + L.csr_item[lc]),
-                          W + (t.op == OP_GFC_A ? L.lam_recA[lc] : L.lam_recB[lc]), c->ld[lc].nsrc};
+                          W + (t.op == OP_GFC_A ? L.lam_recA[lc] : L.lam_recB[lc]), c->ld[lc].nsrc,
+                          mom_stride(c->Q)};
           launch_adj_gather(fp64, g, st);
         } else if (t.op == OP_GFF) {
           if (H.nG1 + H.nG2 == 0) continue;

@@ -472,17 +472,17 @@ __global__ void __launch_bounds__(128) k_adj_moments(const AdjMomArgs a) {
   R part[1] = {R(0)};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.nsrc; k += stride) {
-    R* lr = static_cast<R*>(a.lam_rec) + (size_t)k * kMomStride;
-    R rec[kMomStride];
+    R* lr = static_cast<R*>(a.lam_rec) + (size_t)k * RL::STRIDE;
+    R rec[RL::STRIDE];
 #pragma unroll
-    for (int f = 0; f < kMomStride; ++f) {
+    for (int f = 0; f < RL::STRIDE; ++f) {
       rec[f] = lr[f];
       lr[f] = R(0);
     }
     if (a.lam_rec_prev) {
-      R* lp = static_cast<R*>(a.lam_rec_prev) + (size_t)k * kMomStride;
+      R* lp = static_cast<R*>(a.lam_rec_prev) + (size_t)k * RL::STRIDE;
 #pragma unroll
-      for (int f = 0; f < kMomStride; ++f) {
+      for (int f = 0; f < RL::STRIDE; ++f) {
         rec[f] *= R(0.5);
         lp[f] += rec[f];
       }
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.ng; k += stride) {
     const R* rec[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) rec[s] = mom + (size_t)a.gsrc[(size_t)s * a.ng + k] * kMomStride;
+    for (int s = 0; s < 4; ++s) rec[s] = mom + (size_t)a.gsrc[(size_t)s * a.ng + k] * RL::STRIDE;
     const uint8_t oct = a.oct[k];
     R sg[3];
 #pragma unroll
@@ -594,12 +594,12 @@ __global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
         lSl[s][c] = o[0] * lam_uloc[0] + o[1] * lam_uloc[1] + o[2] * lam_uloc[2];
       }
     }
-    R* out = static_cast<R*>(a.contrib) + (size_t)k * 4 * kMomStride;
+    R* out = static_cast<R*>(a.contrib) + (size_t)k * 4 * RL::STRIDE;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      R v[kMomStride];
+      R v[RL::STRIDE];
 #pragma unroll
-      for (int f = 0; f < kMomStride; ++f) v[f] = R(0);
+      for (int f = 0; f < RL::STRIDE; ++f) v[f] = R(0);
 #pragma unroll
       for (int q = 0; q < Q; ++q) v[RL::FN + q] = lw[s] * scale * lo[q];
       v[RL::RP] = lw[s] * lam_rp;
@@ -610,25 +610,25 @@ __global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
 #pragma unroll
         for (int c = b; c < D; ++c) v[RL::SS + sidx<D>(b, c)] = sg[b] * sg[c] * lSl[s][sidx<D>(b, c)];
 #pragma unroll
-      for (int f = 0; f < kMomStride; f += 4) st4(out + s * kMomStride + f, v + f);
+      for (int f = 0; f < RL::STRIDE; f += 4) st4(out + s * RL::STRIDE + f, v + f);
     }
   }
   store_partials<R, 2>(part, a.c.partial);
 }
 
-template <class R>
+template <class R, int MS>
 __global__ void __launch_bounds__(128) k_adj_gather(const AdjGatherArgs a) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.nsrc) return;
   const R* c = static_cast<const R*>(a.contrib);
-  R acc[kMomStride];
-  R* lr = static_cast<R*>(a.lam_rec) + (size_t)k * kMomStride;
+  R acc[MS];
+  R* lr = static_cast<R*>(a.lam_rec) + (size_t)k * MS;
 #pragma unroll
-  for (int f = 0; f < kMomStride; ++f) acc[f] = lr[f];
+  for (int f = 0; f < MS; ++f) acc[f] = lr[f];
   for (int j = a.off[k]; j < a.off[k + 1]; ++j) {
-    const R* p = c + (size_t)a.item[j] * kMomStride;
+    const R* p = c + (size_t)a.item[j] * MS;
 #pragma unroll
-    for (int f = 0; f < kMomStride; f += 4) {
+    for (int f = 0; f < MS; f += 4) {
       R v[4];
       ld4(p + f, v);
 #pragma unroll
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(128) k_adj_gather(const AdjGatherArgs a) {
     }
   }
 #pragma unroll
-  for (int f = 0; f < kMomStride; f += 4) st4(lr + f, acc + f);
+  for (int f = 0; f < MS; f += 4) st4(lr + f, acc + f);
 }
 
 // ----------------------------------------------------------------- GhostFromFiner
@@ -781,32 +781,26 @@ template <class S>
 struct AdjLaunch {
   static void seed(int Q, const AdjSeedArgs& a, cudaStream_t st) {
     const int64_t n = a.objective == 0 ? a.end - a.begin : a.obs_n;
-    if (Q == 9) k_adj_seed<9, S><<<adj_grid(n, 256), 256, 0, st>>>(a);
-    else k_adj_seed<19, S><<<adj_grid(n, 256), 256, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_adj_seed<decltype(q)::value, S><<<adj_grid(n, 256), 256, 0, st>>>(a); });
   }
   static void sc(int Q, const AdjSCArgs& a, cudaStream_t st) {
-    if (Q == 9) k_adj_sc<9, S><<<kAdjBlocks, 256, 0, st>>>(a);
-    else k_adj_sc<19, S><<<kAdjBlocks, 256, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_adj_sc<decltype(q)::value, S><<<kAdjBlocks, 256, 0, st>>>(a); });
   }
   static void outlet(int Q, const AdjOutletArgs& a, cudaStream_t st) {
     // the normal-link pass writes one row of omega partials per block, so it
     // runs on the full kAdjBlocks grid that k_accum sums over
     if (a.which != 0 && a.end <= a.begin) return;
     const unsigned g = a.which == 0 ? (unsigned)kAdjBlocks : adj_grid(a.end - a.begin, 256);
-    if (Q == 9) k_adj_outlet<9, S><<<g, 256, 0, st>>>(a);
-    else k_adj_outlet<19, S><<<g, 256, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_adj_outlet<decltype(q)::value, S><<<g, 256, 0, st>>>(a); });
   }
   static void moments(int Q, const AdjMomArgs& a, cudaStream_t st) {
-    if (Q == 9) k_adj_moments<9, S><<<kAdjBlocks, 128, 0, st>>>(a);
-    else k_adj_moments<19, S><<<kAdjBlocks, 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_adj_moments<decltype(q)::value, S><<<kAdjBlocks, 128, 0, st>>>(a); });
   }
   static void gfc(int Q, const AdjGfcArgs& a, cudaStream_t st) {
-    if (Q == 9) k_adj_gfc<9, S><<<kAdjBlocks, 128, 0, st>>>(a);
-    else k_adj_gfc<19, S><<<kAdjBlocks, 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_adj_gfc<decltype(q)::value, S><<<kAdjBlocks, 128, 0, st>>>(a); });
   }
   static void gff(int Q, const AdjGffArgs& a, cudaStream_t st) {
-    if (Q == 9) k_adj_gff<9, S><<<kAdjBlocks, 256, 0, st>>>(a);
-    else k_adj_gff<19, S><<<kAdjBlocks, 256, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_adj_gff<decltype(q)::value, S><<<kAdjBlocks, 256, 0, st>>>(a); });
   }
 };
 

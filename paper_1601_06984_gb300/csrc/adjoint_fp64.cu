@@ -63,8 +63,13 @@ void launch_accum(const AccumArgs& a, cudaStream_t st) { dev::k_accum<<<1, 256, 
 void launch_adj_gather(bool fp64, const AdjGatherArgs& a, cudaStream_t st) {
   if (a.nsrc <= 0) return;
   const unsigned g = dev::blocks_for(a.nsrc, 128);
-  if (fp64) dev::k_adj_gather<double><<<g, 128, 0, st>>>(a);
-  else dev::k_adj_gather<float><<<g, 128, 0, st>>>(a);
+  if (a.stride == 32) {
+    if (fp64) dev::k_adj_gather<double, 32><<<g, 128, 0, st>>>(a);
+    else dev::k_adj_gather<float, 32><<<g, 128, 0, st>>>(a);
+  } else {
+    if (fp64) dev::k_adj_gather<double, 40><<<g, 128, 0, st>>>(a);
+    else dev::k_adj_gather<float, 40><<<g, 128, 0, st>>>(a);
+  }
 }
 
 void launch_gather_force_user(const double* lam_force, const int32_t* uslot, double* stage, int64_t first,

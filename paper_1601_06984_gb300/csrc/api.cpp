@@ -20,24 +20,6 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// device lattice weights and velocities for the inlet term (lbm.h order)
-void lattice_host(int Q, int c[19][3], double w[19]) {
-  static const int c9[9][3] = {{0, 0, 0}, {1, 0, 0},  {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
-                               {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
-  static const int c19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
-                                 {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
-                                 {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                                 {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
-  for (int i = 0; i < Q; ++i) {
-    int n2 = 0;
-    for (int a = 0; a < 3; ++a) {
-      c[i][a] = Q == 9 ? c9[i][a] : c19[i][a];
-      n2 += c[i][a] * c[i][a];
-    }
-    if (Q == 9) w[i] = n2 == 0 ? 4.0 / 9.0 : (n2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
-    else w[i] = n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
-  }
-}
 
 }  // namespace
 
@@ -60,7 +42,7 @@ void lbm_ctx::layout() {
   oBrickTab = take(m.brick_tab.size() * 2);
   oF = p.use_force ? take((size_t)d * N * cb) : 0;
   ld.assign(nlev, LevelDev());
-  const size_t M_ = kMomStride;
+  const size_t M_ = mom_stride(Q);
   for (int li = 0; li < nlev; ++li) {
     const HostLevel& H = m.lv[li];
     LevelDev& L = ld[li];
@@ -366,9 +348,9 @@ lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t
   c->nS = c->M.nS;
   c->nlev = (int)c->M.lv.size();
   c->rho_off = params->precision == LBM_FP64 ? 0.0 : params->rho0;
-  int cc[19][3];
-  double w[19];
-  lattice_host(c->Q, cc, w);
+  int cc[kQmax][3];
+  double w[kQmax];
+  host_lattice(c->Q, cc, w);
   for (int i = 0; i < c->Q; ++i) {
     double cu = 0;
     for (int a = 0; a < c->d; ++a) cu += cc[i][a] * params->u_in[a];

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "lbm_internal.h"
@@ -55,6 +56,21 @@ struct Lat<19> {
   }
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+template <>
+struct Lat<27> {
+  static constexpr int D = 3, NS = 6;
+  // base-3 code (cx+1) + 3 (cy+1) + 9 (cz+1) of each velocity, in lbm.h order
+  __host__ __device__ static constexpr int code(int i) {
+    return i == 0 ? 13 : i == 1 ? 14 : i == 2 ? 12 : i == 3 ? 16 : i == 4 ? 10 : i == 5 ? 22 : i == 6 ? 4 : i == 7 ? 17 : i == 8 ? 9 : i == 9 ? 11 : i == 10 ? 15 : i == 11 ? 23 : i == 12 ? 3 : i == 13 ? 5 : i == 14 ? 21 : i == 15 ? 25 : i == 16 ? 1 : i == 17 ? 7 : i == 18 ? 19 : i == 19 ? 26 : i == 20 ? 0 : i == 21 ? 8 : i == 22 ? 18 : i == 23 ? 20 : i == 24 ? 6 : i == 25 ? 24 : 2;
+  }
+  __host__ __device__ static constexpr int c(int i, int a) {
+    return (a == 0 ? code(i) % 3 : (a == 1 ? code(i) / 3 % 3 : code(i) / 9)) - 1;
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 8.0 / 27.0 : (i <= 6 ? 2.0 / 27.0 : (i <= 18 ? 1.0 / 54.0 : 1.0 / 216.0));
   }
 };
 
@@ -464,7 +480,7 @@ __global__ void k_outlet(const OutletArgs a) {
 }
 
 // ----------------------------------------------------------------- GFC source moments
-// Record of one source (compute type, kMomStride values, 16-byte aligned
+// Record of one source (compute type, mom_stride(Q) values, 16-byte aligned
 // groups): f^neq[Q] padded to a multiple of 4, then rho - rho_off, u[D], S[nS],
 // padding.  Vector loads/stores move a record in 8 (float) or 16 (double) pieces.
 template <int Q>
@@ -475,7 +491,8 @@ struct RecLayout {
   static constexpr int U = RP + 1;
   static constexpr int SS = U + D;
   static constexpr int END = SS + NS;
-  static_assert(END <= kMomStride, "moment record too long");
+  static constexpr int STRIDE = mom_stride(Q);
+  static_assert(END <= STRIDE && STRIDE % 4 == 0, "moment record too long");
 };
 
 __device__ __forceinline__ void ld4(const float* p, float* o) {
@@ -522,9 +539,9 @@ __global__ void __launch_bounds__(128) k_source_moments(const MomentsArgs a) {
   if (a.force)
 #pragma unroll
     for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(a.force)[(size_t)b * N + e];
-  R rec[kMomStride];
+  R rec[RL::STRIDE];
 #pragma unroll
-  for (int f = 0; f < kMomStride; ++f) rec[f] = R(0);
+  for (int f = 0; f < RL::STRIDE; ++f) rec[f] = R(0);
   R rp, u[3], fneq[Q], Sv[NS];
   post_moments<Q, R, true>(g, R(a.omega), R(a.rho_off), F, rp, u, fneq, Sv);
 #pragma unroll
@@ -534,10 +551,10 @@ __global__ void __launch_bounds__(128) k_source_moments(const MomentsArgs a) {
   for (int b = 0; b < D; ++b) rec[RL::U + b] = u[b];
 #pragma unroll
   for (int s = 0; s < NS; ++s) rec[RL::SS + s] = Sv[s];
-  R* out = static_cast<R*>(a.mom) + (size_t)k * kMomStride;
-  const R* prev = a.prev ? static_cast<const R*>(a.prev) + (size_t)k * kMomStride : nullptr;
+  R* out = static_cast<R*>(a.mom) + (size_t)k * RL::STRIDE;
+  const R* prev = a.prev ? static_cast<const R*>(a.prev) + (size_t)k * RL::STRIDE : nullptr;
 #pragma unroll
-  for (int f = 0; f < kMomStride; f += 4) {
+  for (int f = 0; f < RL::STRIDE; f += 4) {
     if (f >= RL::END) break;
     if (prev) {
       R pv[4];
@@ -606,7 +623,7 @@ __global__ void __launch_bounds__(128) k_fill_gfc(const GfcArgs a) {
   const R* __restrict__ mom = static_cast<const R*>(a.mom);
   const R* rec[4];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) rec[s] = mom + (size_t)a.gsrc[(size_t)s * a.ng + k] * kMomStride;
+  for (int s = 0; s < 4; ++s) rec[s] = mom + (size_t)a.gsrc[(size_t)s * a.ng + k] * RL::STRIDE;
   const uint8_t oct = a.oct[k];
   R sg[3];
 #pragma unroll
@@ -616,9 +633,9 @@ __global__ void __launch_bounds__(128) k_fill_gfc(const GfcArgs a) {
   R ul[4][3], Sl[4][NS], rps[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    R h[kMomStride - RL::RP];
+    R h[RL::STRIDE - RL::RP];
 #pragma unroll
-    for (int f = RL::RP; f < kMomStride; f += 4)
+    for (int f = RL::RP; f < RL::STRIDE; f += 4)
       if (f < RL::END) ld4(rec[s] + f, h + (f - RL::RP));
     rps[s] = h[0];
 #pragma unroll
@@ -946,80 +963,78 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
 // ----------------------------------------------------------------- launchers
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Calls f with std::integral_constant<int, Q> for the run-time stencil Q
+// (9, 19 or 27; the mesh builder rejects anything else).
+template <class F>
+inline void with_q(int Q, F&& f) {
+  if (Q == 9) f(std::integral_constant<int, 9>{});
+  else if (Q == 19) f(std::integral_constant<int, 19>{});
+  else f(std::integral_constant<int, 27>{});
+}
+
 template <class S>
 struct Launch {
   static void stream_collide_brick(int Q, bool force, const BrickArgs& a, cudaStream_t st) {
     if (a.nB <= 0) return;
     const unsigned g = blocks_for(a.nB, LBM_BR_BLOCK / 64);
-    if (Q == 9) {
-      if (force) k_stream_collide_brick<9, S, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
-      else k_stream_collide_brick<9, S, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
-    } else {
-      if (force) k_stream_collide_brick<19, S, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
-      else k_stream_collide_brick<19, S, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
-    }
+    with_q(Q, [&](auto q) {
+      constexpr int QQ = decltype(q)::value;
+      if (force) k_stream_collide_brick<QQ, S, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+      else k_stream_collide_brick<QQ, S, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+    });
   }
   static void stream_collide(int Q, bool force, const StreamCollideArgs& a, cudaStream_t st) {
     const int64_t n = a.end - a.begin;
     if (n <= 0) return;
     constexpr int EPT = LBM_SC_EPT;
     const unsigned g = blocks_for(n, LBM_SC_BLOCK * EPT);
-    if (Q == 9) {
-      if (force) k_stream_collide<9, S, true, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
-      else k_stream_collide<9, S, false, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
-    } else {
-      if (force) k_stream_collide<19, S, true, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
-      else k_stream_collide<19, S, false, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
-    }
+    with_q(Q, [&](auto q) {
+      constexpr int QQ = decltype(q)::value;
+      if (force) k_stream_collide<QQ, S, true, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+      else k_stream_collide<QQ, S, false, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+    });
   }
   static void outlet(int Q, const OutletArgs& a, cudaStream_t st) {
     const int64_t n = a.end - a.begin;
     if (n <= 0) return;
-    if (Q == 9) k_outlet<9, S><<<blocks_for(n, 128), 128, 0, st>>>(a);
-    else k_outlet<19, S><<<blocks_for(n, 128), 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_outlet<decltype(q)::value, S><<<blocks_for(n, 128), 128, 0, st>>>(a); });
   }
   static void source_moments(int Q, const MomentsArgs& a, cudaStream_t st) {
     if (a.nsrc <= 0) return;
-    if (Q == 9) k_source_moments<9, S><<<blocks_for(a.nsrc, 128), 128, 0, st>>>(a);
-    else k_source_moments<19, S><<<blocks_for(a.nsrc, 128), 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_source_moments<decltype(q)::value, S><<<blocks_for(a.nsrc, 128), 128, 0, st>>>(a); });
   }
   static void fill_gfc(int Q, const GfcArgs& a, cudaStream_t st) {
     if (a.ng <= 0) return;
-    if (Q == 9) k_fill_gfc<9, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a);
-    else k_fill_gfc<19, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_fill_gfc<decltype(q)::value, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a); });
   }
   static void fill_gff(int Q, const GffArgs& a, cudaStream_t st) {
     if (a.ng <= 0) return;
-    if (Q == 9) k_fill_gff<9, S><<<blocks_for(a.ng * 4, 256), 256, 0, st>>>(a);
-    else k_fill_gff<19, S><<<blocks_for(a.ng * 8, 256), 256, 0, st>>>(a);
+    with_q(Q, [&](auto q) {
+      constexpr int QQ = decltype(q)::value;
+      k_fill_gff<QQ, S><<<blocks_for(a.ng * (1 << Lat<QQ>::D), 256), 256, 0, st>>>(a);
+    });
   }
   static void fill_rest(int Q, const FillArgs& a, cudaStream_t st) {
-    if (Q == 9) k_fill_rest<9, S><<<blocks_for(a.Ntot, 256), 256, 0, st>>>(a);
-    else k_fill_rest<19, S><<<blocks_for(a.Ntot, 256), 256, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_fill_rest<decltype(q)::value, S><<<blocks_for(a.Ntot, 256), 256, 0, st>>>(a); });
   }
   static void init(int Q, const InitArgs& a, cudaStream_t st) {
     if (a.cnt <= 0) return;
-    if (Q == 9) k_init<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
-    else k_init<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_init<decltype(q)::value, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a); });
   }
   static void out(int Q, const OutArgs& a, cudaStream_t st) {
     if (a.cnt <= 0) return;
-    if (Q == 9) k_out<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
-    else k_out<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_out<decltype(q)::value, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a); });
   }
   static void set_state(int Q, const SetStateArgs& a, cudaStream_t st) {
     if (a.cnt <= 0) return;
-    if (Q == 9) k_set_state<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
-    else k_set_state<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_set_state<decltype(q)::value, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a); });
   }
   static void gather_ghosts(int Q, const GatherGhostArgs& a, cudaStream_t st) {
     if (a.cnt <= 0) return;
-    if (Q == 9) k_gather_ghosts<9, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
-    else k_gather_ghosts<19, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_gather_ghosts<decltype(q)::value, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a); });
   }
   static void reduce(int Q, const ReduceArgs& a, cudaStream_t st) {
-    if (Q == 9) k_reduce<9, S><<<a.nblocks, 256, 0, st>>>(a);
-    else k_reduce<19, S><<<a.nblocks, 256, 0, st>>>(a);
+    with_q(Q, [&](auto q) { k_reduce<decltype(q)::value, S><<<a.nblocks, 256, 0, st>>>(a); });
   }
 };
 

@@ -28,7 +28,7 @@ struct lbm_ctx {
   std::string err;
   int d = 2, Q = 9, nS = 3, nlev = 1;
   double rho_off = 0.0;
-  double inlet[19] = {};
+  double inlet[lbm::kQmax] = {};
   // layout (byte offsets into the workspace)
   size_t oA = 0, oB = 0, oNbr = 0, oBrickNb = 0, oBrickTab = 0, oF = 0, oOutElem = 0, oOutA = 0, oOutB = 0, oOutDir = 0, oOutKind = 0,
          oSide = 0, oObsElem = 0, oObsDir = 0, oUslot = 0, oUlev = 0, oStage = 0, oPartial = 0, oRed = 0;

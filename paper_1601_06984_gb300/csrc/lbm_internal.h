@@ -23,6 +23,30 @@ constexpr uint32_t NB_INDEX = 0x3FFFFFFFu;
 constexpr int kPad = 32;  // every level segment is padded to a multiple of this
 
 enum { K_FLUID = 0, K_GFC = 1, K_GFF = 2, K_PAD = 3 };
+
+// Discrete velocities in the order documented in lbm.h (D2Q9, D3Q19, and
+// D3Q27 = D3Q19 followed by the corners in opposite pairs) and the standard
+// weights by |c|^2 (Sec. 2.1): D2Q9 4/9, 1/9, 1/36; D3Q19 1/3, 1/18, 1/36;
+// D3Q27 8/27, 2/27, 1/54, 1/216.  The one host copy of the lattice.
+constexpr int kQmax = 27;
+inline void host_lattice(int Q, int c[kQmax][3], double w[kQmax]) {
+  static const int c27[27][3] = {{0, 0, 0},   {1, 0, 0},    {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},  {0, 0, 1},
+                                 {0, 0, -1},  {1, 1, 0},    {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},  {1, 0, 1},
+                                 {-1, 0, -1}, {1, 0, -1},   {-1, 0, 1}, {0, 1, 1},   {0, -1, -1}, {0, 1, -1},
+                                 {0, -1, 1},  {1, 1, 1},    {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1},
+                                 {-1, 1, -1}, {-1, 1, 1},   {1, -1, -1}};
+  // D2Q9 order: rest, +x, -x, +y, -y, (+x+y), (-x-y), (+x-y), (-x+y)
+  static const int c9[9][3] = {{0, 0, 0}, {1, 0, 0},  {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                               {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+  for (int i = 0; i < kQmax; ++i) {
+    for (int a = 0; a < 3; ++a) c[i][a] = i < Q ? (Q == 9 ? c9[i][a] : c27[i][a]) : 0;
+    const int n2 = c[i][0] * c[i][0] + c[i][1] * c[i][1] + c[i][2] * c[i][2];
+    if (i >= Q) w[i] = 0.0;
+    else if (Q == 9) w[i] = n2 == 0 ? 4.0 / 9.0 : (n2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+    else if (Q == 19) w[i] = n2 == 0 ? 1.0 / 3.0 : (n2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+    else w[i] = n2 == 0 ? 8.0 / 27.0 : (n2 == 1 ? 2.0 / 27.0 : (n2 == 2 ? 1.0 / 54.0 : 1.0 / 216.0));
+  }
+}
 enum { OUT_NORMAL = 0, OUT_EXTRAP = 1 };
 
 struct HostLevel {
@@ -95,7 +119,7 @@ struct StreamCollideArgs {
   int64_t Ntot, begin, end;  // linear range; element = lin + (lin >= hole_at ? hole_len : 0)
   int64_t hole_at, hole_len;  // interior bricks skipped by this kernel (0 length: none)
   double omega, rho_off;
-  double inlet[19];   // 6 w_i rho0 (c_i . u_in)
+  double inlet[kQmax];  // 6 w_i rho0 (c_i . u_in)
 };
 
 // Stream-collide of the interior bricks of one level: nB bricks of 64
@@ -122,21 +146,22 @@ struct OutletArgs {
   int zero_gradient;  // extrapolate with f(x - n) instead of 2 f(x - n) - f(x - 2n)
 };
 
-// GFC source moments: one record of kMomStride values per source (compute
-// type): rho - rho_off, u[d], S[nS], f^neq[Q], zero padding.
-constexpr int kMomStride = 32;
+// GFC source moments: one record of mom_stride(Q) values per source (compute
+// type): f^neq[Q] padded to a multiple of 4, rho - rho_off, u[d], S[nS], zero
+// padding.
+constexpr int mom_stride(int Q) { return Q == 27 ? 40 : 32; }
 struct MomentsArgs {
   const void* src;
   const void* force;
   const int32_t* elem;
-  void* mom;         // [nsrc][kMomStride]
+  void* mom;         // [nsrc][mom_stride(Q)]
   const void* prev;  // if set: mom = (prev + moments now) / 2 (mean of two time levels)
   int64_t Ntot, nsrc;
   double omega, rho_off;
 };
 
 struct GfcArgs {
-  const void* mom;       // [nsrc][kMomStride] source records
+  const void* mom;       // [nsrc][mom_stride(Q)] source records
   int64_t nsrc;
   const int32_t* gsrc;   // [4][ng]
   const uint8_t* oct;    // [ng]
@@ -276,7 +301,7 @@ struct AdjSCArgs {
   void* lam_side;        // adjoint of the outlet values (written)
   int64_t begin, end;
   double omega;
-  double inlet[19];      // 6 w_i rho0 (c_i . u_in) of the forward
+  double inlet[kQmax];   // 6 w_i rho0 (c_i . u_in) of the forward
 };
 
 struct AdjOutletArgs {
@@ -293,7 +318,7 @@ struct AdjOutletArgs {
 struct AdjMomArgs {  // reverse of the source moments
   AdjCommon c;       // lam_b: adjoint of the coarse state
   const int32_t* elem;
-  void* lam_rec;       // [nsrc][kMomStride] adjoint of the records (consumed, zeroed)
+  void* lam_rec;       // [nsrc][mom_stride(Q)] adjoint of the records (consumed, zeroed)
   void* lam_rec_prev;  // averaging mode: receives half of lam_rec (else null)
   int64_t nsrc;
   double omega;
@@ -301,10 +326,10 @@ struct AdjMomArgs {  // reverse of the source moments
 
 struct AdjGfcArgs {  // reverse of the GhostFromCoarser fill, per ghost
   AdjCommon c;       // lam_a: adjoint of the fine state holding the ghosts
-  const void* rec;   // forward source records [nsrc][kMomStride]
+  const void* rec;   // forward source records [nsrc][mom_stride(Q)]
   const int32_t* gsrc;
   const uint8_t* oct;
-  void* contrib;     // [ng][4][kMomStride] per-ghost adjoint of each source record
+  void* contrib;     // [ng][4][mom_stride(Q)] per-ghost adjoint of each source record
   int64_t ng, dest0;
   double omega_c, omega_f;
 };
@@ -313,8 +338,9 @@ struct AdjGatherArgs {  // deterministic sum of the per-ghost contributions per 
   const void* contrib;
   const int32_t* off;   // [nsrc+1]
   const int32_t* item;  // ghost*4 + source slot
-  void* lam_rec;        // [nsrc][kMomStride] accumulated
+  void* lam_rec;        // [nsrc][stride] accumulated
   int64_t nsrc;
+  int stride;           // mom_stride(Q): 32 or 40
 };
 
 struct AdjGffArgs {

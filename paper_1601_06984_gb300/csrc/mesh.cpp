@@ -25,21 +25,15 @@ namespace {
 // Discrete velocities in the order documented in lbm.h.
 struct Dirs {
   int Q = 9, d = 2;
-  int c[19][3] = {};
+  int c[kQmax][3] = {};
 };
 
 Dirs make_dirs(int Q) {
   Dirs r;
   r.Q = Q;
   r.d = Q == 9 ? 2 : 3;
-  static const int c9[9][3] = {{0, 0, 0}, {1, 0, 0},  {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
-                               {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
-  static const int c19[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
-                                 {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
-                                 {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                                 {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
-  for (int i = 0; i < Q; ++i)
-    for (int a = 0; a < 3; ++a) r.c[i][a] = Q == 9 ? c9[i][a] : c19[i][a];
+  double w[kQmax];
+  host_lattice(Q, r.c, w);
   return r;
 }
 
@@ -160,7 +154,7 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     return s;
   };
   if (!tid || n <= 0) return bad(LBM_ERR_ARG, "empty mesh");
-  if (p.stencil != 9 && p.stencil != 19) return bad(LBM_ERR_ARG, "stencil must be 9 or 19");
+  if (p.stencil != 9 && p.stencil != 19 && p.stencil != 27) return bad(LBM_ERR_ARG, "stencil must be 9, 19 or 27");
   if (p.time_mode != LBM_TIME_LINEAR && p.time_mode != LBM_TIME_TWO_LAYER)
     return bad(LBM_ERR_ARG, "bad time mode");
   if (!(p.omega_coarse > 0.0 && p.omega_coarse < 2.0)) return bad(LBM_ERR_ARG, "omega must lie in (0,2)");

@@ -35,6 +35,8 @@ def test_exports_every_declared_symbol(lbm):
 MESHES = [
     ("tgv2d", W.config_tgv2d, 9, 1.6),
     ("tgv3d", lambda: W.config_tgv3d(16), 19, 1.6),
+    ("tgv3d_q27", lambda: W.config_tgv3d(16), 27, 1.6),
+    ("sphere_q27", W.config_sphere_small, 27, 1.7),
     ("half", lambda: W.half_refined_2d(16), 9, 1.6),
     ("cylinder", W.config_cylinder, 9, 1.8605),
 ]
@@ -141,15 +143,16 @@ def test_updates_weighting():
     assert m3.updates_per_coarse_step() == 229376 + 2 * 262144
 
 
-def _interior_bricks(mesh):
+def _interior_bricks(mesh, Q):
     """Per level, interior bricks counted from the element coordinates alone:
-    aligned blocks of 64 same-level elements (4^3 / 8^2) whose face and edge
-    neighbour blocks (all eight in 2D) are complete too; periodic axes wrap
-    when their extent is a whole number of blocks."""
+    aligned blocks of 64 same-level elements (4^3 / 8^2) whose neighbour
+    blocks reached by the stencil are complete too (D3Q19: faces and edges;
+    D2Q9 and D3Q27: all of them); periodic axes wrap when their extent is a
+    whole number of blocks."""
     d = mesh.d
     side = 4 if d == 3 else 8
     offs = [o for o in itertools.product((-1, 0, 1), repeat=d) if any(o)]
-    if d == 3:
+    if Q == 19:
         offs = [o for o in offs if sum(map(abs, o)) <= 2]  # D3Q19 reaches no corner block
     out = []
     for L in sorted(set(int(v) for v in mesh.levels)):
@@ -180,12 +183,14 @@ def _interior_bricks(mesh):
     return out
 
 
-@pytest.mark.parametrize("name", ["tgv2d", "tgv3d16", "half2d", "cylinder", "sphere_small"])
+@pytest.mark.parametrize("name", ["tgv2d", "tgv3d16", "half2d", "cylinder", "sphere_small", "tgv3d32_q27",
+                                  "sphere_small_q27"])
 def test_interior_brick_counts(lbm, name):
     """The builder's interior bricks match an independent count, and the
     builder has checked each brick's link table against the neighbour list."""
     mesh, Q = {"tgv2d": (W.config_tgv2d(), 9), "tgv3d16": (W.config_tgv3d(16), 19),
                "half2d": (W.half_refined_2d(32), 9), "cylinder": (W.config_cylinder(), 9),
-               "sphere_small": (W.config_sphere_small(), 19)}[name]
+               "sphere_small": (W.config_sphere_small(), 19), "tgv3d32_q27": (W.config_tgv3d(32), 27),
+               "sphere_small_q27": (W.config_sphere_small(), 27)}[name]
     info = lbm.Sim(mesh, Q, 1.7, u_in=(0.04, 0, 0), device=None).mesh_info()
-    assert [int(r[8]) for r in info] == _interior_bricks(mesh)
+    assert [int(r[8]) for r in info] == _interior_bricks(mesh, Q)

@@ -41,6 +41,13 @@ def make(name):
         m = W.config_sphere_small()
         return (m, 19, W.omega_coarse_from_finest(1.6, 3), (0.04, 0.0, 0.0),
                 lambda m: W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), 3, 2)
+    if name == "tgv3d_q27":
+        m = W.config_tgv3d(16)
+        return m, 27, 1.6, (0.0, 0.0, 0.0), lambda m: W.tgv_fields(m, 0.02), 4, 3
+    if name == "sphere_q27":
+        m = W.config_sphere_small()
+        return (m, 27, W.omega_coarse_from_finest(1.6, 3), (0.04, 0.0, 0.0),
+                lambda m: W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), 3, 2)
     if name in ("channel", "channel_zg"):
         # walled inlet/outlet channel, refined block in the middle; omega near 2
         # on the coarse level exercises the outlet's f^neq rescale
@@ -54,7 +61,8 @@ def make(name):
 OUTLET = {"channel_zg": 1}
 CASES = [("uni2d", 0, 0), ("tgv2d", 0, 0), ("tgv2d", 1, 0), ("half2d", 0, 0), ("tgv3d", 0, 0), ("tgv3d", 1, 0),
          ("sphere", 0, 0), ("sphere", 1, 0), ("sphere", 0, 1), ("sphere", 1, 3),
-         ("channel", 0, 0), ("channel", 1, 0), ("channel_zg", 0, 0)]
+         ("channel", 0, 0), ("channel", 1, 0), ("channel_zg", 0, 0),
+         ("tgv3d_q27", 0, 0), ("tgv3d_q27", 1, 0), ("sphere_q27", 0, 1)]
 
 
 def J_of(red, objective):

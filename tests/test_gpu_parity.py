@@ -49,6 +49,18 @@ def make_case(name):
         om = W.omega_coarse_from_finest(W.omega_for_re(0.05, 40, 20), 4)
         return (m, 9, om, (0.05, 0, 0),
                 lambda m: (*W.uniform_fields(m, 1.0, (0.05, 0.0)), W.pdf_perturbation(m, 9, 1e-4)), None, 2)
+    if name == "tgv3d_q27":
+        m = W.config_tgv3d(16)
+        return m, 27, 1.6, (0, 0, 0), lambda m: (*W.tgv_fields(m, 0.01), W.pdf_perturbation(m, 27)), None, 8
+    if name == "tgv3d_force_q27":
+        m = W.config_tgv3d(16)
+        return (m, 27, 1.6, (0, 0, 0), lambda m: (*W.tgv_fields(m, 0.01), None),
+                W.gaussian_force(m, 1e-5), 6)
+    if name == "sphere_small_q27":
+        m = W.config_sphere_small()
+        om = W.omega_coarse_from_finest(1.6, 3)
+        return (m, 27, om, (0.04, 0, 0),
+                lambda m: (*W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), W.pdf_perturbation(m, 27, 1e-4)), None, 3)
     if name == "channel_zg":
         m = W.nested_boxes(2, 5, (32, 16), [((16, 8), (40, 24))],
                            (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_WALL, W.BC_WALL))
@@ -82,7 +94,8 @@ def run_both(lbm, oracle_mod, name, mode, precision=0):
     return m, o, g
 
 
-CASES = ["tgv2d", "tgv2d_half", "tgv3d", "tgv3d_force", "cylinder", "channel_zg", "sphere_small"]
+CASES = ["tgv2d", "tgv2d_half", "tgv3d", "tgv3d_force", "cylinder", "channel_zg", "sphere_small",
+         "tgv3d_q27", "tgv3d_force_q27", "sphere_small_q27"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -104,7 +117,7 @@ def test_fp64_matches_oracle(lbm, oracle_mod, name, mode):
         assert np.abs(red_g[4:7] - red_o[4:7]).max() / np.abs(red_o[4:7]).max() < 1e-10
 
 
-@pytest.mark.parametrize("name", ["tgv2d", "tgv3d", "sphere_small"])
+@pytest.mark.parametrize("name", ["tgv2d", "tgv3d", "sphere_small", "tgv3d_q27"])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_ghost_fill_matches_oracle(lbm, oracle_mod, name, mode):
     """GhostFromFiner and GhostFromCoarser values after one synchronous fill."""
@@ -258,3 +271,22 @@ def test_graph_steps_match_eager_steps(lbm, precision, mode):
     for _ in range(4):
         b.step(1)
     assert np.array_equal(a.get_state(), b.get_state())
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_q27_reduced_precision_tracks_fp64(lbm, oracle_mod, precision):
+    """D3Q27 with FP32 / BF16 deviation storage on the two-level 16^3 Taylor-Green
+    (40 coarse steps) stays within the same bounds as D2Q9 / D3Q19 against the
+    FP64 oracle: velocity l2 1e-4 (FP32) and 5e-2 (BF16)."""
+    m = W.config_tgv3d(16)
+    rho, u, S = W.tgv_fields(m, 0.01)
+    o = oracle_mod.Oracle(m, 27, 1.6)
+    o.init(rho, u, S)
+    o.step(40)
+    _, u_o, _ = o.moments()
+    g = lbm.Sim(m, 27, 1.6, precision=precision)
+    g.init(rho, u, S)
+    g.step(40)
+    _, u_g, _ = g.moments()
+    err = math.sqrt(((u_g - u_o) ** 2).sum() / (u_o ** 2).sum())
+    assert err < {1: 1e-4, 2: 5e-2}[precision], err
