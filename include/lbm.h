@@ -5,7 +5,7 @@
  * Roller, "Implementation of the compact interpolation within the octree based
  * Lattice Boltzmann solver Musubi" (arXiv:1601.06984): per-level pull
  * stream + BGK collide over level-wise, space-filling-curve ordered element
- * arrays (D2Q9 / D3Q19), ghost filling between levels by compact interpolation
+ * arrays (D2Q9 / D3Q19 / D3Q27), ghost filling between levels by compact interpolation
  * (GhostFromCoarser) and by restriction from the children (GhostFromFiner), and
  * the recursive level time stepping with two fine substeps per coarse step.
  *
@@ -32,6 +32,8 @@
  *      D3Q19: 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z, 7 (+x+y), 8 (-x-y),
  *             9 (+x-y), 10 (-x+y), 11 (+x+z), 12 (-x-z), 13 (+x-z), 14 (-x+z),
  *             15 (+y+z), 16 (-y-z), 17 (+y-z), 18 (-y+z)
+ *      D3Q27: the D3Q19 directions, then 19 (+x+y+z), 20 (-x-y-z), 21 (+x+y-z),
+ *             22 (-x-y+z), 23 (+x-y+z), 24 (-x+y-z), 25 (-x+y+z), 26 (+x-y-z)
  *    Strain-rate components: 2D xx, yy, xy; 3D xx, yy, zz, xy, yz, xz.
  */
 #ifndef LBM_H
@@ -62,7 +64,9 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_VELOCITY_IN = 2, LBM_BC_PRES
 enum { LBM_OUTLET_LINEAR = 0, LBM_OUTLET_ZERO_GRADIENT = 1 };
 
 /* Simulation parameters.
- *  stencil       9 (D2Q9) or 19 (D3Q19); Sec. 2.1.
+ *  stencil       9 (D2Q9), 19 (D3Q19) or 27 (D3Q27, the paper's 3D lattice); Sec. 2.1.
+ *                Weights by |c|^2: D2Q9 4/9, 1/9, 1/36; D3Q19 1/3, 1/18, 1/36;
+ *                D3Q27 8/27, 2/27, 1/54, 1/216.
  *  precision     LBM_FP64: pdfs stored and computed in double.
  *                LBM_FP32DEV: each pdf stored as float deviation g_i = f_i - w_i rho0,
  *                             arithmetic in float.
