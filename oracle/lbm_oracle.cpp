@@ -151,9 +151,11 @@ inline int64_t pack(const Coord& p) {
 struct Link {
   int kind = LK_SELF;
   int src = -1;     // element index (same level) for LK_PULL
-  int a = -1, b = -1;  // extrapolation sources for LK_OUT_EXTRAP
+  int a = -1, b = -1;  // extrapolation sources for LK_OUT_EXTRAP; a: second node x + c_i of an obstacle link
   int face = -1;
   bool obstacle = false;
+  double q = 0.5;      // obstacle link: wall at x - q c_i (Bouzidi); 1/2 is half-way bounce-back
+  double s = 1.0;      // inlet link: velocity profile factor at the boundary point
 };
 
 template <class T>
@@ -199,6 +201,43 @@ struct Sim {
   double uin[3] = {0.0, 0.0, 0.0};
   T uinT[3] = {T(0.0), T(0.0), T(0.0)};  // inlet velocity carried in T (tangent for the dual twin)
   bool outlet_zero_gradient = false;     // outlet extrapolation order 0 instead of 1
+
+  // Inlet velocity profile: 0 uniform, 1 parabolic in the axes tangential to
+  // the inlet face, 6 t (1 - t) per axis with t the boundary point's position
+  // across the domain (mean 1).  The boundary point of the link i of element x
+  // is x - c_i / 2.
+  void set_inlet_profile(int profile) {
+    for (int li = 0; li < nlev(); ++li)
+      for (auto& e : lv[li].e)
+        for (int i = 1; i < Q; ++i) {
+          Link& lk = e.link[i];
+          if (lk.kind != LK_INLET) continue;
+          lk.s = 1.0;
+          if (profile != 1) continue;
+          int nface = -1;
+          for (int f = 0; f < 2 * d; ++f)
+            if (bc[f] == BC_VELOCITY_IN) nface = f / 2;
+          for (int a = 0; a < d; ++a) {
+            if (a == nface) continue;
+            const double t = (e.x[a] + 0.5 - 0.5 * lat.c[i][a]) / (double)ext(li, a);
+            lk.s *= 6.0 * t * (1.0 - t);
+          }
+        }
+  }
+
+  // Wall distance of obstacle links, given per (user element, direction i with
+  // x - c_i solid); false if a pair is not an obstacle link or q is outside (0,1].
+  bool set_link_q(int64_t n, const int64_t* user, const int* dir, const double* q) {
+    for (int64_t k = 0; k < n; ++k) {
+      if (user[k] < 0 || user[k] >= (int64_t)upos.size() || dir[k] < 1 || dir[k] >= Q) return false;
+      if (!(q[k] > 0.0 && q[k] <= 1.0)) return false;
+      auto& e = lv[upos[user[k]].first].e[upos[user[k]].second];
+      Link& lk = e.link[dir[k]];
+      if (lk.kind != LK_BOUNCE || !lk.obstacle) return false;
+      lk.q = q[k];
+    }
+    return true;
+  }
   bool use_force = false;
   T omega_c = T(1.0);
   int Lmin = 0, Lmax = 0;
@@ -503,6 +542,9 @@ struct Sim {
               if (e.kind != FLUID) return fail("ghost element next to a solid");
               lk.kind = LK_BOUNCE;
               lk.obstacle = true;
+              // second node of the interpolated bounce-back: the element
+              // behind x, away from the wall (any element of this level)
+              lk.a = index_at(li, Coord{e.x[0] + lat.c[i][0], e.x[1] + lat.c[i][1], e.x[2] + lat.c[i][2]});
             } else {
               return fail("neighbour on another level has no ghost element");
             }
@@ -557,13 +599,27 @@ struct Sim {
         return e.f[i];
       case LK_PULL:
         return l.e[lk.src].f[i];
-      case LK_BOUNCE:
-        return e.f[ib];
+      case LK_BOUNCE: {
+        if (!lk.obstacle) return e.f[ib];
+        // linearly interpolated bounce-back (Bouzidi, Sec. 2.3): the pdf
+        // leaving toward the wall at x - q c_i returns as
+        //   q <  1/2: 2q f*_ib(x) + (1 - 2q) f*_ib(x + c_i)
+        //   q >= 1/2: f*_ib(x) / (2q) + (2q - 1)/(2q) f*_i(x)
+        // (q = 1/2 is half-way bounce-back; without a node behind x the link
+        // falls back to it)
+        const double q = lk.q;
+        if (q < 0.5) {
+          if (lk.a < 0) return e.f[ib];
+          return T(2.0 * q) * e.f[ib] + T(1.0 - 2.0 * q) * l.e[lk.a].f[ib];
+        }
+        return T(1.0 / (2.0 * q)) * e.f[ib] + T((2.0 * q - 1.0) / (2.0 * q)) * e.f[i];
+      }
       case LK_INLET: {
-        // velocity bounce-back (Ladd): f_i = f*_ib + 2 w_i rho0 (c_i.U) / c_s^2
+        // velocity bounce-back (Ladd): f_i = f*_ib + 2 w_i rho0 (c_i.U) / c_s^2,
+        // U = u_in times the profile factor at the boundary point
         T cu = T(0.0);
         for (int a = 0; a < d; ++a) cu += T((double)lat.c[i][a]) * uinT[a];
-        return e.f[ib] + T(6.0 * lat.w[i] * rho0) * cu;
+        return e.f[ib] + T(6.0 * lat.w[i] * rho0 * lk.s) * cu;
       }
       case LK_OUT_NORMAL: {
         // pressure-corrected outlet along the normal: f^eq_i(rho0, u) + f^neq_ib.
@@ -964,14 +1020,16 @@ void reduce_sim(const Sim<T>* s, T out[8]) {
         uu += m.u[a] * m.u[a];
       }
       out[7] += T(0.5 * vol) * m.rho * uu;
-      // momentum exchange on obstacle links (Sec. 2.3): with half-way bounce-
-      // back the pdf f*_ib(x_b) leaving toward the body returns unchanged, so
-      // the link carries 2 c_ib f*_ib(x_b) to the body.
+      // momentum exchange on obstacle links (Sec. 2.3): the pdf f*_ib(x_b)
+      // leaves toward the body and f_i(x_b) (the bounce-back value of the next
+      // step) returns, so the link carries c_ib (f*_ib + f_i) to the body; with
+      // half-way bounce-back that is 2 c_ib f*_ib.
       for (int i = 1; i < s->Q; ++i) {
         if (e.link[i].kind != LK_BOUNCE || !e.link[i].obstacle) continue;
         int ib = s->lat.opp[i];
+        const T back = s->pull(l, e, i);
         for (int a = 0; a < d; ++a)
-          out[4 + a] += T(2.0 * fscale * s->lat.c[ib][a]) * e.f[ib];
+          out[4 + a] += T(fscale * s->lat.c[ib][a]) * (e.f[ib] + back);
       }
     }
   }
@@ -1022,6 +1080,16 @@ int orc_init(void* h, const double* rho, const double* u, const double* S, const
 int orc_set_outlet(void* h, int mode) {
   static_cast<Sim<double>*>(h)->outlet_zero_gradient = mode == 1;
   return mode == 0 || mode == 1 ? 0 : -1;
+}
+
+int orc_set_inlet_profile(void* h, int profile) {
+  if (profile != 0 && profile != 1) return -1;
+  static_cast<Sim<double>*>(h)->set_inlet_profile(profile);
+  return 0;
+}
+
+int orc_set_link_q(void* h, int64_t n, const int64_t* user, const int* dir, const double* q) {
+  return static_cast<Sim<double>*>(h)->set_link_q(n, user, dir, q) ? 0 : -1;
 }
 
 int orc_set_force(void* h, const double* F) {
@@ -1154,6 +1222,16 @@ int orc_dual_init(void* h, const double* rho, const double* u, const double* S, 
 int orc_dual_set_outlet(void* h, int mode) {
   static_cast<Sim<Dual>*>(h)->outlet_zero_gradient = mode == 1;
   return mode == 0 || mode == 1 ? 0 : -1;
+}
+
+int orc_dual_set_inlet_profile(void* h, int profile) {
+  if (profile != 0 && profile != 1) return -1;
+  static_cast<Sim<Dual>*>(h)->set_inlet_profile(profile);
+  return 0;
+}
+
+int orc_dual_set_link_q(void* h, int64_t n, const int64_t* user, const int* dir, const double* q) {
+  return static_cast<Sim<Dual>*>(h)->set_link_q(n, user, dir, q) ? 0 : -1;
 }
 
 int orc_dual_set_force(void* h, const double* F, const double* F_dot) {

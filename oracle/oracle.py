@@ -51,6 +51,10 @@ def lib():
         L.orc_set_force.argtypes = [P, P]
         L.orc_set_outlet.argtypes = [P, I]
         L.orc_dual_set_outlet.argtypes = [P, I]
+        L.orc_set_inlet_profile.argtypes = [P, I]
+        L.orc_dual_set_inlet_profile.argtypes = [P, I]
+        L.orc_set_link_q.argtypes = [P, I64, P, P, P]
+        L.orc_dual_set_link_q.argtypes = [P, I64, P, P, P]
         L.orc_dual_set_force.argtypes = [P, P, P]
         L.orc_step.argtypes = [P, I64]
         L.orc_dual_step.argtypes = [P, I64]
@@ -91,7 +95,8 @@ class Oracle:
     carries a tangent (forward-mode derivative along omega_dot and F_dot)."""
 
     def __init__(self, mesh, stencil, omega_c, time_mode=0, rho0=1.0, u_in=(0.0, 0.0, 0.0),
-                 use_force=False, dual=False, omega_dot=0.0, u_in_dot=(0.0, 0.0, 0.0), outlet=0):
+                 use_force=False, dual=False, omega_dot=0.0, u_in_dot=(0.0, 0.0, 0.0), outlet=0,
+                 inlet_profile=0):
         L = lib()
         self.mesh, self.stencil, self.dual = mesh, stencil, dual
         self.d = 2 if stencil == 9 else 3
@@ -117,6 +122,9 @@ class Oracle:
         # outlet extrapolation: 0 linear (Sec. 2.3), 1 zero-gradient
         if (L.orc_dual_set_outlet if dual else L.orc_set_outlet)(h, int(outlet)) != 0:
             raise OracleError("outlet must be 0 (linear) or 1 (zero-gradient)")
+        # inlet velocity profile: 0 uniform, 1 parabolic across the channel (mean 1)
+        if (L.orc_dual_set_inlet_profile if dual else L.orc_set_inlet_profile)(h, int(inlet_profile)) != 0:
+            raise OracleError("inlet_profile must be 0 (uniform) or 1 (parabolic)")
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -125,6 +133,16 @@ class Oracle:
             self.h = None
 
     # ------------------------------------------------------------------
+    def set_link_q(self, user_elem, direction, q):
+        """Wall distance q in (0, 1] of obstacle links (user element index,
+        direction i with x - c_i solid): the wall lies at x - q c_i."""
+        ue = np.ascontiguousarray(user_elem, dtype=np.int64)
+        dr = np.ascontiguousarray(direction, dtype=np.int32)
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        fn = lib().orc_dual_set_link_q if self.dual else lib().orc_set_link_q
+        if fn(self.h, len(ue), _p(ue), _p(dr), _p(qq)) != 0:
+            raise OracleError("set_link_q: not an obstacle link, or q outside (0, 1]")
+
     def counts(self):
         out = np.zeros((16, 6), dtype=np.int64)
         n = lib().orc_counts(self.h, _p(out), 16)

@@ -395,6 +395,85 @@ def test_outlet_bounded_near_omega_two(oracle_mod, outlet, omega, steps):
     assert np.isfinite(umax) and umax < 0.1
 
 
+def _wall_channel(oracle_mod, N, qb, qt, omega=1.2, set_q=True, steps=None):
+    """Force-driven channel, periodic in x and y, with solid rows y = 0 and
+    y = N + 1: the bottom wall sits at distance qb below the first fluid row,
+    the top wall qt above the last one (wall at x - q c_i on every link into a
+    solid cell).  Returns the oracle, the mesh and the exact steady Poiseuille
+    profile."""
+    ny = N + 2
+    L = int(np.ceil(np.log2(ny)))
+    mesh = W.uniform(2, L, (4, ny), (W.BC_PERIODIC,) * 4,
+                     solid=lambda lev, cen: (cen[:, 1] < 1) | (cen[:, 1] > N + 1))
+    o = oracle_mod.Oracle(mesh, 9, omega, use_force=True)
+    fluid = {tuple(c) for c in mesh.coords}
+    ue, dr, qq = [], [], []
+    for k, c in enumerate(mesh.coords):
+        for i in range(1, 9):
+            p = ((c[0] - C9[i][0]) % 4, (c[1] - C9[i][1]) % ny)
+            if p not in fluid:
+                ue.append(k)
+                dr.append(i)
+                qq.append(qb if C9[i][1] > 0 else qt)
+    if set_q:
+        o.set_link_q(ue, dr, qq)
+    F0 = 1e-6
+    F = np.zeros((mesh.n, 2))
+    F[:, 0] = F0
+    o.init(*W.uniform_fields(mesh, 1.0, (0.0, 0.0)))
+    o.set_force(F)
+    nu = (1 / omega - 0.5) / 3
+    o.step(steps if steps is not None else int(4 * (N + 1) ** 2 / nu) + 200)
+    y = mesh.coords[:, 1] + 0.5
+    exact = F0 / (2 * nu) * (y - (1.5 - qb)) * (N + 0.5 + qt - y)
+    return o, mesh, exact
+
+
+def test_bouzidi_off_grid_walls_second_order(oracle_mod):
+    """Sec. 2.3, linearly interpolated bounce-back (Bouzidi): with the walls
+    0.3 and 0.7 of a link away from the first and last fluid rows, the steady
+    force-driven channel converges to the exact parabola between the true wall
+    positions at second order (error ratio near 4 from 8 to 16 rows).  Half-way
+    bounce-back on the same geometry places the walls at 1/2 and converges at
+    first order only (ratio near 2).  At the steady state the momentum exchange
+    on the wall links balances the body force."""
+    err = []
+    for N in (8, 16):
+        o, mesh, exact = _wall_channel(oracle_mod, N, 0.3, 0.7)
+        _, u, _ = o.moments()
+        err.append(np.abs(u[:, 0] - exact).max() / exact.max())
+        # steady state: the momentum exchange c_ib (f*_ib + f_i) on the wall
+        # links balances the body force on the fluid
+        assert abs(o.reduce()[4] / (mesh.n * 1e-6) - 1) < 1e-8
+    assert err[1] < 5e-3
+    assert err[0] / err[1] > 3.2, err
+
+
+def test_bouzidi_half_is_halfway_bounce_back(oracle_mod):
+    """q = 1/2 on every link reproduces half-way bounce-back bit for bit."""
+    a, _, _ = _wall_channel(oracle_mod, 8, 0.5, 0.5, steps=50)
+    b, _, _ = _wall_channel(oracle_mod, 8, 0.5, 0.5, set_q=False, steps=50)
+    assert np.array_equal(a.get_f(), b.get_f())
+    assert np.array_equal(a.reduce(), b.reduce())
+
+
+def test_parabolic_inlet_profile(oracle_mod):
+    """Velocity inlet with the parabolic profile 6 U t (1 - t) across a walled
+    channel (mean U): the first fluid column carries the parabola (a uniform
+    inlet there is 36% off) with mean velocity U, and the flow stays parallel."""
+    U, H = 0.02, 16
+    mesh = W.uniform(2, 6, (64, H), (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_WALL, W.BC_WALL))
+    o = oracle_mod.Oracle(mesh, 9, 1.2, u_in=(U, 0.0, 0.0), inlet_profile=1)
+    o.init(*W.uniform_fields(mesh, 1.0, (U, 0.0)))
+    o.step(4000)
+    _, u, _ = o.moments()
+    col = mesh.coords[:, 0] == 0
+    t = (mesh.coords[col, 1] + 0.5) / H
+    assert np.abs(u[col, 0] - 6 * U * t * (1 - t)).max() < 0.04 * 1.5 * U
+    assert abs(u[col, 0].mean() / U - 1) < 0.03
+    assert np.abs(u[col, 1]).max() < 0.01 * U
+
+
 def test_obstacle_force_balances_body_force(oracle_mod):
     """Sec. 2.3 momentum exchange: in a periodic box driven by a uniform body
     force, the steady drag on a bounce-back obstacle equals the total body
