@@ -62,6 +62,7 @@ enum { LBM_FP64 = 0, LBM_FP32DEV = 1, LBM_BF16DEV = 2 };
 enum { LBM_TIME_LINEAR = 0, LBM_TIME_TWO_LAYER = 1 };
 enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_VELOCITY_IN = 2, LBM_BC_PRESSURE_OUT = 3 };
 enum { LBM_OUTLET_LINEAR = 0, LBM_OUTLET_ZERO_GRADIENT = 1 };
+enum { LBM_INLET_UNIFORM = 0, LBM_INLET_PARABOLIC = 1 };
 
 /* Simulation parameters.
  *  stencil       9 (D2Q9), 19 (D3Q19) or 27 (D3Q27, the paper's 3D lattice); Sec. 2.1.
@@ -90,7 +91,14 @@ enum { LBM_OUTLET_LINEAR = 0, LBM_OUTLET_ZERO_GRADIENT = 1 };
  *                LBM_OUTLET_LINEAR (0): 2 f(x - n) - f(x - 2n), as in Sec. 2.3;
  *                LBM_OUTLET_ZERO_GRADIENT (1): f(x - n), for relaxation rates
  *                near 2 where the linear rule is unstable.  Other values:
- *                LBM_ERR_ARG from lbm_build_mesh. */
+ *                LBM_ERR_ARG from lbm_build_mesh.
+ *  inlet_profile LBM_INLET_UNIFORM (0): u_in on every inlet link;
+ *                LBM_INLET_PARABOLIC (1): u_in 6 t (1 - t) per axis tangential to
+ *                the inlet face, t the position of the link's boundary point
+ *                x - c_i / 2 across the domain (mean u_in; Sec. 4.2 inflow).
+ *  bouzidi       0: half-way bounce-back on obstacle links; 1: linearly
+ *                interpolated bounce-back (Bouzidi, Sec. 2.3) with the wall at
+ *                x - q c_i, q per link from lbm_set_link_q (1/2 until set). */
 typedef struct {
   int32_t stencil;
   int32_t precision;
@@ -102,6 +110,8 @@ typedef struct {
   double u_in[3];
   int32_t use_force;
   int32_t outlet;
+  int32_t inlet_profile;
+  int32_t bouzidi;
 } lbm_params;
 
 /* Build the multilevel mesh on the host (no device work).
@@ -125,6 +135,19 @@ lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t
  * stream-collide locates their pull sources from a per-brick table instead
  * of the neighbour list.  cap = rows available in info. */
 lbm_status lbm_mesh_info(const lbm_ctx* ctx, int64_t* info, int32_t cap, int32_t* nlevels);
+
+/* Obstacle links: fluid elements whose neighbour x - c_i is a solid cell.
+ * Per link the caller-order element index and the direction i (lbm.h order),
+ * level by level, elements ascending.  Writes min(cap, count) entries (elem and
+ * dir may be NULL when cap is 0) and the count to *n. */
+lbm_status lbm_obstacle_links(const lbm_ctx* ctx, int64_t* elem, int8_t* dir, int64_t cap, int64_t* n);
+
+/* Wall distance per obstacle link, n = the count of lbm_obstacle_links and q in
+ * that order: the wall lies at x - q c_i, q in (0, 1].  Sec. 2.3 interpolated
+ * bounce-back; requires params.bouzidi (LBM_ERR_STATE otherwise), q outside
+ * (0, 1] or a wrong n give LBM_ERR_ARG.  Host array; may be called before or
+ * after lbm_bind. */
+lbm_status lbm_set_link_q(lbm_ctx* ctx, const double* q, int64_t n);
 
 /* Bytes of the single device workspace the caller must allocate (256-byte
  * aligned start) before lbm_bind. */

@@ -331,9 +331,20 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
     a.vol = std::ldexp(1.0, -c->d * li);
     a.obs_elem = c->at<int32_t>(c->oObsElem) + H.obs_begin;
     a.obs_dir = c->at<int8_t>(c->oObsDir) + H.obs_begin;
+    a.obs_a = c->at<int32_t>(c->oObsA) + H.obs_begin;
+    a.obs_q = c->at<double>(c->oObsQ) + H.obs_begin;
     a.obs_n = H.obs_end - H.obs_begin;
     a.fscale = std::ldexp(1.0, (c->d - 1) * (c->nlev - 1 - li));
-    if (objective == 0 ? a.end > a.begin : a.obs_n > 0) aops->seed(c->Q, a, st);
+    if (objective == 0) {
+      if (a.end > a.begin) aops->seed(c->Q, a, st);
+    } else if (a.obs_n > 0) {
+      // the own slot, then (interpolated bounce-back only) the second node and
+      // the opposite slot, one pass each so that no two links share a slot
+      for (int which = 0; which < (c->p.bouzidi ? 3 : 1); ++which) {
+        a.which = which;
+        aops->seed(c->Q, a, st);
+      }
+    }
   }
   // ---- reverse sweep
   const int nseg = L.n_ck;
@@ -401,6 +412,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
             o.rho_off = c->rho_off;
             o.rho0 = c->p.rho0;
             o.zero_gradient = c->p.outlet == LBM_OUTLET_ZERO_GRADIENT;
+            o.q = c->at<double>(c->oOutQ);
             c->ops->outlet(c->Q, o, st);
           }
           AdjSCArgs a{};
@@ -417,10 +429,11 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
           }
           a.omega = H.omega;
           std::memcpy(a.inlet, c->inlet, sizeof(a.inlet));
+          a.inlet_s = c->at<double>(c->oInletS);
           aops->sc(c->Q, a, st);
           accum(li, -1);
           if (outlet) {
-            for (int which = 0; which < 3; ++which) {
+            for (int which = 0; which < (c->p.bouzidi ? 6 : 3); ++which) {
               AdjOutletArgs o{};
               o.c = common(snap(t.snap), nullptr, lam_for(p));
               o.elem = c->at<int32_t>(c->oOutElem);
@@ -434,6 +447,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
               o.which = which;
               o.omega = H.omega;
               o.zero_gradient = c->p.outlet == LBM_OUTLET_ZERO_GRADIENT;
+              o.q = c->at<double>(c->oOutQ);
               aops->outlet(c->Q, o, st);
               if (which == 0) accum(li, -1);  // d/d omega through the normal links' f^neq
             }

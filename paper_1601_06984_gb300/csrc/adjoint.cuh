@@ -256,15 +256,32 @@ __global__ void __launch_bounds__(256) k_adj_seed(const AdjSeedArgs a) {
       add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
     }
   } else {
+    // F_k = fscale c_ib,k (f*_ib(x) + f_i(x)), f_i the (interpolated) bounce-
+    // back value: pass 0 seeds f*_ib(x), pass 1 f*_ib(x + c_i), pass 2 f*_i(x)
     const int k = a.objective - 1;
     for (int64_t l = t0; l < a.obs_n; l += stride) {
-      const int ib = opp(a.obs_dir[l]);
+      const int i = a.obs_dir[l];
+      const int ib = opp(i);
       const int64_t e = a.obs_elem[l];
       int cb = 0;
 #pragma unroll
       for (int q = 0; q < Q; ++q)
         if (q == ib) cb = LT::c(q, k < D ? k : 0);
-      if (k < D) lam[(size_t)ib * N + e] += R(2.0 * a.fscale) * R(cb);
+      if (k >= D) continue;
+      const double q = a.obs_q ? a.obs_q[l] : 0.5;
+      const int32_t a2 = a.obs_a ? a.obs_a[l] : -1;
+      double w_own, w_a = 0.0, w_i = 0.0;
+      if (q < 0.5) {
+        w_own = a2 < 0 ? 2.0 : 1.0 + 2.0 * q;
+        if (a2 >= 0) w_a = 1.0 - 2.0 * q;
+      } else {
+        w_own = 1.0 + 1.0 / (2.0 * q);
+        w_i = (2.0 * q - 1.0) / (2.0 * q);
+      }
+      const double base = a.fscale * cb;
+      if (a.which == 0) lam[(size_t)ib * N + e] += R(base * w_own);
+      if (a.which == 1 && w_a != 0.0) lam[(size_t)ib * N + a2] += R(base * w_a);
+      if (a.which == 2 && w_i != 0.0) lam[(size_t)i * N + e] += R(base * w_i);
     }
   }
 }
@@ -310,7 +327,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
       const uint32_t n = nb[i];
       if (n >= NB_FLAG30) {
         if (n & NB_BOUNCE) {
-          if (n & NB_FLAG30) g[i] += R(a.inlet[i]);
+          if (n & NB_FLAG30) g[i] += R(a.inlet[i]) * (a.inlet_s ? R(a.inlet_s[n & NB_INDEX]) : R(1));
         } else {
           g[i] = static_cast<const R*>(a.side_fwd)[n & NB_INDEX];
         }
@@ -390,9 +407,10 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
       }
       lam_in[target(i)] = cur[i] + lg;
       if (i > 0 && (n & NB_BOUNCE) && (n & NB_FLAG30)) {
-        // d f_i / d u_in = 6 w_i rho0 c_i
+        // d f_i / d u_in = 6 w_i rho0 s c_i, s the link's inlet profile factor
+        const R sf = a.inlet_s ? R(a.inlet_s[n & NB_INDEX]) : R(1);
 #pragma unroll
-        for (int b = 0; b < D; ++b) part[2 + b] += lg * R(6.0 * LT::w(i) * a.c.rho0 * LT::c(i, b));
+        for (int b = 0; b < D; ++b) part[2 + b] += lg * sf * R(6.0 * LT::w(i) * a.c.rho0 * LT::c(i, b));
       }
     }
   }
@@ -417,6 +435,22 @@ __global__ void __launch_bounds__(256) k_adj_outlet(const AdjOutletArgs a) {
     if (a.kind[k] == OUT_EXTRAP) {
       if (a.which == 1) lam_in[(size_t)i * N + a.a[k]] += a.zero_gradient ? ls : R(2) * ls;
       if (a.which == 2 && !a.zero_gradient) lam_in[(size_t)i * N + a.b[k]] -= ls;
+      continue;
+    }
+    if (a.kind[k] == OUT_BOUZIDI) {
+      // interpolated bounce-back value, linear in f*_i(x) (pass 3), f*_ib(x)
+      // (pass 4) and f*_ib(x + c_i) (pass 5); one slot per link and pass
+      const int ib = opp(i);
+      const int64_t e = a.elem[k];
+      const double q = a.q ? a.q[k] : 0.5;
+      const int32_t a2 = a.a[k];
+      if (q < 0.5) {
+        if (a.which == 4) lam_in[(size_t)ib * N + e] += a2 < 0 ? ls : R(2.0 * q) * ls;
+        if (a.which == 5 && a2 >= 0) lam_in[(size_t)ib * N + a2] += R(1.0 - 2.0 * q) * ls;
+      } else {
+        if (a.which == 4) lam_in[(size_t)ib * N + e] += R(1.0 / (2.0 * q)) * ls;
+        if (a.which == 3) lam_in[(size_t)i * N + e] += R((2.0 * q - 1.0) / (2.0 * q)) * ls;
+      }
       continue;
     }
     if (a.which != 0) continue;

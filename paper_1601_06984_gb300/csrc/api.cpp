@@ -40,6 +40,10 @@ void lbm_ctx::layout() {
   oNbr = take((size_t)(Q - 1) * N * 4);
   oBrickNb = take(m.brick_nb.size() * 4);
   oBrickTab = take(m.brick_tab.size() * 2);
+  oInletS = take(m.inlet_s.size() * 8);
+  oOutQ = take(m.out_q.size() * 8);
+  oObsA = take(m.obs_a.size() * 4);
+  oObsQ = take(m.obs_q.size() * 8);
   oF = p.use_force ? take((size_t)d * N * cb) : 0;
   ld.assign(nlev, LevelDev());
   const size_t M_ = mom_stride(Q);
@@ -149,6 +153,7 @@ void lbm_ctx::stream_collide(int li) {
     o.rho_off = rho_off;
     o.rho0 = p.rho0;
     o.zero_gradient = p.outlet == LBM_OUTLET_ZERO_GRADIENT;
+    o.q = at<double>(oOutQ);
     ops->outlet(Q, o, st);
     ++launches;
   }
@@ -173,6 +178,7 @@ void lbm_ctx::stream_collide(int li) {
   a.nbr = at<uint32_t>(oNbr);
   a.force = force_ptr();
   a.side = at(oSide);
+  a.inlet_s = at<double>(oInletS);
   a.Ntot = M.Ntot;
   if (p.time_mode == LBM_TIME_TWO_LAYER) {
     a.begin = H.base + H.oC;
@@ -298,6 +304,8 @@ lbm_status reduce_plan(lbm_ctx* c, ReducePlan* plan) {
     a.nblocks = kReduceBlocks;
     a.obs_elem = c->at<int32_t>(c->oObsElem) + H.obs_begin;
     a.obs_dir = c->at<int8_t>(c->oObsDir) + H.obs_begin;
+    a.obs_a = c->at<int32_t>(c->oObsA) + H.obs_begin;
+    a.obs_q = c->at<double>(c->oObsQ) + H.obs_begin;
     a.obs_n = H.obs_end - H.obs_begin;
     a.fscale = std::ldexp(1.0, (d - 1) * (c->nlev - 1 - li));
     plan->levels.push_back(a);
@@ -375,6 +383,43 @@ lbm_status lbm_mesh_info(const lbm_ctx* c, int64_t* info, int32_t cap, int32_t* 
   return LBM_OK;
 }
 
+lbm_status lbm_obstacle_links(const lbm_ctx* c, int64_t* elem, int8_t* dir, int64_t cap, int64_t* n) {
+  if (!c || !n || cap < 0 || (cap > 0 && (!elem || !dir))) return LBM_ERR_ARG;
+  const HostMesh& m = c->M;
+  const int64_t cnt = (int64_t)m.obs_elem.size();
+  *n = cnt;
+  if (cap == 0 || cnt == 0) return LBM_OK;
+  // global element slot -> caller index
+  std::vector<int64_t> user_of(m.Ntot, -1);
+  for (int64_t k = 0; k < m.n_user; ++k) user_of[m.uslot[k]] = k;
+  for (int64_t l = 0; l < std::min(cap, cnt); ++l) {
+    elem[l] = user_of[m.obs_elem[l]];
+    dir[l] = m.obs_dir[l];
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_link_q(lbm_ctx* c, const double* q, int64_t n) {
+  if (!c || (n > 0 && !q)) return LBM_ERR_ARG;
+  if (!c->p.bouzidi) return c->fail(LBM_ERR_STATE, "params.bouzidi is 0");
+  HostMesh& m = c->M;
+  if (n != (int64_t)m.obs_elem.size()) return c->fail(LBM_ERR_ARG, "n differs from the obstacle link count");
+  for (int64_t l = 0; l < n; ++l)
+    if (!(q[l] > 0.0 && q[l] <= 1.0)) return c->fail(LBM_ERR_ARG, "wall distance outside (0, 1]");
+  for (int64_t l = 0; l < n; ++l) {
+    m.obs_q[l] = q[l];
+    if (m.obs_side[l] >= 0) m.out_q[m.obs_side[l]] = q[l];
+  }
+  if (!c->bound) return LBM_OK;  // uploaded by lbm_bind
+  lbm_status s = c->cuda_check(
+      cudaMemcpyAsync(c->ws + c->oObsQ, m.obs_q.data(), m.obs_q.size() * 8, cudaMemcpyHostToDevice, c->st), "link q");
+  if (s == LBM_OK)
+    s = c->cuda_check(
+        cudaMemcpyAsync(c->ws + c->oOutQ, m.out_q.data(), m.out_q.size() * 8, cudaMemcpyHostToDevice, c->st), "link q");
+  if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "link q");
+  return s;
+}
+
 lbm_status lbm_device_bytes(const lbm_ctx* c, uint64_t* bytes) {
   if (!c || !bytes || !c->ops || c->M.lv.empty()) return LBM_ERR_ARG;
   *bytes = c->bytes;
@@ -397,6 +442,10 @@ lbm_status lbm_bind(lbm_ctx* c, void* ws, uint64_t bytes, void* stream) {
   lbm_status s = up(c->oNbr, m.nbr.data(), m.nbr.size() * 4);
   if (s == LBM_OK) s = up(c->oBrickNb, m.brick_nb.data(), m.brick_nb.size() * 4);
   if (s == LBM_OK) s = up(c->oBrickTab, m.brick_tab.data(), m.brick_tab.size() * 2);
+  if (s == LBM_OK) s = up(c->oInletS, m.inlet_s.data(), m.inlet_s.size() * 8);
+  if (s == LBM_OK) s = up(c->oOutQ, m.out_q.data(), m.out_q.size() * 8);
+  if (s == LBM_OK) s = up(c->oObsA, m.obs_a.data(), m.obs_a.size() * 4);
+  if (s == LBM_OK) s = up(c->oObsQ, m.obs_q.data(), m.obs_q.size() * 8);
   for (int li = 0; li < c->nlev && s == LBM_OK; ++li) {
     const HostLevel& H = m.lv[li];
     s = up(c->ld[li].gff_child0, H.gff_child0.data(), H.gff_child0.size() * 4);
@@ -600,24 +649,14 @@ lbm_status lbm_set_state(lbm_ctx* c, const double* f) {
 lbm_status lbm_reduce(lbm_ctx* c, double out[8]) {
   if (!c || !out) return LBM_ERR_ARG;
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_reduce before lbm_bind");
-  const int d = c->d;
+  // the per-level arguments come from the one plan builder (also used by
+  // lbm_reduce_noalloc); only the partial rows differ
+  ReducePlan plan;
+  lbm_status ps = reduce_plan(c, &plan);
+  if (ps != LBM_OK) return ps;
   for (int li = 0; li < c->nlev; ++li) {
-    const HostLevel& H = c->M.lv[li];
-    ReduceArgs a{};
-    a.pdf = c->cur(li);
-    a.force = c->force_ptr();
-    a.Ntot = c->M.Ntot;
-    a.begin = H.base + H.oF;
-    a.end = H.base + H.oF + H.nF;
-    a.omega = H.omega;
-    a.rho_off = c->rho_off;
-    a.vol = std::ldexp(1.0, -d * li);
+    ReduceArgs a = plan.levels[li];
     a.partial = c->at<double>(c->oPartial) + (size_t)li * kReduceBlocks * 8;
-    a.nblocks = kReduceBlocks;
-    a.obs_elem = c->at<int32_t>(c->oObsElem) + H.obs_begin;
-    a.obs_dir = c->at<int8_t>(c->oObsDir) + H.obs_begin;
-    a.obs_n = H.obs_end - H.obs_begin;
-    a.fscale = std::ldexp(1.0, (d - 1) * (c->nlev - 1 - li));
     c->ops->reduce(c->Q, a, c->st);
     ++c->launches;
   }

@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
       const uint32_t n = nb[k][i - 1];
       if (n >= NB_FLAG30) {
         if (n & NB_BOUNCE) {
-          if (n & NB_FLAG30) g[k][i] += R(a.inlet[i]);
+          if (n & NB_FLAG30) g[k][i] += R(a.inlet[i]) * (a.inlet_s ? R(a.inlet_s[n & NB_INDEX]) : R(1));
         } else {
           g[k][i] = static_cast<const R*>(a.side)[n & NB_INDEX];
         }
@@ -446,6 +446,23 @@ __global__ void k_outlet(const OutletArgs a) {
   if (a.kind[k] == OUT_EXTRAP) {
     const R fa = Sto<S>::ld(src + (size_t)i * N + a.a[k]);
     side[k] = a.zero_gradient ? fa : R(2) * fa - Sto<S>::ld(src + (size_t)i * N + a.b[k]);
+    return;
+  }
+  if (a.kind[k] == OUT_BOUZIDI) {
+    // interpolated bounce-back with the wall at x - q c_i (Sec. 2.3, Bouzidi):
+    //   q <  1/2: 2q f*_ib(x) + (1 - 2q) f*_ib(x + c_i)
+    //   q >= 1/2: f*_ib(x) / (2q) + (2q - 1) / (2q) f*_i(x)
+    // (deviation storage: the weights of each branch sum to one and w_i = w_ib)
+    const int ib = opp(i);
+    const int64_t e = a.elem[k];
+    const double q = a.q ? a.q[k] : 0.5;
+    const R fo = Sto<S>::ld(src + (size_t)ib * N + e);
+    if (q < 0.5) {
+      const int32_t a2 = a.a[k];
+      side[k] = a2 < 0 ? fo : R(2.0 * q) * fo + R(1.0 - 2.0 * q) * Sto<S>::ld(src + (size_t)ib * N + a2);
+    } else {
+      side[k] = R(1.0 / (2.0 * q)) * fo + R((2.0 * q - 1.0) / (2.0 * q)) * Sto<S>::ld(src + (size_t)i * N + e);
+    }
     return;
   }
   const int64_t e = a.elem[k];
@@ -949,13 +966,25 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
     }
     acc[7] += 0.5 * a.vol * uu / rho;
   }
+  // momentum exchange (Sec. 2.3): the link carries c_ib (f*_ib(x) + f_i(x)) to
+  // the body, f_i the bounce-back value of the next step (interpolated with
+  // the wall distance q; q = 1/2 gives 2 c_ib f*_ib)
   for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < a.obs_n; l += stride) {
     const int i = a.obs_dir[l];
     const int ib = opp(i);
     const int64_t e = a.obs_elem[l];
-    const double fib = (double)Sto<S>::ld(p + (size_t)ib * N + e) + LT::w(ib) * a.rho_off;
+    const double q = a.obs_q ? a.obs_q[l] : 0.5;
+    const double go = (double)Sto<S>::ld(p + (size_t)ib * N + e);
+    double gb;
+    if (q < 0.5) {
+      const int32_t a2 = a.obs_a ? a.obs_a[l] : -1;
+      gb = a2 < 0 ? go : 2.0 * q * go + (1.0 - 2.0 * q) * (double)Sto<S>::ld(p + (size_t)ib * N + a2);
+    } else {
+      gb = go / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * (double)Sto<S>::ld(p + (size_t)i * N + e);
+    }
+    const double sum = go + gb + 2.0 * LT::w(ib) * a.rho_off;
 #pragma unroll
-    for (int b = 0; b < D; ++b) acc[4 + b] += 2.0 * a.fscale * LT::c(ib, b) * fib;
+    for (int b = 0; b < D; ++b) acc[4 + b] += a.fscale * LT::c(ib, b) * sum;
   }
   block_sum_store<8>(acc, a.partial + (size_t)blockIdx.x * 8);
 }

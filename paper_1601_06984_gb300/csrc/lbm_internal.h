@@ -47,7 +47,7 @@ inline void host_lattice(int Q, int c[kQmax][3], double w[kQmax]) {
     else w[i] = n2 == 0 ? 8.0 / 27.0 : (n2 == 1 ? 2.0 / 27.0 : (n2 == 2 ? 1.0 / 54.0 : 1.0 / 216.0));
   }
 }
-enum { OUT_NORMAL = 0, OUT_EXTRAP = 1 };
+enum { OUT_NORMAL = 0, OUT_EXTRAP = 1, OUT_BOUZIDI = 2 };
 
 struct HostLevel {
   int L = 0;
@@ -84,12 +84,20 @@ struct HostMesh {
   std::vector<int32_t> uslot;   // [n_user] global element index
   std::vector<uint8_t> ulev;    // [n_user] level index (L - Lmin)
   std::vector<uint8_t> kind;    // [Ntot] element kind (K_*)
-  // outlet links (all levels, grouped by level)
+  // boundary-value links (all levels, grouped by level): outlet links and, with
+  // interpolated bounce-back, obstacle links; a, b: extrapolation sources or the
+  // second node x + c_i of an obstacle link (-1: none); q: wall distance
   std::vector<int32_t> out_elem, out_a, out_b;
   std::vector<int8_t> out_dir, out_kind;
-  // obstacle links (all levels, grouped by level): element, direction i with x - c_i solid
-  std::vector<int32_t> obs_elem;
+  std::vector<double> out_q;
+  // obstacle links (all levels, grouped by level): element, direction i with
+  // x - c_i solid, second node x + c_i (-1: none), wall distance q, and the
+  // link's boundary-value index (-1 with half-way bounce-back)
+  std::vector<int32_t> obs_elem, obs_a, obs_side;
   std::vector<int8_t> obs_dir;
+  std::vector<double> obs_q;
+  // inlet links: velocity profile factor per link (nbr low bits index it)
+  std::vector<double> inlet_s;
   // interior bricks (64 elements each, z-curve order inside): per brick the
   // first element of the brick at offset slot t = (sx+1) + 3 (sy+1) + 9 (sz+1),
   // relative to the brick's own first element (slot 13, the brick itself, is
@@ -116,6 +124,7 @@ struct StreamCollideArgs {
   const uint32_t* nbr;
   const void* force;  // [d][Ntot] compute type, or null
   const void* side;   // boundary values, compute type, or null
+  const double* inlet_s;  // inlet profile factor per inlet link
   int64_t Ntot, begin, end;  // linear range; element = lin + (lin >= hole_at ? hole_len : 0)
   int64_t hole_at, hole_len;  // interior bricks skipped by this kernel (0 length: none)
   double omega, rho_off;
@@ -144,6 +153,7 @@ struct OutletArgs {
   int64_t Ntot, begin, end;
   double omega, rho_off, rho0;
   int zero_gradient;  // extrapolate with f(x - n) instead of 2 f(x - n) - f(x - 2n)
+  const double* q;    // wall distance of interpolated bounce-back links
 };
 
 // GFC source moments: one record of mom_stride(Q) values per source (compute
@@ -249,6 +259,8 @@ struct ReduceArgs {
   // obstacle links of the level
   const int32_t* obs_elem;
   const int8_t* obs_dir;
+  const int32_t* obs_a;   // second node of the interpolated bounce-back (-1: none)
+  const double* obs_q;    // wall distance (1/2: half-way bounce-back)
   int64_t obs_n;
   double fscale;
 };
@@ -302,6 +314,7 @@ struct AdjSCArgs {
   int64_t begin, end;
   double omega;
   double inlet[kQmax];   // 6 w_i rho0 (c_i . u_in) of the forward
+  const double* inlet_s;  // inlet profile factor per inlet link
 };
 
 struct AdjOutletArgs {
@@ -310,9 +323,12 @@ struct AdjOutletArgs {
   const int8_t *dir, *kind;
   const void* lam_side;
   int64_t begin, end;
-  int which;  // 0: normal links, 1: extrapolation term of source a, 2: of source b
+  // outlet links: 0 normal links, 1 extrapolation term of source a, 2 of source b;
+  // interpolated bounce-back links: 3 term f*_i(x), 4 term f*_ib(x), 5 term f*_ib(x + c_i)
+  int which;
   double omega;
   int zero_gradient;
+  const double* q;
 };
 
 struct AdjMomArgs {  // reverse of the source moments
@@ -357,8 +373,11 @@ struct AdjSeedArgs {
   double vol;
   const int32_t* obs_elem;
   const int8_t* obs_dir;
+  const int32_t* obs_a;
+  const double* obs_q;
   int64_t obs_n;
   double fscale;
+  int which;  // force objective: 0 the link's own slot, 1 its second node, 2 the opposite slot
 };
 
 struct AccumArgs {

@@ -157,6 +157,9 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
   if (p.stencil != 9 && p.stencil != 19 && p.stencil != 27) return bad(LBM_ERR_ARG, "stencil must be 9, 19 or 27");
   if (p.time_mode != LBM_TIME_LINEAR && p.time_mode != LBM_TIME_TWO_LAYER)
     return bad(LBM_ERR_ARG, "bad time mode");
+  if (p.inlet_profile != LBM_INLET_UNIFORM && p.inlet_profile != LBM_INLET_PARABOLIC)
+    return bad(LBM_ERR_ARG, "bad inlet profile");
+  if (p.bouzidi != 0 && p.bouzidi != 1) return bad(LBM_ERR_ARG, "bouzidi must be 0 or 1");
   if (!(p.omega_coarse > 0.0 && p.omega_coarse < 2.0)) return bad(LBM_ERR_ARG, "omega must lie in (0,2)");
   if (!(p.rho0 > 0.0)) return bad(LBM_ERR_ARG, "rho0 must be positive");
   B.Q = p.stencil;
@@ -668,9 +671,14 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
   // ---- pull neighbour lists (Sec. 2.1) with boundary rules (Sec. 2.3)
   M.nbr.assign((size_t)(Q - 1) * M.Ntot, 0);
   struct OutLink { int64_t e; int i, kind; int32_t a, b; };
-  struct ObsLink { int64_t e; int i; };
+  struct ObsLink { int64_t e; int i; int32_t a; };
+  struct InLink { int64_t e; int i; double s; };
   std::vector<std::vector<OutLink>> outl(nlev);
   std::vector<std::vector<ObsLink>> obsl(nlev);
+  std::vector<std::vector<InLink>> inl_(nlev);
+  int inlet_axis = -1;
+  for (int f = 0; f < 2 * d; ++f)
+    if (B.bc[f] == LBM_BC_VELOCITY_IN) inlet_axis = f / 2;
   for (int li = 0; li < nlev; ++li) {
     const HostLevel& H = M.lv[li];
     const std::vector<uint8_t>& kd = B.kind[li];
@@ -689,6 +697,7 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     for (int64_t k = 0; k < H.nG1; ++k) layer[H.oG1 + k] = 1;
     std::vector<std::vector<OutLink>> po;
     std::vector<std::vector<ObsLink>> pb;
+    std::vector<std::vector<InLink>> pi;
     int failed = 0;
     std::string ferr;
 #pragma omp parallel
@@ -702,9 +711,11 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       {
         po.resize(nt);
         pb.resize(nt);
+        pi.resize(nt);
       }
       std::vector<OutLink> myo;
       std::vector<ObsLink> myb;
+      std::vector<InLink> myi;
       std::string myerr;
 #pragma omp for schedule(static)
       for (int64_t e = 0; e < H.N; ++e) {
@@ -741,7 +752,16 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
                 if (wall) {
                   code = NB_BOUNCE;
                 } else if (inl) {
-                  code = NB_BOUNCE | NB_FLAG30;
+                  // inlet profile factor at the boundary point x - c_i / 2
+                  double sf = 1.0;
+                  if (p.inlet_profile == LBM_INLET_PARABOLIC)
+                    for (int a = 0; a < d; ++a) {
+                      if (a == inlet_axis) continue;
+                      const double t = ((double)pos[3 * e + a] + 0.5 - 0.5 * B.dr.c[i][a]) / (double)B.ext(li, a);
+                      sf *= 6.0 * t * (1.0 - t);
+                    }
+                  myi.push_back({ge, i, sf});
+                  code = NB_BOUNCE | NB_FLAG30;  // index filled in after merging
                 } else if (nout != 1) {
                   myerr = "outlet corner without wall";
                 } else {
@@ -779,8 +799,19 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
                 if (v == G_SUB || B.covered_by_coarser(li, q))
                   myerr = "neighbour on another level has no ghost element";
                 else {
-                  code = NB_BOUNCE;
-                  myb.push_back({ge, i});
+                  // second node of the interpolated bounce-back: the element
+                  // behind x, away from the wall (any element of this level)
+                  int64_t pa[3] = {pos[3 * e] + B.dr.c[i][0], pos[3 * e + 1] + B.dr.c[i][1],
+                                   pos[3 * e + 2] + B.dr.c[i][2]};
+                  const int32_t va = B.wrap(li, pa) ? G_NONE : B.value(li, pa);
+                  const int32_t a2 = va >= 0 ? (int32_t)(H.base + va) : -1;
+                  myb.push_back({ge, i, a2});
+                  if (p.bouzidi) {
+                    myo.push_back({ge, i, OUT_BOUZIDI, a2, -1});
+                    code = NB_FLAG30;  // index filled in after merging
+                  } else {
+                    code = NB_BOUNCE;
+                  }
                 }
               } else if (strict_ghost) {
                 myerr = "ghost element next to a solid or missing neighbour";
@@ -794,6 +825,7 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       {
         po[tid_].swap(myo);
         pb[tid_].swap(myb);
+        pi[tid_].swap(myi);
         if (!myerr.empty()) {
           failed = 1;
           if (ferr.empty()) ferr = myerr;
@@ -803,6 +835,9 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     if (failed) return bad(LBM_ERR_MESH, ferr);
     for (auto& v : po) outl[li].insert(outl[li].end(), v.begin(), v.end());
     for (auto& v : pb) obsl[li].insert(obsl[li].end(), v.begin(), v.end());
+    for (auto& v : pi) inl_[li].insert(inl_[li].end(), v.begin(), v.end());
+    std::sort(inl_[li].begin(), inl_[li].end(),
+              [](const InLink& a, const InLink& b) { return a.e != b.e ? a.e < b.e : a.i < b.i; });
     std::sort(outl[li].begin(), outl[li].end(),
               [](const OutLink& a, const OutLink& b) { return a.e != b.e ? a.e < b.e : a.i < b.i; });
     std::sort(obsl[li].begin(), obsl[li].end(),
@@ -811,6 +846,7 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
   for (int li = 0; li < nlev; ++li) {
     HostLevel& H = M.lv[li];
     H.out_begin = (int64_t)M.out_elem.size();
+    std::unordered_map<int64_t, int64_t> side_of;  // (element, direction) -> boundary-value index
     for (const OutLink& o : outl[li]) {
       const int64_t idx = (int64_t)M.out_elem.size();
       M.nbr[(size_t)(o.i - 1) * M.Ntot + o.e] = NB_FLAG30 | (uint32_t)idx;
@@ -819,16 +855,49 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       M.out_kind.push_back((int8_t)o.kind);
       M.out_a.push_back(o.a);
       M.out_b.push_back(o.b);
+      M.out_q.push_back(0.5);
+      if (o.kind == OUT_BOUZIDI) side_of[o.e * 32 + o.i] = idx;
     }
     H.out_end = (int64_t)M.out_elem.size();
     H.obs_begin = (int64_t)M.obs_elem.size();
     for (const ObsLink& o : obsl[li]) {
       M.obs_elem.push_back((int32_t)o.e);
       M.obs_dir.push_back((int8_t)o.i);
+      M.obs_a.push_back(o.a);
+      M.obs_q.push_back(0.5);
+      auto it = side_of.find(o.e * 32 + o.i);
+      M.obs_side.push_back(it == side_of.end() ? -1 : (int32_t)it->second);
     }
     H.obs_end = (int64_t)M.obs_elem.size();
+    for (const InLink& o : inl_[li]) {
+      const int64_t idx = (int64_t)M.inlet_s.size();
+      M.nbr[(size_t)(o.i - 1) * M.Ntot + o.e] = NB_BOUNCE | NB_FLAG30 | (uint32_t)idx;
+      M.inlet_s.push_back(o.s);
+    }
   }
+  if ((int64_t)M.inlet_s.size() >= (int64_t)NB_INDEX) return bad(LBM_ERR_MESH, "too many inlet links");
   if ((int64_t)M.out_elem.size() >= (int64_t)NB_INDEX) return bad(LBM_ERR_MESH, "too many outlet links");
+  // every code the kernels decode stays inside its table, and every element
+  // index of the boundary tables is -1 or an element
+  {
+    const uint64_t nout = M.out_elem.size(), nin = M.inlet_s.size();
+    int badc = 0;
+#pragma omp parallel for schedule(static) reduction(| : badc)
+    for (int64_t k = 0; k < (int64_t)M.nbr.size(); ++k) {
+      const uint32_t c = M.nbr[k];
+      if (c < NB_FLAG30) badc |= (int64_t)c >= M.Ntot;
+      else if ((c & NB_BOUNCE) && (c & NB_FLAG30)) badc |= (uint64_t)(c & NB_INDEX) >= nin;
+      else if (!(c & NB_BOUNCE)) badc |= (uint64_t)(c & NB_INDEX) >= nout;
+    }
+    auto in_range = [&](const std::vector<int32_t>& v) {
+      for (int32_t x : v)
+        if (x < -1 || (int64_t)x >= M.Ntot) return false;
+      return true;
+    };
+    if (badc || !in_range(M.out_elem) || !in_range(M.out_a) || !in_range(M.out_b) || !in_range(M.obs_elem) ||
+        !in_range(M.obs_a))
+      return bad(LBM_ERR_INTERNAL, "boundary table index out of range");
+  }
   // interior bricks must reproduce the neighbour list exactly
   for (int li = 0; li < nlev; ++li) {
     const HostLevel& H = M.lv[li];

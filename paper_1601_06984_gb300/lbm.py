@@ -21,11 +21,12 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_MESH", -3: "LBM_ERR_CUDA"
 FP64, FP32DEV, BF16DEV = 0, 1, 2
 TIME_LINEAR, TIME_TWO_LAYER = 0, 1
 OUTLET_LINEAR, OUTLET_ZERO_GRADIENT = 0, 1
+INLET_UNIFORM, INLET_PARABOLIC = 0, 1
 EXPORTS = ["lbm_build_mesh", "lbm_mesh_info", "lbm_device_bytes", "lbm_bind", "lbm_init", "lbm_set_force",
            "lbm_step", "lbm_fill_ghosts", "lbm_moments", "lbm_reduce", "lbm_get_state", "lbm_set_state", "lbm_ghost_count",
            "lbm_get_ghosts", "lbm_sfc_partition", "lbm_kernel_launches", "lbm_timing_enable", "lbm_timing_read",
            "lbm_reduce_noalloc", "lbm_set_params", "lbm_adjoint_bytes", "lbm_adjoint", "lbm_last_error",
-           "lbm_destroy"]
+           "lbm_destroy", "lbm_obstacle_links", "lbm_set_link_q"]
 
 
 class LBMError(RuntimeError):
@@ -38,7 +39,7 @@ class lbm_params(C.Structure):
     _fields_ = [("stencil", C.c_int32), ("precision", C.c_int32), ("time_mode", C.c_int32),
                 ("extent", C.c_int32 * 3), ("bc", C.c_int32 * 6), ("omega_coarse", C.c_double),
                 ("rho0", C.c_double), ("u_in", C.c_double * 3), ("use_force", C.c_int32),
-                ("outlet", C.c_int32)]
+                ("outlet", C.c_int32), ("inlet_profile", C.c_int32), ("bouzidi", C.c_int32)]
 
 
 _lib = None
@@ -76,6 +77,8 @@ def lib():
             "lbm_set_params": [P, C.c_double, P],
             "lbm_adjoint_bytes": [P, I64, I32, C.POINTER(U64)],
             "lbm_adjoint": [P, I64, I32, I32, P, U64, P, P, P, P, P],
+            "lbm_obstacle_links": [P, P, P, I64, C.POINTER(I64)],
+            "lbm_set_link_q": [P, P, I64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -148,7 +151,8 @@ class Sim:
     the host only (no GPU needed); otherwise a torch CUDA device."""
 
     def __init__(self, mesh, stencil, omega_c, precision=FP64, time_mode=TIME_LINEAR, rho0=1.0,
-                 u_in=(0.0, 0.0, 0.0), use_force=False, device="cuda", stream=None, outlet=OUTLET_LINEAR):
+                 u_in=(0.0, 0.0, 0.0), use_force=False, device="cuda", stream=None, outlet=OUTLET_LINEAR,
+                 inlet_profile=INLET_UNIFORM, bouzidi=False):
         self.d = 2 if stencil == 9 else 3
         self.Q = stencil
         self.ns = 3 if self.d == 2 else 6
@@ -164,6 +168,8 @@ class Sim:
             p.bc[f] = int(bc[f])
         p.omega_coarse, p.rho0, p.use_force = float(omega_c), float(rho0), int(bool(use_force))
         p.outlet = int(outlet)
+        p.inlet_profile = int(inlet_profile)
+        p.bouzidi = int(bool(bouzidi))
         self.params = p
         self.ctx = lbm_build_mesh(mesh.tree_ids, mesh.levels, p)
         self.ws = None
@@ -195,6 +201,21 @@ class Sim:
         nl = C.c_int32()
         _check(self.ctx, lib().lbm_mesh_info(self.ctx, _p(info), 32, C.byref(nl)))
         return info[: nl.value]
+
+    def obstacle_links(self):
+        """(caller element index [m], direction [m]) of the links x -> x - c_i
+        into solid cells, in the order lbm_set_link_q expects."""
+        n = C.c_int64()
+        _check(self.ctx, lib().lbm_obstacle_links(self.ctx, None, None, 0, C.byref(n)))
+        elem = np.zeros(n.value, np.int64)
+        dr = np.zeros(n.value, np.int8)
+        _check(self.ctx, lib().lbm_obstacle_links(self.ctx, _p(elem), _p(dr), n.value, C.byref(n)))
+        return elem, dr
+
+    def set_link_q(self, q):
+        """Wall distance q in (0, 1] per obstacle link (wall at x - q c_i)."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        _check(self.ctx, lib().lbm_set_link_q(self.ctx, _p(q), len(q)))
 
     def device_bytes(self):
         nbytes = C.c_uint64()

@@ -204,6 +204,54 @@ def config_cylinder(D=40, walls=True):
     return nested_boxes(2, lmin, (nx, ny), boxes, bc, solid)
 
 
+def config_cylinder_schafer(D=40):
+    """The paper's cylinder geometry (Sec. 4.2, the Schaefer-Turek channel):
+    channel 2.2 x 0.41 with a cylinder of diameter 0.1 centred at (0.2, 0.2),
+    in units where D is the cylinder diameter in finest cells.  Two levels: the
+    bulk at dx = 2/D of a diameter, and one refined box [0.05, 0.35]^2 around
+    the cylinder (the paper's ring of thickness 0.1 around it).  Velocity inlet
+    at x-, pressure outlet at x+, walls on y.  D must be a multiple of 20."""
+    assert D % 20 == 0, "D must be a multiple of 20 (whole cells for H = 4.1 D on the coarse level)"
+    nx, ny = 22 * D // 2, 41 * D // 20          # coarse cells
+    lmin = int(math.ceil(math.log2(max(nx, ny))))
+    lo, hi = D // 2, 7 * D // 2                 # refined box [0.05, 0.35] in fine cells
+    cx = cy = 2 * D                             # centre (0.2, 0.2) in fine cells
+    r = 0.5 * D
+
+    def solid(L, cen):
+        return (cen[:, 0] - cx) ** 2 + (cen[:, 1] - cy) ** 2 < r * r
+
+    return nested_boxes(2, lmin, (nx, ny), [((lo, lo), (hi, hi))],
+                        (BC_VELOCITY_IN, BC_PRESSURE_OUT, BC_WALL, BC_WALL), solid)
+
+
+_C27 = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                 [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1], [1, 0, -1],
+                 [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1], [1, 1, 1], [-1, -1, -1],
+                 [1, 1, -1], [-1, -1, 1], [1, -1, 1], [-1, 1, -1], [-1, 1, 1], [1, -1, -1]])
+_C9 = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [1, 1, 0], [-1, -1, 0],
+                [1, -1, 0], [-1, 1, 0]])
+
+
+def wall_distance_ball(mesh: Mesh, elem, dirs, centre, radius, Q):
+    """Geometry input of the interpolated bounce-back: for each link (element,
+    direction i with x - c_i inside the ball), the fraction q in (0, 1] of the
+    link from the element centre x to the surface, so that the wall lies at
+    x - q c_i.  A circle in 2D, a sphere in 3D; centre and radius in finest
+    cells; directions in the library's order."""
+    c = (_C9 if Q == 9 else _C27)[np.asarray(dirs, dtype=np.int64)][:, :mesh.d].astype(float)
+    elem = np.asarray(elem, dtype=np.int64)
+    h = np.ldexp(1.0, int(mesh.levels.max()) - mesh.levels[elem].astype(np.int64))   # cell size, finest units
+    x = (mesh.coords[elem].astype(float) + 0.5) * h[:, None]
+    p = x - np.asarray(centre, float)[: mesh.d]
+    v = -c * h[:, None]                         # from x toward x - c_i
+    a = (v * v).sum(1)
+    b = (p * v).sum(1)
+    cc = (p * p).sum(1) - radius * radius
+    q = (-b - np.sqrt(np.maximum(b * b - a * cc, 0.0))) / a
+    return np.clip(q, 1e-6, 1.0)
+
+
 def config_sphere(scale=1):
     """D3Q19 sphere: box 32D x 16D x 16D, sphere diameter D = 64/scale finest
     cells at (8D,8D,8D), 5 levels from D/4 to D/64 with nested boxes

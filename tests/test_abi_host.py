@@ -194,3 +194,32 @@ def test_interior_brick_counts(lbm, name):
                "sphere_small_q27": (W.config_sphere_small(), 27)}[name]
     info = lbm.Sim(mesh, Q, 1.7, u_in=(0.04, 0, 0), device=None).mesh_info()
     assert [int(r[8]) for r in info] == _interior_bricks(mesh, Q)
+
+
+def test_obstacle_links_and_link_q(lbm):
+    """lbm_obstacle_links lists exactly the (element, direction) pairs whose
+    upstream cell x - c_i lies inside the cylinder (computed here from the
+    geometry), and lbm_set_link_q checks its arguments."""
+    D = 20
+    m = W.config_cylinder_schafer(D)
+    s = lbm.Sim(m, 9, 1.6, u_in=(0.05, 0, 0), device=None, bouzidi=True, inlet_profile=1)
+    e, d = s.obstacle_links()
+    c9 = np.array([[0, 0], [1, 0], [-1, 0], [0, 1], [0, -1], [1, 1], [-1, -1], [1, -1], [-1, 1]])
+    fine = m.levels == m.levels.max()
+    want = set()
+    for k in np.nonzero(fine)[0]:
+        for i in range(1, 9):
+            p = m.coords[k] - c9[i] + 0.5
+            if (p[0] - 2 * D) ** 2 + (p[1] - 2 * D) ** 2 < (D / 2) ** 2:
+                want.add((int(k), i))
+    assert set(zip(e.tolist(), d.tolist())) == want
+    q = W.wall_distance_ball(m, e, d, (2 * D, 2 * D), D / 2, 9)
+    assert np.all((q > 0) & (q <= 1))
+    s.set_link_q(q)
+    with pytest.raises(lbm.LBMError, match="obstacle link count"):
+        s.set_link_q(q[:-1])
+    with pytest.raises(lbm.LBMError, match="outside"):
+        s.set_link_q(np.zeros(len(q)))
+    hb = lbm.Sim(m, 9, 1.6, u_in=(0.05, 0, 0), device=None)
+    with pytest.raises(lbm.LBMError, match="bouzidi"):
+        hb.set_link_q(q)

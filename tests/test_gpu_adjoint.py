@@ -41,6 +41,11 @@ def make(name):
         m = W.config_sphere_small()
         return (m, 19, W.omega_coarse_from_finest(1.6, 3), (0.04, 0.0, 0.0),
                 lambda m: W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), 3, 2)
+    if name == "schafer20":
+        # the paper's cylinder: interpolated bounce-back, parabolic inflow
+        m = W.config_cylinder_schafer(20)
+        om = W.omega_coarse_from_finest(W.omega_for_re(0.05, 20, 20.0), 2)
+        return m, 9, om, (0.05, 0.0, 0.0), lambda m: W.uniform_fields(m, 1.0, (0.05, 0.0)), 3, 2
     if name == "tgv3d_q27":
         m = W.config_tgv3d(16)
         return m, 27, 1.6, (0.0, 0.0, 0.0), lambda m: W.tgv_fields(m, 0.02), 4, 3
@@ -59,10 +64,25 @@ def make(name):
 
 
 OUTLET = {"channel_zg": 1}
+BOUZIDI = {"schafer20": ((40.0, 40.0), 10.0)}  # circle centre and radius, finest cells
+
+
+def configure(name, m, Q, g, oracles=()):
+    """Interpolated bounce-back wall distances of the circle on the GPU context
+    and the oracles (same links, same q)."""
+    if name not in BOUZIDI:
+        return
+    e, d = g.obstacle_links()
+    q = W.wall_distance_ball(m, e, d, BOUZIDI[name][0], BOUZIDI[name][1], Q)
+    g.set_link_q(q)
+    for o in oracles:
+        o.set_link_q(e, d, q)
+    return e, d, q
 CASES = [("uni2d", 0, 0), ("tgv2d", 0, 0), ("tgv2d", 1, 0), ("half2d", 0, 0), ("tgv3d", 0, 0), ("tgv3d", 1, 0),
          ("sphere", 0, 0), ("sphere", 1, 0), ("sphere", 0, 1), ("sphere", 1, 3),
          ("channel", 0, 0), ("channel", 1, 0), ("channel_zg", 0, 0),
-         ("tgv3d_q27", 0, 0), ("tgv3d_q27", 1, 0), ("sphere_q27", 0, 1)]
+         ("tgv3d_q27", 0, 0), ("tgv3d_q27", 1, 0), ("sphere_q27", 0, 1),
+         ("schafer20", 0, 1), ("schafer20", 1, 0)]
 
 
 def J_of(red, objective):
@@ -76,7 +96,10 @@ def test_adjoint_matches_dual_oracle(lbm, oracle_mod, name, mode, objective):
     rho, u, S = fields(m)
     F = W.gaussian_force(m, 1e-5)
     out = OUTLET.get(name, 0)
-    g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True, outlet=out)
+    bz = name in BOUZIDI
+    g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True, outlet=out, bouzidi=bz,
+                inlet_profile=1 if bz else 0)
+    links = configure(name, m, Q, g)
     g.init(rho, u, S, W.pdf_perturbation(m, Q, 1e-5))
     g.set_force(F)
     f0 = g.get_state()
@@ -93,7 +116,9 @@ def test_adjoint_matches_dual_oracle(lbm, oracle_mod, name, mode, objective):
             continue
         adj = float((dF * a).sum() + dw * b + (dU * c).sum() + (0.0 if fd0 is None else (df0 * fd0).sum()))
         od = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin, use_force=True, dual=True, omega_dot=b,
-                               u_in_dot=tuple(c), outlet=out)
+                               u_in_dot=tuple(c), outlet=out, inlet_profile=1 if bz else 0)
+        if links is not None:
+            od.set_link_q(*links)
         od.set_f(f0, fd0)
         od.set_force(F, a)
         od.step(n)

@@ -61,6 +61,11 @@ def make_case(name):
         om = W.omega_coarse_from_finest(1.6, 3)
         return (m, 27, om, (0.04, 0, 0),
                 lambda m: (*W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), W.pdf_perturbation(m, 27, 1e-4)), None, 3)
+    if name == "schafer20":
+        m = W.config_cylinder_schafer(20)
+        om = W.omega_coarse_from_finest(W.omega_for_re(0.05, 20, 20.0), 2)
+        return (m, 9, om, (0.05, 0, 0),
+                lambda m: (*W.uniform_fields(m, 1.0, (0.05, 0.0)), W.pdf_perturbation(m, 9, 1e-4)), None, 4)
     if name == "channel_zg":
         m = W.nested_boxes(2, 5, (32, 16), [((16, 8), (40, 24))],
                            (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_WALL, W.BC_WALL))
@@ -75,16 +80,26 @@ def make_case(name):
 
 
 OUTLET = {"channel_zg": 1}  # zero-gradient outlet extrapolation
+# the paper's cylinder: interpolated bounce-back with the wall distances of the
+# circle, parabolic inflow
+BOUZIDI = {"schafer20": (20, (40.0, 40.0), 10.0)}
 
 
 def run_both(lbm, oracle_mod, name, mode, precision=0):
     m, Q, om, uin, fields, force, steps = make_case(name)
     rho, u, S, df = fields(m)
     out = OUTLET.get(name, 0)
-    o = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin, use_force=force is not None, outlet=out)
+    bz = BOUZIDI.get(name)
+    o = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin, use_force=force is not None, outlet=out,
+                          inlet_profile=1 if bz else 0)
     o.init(rho, u, S, df)
     g = lbm.Sim(m, Q, om, precision=precision, time_mode=mode, u_in=uin, use_force=force is not None,
-                outlet=out)
+                outlet=out, inlet_profile=1 if bz else 0, bouzidi=bz is not None)
+    if bz:
+        e, d = g.obstacle_links()
+        q = W.wall_distance_ball(m, e, d, bz[1], bz[2], Q)
+        g.set_link_q(q)
+        o.set_link_q(e, d, q)
     g.init(rho, u, S, df)
     if force is not None:
         o.set_force(force)
@@ -95,7 +110,7 @@ def run_both(lbm, oracle_mod, name, mode, precision=0):
 
 
 CASES = ["tgv2d", "tgv2d_half", "tgv3d", "tgv3d_force", "cylinder", "channel_zg", "sphere_small",
-         "tgv3d_q27", "tgv3d_force_q27", "sphere_small_q27"]
+         "tgv3d_q27", "tgv3d_force_q27", "sphere_small_q27", "schafer20"]
 
 
 @pytest.mark.parametrize("name", CASES)

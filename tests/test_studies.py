@@ -21,8 +21,11 @@ def test_strouhal_of_a_sinusoid(period):
 
 def test_strouhal_none_without_a_period():
     rng = np.random.default_rng(8)
+    t = np.arange(4000)
     assert _strouhal(np.zeros(1000), 8, 40.0, 0.05) is None
     assert _strouhal(1e-3 * rng.standard_normal(4000), 8, 40.0, 0.05) is None
+    # a steady lift with a decaying wiggle of 1e-4
+    assert _strouhal(0.011 + 1e-4 * np.exp(-t / 800) * np.sin(t / 3.0), 8, 40.0, 0.05) is None
 
 
 def test_outlet_choice():
