@@ -129,7 +129,8 @@ lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t
                           const lbm_params* params, lbm_ctx** out);
 
 /* Per level, 10 int64 each: level, fluid, GFC, GFF inner, GFF outer, padded
- * element count, outlet links, obstacle links, interior bricks, 0.  An
+ * element count, boundary-value links (outlet links, plus the obstacle links
+ * with params.bouzidi), obstacle links, interior bricks, 0.  An
  * interior brick is an aligned block of 64 fluid elements of the level (4^3
  * in 3D, 8^2 in 2D) whose stencil neighbours are all such blocks; the
  * stream-collide locates their pull sources from a per-brick table instead
