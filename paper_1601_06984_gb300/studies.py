@@ -129,14 +129,21 @@ def schafer(Re=20.0, precision="fp32dev", steps=20000, window=5000, D=40, U=0.05
             "samples_every_coarse_steps": chunk}
 
 
-def sphere(precision="fp32dev", steps=2000, window=200, U=0.04, Re=100.0, outlet="auto", device="cuda"):
+def sphere(precision="fp32dev", steps=2000, window=200, U=0.04, Re=100.0, outlet="auto", Q=19, bouzidi=False,
+           device="cuda"):
+    """The bench's sphere (D = 64 finest cells, 5 levels), D3Q19 or the paper's
+    D3Q27, half-way or interpolated bounce-back with the sphere's wall
+    distances.  c_D = 2 F_x / (rho U^2 pi D^2 / 4)."""
     mesh = W.config_sphere(1)
     D = 64.0
     om_f = W.omega_for_re(U, D, Re)
     om_c = W.omega_coarse_from_finest(om_f, 5)
     outlet, out_code = _outlet(outlet, om_c)
-    sim = lbm.Sim(mesh, 19, om_c, precision=PRECISION[precision], u_in=(U, 0.0, 0.0), device=device,
-                  outlet=out_code)
+    sim = lbm.Sim(mesh, Q, om_c, precision=PRECISION[precision], u_in=(U, 0.0, 0.0), device=device,
+                  outlet=out_code, bouzidi=bouzidi)
+    if bouzidi:
+        e, d = sim.obstacle_links()
+        sim.set_link_q(W.wall_distance_ball(mesh, e, d, (8 * D,) * 3, 0.5 * D, Q))
     sim.init(*W.uniform_fields(mesh, 1.0, (U, 0.0, 0.0)))
     A = math.pi * D * D / 4.0
     cd = []
@@ -146,7 +153,9 @@ def sphere(precision="fp32dev", steps=2000, window=200, U=0.04, Re=100.0, outlet
         if k >= steps - window:
             cd.append(2.0 * sim.reduce()[4] / (U * U * A))
     wall = time.perf_counter() - t0
-    return {"case": "sphere", "Re": Re, "precision": precision, "outlet": outlet, "coarse_steps": steps,
+    return {"case": "sphere", "Re": Re, "precision": precision, "stencil": f"D3Q{Q}",
+            "walls": "interpolated bounce-back" if bouzidi else "half-way bounce-back", "outlet": outlet,
+            "coarse_steps": steps,
             "omega_coarsest": om_c, "c_D_last": cd[-1],
             "c_D_mean": float(np.mean(cd)), "seconds": wall}
 
@@ -155,6 +164,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["cylinder", "sphere", "schafer"])
     ap.add_argument("--D", type=int, default=40)
+    ap.add_argument("--Q", type=int, default=19, choices=[19, 27])
+    ap.add_argument("--bouzidi", action="store_true")
     ap.add_argument("--re", type=float, default=None)
     ap.add_argument("--precision", default="fp32dev", choices=list(PRECISION))
     ap.add_argument("--steps", type=int, default=None)
@@ -179,7 +190,7 @@ def main():
             kw["window"] = a.window
         print(json.dumps(schafer(**kw)), flush=True)
     else:
-        kw = {"precision": a.precision, "outlet": a.outlet}
+        kw = {"precision": a.precision, "outlet": a.outlet, "Q": a.Q, "bouzidi": a.bouzidi}
         if a.steps:
             kw["steps"] = a.steps
         if a.window:
