@@ -69,6 +69,7 @@ void lbm_ctx::layout() {
   oObsDir = take(nobs);
   oUslot = take((size_t)m.n_user * 4);
   oUlev = take((size_t)m.n_user);
+  oSlotUser = take((size_t)N * 4);
   chunk = std::min<int64_t>(m.n_user, (int64_t)1 << 20);
   oStage = take((size_t)chunk * (1 + d + nS + Q + Q) * 8);
   oPartial = take((size_t)nlev * kReduceBlocks * 8 * 8);
@@ -462,6 +463,7 @@ lbm_status lbm_bind(lbm_ctx* c, void* ws, uint64_t bytes, void* stream) {
   if (s == LBM_OK) s = up(c->oObsDir, m.obs_dir.data(), m.obs_dir.size());
   if (s == LBM_OK) s = up(c->oUslot, m.uslot.data(), m.uslot.size() * 4);
   if (s == LBM_OK) s = up(c->oUlev, m.ulev.data(), m.ulev.size());
+  if (s == LBM_OK) s = up(c->oSlotUser, m.slot_user.data(), m.slot_user.size() * 4);
   if (s != LBM_OK) return s;
   if (c->p.use_force) {
     s = c->cuda_check(cudaMemsetAsync(c->ws + c->oF, 0, (size_t)c->d * m.Ntot * c->ops->compute_bytes, c->st),
@@ -490,6 +492,10 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u, const double
   double* su = sr + CH;
   double* sS = su + CH * d;
   double* sdf = sS + CH * nS;
+  // Every level starts in A.  The chunks are computed in caller order into B
+  // (coalesced writes, B holds nothing that survives an init), then placed
+  // into the element slots of A in slot order, and B is reset to rest.
+  std::fill(c->parity.begin(), c->parity.end(), 0);
   for (int64_t first = 0; first < n; first += CH) {
     const int64_t cnt = std::min(CH, n - first);
     lbm_status s = c->cuda_check(cudaMemcpyAsync(sr, rho + first, cnt * 8, cudaMemcpyHostToDevice, c->st), "init copy");
@@ -501,23 +507,26 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u, const double
       s = c->cuda_check(cudaMemcpyAsync(sdf, df + first * Q, cnt * Q * 8, cudaMemcpyHostToDevice, c->st), "init copy");
     if (s != LBM_OK) return s;
     InitArgs a{};
-    a.A = c->at(c->oA);
-    a.B = c->at(c->oB);
-    a.uslot = c->at<int32_t>(c->oUslot);
+    a.temp = c->at(c->oB);
     a.ulev = c->at<uint8_t>(c->oUlev);
-    a.parity = c->parity_mask();
     a.rho = sr;
     a.u = su;
     a.S = S ? sS : nullptr;
     a.df = df ? sdf : nullptr;
     a.first = first;
     a.cnt = cnt;
-    a.Ntot = c->M.Ntot;
+    a.n_user = n;
     for (int li = 0; li < c->nlev; ++li) a.omega[li] = c->M.lv[li].omega;
     a.rho_off = c->rho_off;
     c->ops->init(Q, a, c->st);
     ++c->launches;
   }
+  PlaceArgs pl{c->at(c->oB), c->at(c->oA), c->at<int32_t>(c->oSlotUser), n, c->M.Ntot};
+  c->ops->init_place(Q, pl, c->st);
+  ++c->launches;
+  FillArgs f{c->at(c->oB), c->M.Ntot, c->p.rho0, c->rho_off};
+  c->ops->fill_rest(Q, f, c->st);
+  ++c->launches;
   lbm_status s = c->launched("init");
   if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "init sync");
   return s;

@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(256) k_fill_gff(const GffArgs a) {
     if (q % NCH == b) dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rpm, rho, uP, usq) + scale * fneq[q]);
 }
 
-// ----------------------------------------------------------------- set-up / output (FP64 arithmetic)
+// ----------------------------------------------------------------- set-up (compute type) / output (FP64)
 template <int Q, class S>
 __global__ void k_fill_rest(const FillArgs a) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -802,45 +802,59 @@ __global__ void k_fill_rest(const FillArgs a) {
 // f^neq_i = -(3 w_i rho / omega) (c_i c_i - I/3) : S.
 template <int Q, class S>
 __global__ void k_init(const InitArgs a) {
+  using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D, NS = LT::NS;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.cnt) return;
   const int64_t k = a.first + t;
   const int li = a.ulev[k];
-  S* cur = static_cast<S*>(((a.parity >> li) & 1) ? a.B : a.A);
-  const int64_t e = a.uslot[k];
-  const double rho = a.rho[t];
-  double u[3] = {0, 0, 0}, usq = 0;
+  // equilibrium in the deviation form of the storage (g = f - w rho_off),
+  // computed in the storage's compute type like the collision's equilibrium
+  const R rho = R(a.rho[t]);
+  const R rp = R(a.rho[t] - a.rho_off);
+  R u[3] = {R(0), R(0), R(0)}, usq = R(0);
 #pragma unroll
   for (int b = 0; b < D; ++b) {
-    u[b] = a.u[t * D + b];
+    u[b] = R(a.u[t * D + b]);
     usq += u[b] * u[b];
   }
   const double* Sv = a.S ? a.S + t * NS : nullptr;
   const double* df = a.df ? a.df + t * Q : nullptr;
-  const double om = a.omega[li];
+  const R om = R(a.omega[li]);
+  S* out = static_cast<S*>(a.temp) + k;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    double cu = 0;
-#pragma unroll
-    for (int b = 0; b < D; ++b) cu += LT::c(q, b) * u[b];
-    double f = LT::w(q) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+    R g = geq<Q, R>(q, rp, rho, u, usq);
     if (Sv) {
-      double qs = 0, tr = 0;
+      R qs = R(0), tr = R(0);
 #pragma unroll
       for (int b = 0; b < D; ++b)
 #pragma unroll
         for (int c = b; c < D; ++c) {
-          const double w2 = b == c ? 1.0 : 2.0;
-          qs += w2 * LT::c(q, b) * LT::c(q, c) * Sv[sidx<D>(b, c)];
-          if (b == c) tr += Sv[sidx<D>(b, b)];
+          const R sv = R(Sv[sidx<D>(b, c)]);
+          qs += R((b == c ? 1 : 2) * LT::c(q, b) * LT::c(q, c)) * sv;
+          if (b == c) tr += sv;
         }
-      f += (1.0 - om) * (-(3.0 * LT::w(q) * rho / om) * (qs - tr / 3.0));
+      // post-collision non-equilibrium part (1 - omega) f^neq of the strain rate
+      g += (R(1) - om) * (-(R(3.0 * LT::w(q)) * rho / om) * (qs - tr / R(3)));
     }
-    if (df) f += df[q];
-    cur[(size_t)q * a.Ntot + e] = Sto<S>::cv(typename Sto<S>::R(f - LT::w(q) * a.rho_off));
+    if (df) g += R(df[q]);
+    out[(size_t)q * a.n_user] = Sto<S>::cv(g);
   }
+}
+
+// caller-ordered initial pdfs -> element slots (coalesced writes in slot order)
+template <int Q, class S>
+__global__ void k_init_place(const PlaceArgs a) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.Ntot) return;
+  const int32_t u = a.slot_user[e];
+  if (u < 0) return;
+  const S* src = static_cast<const S*>(a.temp) + u;
+  S* dst = static_cast<S*>(a.dst) + e;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) dst[(size_t)q * a.Ntot] = src[(size_t)q * a.n_user];
 }
 
 template <int Q, class S>
@@ -942,30 +956,36 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
   const S* p = static_cast<const S*>(a.pdf);
   const size_t N = (size_t)a.Ntot;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // each element's moments in the storage's compute type (the sums of its Q
+  // stored values); the accumulation over elements in FP64
+  // (the level volume and rho_off are applied once per thread below)
+  using R = typename Sto<S>::R;
+  int64_t cnt = 0;
   for (int64_t e = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.end; e += stride) {
-    double g[Q];
+    R g[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) g[q] = (double)Sto<S>::ld(p + (size_t)q * N + e);
-    double rp, j[3];
-    raw_moments<Q, double>(g, rp, j);
-    double F[3] = {0, 0, 0};
-    if (a.force) {
-      if (sizeof(typename Sto<S>::R) == 8)
-        for (int b = 0; b < D; ++b) F[b] = static_cast<const double*>(a.force)[(size_t)b * N + e];
-      else
-        for (int b = 0; b < D; ++b) F[b] = static_cast<const float*>(a.force)[(size_t)b * N + e];
-    }
-    const double rho = a.rho_off + rp;
-    double uu = 0;
-    acc[0] += a.vol * rho;
+    for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(p + (size_t)q * N + e);
+    R rp, j[3];
+    raw_moments<Q, R>(g, rp, j);
+    R F[3] = {R(0), R(0), R(0)};
+    if (a.force)
+      for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(a.force)[(size_t)b * N + e];
+    const R rho = R(a.rho_off) + rp;
+    R uu = R(0);
+    acc[0] += (double)rp;
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-      const double m = j[b] - 0.5 * F[b];  // rho u
-      acc[1 + b] += a.vol * m;
+      const R m = j[b] - R(0.5) * F[b];  // rho u
+      acc[1 + b] += (double)m;
       uu += m * m;
     }
-    acc[7] += 0.5 * a.vol * uu / rho;
+    acc[7] += (double)(R(0.5) * uu / rho);
+    ++cnt;
   }
+  acc[0] = a.vol * (acc[0] + (double)cnt * a.rho_off);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) acc[1 + b] *= a.vol;
+  acc[7] *= a.vol;
   // momentum exchange (Sec. 2.3): the link carries c_ib (f*_ib(x) + f_i(x)) to
   // the body, f_i the bounce-back value of the next step (interpolated with
   // the wall distance q; q = 1/2 gives 2 c_ib f*_ib)
@@ -1050,6 +1070,9 @@ struct Launch {
     if (a.cnt <= 0) return;
     with_q(Q, [&](auto q) { k_init<decltype(q)::value, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a); });
   }
+  static void init_place(int Q, const PlaceArgs& a, cudaStream_t st) {
+    with_q(Q, [&](auto q) { k_init_place<decltype(q)::value, S><<<blocks_for(a.Ntot, 256), 256, 0, st>>>(a); });
+  }
   static void out(int Q, const OutArgs& a, cudaStream_t st) {
     if (a.cnt <= 0) return;
     with_q(Q, [&](auto q) { k_out<decltype(q)::value, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a); });
@@ -1072,7 +1095,8 @@ const Ops* make_ops() {
   static const Ops ops = {&Launch<S>::stream_collide, &Launch<S>::stream_collide_brick,
                           &Launch<S>::outlet,         &Launch<S>::source_moments,
                           &Launch<S>::fill_gfc,       &Launch<S>::fill_gff,   &Launch<S>::fill_rest,
-                          &Launch<S>::init,           &Launch<S>::out,        &Launch<S>::set_state,
+                          &Launch<S>::init,           &Launch<S>::init_place, &Launch<S>::out,
+                          &Launch<S>::set_state,
                           &Launch<S>::gather_ghosts,
                           &Launch<S>::reduce,         sizeof(S),              sizeof(typename Sto<S>::R)};
   return &ops;

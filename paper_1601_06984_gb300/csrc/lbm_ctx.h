@@ -31,7 +31,7 @@ struct lbm_ctx {
   double inlet[lbm::kQmax] = {};
   // layout (byte offsets into the workspace)
   size_t oA = 0, oB = 0, oNbr = 0, oBrickNb = 0, oBrickTab = 0, oInletS = 0, oOutQ = 0, oObsA = 0, oObsQ = 0, oF = 0, oOutElem = 0, oOutA = 0, oOutB = 0, oOutDir = 0, oOutKind = 0,
-         oSide = 0, oObsElem = 0, oObsDir = 0, oUslot = 0, oUlev = 0, oStage = 0, oPartial = 0, oRed = 0;
+         oSide = 0, oObsElem = 0, oObsDir = 0, oUslot = 0, oUlev = 0, oSlotUser = 0, oStage = 0, oPartial = 0, oRed = 0;
   std::vector<lbm::LevelDev> ld;
   size_t bytes = 0;
   int64_t chunk = 0;

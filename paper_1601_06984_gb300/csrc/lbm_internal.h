@@ -82,6 +82,7 @@ struct HostMesh {
   std::vector<HostLevel> lv;
   std::vector<uint32_t> nbr;    // [Q-1][Ntot]
   std::vector<int32_t> uslot;   // [n_user] global element index
+  std::vector<int32_t> slot_user;  // [Ntot] caller index of each slot, -1 for ghosts and padding
   std::vector<uint8_t> ulev;    // [n_user] level index (L - Lmin)
   std::vector<uint8_t> kind;    // [Ntot] element kind (K_*)
   // boundary-value links (all levels, grouped by level): outlet links and, with
@@ -198,16 +199,20 @@ struct FillArgs {  // rest equilibrium everywhere
   double rho0, rho_off;
 };
 
-struct InitArgs {
-  void* A;
-  void* B;
-  const int32_t* uslot;
+struct InitArgs {  // initial pdfs of a chunk of caller-order elements, written caller-ordered
+  void* temp;        // [Q][n_user] storage type (the pdf buffer that is not current)
   const uint8_t* ulev;
-  uint32_t parity;  // bit li set: level li's current state lives in B
   const double *rho, *u, *S, *df;  // staged chunk: rho[cnt], u[cnt][d], S[cnt][nS] or null, df[cnt][Q] or null
-  int64_t first, cnt, Ntot;
+  int64_t first, cnt, n_user;
   double omega[16];
   double rho_off;
+};
+
+struct PlaceArgs {  // caller-ordered pdfs -> element slots of the current buffer
+  const void* temp;  // [Q][n_user]
+  void* dst;         // [Q][Ntot]
+  const int32_t* slot_user;  // [Ntot] caller index of each slot, -1 for ghosts and padding
+  int64_t n_user, Ntot;
 };
 
 struct SetStateArgs {  // FP64 [cnt][Q] in user order -> current pdfs
@@ -280,6 +285,7 @@ struct Ops {
   void (*fill_gff)(int Q, const GffArgs&, cudaStream_t);
   void (*fill_rest)(int Q, const FillArgs&, cudaStream_t);
   void (*init)(int Q, const InitArgs&, cudaStream_t);
+  void (*init_place)(int Q, const PlaceArgs&, cudaStream_t);
   void (*out)(int Q, const OutArgs&, cudaStream_t);
   void (*set_state)(int Q, const SetStateArgs&, cudaStream_t);
   void (*gather_ghosts)(int Q, const GatherGhostArgs&, cudaStream_t);

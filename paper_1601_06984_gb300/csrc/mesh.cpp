@@ -915,9 +915,10 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     if (mismatch) return bad(LBM_ERR_INTERNAL, "interior brick table disagrees with the neighbour list");
   }
 
-  // ---- caller order -> element slots
+  // ---- caller order <-> element slots
   M.uslot.resize(n);
   M.ulev.resize(n);
+  M.slot_user.assign(M.Ntot, -1);
   for (int li = 0; li < nlev; ++li) {
     const HostLevel& H = M.lv[li];
 #pragma omp parallel for schedule(static)
@@ -925,6 +926,7 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       const int64_t k = fl[li][r].second;
       M.uslot[k] = (int32_t)(H.base + H.oF + r);
       M.ulev[k] = (uint8_t)li;
+      M.slot_user[H.base + H.oF + r] = (int32_t)k;
     }
   }
   return LBM_OK;
