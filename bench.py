@@ -269,19 +269,26 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     units = int(64 * info[finest, 8]) if kb == 0 else int(info[finest, 1])
     avg_ms = kms[finest, kb] / max(nl[finest, kb], 1) if kernel_timing else float("nan")
     bpu = bytes_per_update(Q, prec, brick=kb == 0)
-    list_units = int(info[finest, 1] - 64 * info[finest, 8])
+    list_units = int(info[finest, 1] - 64 * (info[finest, 8] + info[finest, 9]))
     list_ms = kms[finest, 1] / max(nl[finest, 1], 1)
+    bnd_units = int(64 * info[finest, 9])
+    bnd_ms = kms[finest, 2] / max(nl[finest, 2], 1)
     res = {"ms_total": ms, "ms_per_step": ms / K, "mlups": K * U / (ms * 1e-3) / 1e6, "launches": launches,
            "finest_kernel": "k_stream_collide_brick" if kb == 0 else "k_stream_collide",
            "finest_launch_ms": avg_ms, "finest_launches": int(nl[finest, kb]), "finest_units": units,
            "finest_bytes": units * bpu, "finest_gbs": units * bpu / (avg_ms * 1e-3) / 1e9 if kernel_timing else None,
            "finest_list_units": list_units, "finest_list_launch_ms": list_ms,
+           "finest_boundary_units": bnd_units, "finest_boundary_launch_ms": bnd_ms,
+           "finest_boundary_gbs": (bnd_units * bytes_per_update(Q, prec, brick=True) / (bnd_ms * 1e-3) / 1e9
+                                   if nl[finest, 2] > 0 and bnd_ms > 0 else None),
            "finest_list_gbs": (list_units * bytes_per_update(Q, prec) / (list_ms * 1e-3) / 1e9
                                if nl[finest, 1] > 0 and list_ms > 0 else None),
            "level_ms": kms.sum(axis=1).tolist(), "level_launches": nl.sum(axis=1).tolist(),
            "interior_fraction": float(64 * info[:, 8].sum() / info[:, 1].sum()),
-           "step_bytes": float(sum((1 << li) * (64 * info[li, 8] * bytes_per_update(Q, prec, brick=True)
-                                                + (info[li, 1] - 64 * info[li, 8]) * bytes_per_update(Q, prec))
+           "brick_fraction": float(64 * (info[:, 8] + info[:, 9]).sum() / info[:, 1].sum()),
+           "step_bytes": float(sum((1 << li) * (64 * (info[li, 8] + info[li, 9]) * bytes_per_update(Q, prec, brick=True)
+                                                + (info[li, 1] - 64 * (info[li, 8] + info[li, 9]))
+                                                * bytes_per_update(Q, prec))
                                    for li in range(len(info)))),
            "bytes_per_update": bpu, "build_s": t_build, "device_gb": sim.device_bytes() / 1e9,
            "reduce": sim.reduce().tolist()}
@@ -512,6 +519,11 @@ def main():
                      "avg_launch_ms": r["finest_launch_ms"], "peak_source": peak_src},
         "step_gbs_algorithmic": r["step_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9,
         "interior_brick_fraction": r["interior_fraction"],
+        "brick_fraction": r["brick_fraction"],
+        "finest_boundary_brick_kernel": {"units_per_launch": r["finest_boundary_units"],
+                                         "avg_launch_ms": r["finest_boundary_launch_ms"],
+                                         "achieved_gbs": r["finest_boundary_gbs"],
+                                         "bytes_per_unit": bytes_per_update(Q, lbm.FP32DEV, brick=True)},
         "finest_list_kernel": {"units_per_launch": r["finest_list_units"],
                                "avg_launch_ms": r["finest_list_launch_ms"], "achieved_gbs": r["finest_list_gbs"],
                                "bytes_per_unit": bytes_per_update(Q, lbm.FP32DEV)},

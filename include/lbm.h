@@ -130,11 +130,13 @@ lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t
 
 /* Per level, 10 int64 each: level, fluid, GFC, GFF inner, GFF outer, padded
  * element count, boundary-value links (outlet links, plus the obstacle links
- * with params.bouzidi), obstacle links, interior bricks, 0.  An
+ * with params.bouzidi), obstacle links, interior bricks, boundary bricks.  An
  * interior brick is an aligned block of 64 fluid elements of the level (4^3
  * in 3D, 8^2 in 2D) whose stencil neighbours are all such blocks; the
  * stream-collide locates their pull sources from a per-brick table instead
- * of the neighbour list.  cap = rows available in info. */
+ * of the neighbour list; a boundary brick is a block of 64 fluid elements
+ * whose links through an incomplete neighbour block use the neighbour list.
+ * cap = rows available in info. */
 lbm_status lbm_mesh_info(const lbm_ctx* ctx, int64_t* info, int32_t cap, int32_t* nlevels);
 
 /* Obstacle links: fluid elements whose neighbour x - c_i is a solid cell.
@@ -283,8 +285,8 @@ lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
 /* Device timing of the stream-collide kernel: while enabled, every
  * stream-collide launch is bracketed by CUDA events recorded on the bound
  * stream.  lbm_timing_read synchronises the stream and returns, in row
- * 2 L + k for level index L (coarsest 0) and kernel k (0: interior bricks,
- * 1: neighbour list), the number of timed launches and their summed device
+ * 3 L + k for level index L (coarsest 0) and kernel k (0: interior bricks,
+ * 1: neighbour list, 2: boundary bricks), the number of timed launches and their summed device
  * time in milliseconds (rows 0..cap-1), then clears the record.  Enabling
  * clears it too. */
 lbm_status lbm_timing_enable(lbm_ctx* ctx, int32_t on);

@@ -158,8 +158,10 @@ void lbm_ctx::stream_collide(int li) {
     ops->outlet(Q, o, st);
     ++launches;
   }
-  // interior bricks (the first 64 nB fluid elements) through the brick table
-  const int64_t nbrick = 64 * H.nB;
+  // interior bricks, then boundary bricks (the first 64 (nB + nBb) fluid
+  // elements) through the brick tables
+  const int64_t nbnd = ops->boundary_bricks ? H.nBb : 0;
+  const int64_t nbrick = 64 * (H.nB + nbnd);
   BrickArgs b{};
   b.src = cur(li);
   b.dst = nxt(li);
@@ -171,8 +173,16 @@ void lbm_ctx::stream_collide(int li) {
   b.nB = H.nB;
   b.omega = H.omega;
   b.rho_off = rho_off;
+  b.nbr = at<uint32_t>(oNbr);
+  b.side = at(oSide);
+  b.inlet_s = at<double>(oInletS);
+  std::memcpy(b.inlet, inlet, sizeof(inlet));
+  BrickArgs bb = b;
+  bb.nb = b.nb + (size_t)H.nB * 27;
+  bb.begin = b.begin + 64 * H.nB;
+  bb.nB = nbnd;
   // the rest through the neighbour list; processed range: TWO_LAYER [GFC |
-  // fluid], LINEAR [fluid | GFF inner], minus the interior bricks
+  // fluid], LINEAR [fluid | GFF inner], minus the bricks
   StreamCollideArgs a{};
   a.src = cur(li);
   a.dst = nxt(li);
@@ -196,13 +206,15 @@ void lbm_ctx::stream_collide(int li) {
   a.rho_off = rho_off;
   std::memcpy(a.inlet, inlet, sizeof(inlet));
   const bool use_force = p.use_force != 0;
+  // kernel 0: interior bricks, 1: neighbour list, 2: boundary bricks
   auto launch = [&](int kernel) {
-    if (kernel == 0) ops->stream_collide_brick(Q, use_force, b, st);
+    if (kernel == 0) ops->stream_collide_brick(Q, use_force, false, b, st);
+    else if (kernel == 2) ops->stream_collide_brick(Q, use_force, true, bb, st);
     else ops->stream_collide(Q, use_force, a, st);
     ++launches;
   };
-  for (int kernel = 0; kernel < 2; ++kernel) {
-    if (kernel == 0 ? b.nB == 0 : a.end <= a.begin) continue;
+  for (int kernel : {0, 2, 1}) {
+    if (kernel == 0 ? b.nB == 0 : kernel == 2 ? bb.nB == 0 : a.end <= a.begin) continue;
     if (timing) {
       Timed t{li, kernel, get_event(), get_event()};
       cudaEventRecord(t.a, st);
@@ -376,7 +388,7 @@ lbm_status lbm_mesh_info(const lbm_ctx* c, int64_t* info, int32_t cap, int32_t* 
   for (const HostLevel& H : c->M.lv) {
     if (n >= cap) break;
     int64_t r[10] = {H.L, H.nF, H.nC, H.nG1, H.nG2, H.N, H.out_end - H.out_begin, H.obs_end - H.obs_begin,
-                     H.nB, 0};
+                     H.nB, H.nBb};
     std::memcpy(info + 10 * n, r, sizeof(r));
     ++n;
   }
@@ -757,7 +769,7 @@ lbm_status lbm_timing_read(lbm_ctx* c, int64_t* launches, double* ms, int32_t ca
     float e = 0.f;
     s = c->cuda_check(cudaEventElapsedTime(&e, t.a, t.b), "timing read");
     if (s != LBM_OK) break;
-    const int row = 2 * t.li + t.kernel;
+    const int row = 3 * t.li + t.kernel;
     if (row < cap) {
       launches[row] += 1;
       ms[row] += e;

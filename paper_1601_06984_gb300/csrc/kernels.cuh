@@ -385,8 +385,13 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
 #ifndef LBM_BR_MINB
 #define LBM_BR_MINB 4
 #endif
-template <int Q, class S, bool FORCE>
-__global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_BR_MINB) k_stream_collide_brick(const BrickArgs a) {
+//
+// Boundary bricks (BND): a complete brick whose neighbour brick behind some
+// link is not complete; those links (row entry kBrickMissing) take the
+// element's neighbour-list code like k_stream_collide: a pull, the element's
+// own opposite slot (bounce-back), plus the inlet term, or a boundary value.
+template <int Q, class S, bool FORCE, bool BND>
+__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? 3 : LBM_BR_MINB) k_stream_collide_brick(const BrickArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -409,11 +414,46 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_BR_MINB) k_stream_collide_br
   S* __restrict__ dst = static_cast<S*>(a.dst) + first + l;
   R g[Q];
   g[0] = Sto<S>::ld(src + l);
+  if (!BND) {
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
-    const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
-    g[i] = Sto<S>::ld(src + (int64_t)(i * N) + r + (v & 63));
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
+      const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
+      g[i] = Sto<S>::ld(src + (int64_t)(i * N) + r + (v & 63));
+    }
+  } else {
+    // phase 1: the neighbour-list codes of links through missing bricks, all
+    // issued before any gather (kNoCode: the link stays in the brick tables)
+    constexpr uint32_t kNoCode = 0xffffffffu;
+    const int64_t e = first + l;
+    uint32_t code[Q];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
+      const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
+      code[i] = r == kBrickMissing ? __ldg(a.nbr + (size_t)(i - 1) * N + e) : kNoCode;
+    }
+    // phase 2: the gathers
+    const S* base = static_cast<const S*>(a.src);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
+      const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
+      const uint32_t n = code[i];
+      if (n == kNoCode) g[i] = Sto<S>::ld(src + (int64_t)(i * N) + r + (v & 63));
+      else g[i] = Sto<S>::ld(base + (n < NB_FLAG30 ? (size_t)i * N + n : (size_t)opp(i) * N + (size_t)e));
+    }
+    // phase 3: bounce-back, inlet and boundary-value links
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t n = code[i];
+      if (n == kNoCode || n < NB_FLAG30) continue;
+      if (n & NB_BOUNCE) {
+        if (n & NB_FLAG30) g[i] += R(a.inlet[i]) * (a.inlet_s ? R(a.inlet_s[n & NB_INDEX]) : R(1));
+      } else {
+        g[i] = static_cast<const R*>(a.side)[n & NB_INDEX];
+      }
+    }
   }
   R F[3] = {R(0), R(0), R(0)};
   if (FORCE) {
@@ -1023,13 +1063,18 @@ inline void with_q(int Q, F&& f) {
 
 template <class S>
 struct Launch {
-  static void stream_collide_brick(int Q, bool force, const BrickArgs& a, cudaStream_t st) {
+  static void stream_collide_brick(int Q, bool force, bool boundary, const BrickArgs& a, cudaStream_t st) {
     if (a.nB <= 0) return;
     const unsigned g = blocks_for(a.nB, LBM_BR_BLOCK / 64);
     with_q(Q, [&](auto q) {
       constexpr int QQ = decltype(q)::value;
-      if (force) k_stream_collide_brick<QQ, S, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
-      else k_stream_collide_brick<QQ, S, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+      if (boundary) {
+        if (force) k_stream_collide_brick<QQ, S, true, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+        else k_stream_collide_brick<QQ, S, false, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+      } else {
+        if (force) k_stream_collide_brick<QQ, S, true, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+        else k_stream_collide_brick<QQ, S, false, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+      }
     });
   }
   static void stream_collide(int Q, bool force, const StreamCollideArgs& a, cudaStream_t st) {
@@ -1098,7 +1143,10 @@ const Ops* make_ops() {
                           &Launch<S>::init,           &Launch<S>::init_place, &Launch<S>::out,
                           &Launch<S>::set_state,
                           &Launch<S>::gather_ghosts,
-                          &Launch<S>::reduce,         sizeof(S),              sizeof(typename Sto<S>::R)};
+                          &Launch<S>::reduce,         sizeof(S),              sizeof(typename Sto<S>::R),
+                          // BF16 storage: the boundary-brick kernel measured slower than the
+                          // neighbour-list kernel on the same elements
+                          sizeof(S) != 2};
   return &ops;
 }
 

@@ -48,7 +48,7 @@ struct lbm_ctx {
   // stream-collide timing (events recorded around each launch when enabled)
   bool timing = false;
   struct Timed {
-    int li, kernel;  // kernel 0: interior bricks, 1: neighbour list
+    int li, kernel;  // kernel 0: interior bricks, 1: neighbour list, 2: boundary bricks
     cudaEvent_t a, b;
   };
   std::vector<Timed> timed;

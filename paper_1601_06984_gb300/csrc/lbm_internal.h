@@ -4,6 +4,7 @@
 
 #include <cuda_runtime_api.h>
 
+#include <climits>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -21,6 +22,7 @@ constexpr uint32_t NB_BOUNCE = 0x80000000u;
 constexpr uint32_t NB_FLAG30 = 0x40000000u;
 constexpr uint32_t NB_INDEX = 0x3FFFFFFFu;
 constexpr int kPad = 32;  // every level segment is padded to a multiple of this
+constexpr int32_t kBrickMissing = INT32_MIN;  // brick row entry: neighbour brick not complete
 
 enum { K_FLUID = 0, K_GFC = 1, K_GFF = 2, K_PAD = 3 };
 
@@ -70,8 +72,9 @@ struct HostLevel {
   int64_t out_begin = 0, out_end = 0;
   // obstacle links of this level: global range in the obstacle list
   int64_t obs_begin = 0, obs_end = 0;
-  // interior bricks: the first 64 nB fluid elements; their rows in brick_nb
-  int64_t nB = 0, brick_first = 0;
+  // bricks: the first 64 nB fluid elements are interior bricks, the next
+  // 64 nBb boundary bricks; their rows in brick_nb from brick_first
+  int64_t nB = 0, nBb = 0, brick_first = 0;
 };
 
 struct HostMesh {
@@ -139,10 +142,16 @@ struct BrickArgs {
   const void* src;
   void* dst;
   const void* force;    // [d][Ntot] compute type, or null
-  const int32_t* nb;    // [nB][27] rows of this level (offsets from the brick's first element)
+  const int32_t* nb;    // [nB][27] rows (offsets from the brick's first element, or kBrickMissing)
   const uint16_t* tab;  // [Q-1][64]
   int64_t Ntot, begin, nB;
   double omega, rho_off;
+  // boundary bricks: links through a missing neighbour brick use the element's
+  // neighbour-list code (pull, bounce-back, inlet, boundary value)
+  const uint32_t* nbr;
+  const void* side;
+  const double* inlet_s;
+  double inlet[kQmax];
 };
 
 struct OutletArgs {
@@ -278,7 +287,7 @@ struct FinalArgs {
 
 struct Ops {
   void (*stream_collide)(int Q, bool force, const StreamCollideArgs&, cudaStream_t);
-  void (*stream_collide_brick)(int Q, bool force, const BrickArgs&, cudaStream_t);
+  void (*stream_collide_brick)(int Q, bool force, bool boundary, const BrickArgs&, cudaStream_t);
   void (*outlet)(int Q, const OutletArgs&, cudaStream_t);
   void (*source_moments)(int Q, const MomentsArgs&, cudaStream_t);
   void (*fill_gfc)(int Q, const GfcArgs&, cudaStream_t);
@@ -292,6 +301,7 @@ struct Ops {
   void (*reduce)(int Q, const ReduceArgs&, cudaStream_t);
   size_t storage_bytes;  // bytes per stored pdf
   size_t compute_bytes;  // bytes of the compute type
+  bool boundary_bricks;  // stream boundary bricks with the brick kernel (else with the neighbour list)
 };
 
 // ----------------------------------------------------------------- adjoint kernels

@@ -229,11 +229,15 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
   // from (the face and edge neighbours the stencil reaches) is complete too:
   // all its links are plain pulls between fluid elements of one level, and the
   // source of link i at local position l is brick slot t plus local position
-  // l', a table common to all bricks.  Interior bricks move to the front of
-  // the level's fluid list; everything keeps z-curve order within its part
-  // (so GhostFromFiner children stay contiguous).
+  // l', a table common to all bricks.  A complete brick with some neighbour
+  // brick missing is a boundary brick: its links through the missing slots
+  // take the neighbour list instead.  The level's fluid list becomes interior
+  // bricks, boundary bricks, the rest; everything keeps z-curve order within
+  // its part (so GhostFromFiner children stay contiguous).
   const int bshift = d == 3 ? 2 : 3, bside = 1 << bshift;
-  std::vector<std::vector<std::array<int64_t, 27>>> brick_nbpos(nlev);  // per interior brick: slot -> new position
+  constexpr int64_t kMissingPos = -1;  // neighbour brick not complete (slot value below)
+  std::vector<std::vector<std::array<int64_t, 27>>> brick_nbpos(nlev);  // per brick: slot -> new position
+  std::vector<int64_t> n_interior(nlev, 0), n_boundary(nlev, 0);
   {
     // brick offsets the stencil needs: s_a in {0, -c_a}, not all zero
     bool need[27] = {};
@@ -272,12 +276,13 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
         const int64_t* x0 = &X[3 * f[cstart[b]].second];
         int64_t bc[3] = {0, 0, 0};
         for (int a = 0; a < d; ++a) bc[a] = x0[a] >> bshift;
-        bool ok = true;
-        for (int t = 0; t < 27 && ok; ++t) {
+        bool all = true;
+        for (int t = 0; t < 27; ++t) {
           nbc[b][t] = b;
           if (!need[t]) continue;
           const int sx[3] = {t % 3 - 1, t / 3 % 3 - 1, t / 9 - 1};
           int64_t q[3] = {0, 0, 0};
+          bool ok = true;
           for (int a = 0; a < d && ok; ++a) {
             q[a] = bc[a] + sx[a];
             if (q[a] < 0 || q[a] >= nbx[a]) {
@@ -287,40 +292,49 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
               else q[a] = (q[a] + nbx[a]) % nbx[a];
             }
           }
-          if (!ok) break;
-          auto it = cidx.find(zkey(q, d, B.Lmin + li - bshift));
-          if (it == cidx.end()) ok = false;
-          else nbc[b][t] = it->second;
+          auto it = ok ? cidx.find(zkey(q, d, B.Lmin + li - bshift)) : cidx.end();
+          if (it == cidx.end()) {
+            nbc[b][t] = kMissingPos;
+            all = false;
+          } else {
+            nbc[b][t] = it->second;
+          }
         }
-        interior[b] = ok;
+        interior[b] = all;
       }
-      // new order: interior bricks, then the rest; new position of every complete brick
+      // new order: interior bricks, boundary bricks, then the rest; new position
+      // of every complete brick
       std::vector<int64_t> cnew(nc);
       std::vector<std::pair<uint64_t, int64_t>> g;
       g.reserve(nf);
-      int64_t nint = 0;
-      for (int64_t b = 0; b < nc; ++b)
-        if (interior[b]) {
-          cnew[b] = 64 * nint++;
-          g.insert(g.end(), f.begin() + cstart[b], f.begin() + cstart[b] + 64);
-        }
+      int64_t nint = 0, nbnd = 0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int64_t b = 0; b < nc; ++b)
+          if ((bool)interior[b] == (pass == 0)) {
+            cnew[b] = (int64_t)g.size();
+            (pass == 0 ? nint : nbnd) += 1;
+            g.insert(g.end(), f.begin() + cstart[b], f.begin() + cstart[b] + 64);
+          }
       {
         int64_t b = 0;
         for (int64_t j = 0; j < nf; ++j) {
           while (b < nc && cstart[b] + 64 <= j) ++b;
           const bool in_brick = b < nc && cstart[b] <= j;
-          if (in_brick && interior[b]) continue;
-          if (in_brick && j == cstart[b]) cnew[b] = (int64_t)g.size();
-          g.push_back(f[j]);
+          if (!in_brick) g.push_back(f[j]);
         }
       }
       f.swap(g);
+      n_interior[li] = nint;
+      n_boundary[li] = nbnd;
+      // rows in the new brick order (interior first, then boundary)
+      std::vector<int64_t> order(nc);
+      for (int64_t b = 0; b < nc; ++b) order[cnew[b] / 64] = b;
       auto& bn = brick_nbpos[li];
-      bn.resize(nint);
-      for (int64_t b = 0, k = 0; b < nc; ++b)
-        if (interior[b]) {
-          for (int t = 0; t < 27; ++t) bn[k][t] = cnew[nbc[b][t]];
-          ++k;
+      bn.resize(nc);
+      for (int64_t k = 0; k < nc; ++k)
+        for (int t = 0; t < 27; ++t) {
+          const int64_t src = nbc[order[k]][t];
+          bn[k][t] = src == kMissingPos ? kMissingPos : cnew[src];
         }
     }
   }
@@ -540,16 +554,20 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     int64_t rows = 0;
     for (int li = 0; li < nlev; ++li) {
       HostLevel& H = M.lv[li];
-      H.nB = (int64_t)brick_nbpos[li].size();
+      H.nB = n_interior[li];
+      H.nBb = n_boundary[li];
       H.brick_first = rows;
-      rows += H.nB;
+      rows += H.nB + H.nBb;
     }
     M.brick_nb.resize((size_t)rows * 27);
     for (int li = 0; li < nlev; ++li) {
       const HostLevel& H = M.lv[li];
-      for (int64_t b = 0; b < H.nB; ++b)
-        for (int t = 0; t < 27; ++t)
-          M.brick_nb[(size_t)(H.brick_first + b) * 27 + t] = (int32_t)(brick_nbpos[li][b][t] - 64 * b);
+      for (int64_t b = 0; b < H.nB + H.nBb; ++b)
+        for (int t = 0; t < 27; ++t) {
+          const int64_t pos = brick_nbpos[li][b][t];
+          M.brick_nb[(size_t)(H.brick_first + b) * 27 + t] =
+              pos == kMissingPos ? kBrickMissing : (int32_t)(pos - 64 * b);
+        }
     }
     M.brick_tab.assign((size_t)(Q - 1) * 64, 0);
     for (int i = 1; i < Q; ++i)
@@ -898,21 +916,26 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
         !in_range(M.obs_a))
       return bad(LBM_ERR_INTERNAL, "boundary table index out of range");
   }
-  // interior bricks must reproduce the neighbour list exactly
+  // brick links must reproduce the neighbour list exactly (boundary bricks:
+  // every link not routed to the neighbour list; interior bricks: all links)
   for (int li = 0; li < nlev; ++li) {
     const HostLevel& H = M.lv[li];
     int mismatch = 0;
 #pragma omp parallel for schedule(static) reduction(| : mismatch)
-    for (int64_t b = 0; b < H.nB; ++b) {
+    for (int64_t b = 0; b < H.nB + H.nBb; ++b) {
       const int32_t* nb = &M.brick_nb[(size_t)(H.brick_first + b) * 27];
       for (int i = 1; i < Q; ++i)
         for (int l = 0; l < 64; ++l) {
           const uint16_t v = M.brick_tab[(size_t)(i - 1) * 64 + l];
           const int64_t first = H.base + H.oF + 64 * b;
+          if (nb[v >> 6] == kBrickMissing) {
+            if (b < H.nB) mismatch = 1;
+            continue;
+          }
           if (M.nbr[(size_t)(i - 1) * M.Ntot + first + l] != (uint32_t)(first + nb[v >> 6] + (v & 63))) mismatch = 1;
         }
     }
-    if (mismatch) return bad(LBM_ERR_INTERNAL, "interior brick table disagrees with the neighbour list");
+    if (mismatch) return bad(LBM_ERR_INTERNAL, "brick table disagrees with the neighbour list");
   }
 
   // ---- caller order <-> element slots

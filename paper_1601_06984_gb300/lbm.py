@@ -232,12 +232,13 @@ class Sim:
 
     def timing_read(self):
         """Stream-collide launches and summed device ms since enabled, arrays
-        [level, kernel] with kernel 0 = interior bricks, 1 = neighbour list."""
-        n = np.zeros(64, np.int64)
-        ms = np.zeros(64)
-        _check(self.ctx, lib().lbm_timing_read(self.ctx, _p(n), _p(ms), 64))
+        [level, kernel] with kernel 0 = interior bricks, 1 = neighbour list,
+        2 = boundary bricks."""
+        n = np.zeros(96, np.int64)
+        ms = np.zeros(96)
+        _check(self.ctx, lib().lbm_timing_read(self.ctx, _p(n), _p(ms), 96))
         nl = len(self.mesh_info())
-        return n[: 2 * nl].reshape(nl, 2), ms[: 2 * nl].reshape(nl, 2)
+        return n[: 3 * nl].reshape(nl, 3), ms[: 3 * nl].reshape(nl, 3)
 
     # -- state
     def init(self, rho, u, S=None, df=None):

@@ -154,12 +154,13 @@ def _interior_bricks(mesh, Q):
     offs = [o for o in itertools.product((-1, 0, 1), repeat=d) if any(o)]
     if Q == 19:
         offs = [o for o in offs if sum(map(abs, o)) <= 2]  # D3Q19 reaches no corner block
-    out = []
+    out, complete = [], []
     for L in sorted(set(int(v) for v in mesh.levels)):
         sel = mesh.levels == L
         xyz = mesh.coords[sel][:, :d] // side
         keys, cnt = np.unique(xyz, axis=0, return_counts=True)
         full = {tuple(k) for k, c in zip(keys, cnt) if c == side ** d}
+        complete.append(len(full))
         ext = [e << (L - mesh.lmin) for e in mesh.extent]
         nb = [(e + side - 1) // side for e in ext]
         n = 0
@@ -180,20 +181,23 @@ def _interior_bricks(mesh, Q):
                     break
             n += ok
         out.append(n)
-    return out
+    return out, complete
 
 
 @pytest.mark.parametrize("name", ["tgv2d", "tgv3d16", "half2d", "cylinder", "sphere_small", "tgv3d32_q27",
                                   "sphere_small_q27"])
 def test_interior_brick_counts(lbm, name):
-    """The builder's interior bricks match an independent count, and the
-    builder has checked each brick's link table against the neighbour list."""
+    """The builder's interior bricks match an independent count, every other
+    complete brick is a boundary brick, and the builder has checked each
+    brick's link table against the neighbour list."""
     mesh, Q = {"tgv2d": (W.config_tgv2d(), 9), "tgv3d16": (W.config_tgv3d(16), 19),
                "half2d": (W.half_refined_2d(32), 9), "cylinder": (W.config_cylinder(), 9),
                "sphere_small": (W.config_sphere_small(), 19), "tgv3d32_q27": (W.config_tgv3d(32), 27),
                "sphere_small_q27": (W.config_sphere_small(), 27)}[name]
     info = lbm.Sim(mesh, Q, 1.7, u_in=(0.04, 0, 0), device=None).mesh_info()
-    assert [int(r[8]) for r in info] == _interior_bricks(mesh, Q)
+    interior, complete = _interior_bricks(mesh, Q)
+    assert [int(r[8]) for r in info] == interior
+    assert [int(r[8] + r[9]) for r in info] == complete
 
 
 def test_obstacle_links_and_link_q(lbm):

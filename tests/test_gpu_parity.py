@@ -228,13 +228,15 @@ def test_kernel_launches_counted(lbm):
     g = lbm.Sim(m, 9, 1.6)
     g.init(*W.tgv_fields(m, 0.01))
     info = g.mesh_info()
-    assert info[0, 8] == 0 and info[1, 8] == 4  # interior bricks: none coarse, 4 fine
+    assert info[0, 8] == 0 and info[1, 8] == 4    # interior bricks: none coarse, 4 fine
+    assert info[0, 9] == 12 and info[1, 9] == 12  # boundary bricks: all other complete bricks
     n0 = g.kernel_launches()
     g.step(1)
-    # LINEAR two-level step: GFF, source moments, GFC, coarse stream-collide,
-    # fine stream-collide (bricks + list), source moments, GFC, fine
-    # stream-collide (bricks + list)
-    assert g.kernel_launches() - n0 == 10
+    # LINEAR two-level step: GFF, source moments, GFC, coarse stream-collide
+    # (boundary bricks + neighbour list for the inner GFF layer), fine
+    # stream-collide (interior + boundary bricks), source moments, GFC, fine
+    # stream-collide (interior + boundary bricks)
+    assert g.kernel_launches() - n0 == 11
 
 
 @pytest.mark.parametrize("precision", [0, 1])
