@@ -41,17 +41,34 @@ struct AdjLayout {
   size_t state_bytes = 0, total = 0;
 };
 
+// Copies the rows of level li's segment of a [Q][Ntot] state.
+void copy_level(lbm_ctx* c, const void* from, void* to, int li) {
+  const HostLevel& H = c->M.lv[li];
+  const size_t s = c->ops->storage_bytes;
+  launch_copy_rows(from, to, (size_t)c->M.Ntot * s, (size_t)H.base * s, (size_t)H.N * s, c->Q, s, c->st);
+}
+
+// Walks (dry) or follows (recording) one coarse step and decides, per level
+// state an op reads, where the reverse sweep finds it.  A state is identified
+// by (level, version); the version of a level is bumped by every op that
+// writes it.  A state that no later op of the step overwrites (its buffer
+// keeps it until the next restore) is read in place; the others are copied to
+// the snapshot store when they are first read.
 struct Recorder {
   lbm_ctx* c;
   bool counting = true;
-  std::vector<int> version;                 // per level, bumped by every write
+  std::vector<int> version;                    // per level, bumped by every write
   std::map<std::pair<int, int>, int> snap_of;  // (level, version) -> snapshot index
   std::vector<std::pair<int, int>> snap_key;
+  std::vector<int> snap_buf;                   // buffer (parity) the state lives in
+  std::vector<char> clobbered;                 // a later op of the step wrote that buffer
+  std::vector<char> need_copy;                 // from the dry walk: copy instead of reading in place
+  std::vector<const void*> where;              // recording: where the reverse reads each state
   std::vector<TapeOp> tape;
   int last_mom_a_snap[16], last_mom_b_snap[16];
   char* snap_base = nullptr;
   size_t state_bytes = 0;
-  int max_snaps = 0;
+  int max_snaps = 0, n_copies = 0;
   bool overflow = false;
 
   explicit Recorder(lbm_ctx* ctx) : c(ctx), version(ctx->nlev, 0) {
@@ -59,13 +76,12 @@ struct Recorder {
     std::fill(last_mom_b_snap, last_mom_b_snap + 16, -1);
   }
 
-  void copy_level(const void* from, void* to, int li) {
-    const HostLevel& H = c->M.lv[li];
-    const size_t s = c->ops->storage_bytes;
-    const size_t pitch = (size_t)c->M.Ntot * s;
-    cudaMemcpy2DAsync(static_cast<char*>(to) + (size_t)H.base * s, pitch,
-                      static_cast<const char*>(from) + (size_t)H.base * s, pitch, (size_t)H.N * s, c->Q,
-                      cudaMemcpyDeviceToDevice, c->st);
+  int copies_needed() const { return (int)std::count(clobbered.begin(), clobbered.end(), 1); }
+
+  void wrote(int li, int buf) {
+    for (size_t id = 0; id < snap_key.size(); ++id)
+      if (snap_key[id].first == li && snap_buf[id] == buf) clobbered[id] = 1;
+    version[li]++;
   }
 
   int snapshot(int li) {
@@ -75,12 +91,21 @@ struct Recorder {
     const int id = (int)snap_key.size();
     snap_of[key] = id;
     snap_key.push_back(key);
+    snap_buf.push_back(c->parity[li]);
+    clobbered.push_back(0);
     if (!counting) {
-      if (id >= max_snaps) {
+      const bool copy = id < (int)need_copy.size() ? need_copy[id] != 0 : true;
+      if (!copy) {
+        where.push_back(c->cur(li));
+      } else if (n_copies >= max_snaps) {
         overflow = true;
-        return -1;
+        where.push_back(nullptr);
+        return id;
+      } else {
+        char* dst = snap_base + (size_t)n_copies++ * state_bytes;
+        copy_level(c, c->cur(li), dst, li);
+        where.push_back(dst);
       }
-      copy_level(c->cur(li), snap_base + (size_t)id * state_bytes, li);
     }
     return id;
   }
@@ -94,7 +119,7 @@ struct Recorder {
       case OP_GFF:
         t.snap = snapshot(li + 1);
         tape.push_back(t);
-        version[li]++;
+        wrote(li, c->parity[li]);
         break;
       case OP_MOM_A:
         t.snap = snapshot(li);
@@ -104,12 +129,12 @@ struct Recorder {
       case OP_GFC_A:
         t.snap_a = last_mom_a_snap[li - 1];
         tape.push_back(t);
-        version[li]++;
+        wrote(li, c->parity[li]);
         break;
       case OP_SC:
         t.snap = snapshot(li);
         tape.push_back(t);
-        version[li]++;
+        wrote(li, c->parity[li] ^ 1);
         break;
       case OP_MOM_B:
         t.snap = snapshot(li);
@@ -121,15 +146,15 @@ struct Recorder {
         t.snap_a = last_mom_a_snap[li - 1];
         t.snap_b = last_mom_b_snap[li - 1];
         tape.push_back(t);
-        version[li]++;
+        wrote(li, c->parity[li]);
         break;
     }
   }
 };
 
-// Number of level snapshots one coarse step's tape needs (walks the op order
-// of lbm_ctx::advance without launching anything).
-int count_snapshots(lbm_ctx* c) {
+// Dry walk of one coarse step from the current parities (launches nothing):
+// which of the states its ops read must be copied.
+std::vector<char> plan_snapshots(lbm_ctx* c) {
   Recorder r(c);
   r.counting = true;
   std::vector<int> saved = c->parity;
@@ -139,7 +164,14 @@ int count_snapshots(lbm_ctx* c) {
   c->dry = false;
   c->hook = nullptr;
   c->parity = saved;
-  return (int)r.snap_key.size();
+  return r.clobbered;
+}
+
+// Snapshot copies one coarse step's tape needs (the same for every step: the
+// pattern depends only on which of a level's two buffers an op touches).
+int count_snapshots(lbm_ctx* c) {
+  const std::vector<char> plan = plan_snapshots(c);
+  return (int)std::count(plan.begin(), plan.end(), 1);
 }
 
 AdjLayout adj_layout(lbm_ctx* c, int64_t n, int K) {
@@ -157,7 +189,7 @@ AdjLayout adj_layout(lbm_ctx* c, int64_t n, int K) {
   L.lamF = take((size_t)c->d * N * 8);
   L.side_fwd = take(c->M.out_elem.size() * lb);
   L.lam_side = take(c->M.out_elem.size() * lb);
-  L.partial = take((size_t)kAdjBlocks * kPartCols * 8);
+  L.partial = take((size_t)kAdjBlocks * kAccCols * 8);
   L.acc = take(32 * 8);
   int64_t max_contrib = 0;
   for (int li = 0; li < c->nlev; ++li) {
@@ -265,20 +297,13 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
     if (s == LBM_OK) s = chk(cudaStreamSynchronize(st), "csr sync");
     if (s != LBM_OK) return s;
   }
-  auto copy_level = [&](const void* from, void* to, int li) {
-    const HostLevel& H = c->M.lv[li];
-    const size_t sb = c->ops->storage_bytes, pitch = N * sb;
-    cudaMemcpy2DAsync(static_cast<char*>(to) + (size_t)H.base * sb, pitch,
-                      static_cast<const char*>(from) + (size_t)H.base * sb, pitch, (size_t)H.N * sb, c->Q,
-                      cudaMemcpyDeviceToDevice, st);
-  };
   auto save_state = [&](char* dst) {
-    for (int li = 0; li < c->nlev; ++li) copy_level(c->cur(li), dst, li);
+    for (int li = 0; li < c->nlev; ++li) copy_level(c, c->cur(li), dst, li);
   };
   auto restore_state = [&](const char* src, const std::vector<int>& par) {
     for (int li = 0; li < c->nlev; ++li) {
       c->parity[li] = par[li];
-      copy_level(src, c->cur(li), li);
+      copy_level(c, src, c->cur(li), li);
     }
   };
   // ---- forward with checkpoints
@@ -304,8 +329,10 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   double* partial = reinterpret_cast<double*>(W + L.partial);
   double* acc = reinterpret_cast<double*>(W + L.acc);
   const void* force = c->force_ptr();
-  auto common = [&](const void* fsrc, void* la, void* lbuf) {
+  auto common = [&](const void* fsrc, void* la, void* lbuf, int acc_la = 0, int acc_lb = -1) {
     AdjCommon cm{};
+    cm.la = acc_la;
+    cm.lb = acc_lb;
     cm.fsrc = fsrc;
     cm.force = force;
     cm.lam_a = la;
@@ -316,10 +343,6 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
     cm.rho_off = c->rho_off;
     cm.rho0 = c->p.rho0;
     return cm;
-  };
-  auto accum = [&](int la, int lbv) {
-    AccumArgs a{partial, kAdjBlocks, acc, acc + 16, la, lbv};
-    launch_accum(a, st);
   };
   for (int li = 0; li < c->nlev; ++li) {
     const HostLevel& H = c->M.lv[li];
@@ -350,15 +373,18 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   const int nseg = L.n_ck;
   for (int seg = nseg - 1; seg >= 0 && s == LBM_OK; --seg) {
     const int64_t s0 = (int64_t)seg * K, s1 = std::min<int64_t>(s0 + K, n);
+    // recompute the segment keeping each step's start state; the last step's
+    // is the live state, which its tape pass starts from directly
     restore_state(W + L.ck + (size_t)seg * L.state_bytes, parity_at[s0]);
-    for (int64_t t = s0; t < s1; ++t) {
+    for (int64_t t = s0; t + 1 < s1; ++t) {
       save_state(W + L.steps + (size_t)(t - s0) * L.state_bytes);
-      if (t + 1 < s1) c->advance(0);
+      c->advance(0);
     }
     for (int64_t t = s1 - 1; t >= s0 && s == LBM_OK; --t) {
-      restore_state(W + L.steps + (size_t)(t - s0) * L.state_bytes, parity_at[t]);
+      if (t + 1 < s1) restore_state(W + L.steps + (size_t)(t - s0) * L.state_bytes, parity_at[t]);
       Recorder r(c);
       r.counting = false;
+      r.need_copy = plan_snapshots(c);
       r.snap_base = W + L.snaps;
       r.state_bytes = L.state_bytes;
       r.max_snaps = L.n_snaps;
@@ -366,7 +392,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
       c->advance(0);
       c->hook = nullptr;
       if (r.overflow) return c->fail(LBM_ERR_INTERNAL, "adjoint tape needs more snapshots than counted");
-      auto snap = [&](int id) { return static_cast<const void*>(W + L.snaps + (size_t)id * L.state_bytes); };
+      if (r.clobbered != r.need_copy) return c->fail(LBM_ERR_INTERNAL, "adjoint tape differs from its plan");
+      auto snap = [&](int id) { return r.where[id]; };
       // forward records of an interface, recomputed from the snapshots
       auto records = [&](int lc, int sa, int sb) {
         const HostLevel& Hc = c->M.lv[lc];
@@ -416,7 +443,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
             c->ops->outlet(c->Q, o, st);
           }
           AdjSCArgs a{};
-          a.c = common(snap(t.snap), lam_for(!p), lam_for(p));
+          a.c = common(snap(t.snap), lam_for(!p), lam_for(p), li);
           a.nbr = c->at<uint32_t>(c->oNbr);
           a.side_fwd = W + L.side_fwd;
           a.lam_side = W + L.lam_side;
@@ -431,11 +458,10 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
           std::memcpy(a.inlet, c->inlet, sizeof(a.inlet));
           a.inlet_s = c->at<double>(c->oInletS);
           aops->sc(c->Q, a, st);
-          accum(li, -1);
           if (outlet) {
             for (int which = 0; which < (c->p.bouzidi ? 6 : 3); ++which) {
               AdjOutletArgs o{};
-              o.c = common(snap(t.snap), nullptr, lam_for(p));
+              o.c = common(snap(t.snap), nullptr, lam_for(p), li);
               o.elem = c->at<int32_t>(c->oOutElem);
               o.a = c->at<int32_t>(c->oOutA);
               o.b = c->at<int32_t>(c->oOutB);
@@ -448,27 +474,25 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
               o.omega = H.omega;
               o.zero_gradient = c->p.outlet == LBM_OUTLET_ZERO_GRADIENT;
               o.q = c->at<double>(c->oOutQ);
-              aops->outlet(c->Q, o, st);
-              if (which == 0) accum(li, -1);  // d/d omega through the normal links' f^neq
+              aops->outlet(c->Q, o, st);  // pass 0 also adds d/d omega through the normal links' f^neq
             }
           }
         } else if (t.op == OP_MOM_A || t.op == OP_MOM_B) {
           if (c->ld[li].nsrc == 0) continue;
           AdjMomArgs a{};
-          a.c = common(snap(t.snap), nullptr, lam_for(t.parity[li]));
+          a.c = common(snap(t.snap), nullptr, lam_for(t.parity[li]), li);
           a.elem = c->at<int32_t>(c->ld[li].src_elem);
           a.lam_rec = W + (t.op == OP_MOM_A ? L.lam_recA[li] : L.lam_recB[li]);
           a.lam_rec_prev = t.op == OP_MOM_B ? W + L.lam_recA[li] : nullptr;
           a.nsrc = c->ld[li].nsrc;
           a.omega = H.omega;
           aops->moments(c->Q, a, st);
-          accum(li, -1);
         } else if (t.op == OP_GFC_A || t.op == OP_GFC_B) {
           if (H.nC == 0) continue;
           const int lc = li - 1;
           const void* rec = records(lc, t.snap_a, t.op == OP_GFC_B ? t.snap_b : -1);
           AdjGfcArgs a{};
-          a.c = common(nullptr, lam_for(t.parity[li]), nullptr);
+          a.c = common(nullptr, lam_for(t.parity[li]), nullptr, lc, li);
           a.rec = rec;
           a.gsrc = c->at<int32_t>(c->ld[li].gfc_src);
           a.oct = c->at<uint8_t>(c->ld[li].gfc_oct);
@@ -478,7 +502,6 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
           a.omega_c = c->M.lv[lc].omega;
           a.omega_f = H.omega;
           aops->gfc(c->Q, a, st);
-          accum(lc, li);
           AdjGatherArgs g{W + L.contrib, reinterpret_cast<const int32_t*>(W + L.csr_off[lc]),
                           reinterpret_cast<const int32_t*>(W + L.csr_item[lc]),
                           W + (t.op == OP_GFC_A ? L.lam_recA[lc] : L.lam_recB[lc]), c->ld[lc].nsrc,
@@ -487,7 +510,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
         } else if (t.op == OP_GFF) {
           if (H.nG1 + H.nG2 == 0) continue;
           AdjGffArgs a{};
-          a.c = common(snap(t.snap), lam_for(t.parity[li]), lam_for(t.parity[li + 1]));
+          a.c = common(snap(t.snap), lam_for(t.parity[li]), lam_for(t.parity[li + 1]), li, li + 1);
           a.child0 = c->at<int32_t>(c->ld[li].gff_child0);
           a.ng = H.nG1 + H.nG2;
           a.n_inner = H.nG1;
@@ -496,7 +519,6 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
           a.omega_c = H.omega;
           a.omega_f = c->M.lv[li + 1].omega;
           aops->gff(c->Q, a, st);
-          accum(li, li + 1);
         }
       }
       s = c->launched("adjoint sweep");
@@ -504,7 +526,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   }
   if (s != LBM_OK) return s;
   // ---- parameter gradients
-  double hacc[32];
+  launch_accum(AccumArgs{partial, kAdjBlocks, acc}, st);
+  double hacc[kAccCols];
   s = chk(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st), "adjoint acc");
   if (s == LBM_OK) s = chk(cudaStreamSynchronize(st), "adjoint sync");
   if (s != LBM_OK) return s;

@@ -191,12 +191,23 @@ __device__ __forceinline__ void bgk_rev(const R* g, R om, R rho_off, const R* F,
   }
 }
 
+// Adds the block's sums to its running row: v[0] to omega of level c.la, v[1]
+// to omega of level c.lb, v[2..4] to u_in.
 template <class R, int NV>
-__device__ __forceinline__ void store_partials(R (&v)[NV], double* partial) {
-  double d[kPartCols];
+__device__ __forceinline__ void store_partials(R (&v)[NV], const AdjCommon& c) {
+  __shared__ double tot[NV];
+  double d[NV];
 #pragma unroll
-  for (int c = 0; c < kPartCols; ++c) d[c] = c < NV ? (double)v[c] : 0.0;
-  block_sum_store<kPartCols>(d, partial + (size_t)blockIdx.x * kPartCols);
+  for (int k = 0; k < NV; ++k) d[k] = (double)v[k];
+  block_sum_store<NV>(d, tot);  // written by thread 0, which also reads them
+  if (threadIdx.x == 0) {
+    double* row = c.partial + (size_t)blockIdx.x * kAccCols;
+    row[c.la] += tot[0];
+    if (NV > 1 && c.lb >= 0) row[c.lb] += tot[NV > 1 ? 1 : 0];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      if (NV > 2 + b) row[16 + b] += tot[NV > 2 + b ? 2 + b : 0];
+  }
 }
 
 template <class R>
@@ -414,7 +425,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
       }
     }
   }
-  store_partials<R, 5>(part, a.c.partial);
+  store_partials<R, 5>(part, a.c);
 }
 
 // ----------------------------------------------------------------- outlet values
@@ -490,7 +501,7 @@ __global__ void __launch_bounds__(256) k_adj_outlet(const AdjOutletArgs a) {
     add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
     part[0] += lom;
   }
-  if (a.which == 0) store_partials<R, 1>(part, a.c.partial);
+  if (a.which == 0) store_partials<R, 1>(part, a.c);
 }
 
 // ----------------------------------------------------------------- source moments
@@ -541,7 +552,7 @@ __global__ void __launch_bounds__(128) k_adj_moments(const AdjMomArgs a) {
     add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
     part[0] += lom;
   }
-  store_partials<R, 1>(part, a.c.partial);
+  store_partials<R, 1>(part, a.c);
 }
 
 // ----------------------------------------------------------------- GhostFromCoarser
@@ -647,7 +658,7 @@ __global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
       for (int f = 0; f < RL::STRIDE; f += 4) st4(out + s * RL::STRIDE + f, v + f);
     }
   }
-  store_partials<R, 2>(part, a.c.partial);
+  store_partials<R, 2>(part, a.c);
 }
 
 template <class R, int MS>
@@ -802,7 +813,7 @@ __global__ void __launch_bounds__(256) k_adj_gff(const AdjGffArgs a) {
     add_force<R>(a.c.lam_force, a.c.Ntot, ec, lF, D);
     part[1] += lom;
   }
-  store_partials<R, 2>(part, a.c.partial);
+  store_partials<R, 2>(part, a.c);
 }
 
 // ----------------------------------------------------------------- launchers

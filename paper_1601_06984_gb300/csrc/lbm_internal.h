@@ -306,10 +306,11 @@ struct Ops {
 
 // ----------------------------------------------------------------- adjoint kernels
 // lam* are adjoint pdf buffers [Q][Ntot] in the compute type; lam_force is
-// [d][Ntot] FP64; partial rows hold per-block sums of parameter derivatives:
-// col 0 d/d omega of level la, col 1 d/d omega of level lb, cols 2..4 d/d u_in.
+// [d][Ntot] FP64; partial holds one running row of parameter derivatives per
+// block (cols 0..15 d/d omega of each level, 16..18 d/d u_in): block b of
+// every launch adds its sums to row b, so the totals are deterministic.
 constexpr int kAdjBlocks = 1024;  // fixed grid of the adjoint kernels (deterministic partials)
-constexpr int kPartCols = 8;
+constexpr int kAccCols = 32;
 
 struct AdjCommon {
   const void* fsrc;   // forward state the op read (full [Q][Ntot] snapshot, storage type)
@@ -317,9 +318,10 @@ struct AdjCommon {
   void* lam_a;        // adjoint buffer the op's outputs live in (consumed, zeroed)
   void* lam_b;        // adjoint buffer of the op's inputs (accumulated)
   double* lam_force;  // [d][Ntot] FP64 accumulated (null: not wanted)
-  double* partial;    // [kAdjBlocks][kPartCols]
+  double* partial;    // [kAdjBlocks][kAccCols] running sums
   int64_t Ntot;
   double rho_off, rho0;
+  int la, lb;         // levels whose omega the launch's first / second sums belong to (lb < 0: none)
 };
 
 struct AdjSCArgs {
@@ -397,11 +399,9 @@ struct AdjSeedArgs {
 };
 
 struct AccumArgs {
-  const double* partial;
+  const double* partial;  // [rows][kAccCols]
   int rows;
-  double* acc_omega;  // [16]
-  double* acc_uin;    // [3]
-  int la, lb;
+  double* acc;            // [kAccCols] column sums (assigned)
 };
 
 struct AdjOps {
@@ -418,6 +418,10 @@ const AdjOps* adj_ops_fp32dev();
 const AdjOps* adj_ops_bf16dev();
 void launch_adj_gather(bool fp64, const AdjGatherArgs&, cudaStream_t);
 void launch_accum(const AccumArgs&, cudaStream_t);
+// Copies bytes [off, off + len) of each of `rows` rows of pitch `pitch` from
+// src to dst (same layout); elem is the element size the offsets are multiples of.
+void launch_copy_rows(const void* src, void* dst, size_t pitch, size_t off, size_t len, int rows, size_t elem,
+                      cudaStream_t);
 void launch_gather_lam_user(bool fp64, const void* lamA, const void* lamB, uint32_t parity, const int32_t* uslot,
                             const uint8_t* ulev, double* stage, int64_t first, int64_t cnt, int64_t Ntot, int Q,
                             cudaStream_t);
