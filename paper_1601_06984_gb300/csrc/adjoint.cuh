@@ -210,10 +210,25 @@ __device__ __forceinline__ void store_partials(R (&v)[NV], const AdjCommon& c) {
   }
 }
 
+// Read-modify-writes below issue every load before the first store: the
+// compiler cannot tell that rows q N + e of one array are distinct, and would
+// otherwise wait for each load in turn.
 template <class R>
 __device__ __forceinline__ void add_force(double* lam_force, int64_t Ntot, int64_t e, const R* lF, int D) {
   if (!lam_force) return;
-  for (int b = 0; b < D; ++b) lam_force[(size_t)b * Ntot + e] += (double)lF[b];
+  double cur[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < D; ++b) cur[b] = lam_force[(size_t)b * Ntot + e];
+  for (int b = 0; b < D; ++b) lam_force[(size_t)b * Ntot + e] = cur[b] + (double)lF[b];
+}
+
+// lam[q N + e] += v[q] for q < Q
+template <int Q, class R>
+__device__ __forceinline__ void add_rows(R* lam, size_t N, int64_t e, const R* v) {
+  R cur[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) cur[q] = lam[(size_t)q * N + e];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) lam[(size_t)q * N + e] = cur[q] + v[q];
 }
 
 template <class S, class R>
@@ -254,13 +269,15 @@ __global__ void __launch_bounds__(256) k_adj_seed(const AdjSeedArgs a) {
         usq += u[b] * u[b];
       }
       const R vol = R(a.vol);
+      R v[Q];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         R cu = R(0);
 #pragma unroll
         for (int b = 0; b < D; ++b) cu += R(LT::c(q, b)) * u[b];
-        lam[(size_t)q * N + e] += vol * (cu - R(0.5) * usq);
+        v[q] = vol * (cu - R(0.5) * usq);
       }
+      add_rows<Q, R>(lam, N, e, v);
       R lF[3];
 #pragma unroll
       for (int b = 0; b < D; ++b) lF[b] = -R(0.5) * vol * u[b];
@@ -311,8 +328,8 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   const S* __restrict__ x = static_cast<const S*>(a.c.fsrc);
-  R* lam_out = static_cast<R*>(a.c.lam_a);
-  R* lam_in = static_cast<R*>(a.c.lam_b);
+  R* __restrict__ lam_out = static_cast<R*>(a.c.lam_a);
+  R* __restrict__ lam_in = static_cast<R*>(a.c.lam_b);
   const size_t N = (size_t)a.c.Ntot;
   const R om = R(a.omega), rho_off = R(a.c.rho_off);
   R part[5] = {R(0), R(0), R(0), R(0), R(0)};
@@ -357,30 +374,56 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
       uF += u[b] * F[b];
     }
     const R fpre = R(1) - R(0.5) * om;
-    R S0 = R(0), Sa[3] = {R(0), R(0), R(0)}, lF[3] = {R(0), R(0), R(0)}, lom = R(0);
+    // every sum over i below is linear in P_i = w_i lam_i with polynomial
+    // weights of degree <= 2 in c_i, so it is a combination of the moments
+    // M0 = sum P_i, M1_a = sum P_i c_ia, M2_ab = sum P_i c_ia c_ib
+    R M0 = R(0), M1[3] = {R(0), R(0), R(0)}, M2[3][3] = {}, lg_dot = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      R cu = R(0), cF = R(0);
+      const R P = R(LT::w(i)) * lo[i];
+      lg_dot += lo[i] * g[i];
+      M0 += P;
 #pragma unroll
       for (int b = 0; b < D; ++b) {
-        cu += R(LT::c(i, b)) * u[b];
-        cF += R(LT::c(i, b)) * F[b];
-      }
-      const R w = R(LT::w(i));
-      const R Ai = w * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
-      const R geqi = w * (rp + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
-      const R Gi = w * (R(3) * (cF - uF) + R(9) * cu * cF);
-      const R l = lo[i];
-      S0 += l * Ai;
-      lom += l * (geqi - g[i] - R(0.5) * Gi);
+        if (LT::c(i, b) > 0) M1[b] += P;
+        if (LT::c(i, b) < 0) M1[b] -= P;
 #pragma unroll
-      for (int b = 0; b < D; ++b) {
-        const R cb = R(LT::c(i, b));
-        const R Bib = w * rho * (R(3) * cb + R(9) * cu * cb - R(3) * u[b]);
-        const R Gib = fpre * w * (-R(3) * F[b] + R(9) * cb * cF);
-        Sa[b] += l * (om * Bib + Gib);
-        lF[b] += l * fpre * w * (R(3) * (cb - u[b]) + R(9) * cu * cb);
+        for (int c = b; c < D; ++c) {
+          const int cc = LT::c(i, b) * LT::c(i, c);
+          if (cc > 0) M2[b][c] += P;
+          if (cc < 0) M2[b][c] -= P;
+        }
       }
+    }
+    R M2u[3] = {R(0), R(0), R(0)}, M2F[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const R m = b <= c ? M2[b][c] : M2[c][b];
+        M2u[b] += m * u[c];
+        M2F[b] += m * F[c];
+      }
+    R uM1 = R(0), FM1 = R(0), uM2u = R(0), uM2F = R(0);
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      uM1 += u[b] * M1[b];
+      FM1 += F[b] * M1[b];
+      uM2u += u[b] * M2u[b];
+      uM2F += u[b] * M2F[b];
+    }
+    // sum lam_i A_i, sum lam_i g^eq_i, sum lam_i Guo_i
+    const R quad = R(3) * uM1 + R(4.5) * uM2u - R(1.5) * usq * M0;
+    const R S0 = M0 + quad;
+    const R sum_geq = rp * M0 + rho * quad;
+    const R sum_G = R(3) * (FM1 - uF * M0) + R(9) * uM2F;
+    const R lom = sum_geq - lg_dot - R(0.5) * sum_G;
+    R Sa[3] = {R(0), R(0), R(0)}, lF[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const R lin = R(3) * M1[b] + R(9) * M2u[b] - R(3) * u[b] * M0;  // sum lam_i B_ib / rho
+      Sa[b] = om * rho * lin + fpre * (R(9) * M2F[b] - R(3) * F[b] * M0);
+      lF[b] = fpre * lin;
     }
 #pragma unroll
     for (int b = 0; b < D; ++b) lF[b] += R(0.5) * Sa[b] * inv;
@@ -389,12 +432,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
     R base = om * S0;
 #pragma unroll
     for (int b = 0; b < D; ++b) base -= Sa[b] * u[b] * inv;
-    // reverse streaming (second phase: indices and output adjoints reloaded,
-    // both coalesced, so they need not stay live through the reductions)
-#pragma unroll
-    for (int i = 1; i < Q; ++i) nb[i] = __ldg(a.nbr + (size_t)(i - 1) * N + e);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) lo[i] = lam_out[(size_t)i * N + e];
+    // reverse streaming
     auto target = [&](int i) -> size_t {
       const uint32_t n = nb[i];
       return i == 0 ? (size_t)e : (n < NB_FLAG30 ? (size_t)i * N + n : (size_t)opp(i) * N + (size_t)e);
@@ -496,8 +534,7 @@ __global__ void __launch_bounds__(256) k_adj_outlet(const AdjOutletArgs a) {
 #pragma unroll
     for (int s2 = 0; s2 < NS; ++s2) lS[s2] = R(0);
     post_moments_rev<Q, R>(g, R(a.omega), R(a.c.rho_off), F, R(0), lam_u, lfn, lS, lg, lF, lom);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) lam_in[(size_t)q * N + e] += lg[q];
+    add_rows<Q, R>(lam_in, N, e, lg);
     add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
     part[0] += lom;
   }
@@ -517,20 +554,28 @@ __global__ void __launch_bounds__(128) k_adj_moments(const AdjMomArgs a) {
   R part[1] = {R(0)};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.nsrc; k += stride) {
-    R* lr = static_cast<R*>(a.lam_rec) + (size_t)k * RL::STRIDE;
+    R* __restrict__ lr = static_cast<R*>(a.lam_rec) + (size_t)k * RL::STRIDE;
     R rec[RL::STRIDE];
 #pragma unroll
-    for (int f = 0; f < RL::STRIDE; ++f) {
-      rec[f] = lr[f];
-      lr[f] = R(0);
-    }
+    for (int f = 0; f < RL::STRIDE; f += 4) ld4(lr + f, rec + f);
     if (a.lam_rec_prev) {
-      R* lp = static_cast<R*>(a.lam_rec_prev) + (size_t)k * RL::STRIDE;
+      // the record at t+1/2 is the mean of those at t and t+1
+      R* __restrict__ lp = static_cast<R*>(a.lam_rec_prev) + (size_t)k * RL::STRIDE;
+      R pv[RL::STRIDE];
+#pragma unroll
+      for (int f = 0; f < RL::STRIDE; f += 4) ld4(lp + f, pv + f);
 #pragma unroll
       for (int f = 0; f < RL::STRIDE; ++f) {
         rec[f] *= R(0.5);
-        lp[f] += rec[f];
+        pv[f] += rec[f];
       }
+#pragma unroll
+      for (int f = 0; f < RL::STRIDE; f += 4) st4(lp + f, pv + f);
+    }
+    {
+      R z[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+      for (int f = 0; f < RL::STRIDE; f += 4) st4(lr + f, z);
     }
     const int64_t e = a.elem[k];
     R g[Q];
@@ -547,8 +592,7 @@ __global__ void __launch_bounds__(128) k_adj_moments(const AdjMomArgs a) {
     for (int b = 0; b < D; ++b) lu[b] = rec[RL::U + b];
     R lg[Q], lF[3] = {R(0), R(0), R(0)}, lom = R(0);
     post_moments_rev<Q, R>(g, R(a.omega), R(a.c.rho_off), F, rec[RL::RP], lu, lfn, lS, lg, lF, lom);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) lam_in[(size_t)q * N + e] += lg[q];
+    add_rows<Q, R>(lam_in, N, e, lg);
     add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
     part[0] += lom;
   }
@@ -562,7 +606,7 @@ __global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
   constexpr int D = LT::D, NS = LT::NS;
-  R* lam = static_cast<R*>(a.c.lam_a);
+  R* __restrict__ lam = static_cast<R*>(a.c.lam_a);
   const R* __restrict__ mom = static_cast<const R*>(a.rec);
   const size_t N = (size_t)a.c.Ntot;
   R part[2] = {R(0), R(0)};
@@ -602,16 +646,22 @@ __global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
     const R wf = R(a.omega_f), wc = R(a.omega_c);
     const R scale = (R(1) - wf) * wc / (R(2) * wf);
     const int64_t e = a.dest0 + k;
+    // all loads before the ghost's adjoint is zeroed, so that they overlap
     R lo[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lo[q] = lam[(size_t)q * N + e];
     R lam_scale = R(0);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      lo[q] = lam[(size_t)q * N + e];
-      lam[(size_t)q * N + e] = R(0);
-      const R fn = lw[0] * rec[0][RL::FN + q] + lw[1] * rec[1][RL::FN + q] + lw[2] * rec[2][RL::FN + q] +
-                   lw[3] * rec[3][RL::FN + q];
-      lam_scale += lo[q] * fn;
+    for (int q0 = 0; q0 < Q; q0 += 4) {
+      R f[4][4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) ld4(rec[s] + RL::FN + q0, f[s]);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (q0 + t < Q) lam_scale += lo[q0 + t] * (lw[0] * f[0][t] + lw[1] * f[1][t] + lw[2] * f[2][t] + lw[3] * f[3][t]);
     }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) lam[(size_t)q * N + e] = R(0);
     part[0] += lam_scale * (R(1) - wf) / (R(2) * wf);  // d scale / d omega_c
     part[1] += lam_scale * (-wc / (R(2) * wf * wf));    // d scale / d omega_f
     R lam_rp = R(0), lam_u[3] = {R(0), R(0), R(0)};
@@ -639,7 +689,7 @@ __global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
         lSl[s][c] = o[0] * lam_uloc[0] + o[1] * lam_uloc[1] + o[2] * lam_uloc[2];
       }
     }
-    R* out = static_cast<R*>(a.contrib) + (size_t)k * 4 * RL::STRIDE;
+    R* __restrict__ out = static_cast<R*>(a.contrib) + (size_t)k * 4 * RL::STRIDE;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       R v[RL::STRIDE];
@@ -691,8 +741,9 @@ __global__ void __launch_bounds__(256) k_adj_gff(const AdjGffArgs a) {
   using LT = Lat<Q>;
   constexpr int D = LT::D, NS = LT::NS, NCH = 1 << D;
   const S* __restrict__ x = static_cast<const S*>(a.c.fsrc);
-  R* lam_c = static_cast<R*>(a.c.lam_a);
-  R* lam_f = static_cast<R*>(a.c.lam_b);
+  // coarse ghosts and fine children: disjoint slots, possibly of one buffer
+  R* __restrict__ lam_c = static_cast<R*>(a.c.lam_a);
+  R* __restrict__ lam_f = static_cast<R*>(a.c.lam_b);
   const size_t N = (size_t)a.c.Ntot;
   const R wf = R(a.omega_f), wc = R(a.omega_c), rho_off = R(a.c.rho_off);
   R part[2] = {R(0), R(0)};
@@ -808,8 +859,7 @@ __global__ void __launch_bounds__(256) k_adj_gff(const AdjGffArgs a) {
     for (int q = 0; q < Q; ++q) lfn[q] = scale * lo[q];
     R lg[Q], lF[3] = {R(0), R(0), R(0)}, lom = R(0);
     post_moments_rev<Q, R>(g, wf, rho_off, F, lam_rpm * inv, lu, lfn, lS, lg, lF, lom);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) lam_f[(size_t)q * N + ec] += lg[q];
+    add_rows<Q, R>(lam_f, N, ec, lg);
     add_force<R>(a.c.lam_force, a.c.Ntot, ec, lF, D);
     part[1] += lom;
   }
