@@ -160,6 +160,37 @@ def test_adjoint_matches_central_differences(lbm, name, mode):
     assert abs(adj - fd) <= 1e-5 * abs(fd)
 
 
+# Reduced-precision adjoints against the FP64 adjoint of the same inputs.  The
+# FP32-deviation path rounds every stored pdf and adjoint to FP32 (unit
+# roundoff 6e-8) over a handful of steps, so 1e-4 relative leaves a wide
+# margin; BF16 storage rounds the stored deviations to 8 significant bits
+# (2^-9 = 2e-3 relative) and the gradient inherits errors of that order, so
+# 3e-2.  The cases cover both time modes, K not dividing n, and the inlet,
+# outlet and obstacle paths of the small sphere.
+@pytest.mark.parametrize("prec,tol", [("fp32dev", 1e-4), ("bf16dev", 3e-2)])
+@pytest.mark.parametrize("name,mode,objective", [("tgv3d", 0, 0), ("tgv2d", 1, 0), ("sphere", 0, 0), ("sphere", 0, 1)])
+def test_adjoint_reduced_precision(lbm, prec, tol, name, mode, objective):
+    m, Q, om, uin, fields, n, K = make(name)
+    rho, u, S = fields(m)
+    F = W.gaussian_force(m, 1e-5)
+    res = {}
+    for p in ("fp64", prec):
+        g = lbm.Sim(m, Q, om, precision={"fp64": lbm.FP64, "fp32dev": lbm.FP32DEV, "bf16dev": lbm.BF16DEV}[p],
+                    time_mode=mode, u_in=uin, use_force=True)
+        g.init(rho, u, S)
+        g.set_force(F)
+        res[p] = g.adjoint(n + 1, K, objective)
+        g.close()
+    (J0, dF0, dw0, dU0), (J1, dF1, dw1, dU1) = res["fp64"], res[prec]
+    err = {"J": abs(J1 - J0) / abs(J0),
+           "dF": float(np.linalg.norm(dF1 - dF0) / np.linalg.norm(dF0)),
+           "dw": abs(dw1 - dw0) / abs(dw0)}
+    if np.any(np.asarray(uin) != 0):
+        # the drag of the small sphere after a few steps does not depend on u_in yet
+        err["dU"] = float(np.linalg.norm(dU1 - dU0) / max(np.linalg.norm(dU0), 1e-12 * abs(J0)))
+    assert all(v <= tol for v in err.values()), err
+
+
 def test_adjoint_leaves_final_state_and_is_deterministic(lbm):
     m, Q, om, uin, fields, n, K = make("sphere")
     rho, u, S = fields(m)
