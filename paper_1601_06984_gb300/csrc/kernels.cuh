@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
 // element's neighbour-list code like k_stream_collide: a pull, the element's
 // own opposite slot (bounce-back), plus the inlet term, or a boundary value.
 template <int Q, class S, bool FORCE, bool BND>
-__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? 3 : LBM_BR_MINB) k_stream_collide_brick(const BrickArgs a) {
+__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? 4 : LBM_BR_MINB) k_stream_collide_brick(const BrickArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -669,22 +669,70 @@ __device__ __forceinline__ void compact_uloc(const R (&ul)[4][3], const R (&Sl)[
 // linear (weights 5/8,1/8,1/8,1/8 resp. 9/16,3/16,3/16,1/16), f^neq is
 // rescaled by omega_c / (m omega_f), and f = f^eq + (1 - omega_f) f^neq is
 // stored as the ghost's post-collision state.
+// Ghosts come in groups of 2^d consecutive siblings (the children of one
+// coarse parent, octant b = k mod 2^d), and their 4 x 2^d source records are
+// 13 distinct ones in 3D (the parent and its 12 edge neighbours), 9 in 2D.  A
+// group's lanes stage those records in shared memory with whole-record vector
+// loads (one cache line per record), then each lane reads its four sources
+// from there.
+template <int D>
+struct GfcGroup {
+  static constexpr int G = 1 << D;           // lanes (siblings) per group
+  static constexpr int NSLOT = D == 3 ? 13 : 9;
+  // slot of source s (0: parent, 1-3 as in gsrc) for the sibling in octant b
+  __device__ static int slot(int s, int b) {
+    if (D == 3) return s == 0 ? 0 : s == 1 ? 1 + (b & 3) : s == 2 ? 5 + ((b & 1) | ((b >> 1) & 2)) : 9 + ((b >> 1) & 3);
+    return s == 0 ? 0 : s == 1 ? 1 + (b & 1) : s == 2 ? 3 + ((b >> 1) & 1) : 5 + (b & 3);
+  }
+  // the (source, sibling) pair whose gsrc entry names slot t
+  __host__ __device__ static constexpr int src_of(int t) { return t == 0 ? 0 : D == 3 ? 1 + (t - 1) / 4 : (t < 3 ? 1 : t < 5 ? 2 : 3); }
+  __host__ __device__ static constexpr int lane_of(int t) {
+    return D == 3 ? (t == 0 ? 0 : t < 5 ? t - 1 : t < 9 ? ((t - 5) & 1) | (((t - 5) & 2) << 1) : (t - 9) << 1)
+                  : (t == 0 ? 0 : t < 3 ? t - 1 : t < 5 ? (t - 3) << 1 : t - 5);
+  }
+};
+
+#define LBM_GFC_BLOCK 64
 template <int Q, class S>
-__global__ void __launch_bounds__(128) k_fill_gfc(const GfcArgs a) {
+__global__ void __launch_bounds__(LBM_GFC_BLOCK) k_fill_gfc(const GfcArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
-  constexpr int D = LT::D, NS = LT::NS;
+  using GG = GfcGroup<LT::D>;
+  constexpr int D = LT::D, NS = LT::NS, G = GG::G, NSLOT = GG::NSLOT;
+  constexpr int PSTR = RL::STRIDE + 4;  // padded record: sibling lanes' reads fall in distinct banks
+  constexpr int NGRP = LBM_GFC_BLOCK / G;
+  __shared__ __align__(16) R stage[NGRP * NSLOT * PSTR];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.ng) return;
+  const int oct = threadIdx.x & (G - 1);  // octant of the ghost
+  const int grp = threadIdx.x / G;
+  const bool active = k < a.ng;                   // ng is a multiple of G: whole groups
+  const unsigned lane0 = (threadIdx.x & 31) & ~(unsigned)(G - 1);
+  int32_t src[4] = {0, 0, 0, 0};
+  if (active)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) src[s] = a.gsrc[(size_t)s * a.ng + k];
   const R* __restrict__ mom = static_cast<const R*>(a.mom);
+  R* sg_base = stage + grp * NSLOT * PSTR;
+#pragma unroll
+  for (int t = 0; t < NSLOT; ++t) {
+    const int r = __shfl_sync(0xffffffffu, src[GG::src_of(t)], lane0 + GG::lane_of(t));
+    if (active)
+#pragma unroll
+      for (int c = oct; c < RL::STRIDE / 4; c += G) {
+        R v[4];
+        ld4(mom + (size_t)r * RL::STRIDE + 4 * c, v);
+        st4(sg_base + t * PSTR + 4 * c, v);
+      }
+  }
+  __syncwarp();
+  if (!active) return;
   const R* rec[4];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) rec[s] = mom + (size_t)a.gsrc[(size_t)s * a.ng + k] * RL::STRIDE;
-  const uint8_t oct = a.oct[k];
+  for (int s = 0; s < 4; ++s) rec[s] = sg_base + GG::slot(s, oct) * PSTR;
   R sg[3];
 #pragma unroll
-  for (int b = 0; b < 3; ++b) sg[b] = ((oct >> b) & 1) ? R(1) : R(-1);
+  for (int c = 0; c < 3; ++c) sg[c] = ((oct >> c) & 1) ? R(1) : R(-1);
   // local-frame velocity and strain rate of the sources (vector loads of the
   // record tail: rho, u, S)
   R ul[4][3], Sl[4][NS], rps[4];
@@ -1099,7 +1147,9 @@ struct Launch {
   }
   static void fill_gfc(int Q, const GfcArgs& a, cudaStream_t st) {
     if (a.ng <= 0) return;
-    with_q(Q, [&](auto q) { k_fill_gfc<decltype(q)::value, S><<<blocks_for(a.ng, 128), 128, 0, st>>>(a); });
+    with_q(Q, [&](auto q) {
+      k_fill_gfc<decltype(q)::value, S><<<blocks_for(a.ng, LBM_GFC_BLOCK), LBM_GFC_BLOCK, 0, st>>>(a);
+    });
   }
   static void fill_gff(int Q, const GffArgs& a, cudaStream_t st) {
     if (a.ng <= 0) return;

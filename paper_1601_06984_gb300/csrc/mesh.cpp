@@ -684,6 +684,19 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     H.gfc_src.resize(4 * H.nC);
     for (int64_t k = 0; k < H.nC; ++k)
       for (int s = 0; s < 4; ++s) H.gfc_src[s * H.nC + k] = pos[local[4 * k + s]];
+    // the fill kernel takes the ghosts in sibling groups (octant = k mod 2^d)
+    // whose sources depend only on the octant bits along their offsets
+    const int G = 1 << d;
+    if (H.nC % G) return bad(LBM_ERR_INTERNAL, "GhostFromCoarser ghosts not in complete sibling groups");
+    for (int64_t k = 0; k < H.nC; ++k) {
+      const int b = (int)(k % G);
+      const int64_t k0 = k - b;
+      // the sibling with the same bits along each source's offset and zeros elsewhere
+      const int canon[4] = {0, d == 3 ? (b & 3) : (b & 1), d == 3 ? (b & 5) : (b & 2), d == 3 ? (b & 6) : (b & 3)};
+      bool ok = H.gfc_oct[k] == b;
+      for (int s = 0; s < 4 && ok; ++s) ok = H.gfc_src[s * H.nC + k] == H.gfc_src[s * H.nC + k0 + canon[s]];
+      if (!ok) return bad(LBM_ERR_INTERNAL, "GhostFromCoarser sibling group inconsistent");
+    }
   }
 
   // ---- pull neighbour lists (Sec. 2.1) with boundary rules (Sec. 2.3)
