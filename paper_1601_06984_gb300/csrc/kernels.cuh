@@ -390,8 +390,11 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
 // link is not complete; those links (row entry kBrickMissing) take the
 // element's neighbour-list code like k_stream_collide: a pull, the element's
 // own opposite slot (bounce-back), plus the inlet term, or a boundary value.
+// Four blocks per SM (64 registers) where that fits without spills: D3Q19 and
+// D2Q9 with 4-byte or narrower storage; three otherwise.
+#define LBM_BR_BND_MINB(Q, S) ((Q) > 19 || sizeof(S) > 4 ? 3 : 4)
 template <int Q, class S, bool FORCE, bool BND>
-__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? 4 : LBM_BR_MINB) k_stream_collide_brick(const BrickArgs a) {
+__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : LBM_BR_MINB) k_stream_collide_brick(const BrickArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
