@@ -61,8 +61,8 @@ def test_mesh_counts_match_oracle(lbm, oracle_mod, name, make, Q, omega, mode):
     assert s.ghost_count() == int(oc[:, 2].sum() + oc[:, 3].sum())
 
 
-def test_config1_counts(lbm):
-    """Config-1 figures: 768 coarse and 1024 fine fluid elements, 272 fine
+def test_tgv2d_two_level_counts(lbm):
+    """Two-level 32x32 mesh with a refined 16x16 block: 768 coarse and 1024 fine fluid elements, 272 fine
     GhostFromCoarser, 60 coarse GhostFromFiner (112 with the second layer)."""
     mesh = W.config_tgv2d()
     lin = lbm.Sim(mesh, 9, 1.6, time_mode=0, device=None).mesh_info()

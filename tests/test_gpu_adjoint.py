@@ -231,8 +231,8 @@ def test_autograd_function(lbm):
     assert w.grad is not None and torch.isfinite(w.grad)
 
 
-def test_adjoint_full_size_config5(lbm):
-    """The adjoint configuration at full size: periodic 64^3 coarse with the
+def test_adjoint_full_size_tgv3d_64(lbm):
+    """Two-level Taylor-Green mesh at full size: periodic 64^3 coarse with the
     central 32^3 block refined, Gaussian body force N(0, 1e-6), 400 coarse
     steps, kinetic energy, checkpoints every 20 steps (FP64): the gradient
     along a random force direction and along omega matches central

@@ -251,7 +251,7 @@ def test_user_order_does_not_matter(oracle_mod):
 
 
 # ---------------------------------------------------------------- closed-form flows
-def test_tgv_config1_decay(oracle_mod):
+def test_tgv2d_two_level_decay(oracle_mod):
     """Sec. 4.1 Eq. (tgv): on the two-level 32x32 / 16x16-block mesh with
     u0=0.01, omega_c=1.6 (nu_c=1/24), the velocity amplitude after 200 coarse
     steps follows exp(-2 nu k^2 t) with k = 2 pi / 32 (about 0.526)."""
