@@ -611,19 +611,19 @@ __global__ void __launch_bounds__(128) k_source_moments(const MomentsArgs a) {
   for (int b = 0; b < D; ++b) rec[RL::U + b] = u[b];
 #pragma unroll
   for (int s = 0; s < NS; ++s) rec[RL::SS + s] = Sv[s];
-  R* out = static_cast<R*>(a.mom) + (size_t)k * RL::STRIDE;
-  const R* prev = a.prev ? static_cast<const R*>(a.prev) + (size_t)k * RL::STRIDE : nullptr;
+  R* __restrict__ out = static_cast<R*>(a.mom) + (size_t)k * RL::STRIDE;
+  if (a.prev) {
+    // the whole previous record is read before the first store (the compiler
+    // cannot tell the two records apart and would otherwise serialise them)
+    const R* __restrict__ prev = static_cast<const R*>(a.prev) + (size_t)k * RL::STRIDE;
+    R pv[RL::STRIDE];
 #pragma unroll
-  for (int f = 0; f < RL::STRIDE; f += 4) {
-    if (f >= RL::END) break;
-    if (prev) {
-      R pv[4];
-      ld4(prev + f, pv);
+    for (int f = 0; f < RL::END; f += 4) ld4(prev + f, pv + f);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) rec[f + c] = R(0.5) * (pv[c] + rec[f + c]);
-    }
-    st4(out + f, rec + f);
+    for (int f = 0; f < RL::END; ++f) rec[f] = R(0.5) * (pv[f] + rec[f]);
   }
+#pragma unroll
+  for (int f = 0; f < RL::END; f += 4) st4(out + f, rec + f);
 }
 
 // Compact quadratic velocity at the ghost in the octant's local frame, a linear
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(LBM_GFC_BLOCK) k_fill_gfc(const GfcArgs a) {
 // m omega_f / omega_c; f = f^eq + (1 - omega_c) f^neq.
 // One group of 2^d consecutive lanes per ghost: lane b loads child b (siblings
 // are contiguous, so the group's loads are coalesced), and the sums over the
-// children are butterfly shuffles inside the group.
+// children are shuffles inside the group.
 template <int Q, class S>
 __global__ void __launch_bounds__(256) k_fill_gff(const GffArgs a) {
   using R = typename Sto<S>::R;
@@ -830,43 +830,57 @@ __global__ void __launch_bounds__(256) k_fill_gff(const GffArgs a) {
       for (int c = 0; c < D; ++c) F[c] = static_cast<const R*>(a.force)[(size_t)c * N + e];
     post_moments<Q, R, true>(g, wf, rho_off, F, rp, u, fneq, Sv);
   }
-  // signed strain rates for the derivatives across the children's cube
-  R dS[3][NS];
-#pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const R sgn = ((b >> c) & 1) ? R(1) : R(-1);
-#pragma unroll
-    for (int s = 0; s < NS; ++s) dS[c][s] = sgn * Sv[s];
-  }
-  // butterfly sums over the NCH lanes of the group (all lanes take part)
-#pragma unroll
-  for (int o = 1; o < NCH; o <<= 1) {
-    rp += __shfl_xor_sync(0xffffffffu, rp, o);
-#pragma unroll
-    for (int c = 0; c < D; ++c) u[c] += __shfl_xor_sync(0xffffffffu, u[c], o);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) fneq[q] += __shfl_xor_sync(0xffffffffu, fneq[q], o);
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int s = 0; s < NS; ++s) dS[c][s] += __shfl_xor_sync(0xffffffffu, dS[c][s], o);
-  }
-  if (!active) return;
-  const R inv = R(1) / R(NCH);
+  // The ghost's velocity, mean minus (1/32) lap u, is linear in the children's
+  // values, and so is lap u_a = dfac sum_c (2 d_c S_ac - d_a S_cc) with d_c the
+  // difference across the cube (+ for children with bit c set, - otherwise):
+  // each lane forms its child's share and the group sums d + 1 values.
   // d_c S (coarse units): S_coarse = 2 S_fine; difference of the two half-cubes
   // over a distance of 1/2 coarse cell -> factor 2 * 2^{2-D}
+  const R inv = R(1) / R(NCH);
   const R dfac = R(2) * R(D == 3 ? 0.5 : 1.0);
-  const R rpm = rp * inv;
-  R uP[3] = {R(0), R(0), R(0)};
-  R usq = R(0);
+  R rpm = rp * inv, uP[3] = {R(0), R(0), R(0)};
 #pragma unroll
   for (int aa = 0; aa < D; ++aa) {
+    const R sa = ((b >> aa) & 1) ? R(1) : R(-1);
     R lap = R(0);
 #pragma unroll
-    for (int c = 0; c < D; ++c) lap += dfac * (R(2) * dS[c][sidx<D>(aa, c)] - dS[aa][sidx<D>(c, c)]);
+    for (int c = 0; c < D; ++c) {
+      const R sc = ((b >> c) & 1) ? R(1) : R(-1);
+      lap += dfac * (R(2) * sc * Sv[sidx<D>(aa, c)] - sa * Sv[sidx<D>(c, c)]);
+    }
     uP[aa] = u[aa] * inv - lap * R(1.0 / 32.0);
-    usq += uP[aa] * uP[aa];
   }
+#pragma unroll
+  for (int o = 1; o < NCH; o <<= 1) {
+    rpm += __shfl_xor_sync(0xffffffffu, rpm, o);
+#pragma unroll
+    for (int c = 0; c < D; ++c) uP[c] += __shfl_xor_sync(0xffffffffu, uP[c], o);
+  }
+  // f^neq: reduce-scatter (recursive halving), lane b ends with the sums for
+  // q = j 2^d + b; at half-width h a lane keeps the half of its columns on its
+  // side of bit h and receives its partner's partial sums of that half
+  constexpr int NR = (Q + NCH - 1) / NCH;
+  R W[NR][NCH];
+#pragma unroll
+  for (int j = 0; j < NR; ++j)
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) W[j][c] = j * NCH + c < Q ? fneq[j * NCH + c] : R(0);
+#pragma unroll
+  for (int h = NCH / 2; h >= 1; h >>= 1) {
+    const bool hi = (b & h) != 0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+#pragma unroll
+      for (int c = 0; c < h; ++c) {
+        const R send = hi ? W[j][c] : W[j][c + h];
+        const R keep = hi ? W[j][c + h] : W[j][c];
+        W[j][c] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+      }
+  }
+  if (!active) return;
+  R usq = R(0);
+#pragma unroll
+  for (int aa = 0; aa < D; ++aa) usq += uP[aa] * uP[aa];
   const R wc = R(a.omega_c);
   const R rho = rho_off + rpm;
   const R scale = (R(1) - wc) * R(2) * wf / wc * inv;
@@ -875,7 +889,7 @@ __global__ void __launch_bounds__(256) k_fill_gff(const GffArgs a) {
   // the group's lanes share the Q stores
 #pragma unroll
   for (int q = 0; q < Q; ++q)
-    if (q % NCH == b) dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rpm, rho, uP, usq) + scale * fneq[q]);
+    if (q % NCH == b) dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rpm, rho, uP, usq) + scale * W[q / NCH][0]);
 }
 
 // ----------------------------------------------------------------- set-up (compute type) / output (FP64)
