@@ -39,6 +39,7 @@ struct AdjLayout {
   size_t ck = 0, steps = 0, snaps = 0, fin = 0;
   int n_ck = 0, n_steps = 0, n_snaps = 0;
   size_t state_bytes = 0, total = 0;
+  int partial_rows = 0;  // running rows of the parameter sums: the largest grid of a reverse launch
 };
 
 // Copies the rows of level li's segment of a [Q][Ntot] state.
@@ -53,7 +54,9 @@ void copy_level(lbm_ctx* c, const void* from, void* to, int li) {
 // by (level, version); the version of a level is bumped by every op that
 // writes it.  A state that no later op of the step overwrites (its buffer
 // keeps it until the next restore) is read in place; the others are copied to
-// the snapshot store when they are first read.
+// the snapshot store when they are first read.  A copy fills only its level's
+// segment of a full-size slot, so copies of different levels share slots: the
+// k-th copy of every level goes to slot k.
 struct Recorder {
   lbm_ctx* c;
   bool counting = true;
@@ -68,7 +71,8 @@ struct Recorder {
   int last_mom_a_snap[16], last_mom_b_snap[16];
   char* snap_base = nullptr;
   size_t state_bytes = 0;
-  int max_snaps = 0, n_copies = 0;
+  int max_snaps = 0;
+  int n_copies[16] = {};                       // copies taken so far, per level
   bool overflow = false;
 
   explicit Recorder(lbm_ctx* ctx) : c(ctx), version(ctx->nlev, 0) {
@@ -76,7 +80,6 @@ struct Recorder {
     std::fill(last_mom_b_snap, last_mom_b_snap + 16, -1);
   }
 
-  int copies_needed() const { return (int)std::count(clobbered.begin(), clobbered.end(), 1); }
 
   void wrote(int li, int buf) {
     for (size_t id = 0; id < snap_key.size(); ++id)
@@ -97,12 +100,12 @@ struct Recorder {
       const bool copy = id < (int)need_copy.size() ? need_copy[id] != 0 : true;
       if (!copy) {
         where.push_back(c->cur(li));
-      } else if (n_copies >= max_snaps) {
+      } else if (n_copies[li] >= max_snaps) {
         overflow = true;
         where.push_back(nullptr);
         return id;
       } else {
-        char* dst = snap_base + (size_t)n_copies++ * state_bytes;
+        char* dst = snap_base + (size_t)n_copies[li]++ * state_bytes;
         copy_level(c, c->cur(li), dst, li);
         where.push_back(dst);
       }
@@ -167,11 +170,23 @@ std::vector<char> plan_snapshots(lbm_ctx* c) {
   return r.clobbered;
 }
 
-// Snapshot copies one coarse step's tape needs (the same for every step: the
-// pattern depends only on which of a level's two buffers an op touches).
+// Snapshot slots one coarse step's tape needs: the largest number of copies of
+// one level (the same for every step: the pattern depends only on which of a
+// level's two buffers an op touches).
 int count_snapshots(lbm_ctx* c) {
-  const std::vector<char> plan = plan_snapshots(c);
-  return (int)std::count(plan.begin(), plan.end(), 1);
+  Recorder r(c);
+  r.counting = true;
+  std::vector<int> saved = c->parity;
+  c->hook = [&](int op, int li) { r.on(op, li); };
+  c->dry = true;
+  c->advance(0);
+  c->dry = false;
+  c->hook = nullptr;
+  c->parity = saved;
+  std::vector<int> per_level(c->nlev, 0);
+  for (size_t id = 0; id < r.snap_key.size(); ++id)
+    if (r.clobbered[id]) per_level[r.snap_key[id].first]++;
+  return per_level.empty() ? 0 : *std::max_element(per_level.begin(), per_level.end());
 }
 
 AdjLayout adj_layout(lbm_ctx* c, int64_t n, int K) {
@@ -189,7 +204,10 @@ AdjLayout adj_layout(lbm_ctx* c, int64_t n, int K) {
   L.lamF = take((size_t)c->d * N * 8);
   L.side_fwd = take(c->M.out_elem.size() * lb);
   L.lam_side = take(c->M.out_elem.size() * lb);
-  L.partial = take((size_t)kAdjBlocks * kAccCols * 8);
+  L.partial_rows = kAdjBlocks;
+  for (int li = 0; li < c->nlev; ++li)
+    L.partial_rows = std::max<int>(L.partial_rows, (int)((c->M.lv[li].nB + LBM_BRICKS_PER_BLOCK - 1) / LBM_BRICKS_PER_BLOCK));
+  L.partial = take((size_t)L.partial_rows * kAccCols * 8);
   L.acc = take(32 * 8);
   int64_t max_contrib = 0;
   for (int li = 0; li < c->nlev; ++li) {
@@ -447,16 +465,29 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
           a.nbr = c->at<uint32_t>(c->oNbr);
           a.side_fwd = W + L.side_fwd;
           a.lam_side = W + L.lam_side;
-          if (c->p.time_mode == LBM_TIME_TWO_LAYER) {
-            a.begin = H.base + H.oC;
-            a.end = H.base + H.oG1;
-          } else {
-            a.begin = H.base + H.oF;
-            a.end = H.base + H.oG2;
-          }
           a.omega = H.omega;
           std::memcpy(a.inlet, c->inlet, sizeof(a.inlet));
           a.inlet_s = c->at<double>(c->oInletS);
+          // interior bricks (the first 64 nB fluid elements) through the brick
+          // tables, everything else through the neighbour list
+          const int64_t nbrick = 64 * H.nB;
+          AdjSCArgs ab = a;
+          ab.begin = H.base + H.oF;
+          ab.nB = H.nB;
+          ab.brick_nb = c->at<int32_t>(c->oBrickNb) + (size_t)H.brick_first * 27;
+          ab.brick_tab = c->at<uint16_t>(c->oBrickTab);
+          aops->sc_brick(c->Q, ab, st);
+          if (c->p.time_mode == LBM_TIME_TWO_LAYER) {
+            a.begin = H.base + H.oC;
+            a.end = H.base + H.oG1 - nbrick;
+            a.hole_at = H.base + H.oF;
+            a.hole_len = nbrick;
+          } else {
+            a.begin = H.base + H.oF + nbrick;
+            a.end = H.base + H.oG2;
+            a.hole_at = a.end;
+            a.hole_len = 0;
+          }
           aops->sc(c->Q, a, st);
           if (outlet) {
             for (int which = 0; which < (c->p.bouzidi ? 6 : 3); ++which) {
@@ -526,7 +557,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   }
   if (s != LBM_OK) return s;
   // ---- parameter gradients
-  launch_accum(AccumArgs{partial, kAdjBlocks, acc}, st);
+  launch_accum(AccumArgs{partial, L.partial_rows, acc}, st);
   double hacc[kAccCols];
   s = chk(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st), "adjoint acc");
   if (s == LBM_OK) s = chk(cudaStreamSynchronize(st), "adjoint sync");

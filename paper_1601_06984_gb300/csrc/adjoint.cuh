@@ -145,49 +145,83 @@ __device__ __forceinline__ void post_moments_rev(const R* g, R om, R rho_off, co
   }
 }
 
-// Reverse of the BGK collision with Guo forcing (u = (j + F/2) / rho).
+// Reverse of one element's BGK collision with Guo forcing (u = (j + F/2) / rho),
+// from the pdfs g it pulled and the adjoints lo of its outputs.  The collision
+// Jacobian is the identity times (1 - omega) plus a rank-(1+d) part: with
+//   A_i = d g^eq_i / d rp,  B_ia = d g^eq_i / d u_a,  G_ia = d guo_i / d u_a,
+//   S0 = sum_i lo_i A_i,   S_a = sum_i lo_i (omega B_ia + G_ia),
+// the adjoint of pulled pdf i is
+//   lam_g_i = (1 - omega) lo_i + base + sum_a c_ia sa_a,
+//   base = omega S0 - sum_a S_a u_a / rho,  sa_a = S_a / rho.
+// Every sum over i is linear in P_i = w_i lo_i with weights of degree <= 2 in
+// c_i, so it is formed from M0 = sum P_i, M1_a = sum P_i c_ia and
+// M2_ab = sum P_i c_ia c_ib.  lF and lom receive the element's derivatives with
+// respect to its force and omega.
 template <int Q, class R>
-__device__ __forceinline__ void bgk_rev(const R* g, R om, R rho_off, const R* F, const R* lam_out, R* lam_g,
-                                        R* lam_F, R& lam_om) {
+__device__ __forceinline__ void bgk_rev(const R* g, const R* lo, const R* F, R om, R rho_off, R& base, R* sa,
+                                        R* lF, R& lom) {
   using LT = Lat<Q>;
   constexpr int D = LT::D;
   R rp, j[3];
   raw_moments<Q, R>(g, rp, j);
-  const R rho = rho_off + rp;
-  const R inv = R(1) / rho;
-  R u[3] = {R(0), R(0), R(0)};
-  R usq = R(0);
+  const R rho = rho_off + rp, inv = R(1) / rho;
+  R u[3] = {R(0), R(0), R(0)}, usq = R(0), uF = R(0);
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    u[a] = (j[a] + R(0.5) * F[a]) * inv;
-    usq += u[a] * u[a];
+  for (int b = 0; b < D; ++b) {
+    u[b] = (j[b] + R(0.5) * F[b]) * inv;
+    usq += u[b] * u[b];
+    uF += u[b] * F[b];
   }
-  R lam_geq[Q];
-  R lam_rp = R(0);
-  R lam_u[3] = {R(0), R(0), R(0)};
+  const R fpre = R(1) - R(0.5) * om;
+  R M0 = R(0), M1[3] = {R(0), R(0), R(0)}, M2[3][3] = {}, lg_dot = R(0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    lam_g[i] = (R(1) - om) * lam_out[i];
-    lam_geq[i] = om * lam_out[i];
-    lam_om += lam_out[i] * (geq<Q, R>(i, rp, rho, u, usq) - g[i]);
+    const R P = R(LT::w(i)) * lo[i];
+    lg_dot += lo[i] * g[i];
+    M0 += P;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      if (LT::c(i, b) > 0) M1[b] += P;
+      if (LT::c(i, b) < 0) M1[b] -= P;
+#pragma unroll
+      for (int c = b; c < D; ++c) {
+        const int cc = LT::c(i, b) * LT::c(i, c);
+        if (cc > 0) M2[b][c] += P;
+        if (cc < 0) M2[b][c] -= P;
+      }
+    }
   }
-  guo_rev<Q, R>(lam_out, om, u, F, lam_om, lam_u, lam_F);
-  geq_rev<Q, R>(lam_geq, rho, u, usq, lam_rp, lam_u);
-  R lam_j[3] = {R(0), R(0), R(0)};
-  R lam_rho = R(0);
+  R M2u[3] = {R(0), R(0), R(0)}, M2F[3] = {R(0), R(0), R(0)};
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    lam_j[a] = lam_u[a] * inv;
-    lam_F[a] += R(0.5) * lam_u[a] * inv;
-    lam_rho += -lam_u[a] * u[a] * inv;
+  for (int b = 0; b < D; ++b)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const R m = b <= c ? M2[b][c] : M2[c][b];
+      M2u[b] += m * u[c];
+      M2F[b] += m * F[c];
+    }
+  R uM1 = R(0), FM1 = R(0), uM2u = R(0), uM2F = R(0);
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    uM1 += u[b] * M1[b];
+    FM1 += F[b] * M1[b];
+    uM2u += u[b] * M2u[b];
+    uM2F += u[b] * M2F[b];
   }
-  lam_rp += lam_rho;
+  // sum lo_i A_i, sum lo_i g^eq_i, sum lo_i Guo_i
+  const R quad = R(3) * uM1 + R(4.5) * uM2u - R(1.5) * usq * M0;
+  const R S0 = M0 + quad;
+  const R sum_geq = rp * M0 + rho * quad;
+  const R sum_G = R(3) * (FM1 - uF * M0) + R(9) * uM2F;
+  lom = sum_geq - lg_dot - R(0.5) * sum_G;
+  base = om * S0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    R v = lam_g[i] + lam_rp;
-#pragma unroll
-    for (int a = 0; a < D; ++a) v += R(LT::c(i, a)) * lam_j[a];
-    lam_g[i] = v;
+  for (int b = 0; b < D; ++b) {
+    const R lin = R(3) * M1[b] + R(9) * M2u[b] - R(3) * u[b] * M0;  // sum lo_i B_ib / rho
+    const R Sa = om * rho * lin + fpre * (R(9) * M2F[b] - R(3) * F[b] * M0);
+    lF[b] = fpre * lin + R(0.5) * Sa * inv;
+    base -= Sa * u[b] * inv;
+    sa[b] = Sa * inv;
   }
 }
 
@@ -315,13 +349,11 @@ __global__ void __launch_bounds__(256) k_adj_seed(const AdjSeedArgs a) {
 }
 
 // ----------------------------------------------------------------- stream + collide
-// Reverse of one element's pull + BGK collide.  The collision Jacobian is the
-// identity times (1-omega) plus a rank-(1+d) part: with
-//   A_i = d g^eq_i / d rp,  B_ia = d g^eq_i / d u_a,  G_ia = d guo_i / d u_a,
-//   S0 = sum_i lam_i A_i,   S_a = sum_i lam_i (omega B_ia + G_ia),
-// the adjoint of the pulled pdf k is
-//   lam_g_k = (1-omega) lam_k + omega S0 + sum_a S_a (c_ka - u_a) / rho,
-// so only a handful of scalars are carried (few registers, more warps).
+// Reverse of one element's pull + BGK collide through the neighbour list
+// (every element the interior-brick kernel does not take): the pulled pdfs
+// are gathered as the forward did, bgk_rev gives the adjoint of each, and it
+// is added to the slot the forward pulled from (a conflict-free scatter: each
+// slot has one reader), or to the adjoint of the outlet value it came from.
 template <int Q, class S>
 __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
   using R = typename Sto<S>::R;
@@ -334,7 +366,8 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
   const R om = R(a.omega), rho_off = R(a.c.rho_off);
   R part[5] = {R(0), R(0), R(0), R(0), R(0)};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.end; e += stride) {
+  for (int64_t lin = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; lin < a.end; lin += stride) {
+    const int64_t e = lin + (lin >= a.hole_at ? a.hole_len : 0);
     uint32_t nb[Q];
     nb[0] = (uint32_t)e;
 #pragma unroll
@@ -363,75 +396,10 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
     }
     R F[3];
     load_force<S, R>(a.c.force, a.c.Ntot, e, F, D);
-    R rp, j[3];
-    raw_moments<Q, R>(g, rp, j);
-    const R rho = rho_off + rp, inv = R(1) / rho;
-    R u[3] = {R(0), R(0), R(0)}, usq = R(0), uF = R(0);
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      u[b] = (j[b] + R(0.5) * F[b]) * inv;
-      usq += u[b] * u[b];
-      uF += u[b] * F[b];
-    }
-    const R fpre = R(1) - R(0.5) * om;
-    // every sum over i below is linear in P_i = w_i lam_i with polynomial
-    // weights of degree <= 2 in c_i, so it is a combination of the moments
-    // M0 = sum P_i, M1_a = sum P_i c_ia, M2_ab = sum P_i c_ia c_ib
-    R M0 = R(0), M1[3] = {R(0), R(0), R(0)}, M2[3][3] = {}, lg_dot = R(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const R P = R(LT::w(i)) * lo[i];
-      lg_dot += lo[i] * g[i];
-      M0 += P;
-#pragma unroll
-      for (int b = 0; b < D; ++b) {
-        if (LT::c(i, b) > 0) M1[b] += P;
-        if (LT::c(i, b) < 0) M1[b] -= P;
-#pragma unroll
-        for (int c = b; c < D; ++c) {
-          const int cc = LT::c(i, b) * LT::c(i, c);
-          if (cc > 0) M2[b][c] += P;
-          if (cc < 0) M2[b][c] -= P;
-        }
-      }
-    }
-    R M2u[3] = {R(0), R(0), R(0)}, M2F[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int b = 0; b < D; ++b)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const R m = b <= c ? M2[b][c] : M2[c][b];
-        M2u[b] += m * u[c];
-        M2F[b] += m * F[c];
-      }
-    R uM1 = R(0), FM1 = R(0), uM2u = R(0), uM2F = R(0);
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      uM1 += u[b] * M1[b];
-      FM1 += F[b] * M1[b];
-      uM2u += u[b] * M2u[b];
-      uM2F += u[b] * M2F[b];
-    }
-    // sum lam_i A_i, sum lam_i g^eq_i, sum lam_i Guo_i
-    const R quad = R(3) * uM1 + R(4.5) * uM2u - R(1.5) * usq * M0;
-    const R S0 = M0 + quad;
-    const R sum_geq = rp * M0 + rho * quad;
-    const R sum_G = R(3) * (FM1 - uF * M0) + R(9) * uM2F;
-    const R lom = sum_geq - lg_dot - R(0.5) * sum_G;
-    R Sa[3] = {R(0), R(0), R(0)}, lF[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      const R lin = R(3) * M1[b] + R(9) * M2u[b] - R(3) * u[b] * M0;  // sum lam_i B_ib / rho
-      Sa[b] = om * rho * lin + fpre * (R(9) * M2F[b] - R(3) * F[b] * M0);
-      lF[b] = fpre * lin;
-    }
-#pragma unroll
-    for (int b = 0; b < D; ++b) lF[b] += R(0.5) * Sa[b] * inv;
+    R base, sa[3] = {R(0), R(0), R(0)}, lF[3] = {R(0), R(0), R(0)}, lom;
+    bgk_rev<Q, R>(g, lo, F, om, rho_off, base, sa, lF, lom);
     part[0] += lom;
     add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
-    R base = om * S0;
-#pragma unroll
-    for (int b = 0; b < D; ++b) base -= Sa[b] * u[b] * inv;
     // reverse streaming
     auto target = [&](int i) -> size_t {
       const uint32_t n = nb[i];
@@ -447,7 +415,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
     for (int i = 0; i < Q; ++i) {
       R lg = (R(1) - om) * lo[i] + base;
 #pragma unroll
-      for (int b = 0; b < D; ++b) lg += Sa[b] * R(LT::c(i, b)) * inv;
+      for (int b = 0; b < D; ++b) lg += sa[b] * R(LT::c(i, b));
       const uint32_t n = nb[i];
       lam_out[(size_t)i * N + e] = R(0);
       if (i > 0 && n >= NB_FLAG30 && !(n & NB_BOUNCE)) {
@@ -464,6 +432,72 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
     }
   }
   store_partials<R, 5>(part, a.c);
+}
+
+// Reverse of the interior-brick stream + collide.  The forward kernel's pull:
+// each group of 64 threads takes one brick (thread l its element at z-curve
+// position l), and the pull source of link i is the brick's neighbour row
+// entry for the thread's link-table slot plus the position in that brick.  The
+// reverse gathers the same sources from the snapshot and scatters the pulled
+// pdfs' adjoints back into those slots; interior bricks have no boundary
+// links.  Grid: ceil(nB / 4) blocks of 256, block b adding its sums to running
+// row b.
+static_assert(LBM_BR_BLOCK / 64 == LBM_BRICKS_PER_BLOCK, "host sizes the running rows by this many bricks per block");
+template <int Q, class S>
+__global__ void __launch_bounds__(LBM_BR_BLOCK, 2) k_adj_sc_brick(const AdjSCArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  constexpr int BPB = LBM_BR_BLOCK / 64;
+  constexpr int NW = Q / 2;  // (Q-1)/2 words of two 16-bit entries
+  const int l = threadIdx.x & 63, lane = threadIdx.x & 31;
+  // the brick index is uniform over each warp, so the shuffles run with whole warps
+  const int64_t bk = (int64_t)blockIdx.x * BPB + (threadIdx.x >> 6);
+  R part[1] = {R(0)};
+  if (bk < a.nB) {
+    uint32_t tw[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k)
+      tw[k] = (uint32_t)__ldg(a.brick_tab + (2 * k) * 64 + l) |
+              ((uint32_t)__ldg(a.brick_tab + (2 * k + 1) * 64 + l) << 16);
+    const int32_t row = lane < 27 ? __ldg(a.brick_nb + bk * 27 + lane) : 0;
+    const size_t N = (size_t)a.c.Ntot;
+    const int64_t first = a.begin + bk * 64, e = first + l;
+    const S* __restrict__ x = static_cast<const S*>(a.c.fsrc) + first;
+    R* __restrict__ lam_out = static_cast<R*>(a.c.lam_a);
+    R* __restrict__ lam_in = static_cast<R*>(a.c.lam_b) + first;
+    // pull source of link i, relative to the brick's first element
+    auto src_of = [&](int i) -> int64_t {
+      if (i == 0) return l;
+      const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
+      const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
+      return (int64_t)(i * N) + r + (v & 63);
+    };
+    R g[Q], lo[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = Sto<S>::ld(x + src_of(i));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lo[i] = lam_out[(size_t)i * N + e];
+    R F[3];
+    load_force<S, R>(a.c.force, a.c.Ntot, e, F, D);
+    const R om = R(a.omega);
+    R base, sa[3] = {R(0), R(0), R(0)}, lF[3] = {R(0), R(0), R(0)}, lom;
+    bgk_rev<Q, R>(g, lo, F, om, R(a.c.rho_off), base, sa, lF, lom);
+    part[0] += lom;
+    add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
+    R cur[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) cur[i] = lam_in[src_of(i)];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      R lg = (R(1) - om) * lo[i] + base;
+#pragma unroll
+      for (int b = 0; b < D; ++b) lg += sa[b] * R(LT::c(i, b));
+      lam_out[(size_t)i * N + e] = R(0);
+      lam_in[src_of(i)] = cur[i] + lg;
+    }
+  }
+  store_partials<R, 1>(part, a.c);
 }
 
 // ----------------------------------------------------------------- outlet values
@@ -881,6 +915,11 @@ struct AdjLaunch {
   static void sc(int Q, const AdjSCArgs& a, cudaStream_t st) {
     with_q(Q, [&](auto q) { k_adj_sc<decltype(q)::value, S><<<kAdjBlocks, 256, 0, st>>>(a); });
   }
+  static void sc_brick(int Q, const AdjSCArgs& a, cudaStream_t st) {
+    if (a.nB <= 0) return;
+    const unsigned g = (unsigned)((a.nB + LBM_BRICKS_PER_BLOCK - 1) / LBM_BRICKS_PER_BLOCK);
+    with_q(Q, [&](auto q) { k_adj_sc_brick<decltype(q)::value, S><<<g, LBM_BR_BLOCK, 0, st>>>(a); });
+  }
   static void outlet(int Q, const AdjOutletArgs& a, cudaStream_t st) {
     // the normal-link pass writes one row of omega partials per block, so it
     // runs on the full kAdjBlocks grid that k_accum sums over
@@ -901,9 +940,9 @@ struct AdjLaunch {
 
 template <class S>
 const AdjOps* make_adj_ops() {
-  static const AdjOps ops = {&AdjLaunch<S>::seed, &AdjLaunch<S>::sc,  &AdjLaunch<S>::outlet,
-                             &AdjLaunch<S>::moments, &AdjLaunch<S>::gfc, &AdjLaunch<S>::gff,
-                             sizeof(typename Sto<S>::R)};
+  static const AdjOps ops = {&AdjLaunch<S>::seed,    &AdjLaunch<S>::sc,  &AdjLaunch<S>::sc_brick,
+                             &AdjLaunch<S>::outlet,  &AdjLaunch<S>::moments, &AdjLaunch<S>::gfc,
+                             &AdjLaunch<S>::gff,     sizeof(typename Sto<S>::R)};
   return &ops;
 }
 

@@ -310,6 +310,7 @@ struct Ops {
 // block (cols 0..15 d/d omega of each level, 16..18 d/d u_in): block b of
 // every launch adds its sums to row b, so the totals are deterministic.
 constexpr int kAdjBlocks = 1024;  // fixed grid of the adjoint kernels (deterministic partials)
+#define LBM_BRICKS_PER_BLOCK 4       // bricks of 64 elements per 256-thread block of the brick kernels
 constexpr int kAccCols = 32;
 
 struct AdjCommon {
@@ -329,10 +330,16 @@ struct AdjSCArgs {
   const uint32_t* nbr;
   const void* side_fwd;  // outlet values the forward used (compute type)
   void* lam_side;        // adjoint of the outlet values (written)
-  int64_t begin, end;
+  int64_t begin, end;    // neighbour-list kernel: linear range; element = lin + (lin >= hole_at ? hole_len : 0)
+  int64_t hole_at, hole_len;
   double omega;
   double inlet[kQmax];   // 6 w_i rho0 (c_i . u_in) of the forward
   const double* inlet_s;  // inlet profile factor per inlet link
+  // interior-brick kernel: nB bricks of 64 elements from begin, their rows
+  // [nB][27] and the link table [Q-1][64] (as BrickArgs)
+  const int32_t* brick_nb;
+  const uint16_t* brick_tab;
+  int64_t nB;
 };
 
 struct AdjOutletArgs {
@@ -407,6 +414,7 @@ struct AccumArgs {
 struct AdjOps {
   void (*seed)(int Q, const AdjSeedArgs&, cudaStream_t);
   void (*sc)(int Q, const AdjSCArgs&, cudaStream_t);
+  void (*sc_brick)(int Q, const AdjSCArgs&, cudaStream_t);  // grid ceil(nB / 4) blocks
   void (*outlet)(int Q, const AdjOutletArgs&, cudaStream_t);
   void (*moments)(int Q, const AdjMomArgs&, cudaStream_t);
   void (*gfc)(int Q, const AdjGfcArgs&, cudaStream_t);
