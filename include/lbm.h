@@ -266,7 +266,8 @@ lbm_status lbm_set_params(lbm_ctx* ctx, double omega_coarse, const double* u_in)
  * u_in (dJ_duin[3]), all at fixed initial pdfs, and the gradient with respect to
  * those initial post-collision pdfs dJ_df0[n][Q] (caller order; chain it with
  * the derivative of whatever produced the initial state, e.g. the omega
- * dependence of the lbm_init non-equilibrium part); any output may be NULL.
+ * dependence of the lbm_init non-equilibrium part); any output may be NULL
+ * (with dJ_dF NULL the per-element force adjoint is not accumulated at all).
  * Checkpoints: the state every K
  * coarse steps; each segment is recomputed once, and every step once more while
  * its op inputs are recorded.  adj_ws is a device workspace of

@@ -343,7 +343,8 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   char* lamA = W + L.lamA;
   char* lamB = W + L.lamB;
   auto lam_for = [&](int par) { return par ? lamB : lamA; };
-  double* lamF = reinterpret_cast<double*>(W + L.lamF);
+  // the body-force adjoint is accumulated only when it is asked for
+  double* lamF = dJ_dF ? reinterpret_cast<double*>(W + L.lamF) : nullptr;
   double* partial = reinterpret_cast<double*>(W + L.partial);
   double* acc = reinterpret_cast<double*>(W + L.acc);
   const void* force = c->force_ptr();
