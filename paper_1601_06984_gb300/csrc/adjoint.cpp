@@ -156,9 +156,8 @@ struct Recorder {
 };
 
 // Dry walk of one coarse step from the current parities (launches nothing):
-// which of the states its ops read must be copied.
-std::vector<char> plan_snapshots(lbm_ctx* c) {
-  Recorder r(c);
+// the states its ops read and which of them a later op overwrites.
+void dry_walk(lbm_ctx* c, Recorder& r) {
   r.counting = true;
   std::vector<int> saved = c->parity;
   c->hook = [&](int op, int li) { r.on(op, li); };
@@ -167,6 +166,12 @@ std::vector<char> plan_snapshots(lbm_ctx* c) {
   c->dry = false;
   c->hook = nullptr;
   c->parity = saved;
+}
+
+// Which of the states the next coarse step's ops read must be copied.
+std::vector<char> plan_snapshots(lbm_ctx* c) {
+  Recorder r(c);
+  dry_walk(c, r);
   return r.clobbered;
 }
 
@@ -175,14 +180,7 @@ std::vector<char> plan_snapshots(lbm_ctx* c) {
 // level's two buffers an op touches).
 int count_snapshots(lbm_ctx* c) {
   Recorder r(c);
-  r.counting = true;
-  std::vector<int> saved = c->parity;
-  c->hook = [&](int op, int li) { r.on(op, li); };
-  c->dry = true;
-  c->advance(0);
-  c->dry = false;
-  c->hook = nullptr;
-  c->parity = saved;
+  dry_walk(c, r);
   std::vector<int> per_level(c->nlev, 0);
   for (size_t id = 0; id < r.snap_key.size(); ++id)
     if (r.clobbered[id]) per_level[r.snap_key[id].first]++;
@@ -293,7 +291,6 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   const AdjOps* aops = adj_ops_for(c->p.precision);
   const bool fp64 = c->p.precision == LBM_FP64;
   const size_t N = (size_t)c->M.Ntot;
-  const size_t lb = aops->lam_bytes;
   auto chk = [&](cudaError_t e, const char* w) { return c->cuda_check(e, w); };
   // ---- clear adjoint state, build the transposed GFC source lists
   lbm_status s = chk(cudaMemsetAsync(W, 0, L.ck, st), "adjoint clear");
@@ -603,7 +600,6 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   restore_state(W + L.fin, parity_at[n]);
   s = c->launched("adjoint restore");
   if (s == LBM_OK) s = chk(cudaStreamSynchronize(st), "adjoint end");
-  (void)lb;
   return s;
 }
 

@@ -12,8 +12,9 @@
 // is race-free; the ghost-to-source sums of GhostFromCoarser go through a
 // transposed (CSR) list so that they are deterministic too.  Derivatives with
 // respect to the relaxation rates and the inlet velocity are summed per block
-// and then added in launch order (deterministic); body-force derivatives are
-// accumulated per element in FP64.
+// into the block's own running row (launches are stream-ordered) and the rows
+// are summed once at the end, in block order (deterministic); body-force
+// derivatives are accumulated per element in FP64.
 #pragma once
 
 #include "kernels.cuh"
