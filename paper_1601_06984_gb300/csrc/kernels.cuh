@@ -393,8 +393,12 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
 // Four blocks per SM (64 registers) where that fits without spills: D3Q19 and
 // D2Q9 with 4-byte or narrower storage; three otherwise.
 #define LBM_BR_BND_MINB(Q, S) ((Q) > 19 || sizeof(S) > 4 ? 3 : 4)
+// Interior bricks: BF16 storage moves half the bytes per element, so it needs
+// more elements in flight; five blocks per SM (48 registers, no spills) for
+// D3Q19 / D2Q9 BF16, measured faster than four or six.
+#define LBM_BR_INT_MINB(Q, S) ((Q) <= 19 && sizeof(S) == 2 ? 5 : LBM_BR_MINB)
 template <int Q, class S, bool FORCE, bool BND>
-__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : LBM_BR_MINB) k_stream_collide_brick(const BrickArgs a) {
+__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : LBM_BR_INT_MINB(Q, S)) k_stream_collide_brick(const BrickArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
