@@ -12,8 +12,8 @@
  * Conventions (all entry points):
  *  - Every function returns an lbm_status; on error lbm_last_error() gives a
  *    one-line message.  No exception crosses the ABI.  After LBM_ERR_ARG,
- *    LBM_ERR_MESH or LBM_ERR_STATE the context stays usable; after
- *    LBM_ERR_CUDA it must be destroyed.
+ *    LBM_ERR_MESH, LBM_ERR_STATE or LBM_ERR_NUMERIC the context stays usable;
+ *    after LBM_ERR_CUDA it must be destroyed.
  *  - Host arrays passed in are borrowed for the duration of the call and
  *    copied; host arrays passed out are written before the call returns.
  *  - Element order at the boundary is always the caller's order of the
@@ -54,7 +54,7 @@ typedef enum {
   LBM_ERR_CUDA = -3,     /* a CUDA runtime call failed                             */
   LBM_ERR_OOM = -4,      /* host allocation failed                                 */
   LBM_ERR_STATE = -5,    /* wrong call order (e.g. lbm_step before lbm_bind)       */
-  LBM_ERR_NUMERIC = -6,  /* non-finite mass found by the optional mass check       */
+  LBM_ERR_NUMERIC = -6,  /* the optional mass check (params.check_every) failed   */
   LBM_ERR_INTERNAL = -7
 } lbm_status;
 
@@ -98,7 +98,23 @@ enum { LBM_INLET_UNIFORM = 0, LBM_INLET_PARABOLIC = 1 };
  *                x - c_i / 2 across the domain (mean u_in; Sec. 4.2 inflow).
  *  bouzidi       0: half-way bounce-back on obstacle links; 1: linearly
  *                interpolated bounce-back (Bouzidi, Sec. 2.3) with the wall at
- *                x - q c_i, q per link from lbm_set_link_q (1/2 until set). */
+ *                x - q c_i, q per link from lbm_set_link_q (1/2 until set).
+ *  n_levels      0: the hierarchy spans the levels of the treeIDs (coarsest to
+ *                finest present).  n > 0: exactly n levels from the coarsest
+ *                one present; levels beyond the finest present hold no element
+ *                (an empty refined region), and the recursive stepping of
+ *                Sec. 2.2 still runs through them (each takes its two substeps
+ *                per step of the next coarser level, with nothing to update).
+ *                n below the span of the treeIDs, or above 16: LBM_ERR_ARG.
+ *  check_every   0: no check.  M > 0: lbm_step computes the FP64 mass
+ *                (out[0] of lbm_reduce) every M coarse steps, counted across
+ *                calls, and returns LBM_ERR_NUMERIC if it is not finite or, with
+ *                mass_band > 0, if |mass / mass_ref - 1| > mass_band.  mass_ref
+ *                is the mass at the start of the first lbm_step after lbm_bind,
+ *                lbm_init or lbm_set_state.  The check synchronises the stream.
+ *                Negative: LBM_ERR_ARG.
+ *  mass_band     relative band of the mass check (0: finiteness only; negative
+ *                or not finite: LBM_ERR_ARG). */
 typedef struct {
   int32_t stencil;
   int32_t precision;
@@ -112,6 +128,9 @@ typedef struct {
   int32_t outlet;
   int32_t inlet_profile;
   int32_t bouzidi;
+  int32_t n_levels;
+  int32_t check_every;
+  double mass_band;
 } lbm_params;
 
 /* Build the multilevel mesh on the host (no device work).
@@ -181,7 +200,10 @@ lbm_status lbm_set_force(lbm_ctx* ctx, const double* F);
  * graph captured on first use (one per A/B parity state; dropped by
  * lbm_set_params and lbm_bind) on the bound stream; a remaining single step,
  * and all steps while timing is enabled, are launched kernel by kernel.  Both
- * paths issue the same kernels in the same order. */
+ * paths issue the same kernels in the same order.  With params.check_every = M
+ * the mass is checked after every M-th coarse step (see lbm_params); a failed
+ * check returns LBM_ERR_NUMERIC right after that step, with the state left as
+ * it was then (the context stays usable, e.g. for lbm_set_state). */
 lbm_status lbm_step(lbm_ctx* ctx, int64_t n_coarse);
 
 /* Fill every ghost element from the current state (the synchronous-time part

@@ -9,7 +9,10 @@
 //
 // Every quantity is computed in the most direct way the paper states it: per
 // level hash maps keyed by integer coordinates, one element at a time, scalar
-// loops over the discrete velocities.  The scalar type T is double or a
+// loops over the discrete velocities.  The loops over the elements of a level
+// may be spread over OpenMP threads (orc_set_threads); each element's
+// arithmetic is the same either way, and the sums over elements (reductions)
+// stay sequential, so the results do not depend on the thread count.  The scalar type T is double or a
 // forward-mode dual number (value, tangent) so that directional derivatives of
 // any output can be taken exactly; that is what the adjoint is checked against.
 //
@@ -49,6 +52,10 @@
 #include <unordered_set>
 #include <vector>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 namespace {
 
 // ---------------------------------------------------------------- dual numbers
@@ -86,6 +93,9 @@ inline double tangent_of(const Dual& x) { return x.d; }
 // Weights by |c|^2 (Sec. 2.1 uses the standard D2Q9 / D3Q19 / D3Q27 sets):
 //   D2Q9 4/9, 1/9, 1/36;  D3Q19 1/3, 1/18, 1/36;  D3Q27 8/27, 2/27, 1/54, 1/216.
 constexpr int kQmax = 27;
+// element loops shorter than this stay on one thread (thread start-up would
+// cost more than the loop)
+constexpr int64_t kParMin = 4096;
 struct Lattice {
   int d = 0, Q = 0;
   int c[kQmax][3] = {};
@@ -240,6 +250,7 @@ struct Sim {
   }
   bool use_force = false;
   T omega_c = T(1.0);
+  int n_levels_req = 0;  // 0: the levels the treeIDs span
   int Lmin = 0, Lmax = 0;
   std::vector<Level<T>> lv;
   std::vector<std::pair<int, int>> upos;
@@ -348,6 +359,13 @@ struct Sim {
       if (!decode(tid[k], &L[k], &X[k])) return fail("invalid treeID");
     Lmin = *std::min_element(L.begin(), L.end());
     Lmax = *std::max_element(L.begin(), L.end());
+    // an explicit level count may add finer levels that hold no element yet
+    // (an empty refined region): the recursive stepping of Sec. 2.2 still runs
+    // through them
+    if (n_levels_req > 0) {
+      if (n_levels_req < Lmax - Lmin + 1) return fail("n_levels below the levels the treeIDs span");
+      Lmax = Lmin + n_levels_req - 1;
+    }
     for (int a = 0; a < d; ++a)
       if (ext0[a] < 1 || ext0[a] > ((int64_t)1 << Lmin)) return fail("extent outside the bounding cube");
     lv.assign(Lmax - Lmin + 1, Level<T>());
@@ -640,10 +658,15 @@ struct Sim {
     return e.f[i];
   }
 
+  // The element loops below touch one element each (reading others' stored
+  // pdfs only), so they may run on several threads with the same result.
   void stream_collide(int li) {
     Level<T>& l = lv[li];
     const T omega = l.omega;
-    for (auto& e : l.e) {
+    const int64_t ne = (int64_t)l.e.size();
+#pragma omp parallel for schedule(static) if (ne >= kParMin)
+    for (int64_t k = 0; k < ne; ++k) {
+      Elem<T>& e = l.e[k];
       if (!e.processed) continue;
       T fin[kQmax];
       for (int i = 0; i < Q; ++i) fin[i] = pull(l, e, i);
@@ -658,8 +681,9 @@ struct Sim {
       for (int i = 0; i < Q; ++i)
         e.fn[i] = fin[i] - omega * (fin[i] - feq(i, rho, u)) + guo(i, omega, u, e.F);
     }
-    for (auto& e : l.e)
-      if (e.processed) e.f.swap(e.fn);
+#pragma omp parallel for schedule(static) if (ne >= kParMin)
+    for (int64_t k = 0; k < ne; ++k)
+      if (l.e[k].processed) l.e[k].f.swap(l.e[k].fn);
   }
 
   // ------------------------------------------------------------ GhostFromFiner
@@ -677,7 +701,10 @@ struct Sim {
     Level<T>& lc = lv[li];
     const Level<T>& lf = lv[li + 1];
     const int nch = 1 << d;
-    for (auto& g : lc.e) {
+    const int64_t ng = (int64_t)lc.e.size();
+#pragma omp parallel for schedule(static) if (ng >= kParMin)
+    for (int64_t k = 0; k < ng; ++k) {
+      Elem<T>& g = lc.e[k];
       if (g.kind != GFF) continue;
       Mom<T> mk[8];
       for (int b = 0; b < nch; ++b) moments(lf.e[g.child[b]], lf.omega, &mk[b]);
@@ -733,7 +760,9 @@ struct Sim {
   std::vector<Mom<T>> level_moments(int li) const {
     const Level<T>& l = lv[li];
     std::vector<Mom<T>> out(l.e.size());
-    for (size_t k = 0; k < l.e.size(); ++k)
+    const int64_t ne = (int64_t)l.e.size();
+#pragma omp parallel for schedule(static) if (ne >= kParMin)
+    for (int64_t k = 0; k < ne; ++k)
       if (l.e[k].kind != GFC) moments(l.e[k], l.omega, &out[k]);
     return out;
   }
@@ -886,7 +915,10 @@ void Sim<T>::fill_gfc(int li, const std::vector<Mom<T>>& q0, const std::vector<M
   const double w3[4] = {5.0 / 8.0, 1.0 / 8.0, 1.0 / 8.0, 1.0 / 8.0};
   const double w2[4] = {9.0 / 16.0, 3.0 / 16.0, 3.0 / 16.0, 1.0 / 16.0};
   const double* lw = d == 3 ? w3 : w2;
-  for (auto& g : lf.e) {
+  const int64_t ng = (int64_t)lf.e.size();
+#pragma omp parallel for schedule(static) if (ng >= kParMin)
+  for (int64_t kg = 0; kg < ng; ++kg) {
+    Elem<T>& g = lf.e[kg];
     if (g.kind != GFC) continue;
     // step 1: moments at the sources
     Mom<T> m[4];
@@ -933,7 +965,7 @@ struct Handle {
 template <class T>
 Sim<T>* create_sim(int stencil, int time_mode, const int* extent, const int* bc, double omega_c,
                    double omega_dot, double rho0, const double* u_in, const double* u_in_dot, int use_force,
-                   const int64_t* tree_ids, int64_t n, char* err, int errlen) {
+                   const int64_t* tree_ids, int64_t n, int n_levels, char* err, int errlen) {
   auto* s = new Sim<T>();
   auto bail = [&](const char* m) -> Sim<T>* {
     if (err && errlen > 0) snprintf(err, errlen, "%s", m);
@@ -961,6 +993,8 @@ Sim<T>* create_sim(int stencil, int time_mode, const int* extent, const int* bc,
     if constexpr (std::is_same<T, Dual>::value) s->uinT[a] = Dual(s->uin[a], u_in_dot ? u_in_dot[a] : 0.0);
   }
   s->use_force = use_force != 0;
+  if (n_levels < 0 || n_levels > 16) return bail("n_levels must lie in 0..16");
+  s->n_levels_req = n_levels;
   if (!s->build(tree_ids, n)) return bail(s->err.c_str());
   for (auto& l : s->lv)
     if (std::fabs(1.0 - value_of(l.omega)) < 1e-3) return bail("omega too close to 1 on some level");
@@ -1042,12 +1076,26 @@ extern "C" {
 
 void* orc_create(int stencil, int time_mode, const int* extent, const int* bc, double omega_c,
                  double rho0, const double* u_in, int use_force, const int64_t* tree_ids, int64_t n,
-                 char* err, int errlen) {
+                 int n_levels, char* err, int errlen) {
   return create_sim<double>(stencil, time_mode, extent, bc, omega_c, 0.0, rho0, u_in, nullptr, use_force,
-                            tree_ids, n, err, errlen);
+                            tree_ids, n, n_levels, err, errlen);
 }
 
 void orc_destroy(void* h) { delete static_cast<Sim<double>*>(h); }
+
+// Threads of the element loops (stream-collide, ghost fills, source moments);
+// n <= 0 keeps the OpenMP default.  Returns the count now in use (1 without
+// OpenMP).  Every element is computed by the same arithmetic whatever the
+// count, so results do not depend on it.
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 // per level: level, fluid, GFC, GFF, GFC layer-1, GFF layer-1  (6 int64 each)
 int orc_counts(void* h, int64_t* out, int cap) {
@@ -1208,9 +1256,10 @@ int orc_compact_velocity(int d, const int* s, const double* u4, const double* S4
 // (F_dot, omega_dot, u_in_dot).
 void* orc_dual_create(int stencil, int time_mode, const int* extent, const int* bc, double omega_c,
                       double omega_dot, double rho0, const double* u_in, const double* u_in_dot,
-                      int use_force, const int64_t* tree_ids, int64_t n, char* err, int errlen) {
+                      int use_force, const int64_t* tree_ids, int64_t n, int n_levels, char* err,
+                      int errlen) {
   return create_sim<Dual>(stencil, time_mode, extent, bc, omega_c, omega_dot, rho0, u_in, u_in_dot,
-                          use_force, tree_ids, n, err, errlen);
+                          use_force, tree_ids, n, n_levels, err, errlen);
 }
 
 void orc_dual_destroy(void* h) { delete static_cast<Sim<Dual>*>(h); }

@@ -19,15 +19,16 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (plain -O2, no fast-math, no FMA contraction).
+    """Compile the oracle with g++ (plain -O2, no fast-math, no FMA contraction;
+    OpenMP over the elements of a level, see set_threads).
     ORACLE_LIB_OVERRIDE names a prebuilt oracle library to load instead (used to
     check that the pins catch planted mistakes)."""
     if os.environ.get("ORACLE_LIB_OVERRIDE"):
         return os.environ["ORACLE_LIB_OVERRIDE"]
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + ".tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC",
-                               SRC, "-o", tmp])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-shared",
+                               "-fPIC", SRC, "-o", tmp])
         os.replace(tmp, LIB)
     return LIB
 
@@ -38,9 +39,9 @@ def lib():
         L = C.CDLL(build())
         P, I64, I, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
         L.orc_create.restype = P
-        L.orc_create.argtypes = [I, I, P, P, D, D, P, I, P, I64, C.c_char_p, I]
+        L.orc_create.argtypes = [I, I, P, P, D, D, P, I, P, I64, I, C.c_char_p, I]
         L.orc_dual_create.restype = P
-        L.orc_dual_create.argtypes = [I, I, P, P, D, D, D, P, P, I, P, I64, C.c_char_p, I]
+        L.orc_dual_create.argtypes = [I, I, P, P, D, D, D, P, P, I, P, I64, I, C.c_char_p, I]
         L.orc_destroy.argtypes = [P]
         L.orc_dual_destroy.argtypes = [P]
         L.orc_counts.argtypes = [P, P, I]
@@ -69,12 +70,21 @@ def lib():
         L.orc_reduce.argtypes = [P, P]
         L.orc_dual_reduce.argtypes = [P, P, P]
         L.orc_compact_velocity.argtypes = [I, P, P, P, P]
+        L.orc_set_threads.argtypes = [I]
+        L.orc_set_threads.restype = I
         _lib = L
     return _lib
 
 
 def _p(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads the oracle's element loops use (n <= 0: the OpenMP default, all
+    cores unless OMP_NUM_THREADS says otherwise); returns the count in use.
+    Results are the same for every count."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _f64(a, shape=None):
@@ -92,11 +102,14 @@ class OracleError(RuntimeError):
 
 class Oracle:
     """One multilevel simulation held by the oracle.  With dual=True every value
-    carries a tangent (forward-mode derivative along omega_dot and F_dot)."""
+    carries a tangent (forward-mode derivative along omega_dot and F_dot).
+    n_levels > 0 fixes the number of levels from the coarsest one present; the
+    levels beyond those the treeIDs span hold no element (an empty refined
+    region)."""
 
     def __init__(self, mesh, stencil, omega_c, time_mode=0, rho0=1.0, u_in=(0.0, 0.0, 0.0),
                  use_force=False, dual=False, omega_dot=0.0, u_in_dot=(0.0, 0.0, 0.0), outlet=0,
-                 inlet_profile=0):
+                 inlet_profile=0, n_levels=0):
         L = lib()
         self.mesh, self.stencil, self.dual = mesh, stencil, dual
         self.d = 2 if stencil == 9 else 3
@@ -112,10 +125,10 @@ class Oracle:
         err = C.create_string_buffer(512)
         if dual:
             h = L.orc_dual_create(stencil, time_mode, _p(ext), _p(bc), omega_c, omega_dot, rho0, _p(uin),
-                                  _p(uin_dot), int(use_force), _p(tid), self.n, err, 512)
+                                  _p(uin_dot), int(use_force), _p(tid), self.n, int(n_levels), err, 512)
         else:
             h = L.orc_create(stencil, time_mode, _p(ext), _p(bc), omega_c, rho0, _p(uin), int(use_force),
-                             _p(tid), self.n, err, 512)
+                             _p(tid), self.n, int(n_levels), err, 512)
         if not h:
             raise OracleError(err.value.decode())
         self.h = h

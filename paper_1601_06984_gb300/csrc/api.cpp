@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -355,6 +356,11 @@ lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t
     *out = c;
     return LBM_ERR_ARG;
   }
+  if (params->check_every < 0 || !(params->mass_band >= 0.0) || !std::isfinite(params->mass_band)) {
+    c->err = "check_every must be >= 0 and mass_band finite and >= 0";
+    *out = c;
+    return LBM_ERR_ARG;
+  }
   lbm_status s;
   try {
     s = build_host_mesh(tree_ids, levels, n, c->p, &c->M, &c->err);
@@ -491,6 +497,7 @@ lbm_status lbm_bind(lbm_ctx* c, void* ws, uint64_t bytes, void* stream) {
   if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "bind sync");
   if (s != LBM_OK) return s;
   std::fill(c->parity.begin(), c->parity.end(), 0);
+  c->reset_check();
   c->bound = true;
   return LBM_OK;
 }
@@ -508,6 +515,7 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u, const double
   // (coalesced writes, B holds nothing that survives an init), then placed
   // into the element slots of A in slot order, and B is reset to rest.
   std::fill(c->parity.begin(), c->parity.end(), 0);
+  c->reset_check();
   for (int64_t first = 0; first < n; first += CH) {
     const int64_t cnt = std::min(CH, n - first);
     lbm_status s = c->cuda_check(cudaMemcpyAsync(sr, rho + first, cnt * 8, cudaMemcpyHostToDevice, c->st), "init copy");
@@ -564,9 +572,56 @@ lbm_status lbm_set_force(lbm_ctx* c, const double* F) {
   return s;
 }
 
-lbm_status lbm_step(lbm_ctx* c, int64_t n_coarse) {
-  if (!c || n_coarse < 0) return LBM_ERR_ARG;
-  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_step before lbm_bind");
+// the FP64 reductions of the current state into out[8] (host), synchronising
+static lbm_status reduce_to_host(lbm_ctx* c, double out[8]) {
+  // the per-level arguments come from the one plan builder (also used by
+  // lbm_reduce_noalloc); only the partial rows differ
+  ReducePlan plan;
+  lbm_status ps = reduce_plan(c, &plan);
+  if (ps != LBM_OK) return ps;
+  for (int li = 0; li < c->nlev; ++li) {
+    ReduceArgs a = plan.levels[li];
+    a.partial = c->at<double>(c->oPartial) + (size_t)li * kReduceBlocks * 8;
+    c->ops->reduce(c->Q, a, c->st);
+    ++c->launches;
+  }
+  FinalArgs fa{c->at<double>(c->oPartial), (int64_t)c->nlev * kReduceBlocks, c->at<double>(c->oRed)};
+  launch_final_reduce(fa, c->st);
+  ++c->launches;
+  lbm_status s = c->launched("reduce");
+  if (s == LBM_OK) s = c->cuda_check(cudaMemcpyAsync(out, c->at(c->oRed), 64, cudaMemcpyDeviceToHost, c->st), "reduce copy");
+  if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "reduce sync");
+  return s;
+}
+
+// the mass check of params.check_every: finite, and within mass_band of the
+// reference mass when a band is set
+static lbm_status check_mass(lbm_ctx* c, bool reference) {
+  double r[8];
+  lbm_status s = reduce_to_host(c, r);
+  if (s != LBM_OK) return s;
+  const double m = r[0];
+  char buf[160];
+  if (!std::isfinite(m)) {
+    std::snprintf(buf, sizeof buf, "mass check after %lld coarse steps: mass is not finite (%g)",
+                  (long long)c->steps_done, m);
+    return c->fail(LBM_ERR_NUMERIC, buf);
+  }
+  if (reference) {
+    c->mass_ref = m;
+    c->mass_ref_valid = true;
+    return LBM_OK;
+  }
+  if (c->p.mass_band > 0.0 && std::fabs(m / c->mass_ref - 1.0) > c->p.mass_band) {
+    std::snprintf(buf, sizeof buf, "mass check after %lld coarse steps: mass %.17g outside %g of %.17g",
+                  (long long)c->steps_done, m, c->p.mass_band, c->mass_ref);
+    return c->fail(LBM_ERR_NUMERIC, buf);
+  }
+  return LBM_OK;
+}
+
+// n_coarse coarse steps with no check in between
+static lbm_status step_run(lbm_ctx* c, int64_t n_coarse) {
   int64_t k = 0;
   // pairs of coarse steps replay a captured graph; a single step, timed
   // steps and the adjoint's recorded steps are issued one kernel at a time
@@ -582,6 +637,36 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n_coarse) {
   }
   for (; k < n_coarse; ++k) c->advance(0);
   return c->launched("step");
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t n_coarse) {
+  if (!c || n_coarse < 0) return LBM_ERR_ARG;
+  if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_step before lbm_bind");
+  const int64_t M = c->p.check_every;
+  if (M <= 0) {
+    c->steps_done += n_coarse;
+    return step_run(c, n_coarse);
+  }
+  // the optional mass check: after every M-th coarse step, counted across calls
+  if (!c->mass_ref_valid && n_coarse > 0) {
+    lbm_status s = check_mass(c, true);
+    if (s != LBM_OK) return s;
+  }
+  int64_t done = 0;
+  while (done < n_coarse) {
+    const int64_t chunk = std::min(n_coarse - done, M - c->steps_since_check);
+    lbm_status s = step_run(c, chunk);
+    if (s != LBM_OK) return s;
+    done += chunk;
+    c->steps_done += chunk;
+    c->steps_since_check += chunk;
+    if (c->steps_since_check == M) {
+      c->steps_since_check = 0;
+      s = check_mass(c, false);
+      if (s != LBM_OK) return s;
+    }
+  }
+  return LBM_OK;
 }
 
 lbm_status lbm_fill_ghosts(lbm_ctx* c) {
@@ -652,6 +737,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const double* f) {
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_set_state before lbm_bind");
   const int64_t n = c->M.n_user, CH = c->chunk;
   double* sf = c->at<double>(c->oStage);
+  c->reset_check();
   for (int64_t first = 0; first < n; first += CH) {
     const int64_t cnt = std::min(CH, n - first);
     lbm_status s = c->cuda_check(
@@ -670,24 +756,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const double* f) {
 lbm_status lbm_reduce(lbm_ctx* c, double out[8]) {
   if (!c || !out) return LBM_ERR_ARG;
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_reduce before lbm_bind");
-  // the per-level arguments come from the one plan builder (also used by
-  // lbm_reduce_noalloc); only the partial rows differ
-  ReducePlan plan;
-  lbm_status ps = reduce_plan(c, &plan);
-  if (ps != LBM_OK) return ps;
-  for (int li = 0; li < c->nlev; ++li) {
-    ReduceArgs a = plan.levels[li];
-    a.partial = c->at<double>(c->oPartial) + (size_t)li * kReduceBlocks * 8;
-    c->ops->reduce(c->Q, a, c->st);
-    ++c->launches;
-  }
-  FinalArgs fa{c->at<double>(c->oPartial), (int64_t)c->nlev * kReduceBlocks, c->at<double>(c->oRed)};
-  launch_final_reduce(fa, c->st);
-  ++c->launches;
-  lbm_status s = c->launched("reduce");
-  if (s == LBM_OK) s = c->cuda_check(cudaMemcpyAsync(out, c->at(c->oRed), 64, cudaMemcpyDeviceToHost, c->st), "reduce copy");
-  if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "reduce sync");
-  return s;
+  return reduce_to_host(c, out);
 }
 
 lbm_status lbm_ghost_count(const lbm_ctx* c, int64_t* n) {

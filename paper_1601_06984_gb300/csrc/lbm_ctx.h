@@ -41,6 +41,18 @@ struct lbm_ctx {
   cudaStream_t st = nullptr;
   std::vector<int> parity;
   int64_t launches = 0;
+  // optional mass check (params.check_every): coarse steps since the last
+  // check, and the reference mass (taken at the first lbm_step after bind,
+  // init or set_state)
+  int64_t steps_since_check = 0;
+  bool mass_ref_valid = false;
+  double mass_ref = 0.0;
+  int64_t steps_done = 0;  // coarse steps since bind / init / set_state (for messages)
+  void reset_check() {
+    steps_since_check = 0;
+    mass_ref_valid = false;
+    steps_done = 0;
+  }
   // observer called before every op of advance() (records the adjoint tape);
   // with dry set, advance() only walks the op sequence and flips parities
   std::function<void(int op, int level)> hook;

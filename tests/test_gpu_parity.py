@@ -76,10 +76,17 @@ def make_case(name):
         om = W.omega_coarse_from_finest(1.6, 3)
         return (m, 19, om, (0.04, 0, 0),
                 lambda m: (*W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), W.pdf_perturbation(m, 19, 1e-4)), None, 3)
+    if name == "sphere5":
+        # five levels, four interfaces: the recursion depth of the sphere
+        # workload (coarsest omega 1.969 for omega_f = 1.6, as near 2 as there)
+        m = W.config_sphere_5level_small()
+        om = W.omega_coarse_from_finest(1.6, 5)
+        return (m, 19, om, (0.04, 0, 0),
+                lambda m: (*W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0)), W.pdf_perturbation(m, 19, 1e-4)), None, 4)
     raise KeyError(name)
 
 
-OUTLET = {"channel_zg": 1}  # zero-gradient outlet extrapolation
+OUTLET = {"channel_zg": 1, "sphere5": 1}  # zero-gradient outlet extrapolation
 # the paper's cylinder: interpolated bounce-back with the wall distances of the
 # circle, parabolic inflow
 BOUZIDI = {"schafer20": (20, (40.0, 40.0), 10.0)}
@@ -110,7 +117,7 @@ def run_both(lbm, oracle_mod, name, mode, precision=0):
 
 
 CASES = ["tgv2d", "tgv2d_half", "tgv3d", "tgv3d_force", "cylinder", "channel_zg", "sphere_small",
-         "tgv3d_q27", "tgv3d_force_q27", "sphere_small_q27", "schafer20"]
+         "tgv3d_q27", "tgv3d_force_q27", "sphere_small_q27", "schafer20", "sphere5"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -132,7 +139,7 @@ def test_fp64_matches_oracle(lbm, oracle_mod, name, mode):
         assert np.abs(red_g[4:7] - red_o[4:7]).max() / np.abs(red_o[4:7]).max() < 1e-10
 
 
-@pytest.mark.parametrize("name", ["tgv2d", "tgv3d", "sphere_small", "tgv3d_q27"])
+@pytest.mark.parametrize("name", ["tgv2d", "tgv3d", "sphere_small", "tgv3d_q27", "sphere5"])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_ghost_fill_matches_oracle(lbm, oracle_mod, name, mode):
     """GhostFromFiner and GhostFromCoarser values after one synchronous fill."""
@@ -155,6 +162,20 @@ def test_ghost_fill_matches_oracle(lbm, oracle_mod, name, mode):
     assert rel(fg[idx_g], fo[idx_o]) < 1e-12
     # layers agree too
     assert np.array_equal(ig[idx_g, 2], io[idx_o, 2])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sphere5_levels_and_reduced_precision(lbm, oracle_mod, precision):
+    """The five-level sphere case per level: every level's elements against the
+    oracle after four coarse steps (64 finest substeps), FP64 at 1e-11 and
+    FP32-deviation storage within its rounding (1e-5 of the pdfs' scale)."""
+    m, o, g = run_both(lbm, oracle_mod, "sphere5", 0, precision)
+    info = g.mesh_info()
+    assert len(info) == 5 and (info[:, 1] > 0).all()
+    fo, fg = o.get_f(), g.get_state()
+    for L in np.unique(m.levels):
+        sel = m.levels == L
+        assert rel(fg[sel], fo[sel]) < (TOL if precision == 0 else 1e-5), L
 
 
 def test_fp64_full_size_tgv3d(lbm, oracle_mod):
@@ -307,3 +328,105 @@ def test_q27_reduced_precision_tracks_fp64(lbm, oracle_mod, precision):
     _, u_g, _ = g.moments()
     err = math.sqrt(((u_g - u_o) ** 2).sum() / (u_o ** 2).sum())
     assert err < {1: 1e-4, 2: 5e-2}[precision], err
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_empty_refined_region_is_identity(lbm, oracle_mod, d, mode):
+    """Sec. 2.2 recursive stepping with nothing to couple: one more declared
+    level without elements (an empty refined region) leaves the FP64 result of
+    lbm_step bit for bit equal to the run without it, through the captured
+    graphs and kernel by kernel alike, and equal to the oracle run with the
+    same declared levels to 1e-11.  Single-level periodic Taylor-Green (the
+    two-level code path against the plain single-level one) and the two-level
+    one with a third, empty level."""
+    if d == 2:
+        meshes = ((W.uniform(2, 5, (32, 32), (0,) * 4), 1), (W.config_tgv2d(), 2))
+        Q = 9
+    else:
+        meshes = ((W.uniform(3, 4, (16, 16, 16), (0,) * 6), 1), (W.config_tgv3d(16), 2))
+        Q = 19
+    for mesh, nl in meshes:
+        rho, u, S = W.tgv_fields(mesh, 0.02)
+        df = W.pdf_perturbation(mesh, Q, 1e-6)
+        res = []
+        for n_levels in (0, nl + 1):
+            g = lbm.Sim(mesh, Q, 1.8, time_mode=mode, n_levels=n_levels)
+            assert len(g.mesh_info()) == (nl if n_levels == 0 else nl + 1)
+            g.init(rho, u, S, df)
+            g.step(6)       # three captured two-step graphs
+            g.step(1)       # one step kernel by kernel
+            res.append((g.get_state(), g.reduce(), g.moments()))
+        (f0, r0, m0), (f1, r1, m1) = res
+        assert np.array_equal(f0, f1)
+        assert np.array_equal(r0, r1)
+        assert all(np.array_equal(a, b) for a, b in zip(m0, m1))
+        o = oracle_mod.Oracle(mesh, Q, 1.8, time_mode=mode, n_levels=nl + 1)
+        o.init(rho, u, S, df)
+        o.step(7)
+        assert rel(f1, o.get_f()) < TOL
+
+
+def test_mass_check_stops_on_non_finite_input(lbm):
+    """params.check_every: a NaN planted on the host in one element's initial
+    density (a host-side fault; nothing faults on the GPU) makes lbm_step
+    return LBM_ERR_NUMERIC at its first check, and the context stays usable:
+    a clean state restored with lbm_set_state steps on normally."""
+    m = W.config_tgv2d()
+    rho, u, S = W.tgv_fields(m, 0.01)
+    bad = rho.copy()
+    bad[123] = np.nan
+    g = lbm.Sim(m, 9, 1.6, check_every=4)
+    g.init(bad, u, S)
+    with pytest.raises(lbm.LBMError, match="not finite") as ei:
+        g.step(10)
+    assert ei.value.status == -6
+    clean = lbm.Sim(m, 9, 1.6)
+    clean.init(rho, u, S)
+    g.set_state(clean.get_state())
+    g.step(8)
+    clean.step(8)
+    assert np.array_equal(g.get_state(), clean.get_state())
+
+
+def test_mass_check_catches_a_blow_up_and_a_band(lbm):
+    """A run that diverges on its own (omega_c = 1.99 with u0 = 0.5 and a 1e-3
+    pdf perturbation, far outside the stable range; the oracle overflows after
+    about 500 steps) trips the finiteness check at a multiple of check_every;
+    a mass band trips on an open channel whose mass changes (by 1.5% in its
+    first 10 steps), and only when the band is tighter than that."""
+    m = W.uniform(2, 5, (32, 32), (0,) * 4)
+    g = lbm.Sim(m, 9, 1.99, check_every=25)
+    g.init(*W.tgv_fields(m, 0.5), W.pdf_perturbation(m, 9, 1e-3))
+    with pytest.raises(lbm.LBMError, match=r"after (\d+) coarse steps") as ei:
+        g.step(5000)
+    assert ei.value.status == -6
+    k = int(__import__("re").search(r"after (\d+) coarse", str(ei.value)).group(1))
+    assert k % 25 == 0 and k > 0
+    ch = W.nested_boxes(2, 5, (32, 16), [((16, 8), (40, 24))],
+                        (W.BC_VELOCITY_IN, W.BC_PRESSURE_OUT, W.BC_WALL, W.BC_WALL))
+    fields = W.uniform_fields(ch, 1.0, (0.0, 0.0))
+    tight = lbm.Sim(ch, 9, 1.85, u_in=(0.05, 0, 0), outlet=1, check_every=10, mass_band=1e-9)
+    tight.init(*fields)
+    with pytest.raises(lbm.LBMError, match="outside"):
+        tight.step(100)
+    loose = lbm.Sim(ch, 9, 1.85, u_in=(0.05, 0, 0), outlet=1, check_every=10, mass_band=0.5)
+    loose.init(*fields)
+    loose.step(100)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mass_check_leaves_clean_runs_unchanged(lbm, precision):
+    """With the check on, a clean run takes the same steps in the same order:
+    its state is bit for bit that of the run without the check, whatever the
+    split of the steps over lbm_step calls."""
+    m, Q, om, uin, fields, _, _ = make_case("sphere_small")
+    rho, u, S, df = fields(m)
+    res = []
+    for check, calls in ((0, (7,)), (3, (4, 3)), (2, (1, 1, 5))):
+        g = lbm.Sim(m, Q, om, precision=precision, u_in=uin, check_every=check, mass_band=1e-2 if check else 0.0)
+        g.init(rho, u, S, df)
+        for n in calls:
+            g.step(n)
+        res.append(g.get_state())
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])

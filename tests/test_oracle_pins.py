@@ -233,6 +233,55 @@ def test_single_level_conservation(oracle_mod, Q):
     assert np.abs(m1[1:1 + d] - m0[1:1 + d]).max() / m0[0] < 1e-12
 
 
+@pytest.mark.parametrize("d,Q,mode", [(2, 9, 0), (2, 9, 1), (3, 19, 0), (3, 19, 1)])
+def test_empty_refined_region_is_identity(oracle_mod, d, Q, mode):
+    """Sec. 2.2 recursive level stepping with nothing to couple: declaring one
+    more, finer level that holds no element (an empty refined region) runs the
+    multilevel driver's substeps and ghost fills on empty sets, and leaves the
+    result bit for bit equal to the run without that level.  Checked on a
+    single-level periodic Taylor-Green vortex (the two-level code path against
+    the plain single-level run) and on the two-level one (a third, empty level),
+    with the seeded pdf perturbation, over enough steps for every ghost to be
+    filled many times."""
+    if d == 2:
+        single, two = W.uniform(2, 5, (32, 32), (0,) * 4), W.config_tgv2d()
+    else:
+        single, two = W.uniform(3, 3, (8, 8, 8), (0,) * 6), W.two_level_block(3, 8, 2, 6)
+    for mesh, nl in ((single, 1), (two, 2)):
+        rho, u, S = W.tgv_fields(mesh, 0.02)
+        df = W.pdf_perturbation(mesh, Q, 1e-6)
+        out = []
+        for n_levels in (0, nl + 1):
+            o = oracle_mod.Oracle(mesh, Q, 1.8, time_mode=mode, n_levels=n_levels)
+            assert len(o.counts()) == (nl if n_levels == 0 else nl + 1)
+            o.init(rho, u, S, df)
+            o.step(12)
+            out.append((o.get_f(), o.moments(), o.reduce(), o.ghosts()[1]))
+        (f0, m0, r0, g0), (f1, m1, r1, g1) = out
+        assert np.array_equal(f0, f1)
+        assert all(np.array_equal(a, b) for a, b in zip(m0, m1))
+        assert np.array_equal(r0, r1)
+        assert np.array_equal(g0, g1)
+        assert np.abs(m0[1] - u).max() > 1e-6  # the state did move
+
+
+def test_oracle_threads_do_not_change_results(oracle_mod):
+    """The oracle's element loops may run on several threads: each element's
+    arithmetic is the same, so one thread and many give identical results."""
+    mesh = W.config_sphere_small()
+    rho, u, S = W.uniform_fields(mesh, 1.0, (0.04, 0.0, 0.0))
+    df = W.pdf_perturbation(mesh, 19, 1e-4)
+    out = []
+    for nt in (1, 4):
+        used = oracle_mod.set_threads(nt)
+        o = oracle_mod.Oracle(mesh, 19, 1.9, u_in=(0.04, 0.0, 0.0), outlet=1)
+        o.init(rho, u, S, df)
+        o.step(3)
+        out.append((o.get_f(), o.reduce(), used))
+    oracle_mod.set_threads(0)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_user_order_does_not_matter(oracle_mod):
     """The element order handed in is arbitrary: a shuffled mesh gives the same
     per-element result."""
@@ -270,11 +319,13 @@ def test_tgv2d_two_level_decay(oracle_mod):
         assert abs(amp / math.exp(-2 * nu * k * k * 200) - 1) < 1e-3
 
 
-def tgv_errors(oracle_mod, N, mode, u0_16=0.0025, omega=1.6):
-    mesh = W.half_refined_2d(N)
+def tgv_errors(oracle_mod, N, mode, u0_16=0.0025, omega=1.6, mesh=None):
+    """l2 errors of u_x and S_xx (Sec. 4.1 error norm, S in coarse units) at
+    t = t_D, the vortex decay time 1/(2 nu k^2), where Sec. 4.1 evaluates."""
+    mesh = mesh or W.half_refined_2d(N)
     nu = (1 / omega - 0.5) / 3
     k = 2 * math.pi / N
-    steps = int(round(0.25 / (2 * nu * k * k)))
+    steps = int(round(1.0 / (2 * nu * k * k)))
     u0 = u0_16 * 16 / N  # diffusive scaling: Ma -> 0 with the mesh
     o = oracle_mod.Oracle(mesh, 9, omega, time_mode=mode)
     rho, u, S = W.tgv_fields(mesh, u0)
@@ -288,18 +339,49 @@ def tgv_errors(oracle_mod, N, mode, u0_16=0.0025, omega=1.6):
     return eu, eS
 
 
+RES = (16, 32, 64, 128)  # Sec. 4.1: levels L = 4, 5, 6, 7
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_tgv_second_order_convergence(oracle_mod, mode):
-    """Sec. 4.1, Fig. tgv_conv: with the left half at level L and the right half
-    one level finer, the l2 errors of u_x and S_xx (Eq. error norm) converge at
-    second order.  Diffusive scaling (u0 ~ dx, omega fixed) so the Ma^2 error
-    converges too; errors at t = t_D/4."""
-    errs = [tgv_errors(oracle_mod, N, mode) for N in (16, 32, 64)]
-    for a, b in zip(errs[:-1], errs[1:]):
-        su = math.log2(a[0] / b[0])
-        sS = math.log2(a[1] / b[1])
-        assert 1.8 < su < 2.8, (mode, errs)
-        assert 1.8 < sS < 2.8, (mode, errs)
+    """Sec. 4.1, Fig. tgv_conv: left half of the periodic square at level L,
+    right half one level finer, L = 4..7, errors at t = t_D.  Diffusive
+    scaling (u0 ~ dx, omega fixed) so the Ma^2 error converges too.
+    - The convergence order, the leading exponent p of a fit of
+      e(N) = A N^-p + B N^-(p+1) to the four resolutions, lies in [1.8, 2.2]
+      for u_x and for S_xx.
+    - The local slopes of S_xx lie in [1.8, 2.2] pair by pair.
+    - The local slopes of u_x approach 2 from above (2.6, 2.5, 2.3 here): on
+      these coarse meshes the interface's third-order error is still
+      comparable to its second-order one.  They must decrease monotonically and
+      stay within [1.8, 2.7].
+    A first-order interface (e.g. a plain average of the children's velocity
+    in GhostFromFiner) gives p near 1 and fails all three."""
+    from conv_fit import leading_order, local_slopes
+    errs = np.array([tgv_errors(oracle_mod, N, mode) for N in RES])
+    for col in (0, 1):
+        p = leading_order(RES, errs[:, col])
+        assert 1.8 <= p <= 2.2, (mode, col, p, errs)
+    sS = local_slopes(RES, errs[:, 1])
+    assert np.all((sS >= 1.8) & (sS <= 2.2)), (mode, sS)
+    su = local_slopes(RES, errs[:, 0])
+    assert np.all((su >= 1.8) & (su <= 2.7)) and np.all(np.diff(su) < 0), (mode, su)
+
+
+def test_tgv_single_level_second_order(oracle_mod):
+    """Control for the test above: on a single-level periodic square (no
+    interface) the same Taylor-Green run converges at second order in the
+    local slopes of both u_x and S_xx at t = t_D (the first pair of u_x, at
+    N = 16, is 2.27), so the slopes above 2 of the two-level run come from the
+    interface error, and the lattice's own error is second order."""
+    from conv_fit import leading_order, local_slopes
+    errs = np.array([tgv_errors(oracle_mod, N, 0, mesh=W.uniform(2, int(math.log2(N)), (N, N), (0,) * 4))
+                     for N in RES])
+    su, sS = local_slopes(RES, errs[:, 0]), local_slopes(RES, errs[:, 1])
+    assert np.all((su[1:] >= 1.8) & (su[1:] <= 2.2)) and 1.8 <= su[0] <= 2.4, su
+    assert np.all((sS >= 1.8) & (sS <= 2.2)), sS
+    for col in (0, 1):
+        assert 1.8 <= leading_order(RES, errs[:, col]) <= 2.2
 
 
 def test_poiseuille_exact_at_magic_relaxation(oracle_mod):
