@@ -4,8 +4,8 @@
 Default workload: the sphere flow at Re = 100 (box 32D x 16D x 16D, sphere
 D = 64 finest elements, five levels D/4 .. D/64, about 8.6e7 fluid elements,
 velocity inlet / pressure outlet), FP32-deviation storage.  A "step" is one
-coarse time step of the whole hierarchy (31 stream-collide launches plus the
-ghost fills).  The metric is fine-substep weighted MLUPS,
+coarse time step of the whole hierarchy (31 level substeps of stream-collide
+plus the ghost fills).  The metric is fine-substep weighted MLUPS,
 U = sum_L N_L 2^{L - Lmin} element updates per coarse step.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -29,9 +29,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "multilevel D3Q19 MLUPS & % HBM peak, FP32-dev vs FP64 at stated error"
+NOMINAL_HBM_GBS = 8000.0
 SMI_FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+KINDS = ("interior", "list", "boundary", "gff", "moments", "gfc", "outlet")
 
 
 def parse():
@@ -42,8 +44,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere", choices=["sphere", "sphere_half", "tgv3d"],
                     help="sphere_half: every length halved (about 1.1e7 elements), for profiling captures")
-    ap.add_argument("--no-variants", action="store_true", help="skip the FP64/BF16 and TGV side measurements")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP64/BF16/D3Q27 variants, the precision errors, the side workloads, the "
+                         "adjoint and the oracle timings of the other configurations")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--develop-steps", type=int, default=400,
+                    help="coarse steps from rest before the precision comparison")
     return ap.parse_args()
 
 
@@ -70,20 +76,11 @@ def make_workload(name):
     return mesh, 19, 1.6, (0.0, 0.0, 0.0), fields, desc
 
 
-def small_sample():
-    """Bounded sample of the sphere workload for the CPU oracle: the reduced
-    three-level sphere case (about 1.75e4 elements)."""
-    from paper_1601_06984_gb300 import workloads as W
-    m = W.config_sphere_small()
-    om = W.omega_coarse_from_finest(W.omega_for_re(0.04, 64, 100.0), 3)
-    return m, om, (0.04, 0.0, 0.0)
-
-
 def bytes_per_update(Q, prec, brick=False):
     """Algorithmic HBM bytes of one element update: Q pdf reads and Q writes,
     plus the 32-bit neighbour list (Q-1 entries) for the neighbour-list kernel
     or one 27-entry row of neighbour-brick indices per 64 elements for the
-    interior-brick kernel."""
+    brick kernels."""
     s = {0: 8, 1: 4, 2: 2}[prec]
     return 2 * Q * s + (27 * 4 / 64 if brick else 4 * (Q - 1))
 
@@ -140,32 +137,13 @@ def gpu_uuid(dev):
         return None
 
 
-def stream_collide_traffic():
-    """DRAM bytes per element update of the finest-level interior-brick
-    stream-collide from the committed ncu capture, if the kernel source is
-    unchanged since."""
+def _profile_record(name):
+    """A committed ncu record under profiles/, if the stream-collide source
+    (kernels.cuh, sections "physics" to "outlet values") is unchanged since it
+    was taken."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "stream_collide_brick_fp32_sphere.json")) as fh:
-            rec = json.load(fh)
-        with open(os.path.join(ROOT, "paper_1601_06984_gb300", "csrc", "kernels.cuh")) as fh:
-            src = fh.read()
-        a = src.index("// ----------------------------------------------------------------- physics")
-        b = src.index("// ----------------------------------------------------------------- outlet values")
-        if hashlib.sha256(src[a:b].encode()).hexdigest()[:16] != rec["kernel_source_sha256_16"]:
-            return None
-        return float(rec["dram_bytes_per_unit"])
-    except Exception:
-        return None
-
-
-def fp64_instruction_record():
-    """FP64 instructions per element update of the interior-brick kernel and
-    the FP64 issue peak, from the committed ncu count, if the kernel source is
-    unchanged since."""
-    import hashlib
-    try:
-        with open(os.path.join(ROOT, "profiles", "stream_collide_brick_fp64_tgv3d.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", name)) as fh:
             rec = json.load(fh)
         with open(os.path.join(ROOT, "paper_1601_06984_gb300", "csrc", "kernels.cuh")) as fh:
             src = fh.read()
@@ -176,6 +154,20 @@ def fp64_instruction_record():
         return rec
     except Exception:
         return None
+
+
+def stream_collide_traffic():
+    """DRAM bytes per element update of the finest-level interior-brick
+    stream-collide from the committed ncu capture (None once the kernel
+    changed)."""
+    rec = _profile_record("stream_collide_brick_fp32_sphere.json")
+    return None if rec is None else float(rec["dram_bytes_per_unit"])
+
+
+def fp64_instruction_record():
+    """FP64 instructions and flops per element update of the interior-brick
+    kernel from the committed ncu count (None once the kernel changed)."""
+    return _profile_record("stream_collide_brick_fp64_tgv3d.json")
 
 
 def measured_peaks():
@@ -205,13 +197,32 @@ def job_throughput(updates_per_rank, seconds_per_rank, world, dist=None, device=
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle(seconds, min_steps=2):
-    """Time the CPU oracle (single thread) on the bounded sample."""
-    from oracle.oracle import Oracle
+def oracle_cases():
+    """The oracle timing cases: the configurations' meshes (config 2 and the
+    sphere as bounded samples) with their parameters."""
     from paper_1601_06984_gb300 import workloads as W
-    m, om, uin = small_sample()
-    o = Oracle(m, 19, om, u_in=uin, outlet=1)
-    o.init(*W.uniform_fields(m, 1.0, uin))
+    cyl_om = W.omega_coarse_from_finest(W.omega_for_re(0.05, 40, 100.0), 4)
+    sph_om = W.omega_coarse_from_finest(W.omega_for_re(0.04, 64, 100.0), 3)
+    return {
+        "tgv2d_two_level_32": (W.config_tgv2d, 9, 1.6, (0.0, 0.0, 0.0), 0, lambda m: W.tgv_fields(m, 0.01)),
+        "tgv3d_two_level_64": (lambda: W.config_tgv3d(64), 19, 1.6, (0.0, 0.0, 0.0), 0,
+                               lambda m: W.tgv_fields(m, 0.01)),
+        "cylinder_d2q9_4level": (W.config_cylinder, 9, cyl_om, (0.05, 0.0, 0.0), 1,
+                                 lambda m: W.uniform_fields(m, 1.0, (0.05, 0.0))),
+        "sphere_sample_3level": (W.config_sphere_small, 19, sph_om, (0.04, 0.0, 0.0), 1,
+                                 lambda m: W.uniform_fields(m, 1.0, (0.04, 0.0, 0.0))),
+    }
+
+
+def oracle_rate(name, seconds, threads, min_steps=2):
+    """Time the oracle (FP64, as it stands) on one case with the given thread
+    count (0: every host core); returns MLUPS and what was run."""
+    from oracle import oracle as O
+    make, Q, om, uin, outlet, fields = oracle_cases()[name]
+    used = O.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
+    m = make()
+    o = O.Oracle(m, Q, om, u_in=uin, outlet=outlet)
+    o.init(*fields(m))
     o.step(1)
     steps, t0 = 0, time.perf_counter()
     while steps < min_steps or time.perf_counter() - t0 < seconds:
@@ -219,10 +230,25 @@ def cpu_oracle(seconds, min_steps=2):
         steps += 1
     dt = time.perf_counter() - t0
     U = m.updates_per_coarse_step()
-    return {"value": steps * U / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"reduced 3-level D3Q19 sphere ({m.n} elements, {U} updates/coarse step), "
-                      f"{steps} coarse steps, single-threaded FP64 oracle",
+    O.set_threads(0)
+    return {"value": steps * U / dt / 1e6, "unit": "MLUPS", "cores": used, "kind": "oracle",
+            "sample": f"{name} ({m.n} elements, {U} updates/coarse step), {steps} coarse steps, FP64 oracle on "
+                      f"{used} host thread{'s' if used > 1 else ''}",
             "seconds": round(dt, 2), "ms_per_step": 1e3 * dt / steps}
+
+
+def oracle_timings(seconds_each):
+    """Oracle MLUPS on every configuration, one thread and every host core."""
+    out = {"host_cores": os.cpu_count()}
+    for name in oracle_cases():
+        one = oracle_rate(name, seconds_each, 1)
+        allc = oracle_rate(name, seconds_each, 0)
+        out[name] = {"single_thread_mlups": one["value"], "all_cores_mlups": allc["value"],
+                     "threads": allc["cores"], "sample_steps": allc["sample"].split(", ")[1]}
+    out["note"] = ("config 2 and the sphere are run on their meshes as given (64^3 two-level TGV) and on the "
+                   "reduced 3-level sphere sample; the full 5-level sphere (8.6e7 elements) would take the oracle "
+                   "about 8.6e7 x 31 / rate seconds per coarse step")
+    return out
 
 
 # ---------------------------------------------------------------- GPU runs
@@ -230,11 +256,14 @@ OUTLETS = {"linear": 0, "zero-gradient": 1}
 
 
 def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_moments=False, outlet=0,
-            kernel_timing=True):
+            kernel_timing=True, state=None):
     """Time K coarse steps after W_ warm-up steps.  With kernel_timing the
-    library brackets every stream-collide launch with CUDA events (steps are
-    then launched kernel by kernel); without it the steps replay the library's
-    captured CUDA graphs, as a caller's lbm_step(K) does."""
+    library brackets every launch with CUDA events (steps are then launched
+    kernel by kernel) and the per-kernel times come from those events; without
+    it the steps replay the library's captured CUDA graphs, as a caller's
+    lbm_step(K) does.  state: post-collision pdfs [n, Q] to start from instead
+    of the fields."""
+    import numpy as np
     import torch
 
     from paper_1601_06984_gb300 import lbm
@@ -242,8 +271,11 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     t_build = time.perf_counter()
     sim = lbm.Sim(mesh, Q, om, precision=prec, u_in=uin, device=device, outlet=outlet)
     t_build = time.perf_counter() - t_build
-    rho, u, S = fields(mesh)
-    sim.init(rho, u, S)
+    if state is None:
+        rho, u, S = fields(mesh)
+        sim.init(rho, u, S)
+    else:
+        sim.set_state(state)
     sim.step(W_)
     info = sim.mesh_info()
     stream = sim.stream
@@ -258,11 +290,16 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     sim.step(K)
     ev1.record(stream)
     torch.cuda.synchronize(device)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(device)
     ms = ev0.elapsed_time(ev1)
     launches = sim.kernel_launches() - n0
     nl, kms = sim.timing_read()
+    sim.timing_enable(False)
     ms = max_over_ranks(ms, dist, device)
     finest = len(info) - 1
+    nlev = len(info)
     # dominant kernel: the interior-brick stream-collide of the finest level
     # (the neighbour-list kernel when the level has no interior bricks)
     kb = 0 if info[finest, 8] > 0 else 1
@@ -273,6 +310,13 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     list_ms = kms[finest, 1] / max(nl[finest, 1], 1)
     bnd_units = int(64 * info[finest, 9])
     bnd_ms = kms[finest, 2] / max(nl[finest, 2], 1)
+    # algorithmic bytes of one coarse step: every level's interior and boundary
+    # bricks at the brick rate, the rest at the neighbour-list rate, times its
+    # substeps per coarse step
+    brick_units = [int(64 * (info[li, 8] + info[li, 9])) for li in range(nlev)]
+    step_bytes = float(sum((1 << li) * (brick_units[li] * bytes_per_update(Q, prec, brick=True)
+                                        + (info[li, 1] - brick_units[li]) * bytes_per_update(Q, prec))
+                           for li in range(nlev)))
     res = {"ms_total": ms, "ms_per_step": ms / K, "mlups": K * U / (ms * 1e-3) / 1e6, "launches": launches,
            "finest_kernel": "k_stream_collide_brick" if kb == 0 else "k_stream_collide",
            "finest_launch_ms": avg_ms, "finest_launches": int(nl[finest, kb]), "finest_units": units,
@@ -283,18 +327,41 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
                                    if nl[finest, 2] > 0 and bnd_ms > 0 else None),
            "finest_list_gbs": (list_units * bytes_per_update(Q, prec) / (list_ms * 1e-3) / 1e9
                                if nl[finest, 1] > 0 and list_ms > 0 else None),
-           "level_ms": kms.sum(axis=1).tolist(), "level_launches": nl.sum(axis=1).tolist(),
            "interior_fraction": float(64 * info[:, 8].sum() / info[:, 1].sum()),
            "brick_fraction": float(64 * (info[:, 8] + info[:, 9]).sum() / info[:, 1].sum()),
-           "step_bytes": float(sum((1 << li) * (64 * (info[li, 8] + info[li, 9]) * bytes_per_update(Q, prec, brick=True)
-                                                + (info[li, 1] - 64 * (info[li, 8] + info[li, 9]))
-                                                * bytes_per_update(Q, prec))
-                                   for li in range(len(info)))),
-           "bytes_per_update": bpu, "build_s": t_build, "device_gb": sim.device_bytes() / 1e9,
-           "reduce": sim.reduce().tolist()}
+           "step_bytes": step_bytes, "bytes_per_update": bpu, "build_s": t_build,
+           "device_gb": sim.device_bytes() / 1e9, "reduce": sim.reduce().tolist()}
+    if kernel_timing:
+        per_kind = {k: float(kms[:, i].sum() / K) for i, k in enumerate(KINDS)}
+        res["breakdown_ms_per_step"] = dict(per_kind, between_kernels=ms / K - sum(per_kind.values()))
+        res["level_ms_per_step"] = {f"L{int(info[li, 0])}": {k: round(float(kms[li, i] / K), 4)
+                                                            for i, k in enumerate(KINDS) if nl[li, i] > 0}
+                                    for li in range(nlev)}
+        # every level's brick stream-collide against the HBM roofline
+        res["level_brick_gbs"] = {}
+        for li in range(nlev):
+            for i, key in ((0, "interior"), (2, "boundary")):
+                n_ = int(64 * info[li, 8 if i == 0 else 9])
+                if nl[li, i] > 0 and n_ > 0:
+                    res["level_brick_gbs"][f"L{int(info[li, 0])}_{key}"] = round(
+                        n_ * bytes_per_update(Q, prec, brick=True) / (kms[li, i] / nl[li, i] * 1e-3) / 1e9, 1)
     if want_moments:
         res["moments"] = sim.moments()
     return sim, res
+
+
+def graph_replay(sim, K, device):
+    """K coarse steps on the same context through lbm_step's captured graphs
+    (no per-kernel events), timed with CUDA events on the bound stream."""
+    import torch
+    sim.step(2)  # capture both parity states' graphs outside the timed region
+    torch.cuda.synchronize(device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    sim.step(K)
+    ev1.record(sim.stream)
+    torch.cuda.synchronize(device)
+    return ev0.elapsed_time(ev1) / K
 
 
 def adjoint_run(device):
@@ -375,6 +442,89 @@ def e2e_run(sim, mesh, fields, K):
             "seconds": round(dt, 3), "launches": sim.kernel_launches() - n0}
 
 
+def _rel_l2(a, b):
+    import numpy as np
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def precision_study(mesh, Q, om, uin, fields, K, W_, device, outlet, develop, peak, sim32, done):
+    """Precision variants from a developed flow.  The FP32-deviation run, `done`
+    coarse steps from rest, is carried on by `develop` more; its state (FP64 host copy)
+    then starts an FP64, an FP32-deviation and a BF16-deviation run, each timed
+    over K steps after W_ warm-up steps.  The errors of FP32 and BF16 against
+    FP64 after those W_ + K steps: velocity and strain rate (relative l2 over
+    all fluid elements, strain rate in coarsest-level units as the error norm of
+    Sec. 4.1), drag and lift (momentum exchange on the sphere)."""
+    import numpy as np
+    import torch
+
+    from paper_1601_06984_gb300 import lbm
+    t0 = time.perf_counter()
+    sim32.step(develop)
+    f_dev = sim32.get_state()
+    t_dev = time.perf_counter() - t0
+    sim32.close()
+    torch.cuda.empty_cache()
+    sc = np.ldexp(1.0, mesh.levels.astype(np.int64) - mesh.lmin)[:, None]
+    rec, mom, red = {}, {}, {}
+    for name, prec in (("fp64", lbm.FP64), ("fp32dev", lbm.FP32DEV), ("bf16dev", lbm.BF16DEV)):
+        s, r = run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, None, want_moments=True, outlet=outlet,
+                       state=f_dev)
+        _, u, S = r.pop("moments")
+        mom[name] = (u, S * sc)
+        red[name] = np.asarray(r["reduce"])
+        rec[name] = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "finest_kernel_gbs": r["finest_gbs"],
+                     "finest_kernel_frac": r["finest_gbs"] / peak, "bytes_per_update": r["bytes_per_update"],
+                     "device_gb": r["device_gb"], "step_gbs_algorithmic": r["step_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9,
+                     "breakdown_ms_per_step": r["breakdown_ms_per_step"], "finest_units": r["finest_units"],
+                     "finest_launch_ms": r["finest_launch_ms"], "reduce": r["reduce"]}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    del f_dev
+    ref_u, ref_S = mom["fp64"]
+    rf = red["fp64"]
+    errors = {}
+    for name in ("fp32dev", "bf16dev"):
+        u, S = mom[name]
+        rp = red[name]
+        errors[name] = {"u_l2_rel_vs_fp64": _rel_l2(u, ref_u), "S_l2_rel_vs_fp64": _rel_l2(S, ref_S),
+                        "u_max_abs_vs_fp64": float(np.abs(u - ref_u).max()),
+                        "drag_rel_vs_fp64": float(abs(rp[4] - rf[4]) / abs(rf[4])) if rf[4] else None,
+                        "lift_y_vs_fp64_rel_to_drag": float(abs(rp[5] - rf[5]) / abs(rf[4])) if rf[4] else None,
+                        "lift_z_vs_fp64_rel_to_drag": float(abs(rp[6] - rf[6]) / abs(rf[4])) if rf[4] else None,
+                        "mass_rel_vs_fp64": float(abs(rp[0] - rf[0]) / rf[0])}
+    errors["state"] = (f"flow developed for {done + develop} coarse steps from rest (uniform u_in) in FP32-deviation storage, "
+                       f"then each precision runs {W_ + K} coarse steps from that state; fp64 drag "
+                       f"{rf[4]:.6g}, lift {rf[5]:.3g}, {rf[6]:.3g} (finest-level lattice units)")
+    errors["develop_seconds"] = round(t_dev, 1)
+    return rec, errors
+
+
+def side_workload(mesh, Q, om, uin, fields, precs, steps, device, outlet=0, ref=None):
+    """MLUPS of a small workload through graph replay (lbm_step(steps)), and
+    the velocity error against `ref(mesh, steps)` when given."""
+    import numpy as np
+    import torch
+
+    from paper_1601_06984_gb300 import lbm
+    out = {}
+    for name, prec in precs:
+        s, r = run_gpu(mesh, Q, om, uin, fields, prec, steps, 3, device, None, want_moments=ref is not None,
+                       outlet=outlet, kernel_timing=False)
+        rec = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"],
+               "hbm_gbs_algorithmic": r["step_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9}
+        if ref is not None:
+            _, u, _ = r.pop("moments")
+            ua = ref(mesh, steps + 3)
+            rec["u_l2_rel_vs_closed_form"] = float(np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum()))
+        out[name] = rec
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -386,7 +536,9 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_oracle(max(5.0, min(args.cpu_seconds, 20.0)), min_steps=K)
+        # each timed step is one coarse step of the bounded sample; the oracle
+        # runs until K steps and the time budget are both used
+        cb = oracle_rate("sphere_sample_3level", max(5.0, min(args.cpu_seconds, 20.0)), 0, min_steps=K)
         desc = {"workload": "sphere_re100_d3q19_5level" if args.workload == "sphere" else "tgv3d_two_level_64"}
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
                 "steps": K, "warmup": W_, "ms_per_step": cb["ms_per_step"], "higher_is_better": True,
@@ -420,95 +572,89 @@ def main():
 
     clk = Clocks(uuid=gpu_uuid(device), index=local)
     outlet = OUTLETS.get(desc.get("outlet"), 0)
-    sim, r = run_gpu(mesh, Q, om, uin, fields, lbm.FP32DEV, K, W_, device, dist,
-                     want_moments=not args.no_variants, outlet=outlet)
+    sim, r = run_gpu(mesh, Q, om, uin, fields, lbm.FP32DEV, K, W_, device, dist, outlet=outlet)
     clocks = clk.stop()
+    graph_ms = graph_replay(sim, K, device)
     e2e = e2e_run(sim, mesh, fields, K)
     if dist is not None:
         e2e["value"] = job_throughput(K * U, e2e["seconds"], world, dist, device)
-    mom32 = r.pop("moments", None)
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
 
-    variants, errors, tgv, adj = {}, {}, None, None
+    variants, errors, side, adj, oracles, alu = {}, {}, {}, None, None, None
     if not args.no_variants and rank == 0 and world == 1:
-        mom = {}
-        for name, prec in (("fp64", lbm.FP64), ("bf16dev", lbm.BF16DEV)):
-            s2, r2 = run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, None, want_moments=True,
-                             outlet=outlet)
-            mom[name] = r2.pop("moments")
-            variants[name] = {"mlups": r2["mlups"], "ms_per_step": r2["ms_per_step"],
-                              "finest_kernel_gbs": r2["finest_gbs"], "finest_kernel_frac": r2["finest_gbs"] / peak,
-                              "bytes_per_update": r2["bytes_per_update"], "device_gb": r2["device_gb"],
-                              "reduce": r2["reduce"]}
-            if name == "fp64":
-                rec = fp64_instruction_record()
-                rate = r2["finest_units"] / (r2["finest_launch_ms"] * 1e-3)  # elements / s
-                variants[name]["alu_roofline"] = None if rec is None else {
-                    "bound": "alu", "unit": "G FP64 inst/s",
-                    "achieved": rate * rec["fp64_inst_per_unit"] / 1e9,
-                    "peak": rec["peak_fp64_inst_per_s"] / 1e9,
-                    "frac": rate * rec["fp64_inst_per_unit"] / rec["peak_fp64_inst_per_s"],
-                    "fp64_inst_per_update": rec["fp64_inst_per_unit"], "flops_per_update": rec["flops_per_unit"],
-                    "peak_source": "152 SMs x 2 FP64 inst/clock x 2.07 GHz (profiles/stream_collide_brick_fp64_tgv3d.md)"}
-            s2.close()
-            del s2
-            torch.cuda.empty_cache()
+        # the FP32 context is K steps past its last init (the end-to-end run)
+        rec, errors = precision_study(mesh, Q, om, uin, fields, K, W_, device, outlet, args.develop_steps, peak,
+                                      sim, K)
+        sim = None
+        variants = {"fp64": rec["fp64"], "bf16dev": rec["bf16dev"], "fp32dev_from_developed_state": rec["fp32dev"]}
+        # FP64 against the FP64 pipe: instructions per update from the committed
+        # ncu count, peak from the multiply-add probe run now
+        fp64_peak = lbm.lbm_alu_peak(lbm.FP64, device)
+        fp32_peak = lbm.lbm_alu_peak(lbm.FP32DEV, device)
+        alu = {"fp64_gflops": fp64_peak, "fp32_gflops": fp32_peak,
+               "how": "lbm_alu_peak: register-only multiply-add chains on every SM, CUDA events, 2 flop per FMA"}
+        irec = fp64_instruction_record()
+        v = rec["fp64"]
+        rate = v["finest_units"] / (v["finest_launch_ms"] * 1e-3)  # element updates / s
+        variants["fp64"]["alu_roofline"] = None if irec is None else {
+            "bound": "alu", "unit": "GFLOP/s", "achieved": rate * irec["flops_per_unit"] / 1e9,
+            "peak": fp64_peak, "frac": rate * irec["fp64_inst_per_unit"] / (fp64_peak / 2 * 1e9),
+            "frac_meaning": "FP64 instructions issued / FP64 multiply-adds per second the probe reached",
+            "fp64_inst_per_update": irec["fp64_inst_per_unit"], "flops_per_update": irec["flops_per_unit"],
+            "peak_source": "measured: lbm_alu_peak(LBM_FP64) in this run"}
         # the paper's own 3D stencil on the same mesh, FP32 deviation storage
         s27, r27 = run_gpu(mesh, 27, om, uin, fields, lbm.FP32DEV, K, W_, device, None, outlet=outlet)
         variants["d3q27_fp32dev"] = {
             "mlups": r27["mlups"], "ms_per_step": r27["ms_per_step"], "kernel": r27["finest_kernel"],
             "finest_kernel_gbs": r27["finest_gbs"], "finest_kernel_frac": r27["finest_gbs"] / peak,
             "bytes_per_update": r27["bytes_per_update"], "device_gb": r27["device_gb"],
+            "step_gbs_algorithmic": r27["step_bytes"] / (r27["ms_per_step"] * 1e-3) / 1e9,
             "interior_fraction": r27["interior_fraction"], "reduce": r27["reduce"]}
         s27.close()
         del s27
         torch.cuda.empty_cache()
-        ref_u = mom["fp64"][1]
-        ref_red = variants["fp64"]["reduce"]
-        for name, m_ in (("fp32dev", mom32), ("bf16dev", mom["bf16dev"])):
-            if m_ is None:
-                continue
-            du = m_[1] - ref_u
-            red = r["reduce"] if name == "fp32dev" else variants["bf16dev"]["reduce"]
-            errors[name] = {
-                "u_l2_rel_vs_fp64": float(math.sqrt((du ** 2).sum() / (ref_u ** 2).sum())),
-                "u_max_abs_vs_fp64": float(np.abs(du).max()),
-                "drag_rel_vs_fp64": float(abs(red[4] - ref_red[4]) / abs(ref_red[4])) if ref_red[4] else None,
-                "after_coarse_steps": W_ + K}
-        del mom
-        # secondary: the 64^3 / 32^3 two-level Taylor-Green (working set fits in L2)
+        # side workloads (working sets that fit in L2: launch- and latency-bound sizes)
         from paper_1601_06984_gb300 import workloads as Wk
-        tm, tQ, tom, tuin, tfields, tdesc = make_workload("tgv3d")
-        tgv = {"config": tdesc, "note": "working set (~0.13 GB) fits in the 129 MB L2 plus HBM; L2 not flushed; "
-                                         "steps replay the library's CUDA graphs (launch-bound size)"}
-        for name, prec in (("fp32dev", lbm.FP32DEV), ("fp64", lbm.FP64)):
-            st, rt = run_gpu(tm, tQ, tom, tuin, tfields, prec, 50, 3, device, None, want_moments=True,
-                             kernel_timing=False)
-            _, ut, _ = rt.pop("moments")
-            nu = (1 / 1.6 - 0.5) / 3
-            _, ua, _ = Wk.tgv_fields(tm, 0.01, t=53, nu=nu)
-            tgv[name] = {"mlups": rt["mlups"], "ms_per_step": rt["ms_per_step"],
-                         "u_l2_rel_vs_closed_form": float(math.sqrt(((ut - ua) ** 2).sum() / (ua ** 2).sum()))}
-            st.close()
-            del st
-            torch.cuda.empty_cache()
+        nu = (1 / 1.6 - 0.5) / 3
+        tm = Wk.config_tgv3d(64)
+        side["tgv3d"] = {"config": {"workload": "tgv3d_two_level_64", "box": "64^3 periodic, 32^3 block refined",
+                                    "levels": 2, "u0": 0.01, "omega_coarse": 1.6},
+                         **side_workload(tm, 19, 1.6, (0, 0, 0), lambda m: Wk.tgv_fields(m, 0.01),
+                                         (("fp32dev", lbm.FP32DEV), ("fp64", lbm.FP64)), 50, device,
+                                         ref=lambda m, t: Wk.tgv_fields(m, 0.01, t=t, nu=nu)[1])}
+        cm = Wk.config_cylinder()
+        cyl_om = Wk.omega_coarse_from_finest(Wk.omega_for_re(0.05, 40, 100.0), 4)
+        side["cylinder2d"] = {"config": {"workload": "cylinder_re100_d2q9_4level", "channel": "40D x 20D",
+                                         "D_finest": 40, "levels": 4, "u_in": 0.05, "elements": cm.n,
+                                         "updates_per_coarse_step": cm.updates_per_coarse_step(),
+                                         "omega_coarsest": round(cyl_om, 6), "outlet": "zero-gradient"},
+                              **side_workload(cm, 9, cyl_om, (0.05, 0, 0),
+                                              lambda m: Wk.uniform_fields(m, 1.0, (0.05, 0.0)),
+                                              (("fp32dev", lbm.FP32DEV), ("fp64", lbm.FP64)), 200, device,
+                                              outlet=1)}
+        for v_ in side.values():
+            v_["note"] = ("working set fits in the 129 MB L2 (not flushed); steps replay the library's CUDA "
+                          "graphs; hbm_gbs_algorithmic counts the algorithmic bytes, most of which L2 serves")
         adj = adjoint_run(device)
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    cb = cpu_oracle(args.cpu_seconds) if world == 1 else None
+    cb = None
+    if world == 1:
+        cb = oracle_rate("sphere_sample_3level", args.cpu_seconds, 0)
+        if not args.no_variants:
+            oracles = oracle_timings(max(2.0, args.cpu_seconds / 4))
     value = world * r["mlups"]
+    step_gbs = r["step_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W_,
         "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": dict(desc, elements=mesh.n, updates_per_coarse_step=U, storage="fp32 deviation g=f-w*rho0",
                        time_mode="linear", parallelism="replicas" if world > 1 else "single GPU",
-                       l2="inputs larger than L2 (%.1f GB workspace)" % r["device_gb"]),
+                       l2="inputs larger than L2 (%.1f GB workspace)" % r["device_gb"],
+                       timing="every kernel bracketed by CUDA events on the bound stream, launched kernel by kernel"),
         "roofline": {"bound": "hbm", "achieved": r["finest_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": r["finest_gbs"] / peak,
                      "traffic": None if traffic_per_unit is None else traffic_per_unit * r["finest_units"],
@@ -516,8 +662,17 @@ def main():
                                        "(profiles/stream_collide_brick_fp32_sphere.md)",
                      "kernel": r["finest_kernel"] + "<19,float> on the finest level",
                      "units_per_launch": r["finest_units"], "bytes_per_unit": r["bytes_per_update"],
-                     "avg_launch_ms": r["finest_launch_ms"], "peak_source": peak_src},
-        "step_gbs_algorithmic": r["step_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9,
+                     "avg_launch_ms": r["finest_launch_ms"], "peak_source": peak_src,
+                     "step": {"achieved": step_gbs, "frac_of_measured": step_gbs / peak,
+                              "frac_of_nominal": step_gbs / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
+                              "bytes_per_step": r["step_bytes"],
+                              "meaning": "algorithmic bytes of every level's stream-collide per coarse step "
+                                         "over the whole step's time (ghost fills count as time, not bytes)"}},
+        "breakdown_ms_per_step": r["breakdown_ms_per_step"],
+        "level_ms_per_step": r["level_ms_per_step"],
+        "level_brick_gbs": r["level_brick_gbs"],
+        "graph_replay": {"ms_per_step": graph_ms, "mlups": U / (graph_ms * 1e-3) / 1e6,
+                         "note": "same context, lbm_step(K) through the captured graphs, no per-kernel events"},
         "interior_brick_fraction": r["interior_fraction"],
         "brick_fraction": r["brick_fraction"],
         "finest_boundary_brick_kernel": {"units_per_launch": r["finest_boundary_units"],
@@ -530,16 +685,19 @@ def main():
         "cpu_baseline": cb if cb is None else {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
         "gpu_launches": r["launches"], "clocks": clocks,
-        "level_stream_collide_ms": r["level_ms"], "level_stream_collide_launches": r["level_launches"],
         "drag_force_fp32dev": r["reduce"][4],
     }
     if variants:
         line["variants"] = variants
         line["error_vs_fp64"] = errors
-    if tgv:
-        line["tgv3d"] = tgv
+    if alu:
+        line["alu_peaks"] = alu
+    if side:
+        line["side_workloads"] = side
     if adj:
         line["adjoint"] = adj
+    if oracles:
+        line["oracle_timings"] = oracles
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

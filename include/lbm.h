@@ -257,7 +257,10 @@ lbm_status lbm_get_state(lbm_ctx* ctx, double* f);
 lbm_status lbm_set_state(lbm_ctx* ctx, const double* f);
 
 /* Ghost elements: count, then info[n][6] (level, kind 1=GFC 2=GFF, layer, x, y, z
- * at the element's level) and f[n][Q] (FP64) of the current state. */
+ * at the element's level) and f[n][Q] (FP64) of the current state.  In
+ * LBM_TIME_LINEAR mode lbm_step does not refill the outer GhostFromCoarser
+ * layer (layer 2: no fluid element reads it); lbm_fill_ghosts fills every
+ * ghost. */
 lbm_status lbm_ghost_count(const lbm_ctx* ctx, int64_t* n);
 lbm_status lbm_get_ghosts(lbm_ctx* ctx, int64_t* info, double* f);
 
@@ -305,15 +308,30 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, int64_t n_coarse, int32_t K, int32_t object
 /* Launches of library kernels enqueued by this context since it was bound. */
 lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
 
-/* Device timing of the stream-collide kernel: while enabled, every
- * stream-collide launch is bracketed by CUDA events recorded on the bound
- * stream.  lbm_timing_read synchronises the stream and returns, in row
- * 3 L + k for level index L (coarsest 0) and kernel k (0: interior bricks,
- * 1: neighbour list, 2: boundary bricks), the number of timed launches and their summed device
- * time in milliseconds (rows 0..cap-1), then clears the record.  Enabling
- * clears it too. */
+/* Device timing of the step's kernels: while enabled, every launch of
+ * lbm_step is bracketed by CUDA events recorded on the bound stream (and the
+ * steps are launched kernel by kernel, not replayed from graphs).
+ * lbm_timing_read synchronises the stream and returns, in row 8 L + k for level
+ * index L (coarsest 0) and kernel kind k, the number of timed launches and
+ * their summed device time in milliseconds (rows 0..cap-1), then clears the
+ * record.  Enabling clears it too.  Kinds: 0 stream-collide of the interior
+ * bricks, 1 stream-collide through the neighbour list, 2 stream-collide of the
+ * boundary bricks, 3 GhostFromFiner (L: the coarse level holding the ghosts),
+ * 4 source moments (L: the coarse level), 5 GhostFromCoarser (L: the fine
+ * level holding the ghosts), 6 outlet values, 7 unused. */
 lbm_status lbm_timing_enable(lbm_ctx* ctx, int32_t on);
 lbm_status lbm_timing_read(lbm_ctx* ctx, int64_t* launches, double* ms, int32_t cap);
+
+/* Measured fused multiply-add rate of the current CUDA device in GFLOP/s
+ * (a multiply-add counts as two operations): LBM_FP64 for double,
+ * LBM_FP32DEV for float; other precisions LBM_ERR_ARG.  A probe kernel keeps
+ * every SM busy with independent register-only multiply-add chains, timed with
+ * CUDA events on a private stream (one warm-up launch, then five timed).
+ * device_scratch: caller-owned device memory of at least
+ * 16 x SMs x 256 x 8 bytes (the probe stores one value per thread there);
+ * smaller: LBM_ERR_ARG.  Synchronous.  It is the denominator of the FP64
+ * stream-collide's ALU roofline; the paper has no counterpart. */
+lbm_status lbm_alu_peak(int32_t precision, void* device_scratch, uint64_t bytes, double* gflops);
 
 const char* lbm_last_error(const lbm_ctx* ctx);
 void lbm_destroy(lbm_ctx* ctx);

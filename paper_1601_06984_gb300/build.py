@@ -17,7 +17,7 @@ BUILD = os.path.join(ROOT, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CU = ["kernels_fp64.cu", "kernels_fp32dev.cu", "kernels_bf16dev.cu", "reduce_noalloc.cu",
-      "adjoint_fp64.cu", "adjoint_fp32dev.cu", "adjoint_bf16dev.cu"]
+      "adjoint_fp64.cu", "adjoint_fp32dev.cu", "adjoint_bf16dev.cu", "probe.cu"]
 CPP = ["mesh.cpp", "api.cpp", "adjoint.cpp"]
 
 

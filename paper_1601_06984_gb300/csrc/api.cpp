@@ -96,7 +96,7 @@ void lbm_ctx::fill_gff(int li) {
   a.omega_c = H.omega;
   a.omega_f = Hf.omega;
   a.rho_off = rho_off;
-  ops->fill_gff(Q, a, st);
+  timed_launch(li, TK_GFF, [&] { ops->fill_gff(Q, a, st); });
   ++launches;
 }
 
@@ -112,11 +112,11 @@ void lbm_ctx::source_moments(int li, size_t mom_off, size_t prev_off) {
   a.nsrc = ld[li].nsrc;
   a.omega = M.lv[li].omega;
   a.rho_off = rho_off;
-  ops->source_moments(Q, a, st);
+  timed_launch(li, TK_MOM, [&] { ops->source_moments(Q, a, st); });
   ++launches;
 }
 
-void lbm_ctx::fill_gfc(int lf, bool two_times) {
+void lbm_ctx::fill_gfc(int lf, bool two_times, bool all_layers) {
   const HostLevel& H = M.lv[lf];
   if (H.nC == 0) return;
   const int lc = lf - 1;
@@ -132,7 +132,8 @@ void lbm_ctx::fill_gfc(int lf, bool two_times) {
   a.omega_c = M.lv[lc].omega;
   a.omega_f = H.omega;
   a.rho_off = rho_off;
-  ops->fill_gfc(Q, a, st);
+  a.skip_outer = !all_layers && p.time_mode == LBM_TIME_LINEAR;
+  timed_launch(lf, TK_GFC, [&] { ops->fill_gfc(Q, a, st); });
   ++launches;
 }
 
@@ -156,7 +157,7 @@ void lbm_ctx::stream_collide(int li) {
     o.rho0 = p.rho0;
     o.zero_gradient = p.outlet == LBM_OUTLET_ZERO_GRADIENT;
     o.q = at<double>(oOutQ);
-    ops->outlet(Q, o, st);
+    timed_launch(li, TK_OUTLET, [&] { ops->outlet(Q, o, st); });
     ++launches;
   }
   // interior bricks, then boundary bricks (the first 64 (nB + nBb) fluid
@@ -207,24 +208,15 @@ void lbm_ctx::stream_collide(int li) {
   a.rho_off = rho_off;
   std::memcpy(a.inlet, inlet, sizeof(inlet));
   const bool use_force = p.use_force != 0;
-  // kernel 0: interior bricks, 1: neighbour list, 2: boundary bricks
   auto launch = [&](int kernel) {
-    if (kernel == 0) ops->stream_collide_brick(Q, use_force, false, b, st);
-    else if (kernel == 2) ops->stream_collide_brick(Q, use_force, true, bb, st);
+    if (kernel == TK_INTERIOR) ops->stream_collide_brick(Q, use_force, false, b, st);
+    else if (kernel == TK_BOUNDARY) ops->stream_collide_brick(Q, use_force, true, bb, st);
     else ops->stream_collide(Q, use_force, a, st);
     ++launches;
   };
-  for (int kernel : {0, 2, 1}) {
-    if (kernel == 0 ? b.nB == 0 : kernel == 2 ? bb.nB == 0 : a.end <= a.begin) continue;
-    if (timing) {
-      Timed t{li, kernel, get_event(), get_event()};
-      cudaEventRecord(t.a, st);
-      launch(kernel);
-      cudaEventRecord(t.b, st);
-      timed.push_back(t);
-    } else {
-      launch(kernel);
-    }
+  for (int kernel : {TK_INTERIOR, TK_BOUNDARY, TK_LIST}) {
+    if (kernel == TK_INTERIOR ? b.nB == 0 : kernel == TK_BOUNDARY ? bb.nB == 0 : a.end <= a.begin) continue;
+    timed_launch(li, kernel, [&] { launch(kernel); });
   }
   parity[li] ^= 1;
 }
@@ -675,7 +667,7 @@ lbm_status lbm_fill_ghosts(lbm_ctx* c) {
   for (int li = 0; li + 1 < c->nlev; ++li) {
     c->fill_gff(li);
     c->source_moments(li, c->ld[li].momA);
-    c->fill_gfc(li + 1, false);
+    c->fill_gfc(li + 1, false, true);
   }
   return c->launched("fill_ghosts");
 }
@@ -838,7 +830,7 @@ lbm_status lbm_timing_read(lbm_ctx* c, int64_t* launches, double* ms, int32_t ca
     float e = 0.f;
     s = c->cuda_check(cudaEventElapsedTime(&e, t.a, t.b), "timing read");
     if (s != LBM_OK) break;
-    const int row = 3 * t.li + t.kernel;
+    const int row = kTimedKinds * t.li + t.kernel;
     if (row < cap) {
       launches[row] += 1;
       ms[row] += e;

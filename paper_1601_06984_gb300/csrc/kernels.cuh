@@ -733,7 +733,8 @@ __global__ void __launch_bounds__(LBM_GFC_BLOCK) k_fill_gfc(const GfcArgs a) {
       }
   }
   __syncwarp();
-  if (!active) return;
+  // outer-layer ghosts are staged with their group but, when skipped, not written
+  if (!active || (a.skip_outer && (a.oct[k] & kGfcOuter))) return;
   const R* rec[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) rec[s] = sg_base + GG::slot(s, oct) * PSTR;

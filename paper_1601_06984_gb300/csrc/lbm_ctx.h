@@ -13,6 +13,9 @@
 namespace lbm {
 // Ops of the recursive level step, in the order lbm_ctx::advance issues them.
 enum StepOp { OP_GFF = 0, OP_MOM_A = 1, OP_GFC_A = 2, OP_SC = 3, OP_MOM_B = 4, OP_GFC_B = 5 };
+// Kernel kinds of the per-launch timing (lbm_timing_read row kTimedKinds * L + kind)
+enum TimedKind { TK_INTERIOR = 0, TK_LIST = 1, TK_BOUNDARY = 2, TK_GFF = 3, TK_MOM = 4, TK_GFC = 5, TK_OUTLET = 6 };
+constexpr int kTimedKinds = 8;
 
 struct LevelDev {
   size_t gff_child0 = 0, gfc_src = 0, gfc_oct = 0, src_elem = 0, momA = 0, momB = 0;
@@ -60,7 +63,7 @@ struct lbm_ctx {
   // stream-collide timing (events recorded around each launch when enabled)
   bool timing = false;
   struct Timed {
-    int li, kernel;  // kernel 0: interior bricks, 1: neighbour list, 2: boundary bricks
+    int li, kernel;  // lbm::TimedKind
     cudaEvent_t a, b;
   };
   std::vector<Timed> timed;
@@ -74,6 +77,19 @@ struct lbm_ctx {
     cudaEvent_t e = nullptr;
     cudaEventCreate(&e);
     return e;
+  }
+  // runs launch(), bracketed by events on the bound stream while timing is on
+  template <class F>
+  void timed_launch(int li, int kind, F&& launch) {
+    if (!timing) {
+      launch();
+      return;
+    }
+    Timed t{li, kind, get_event(), get_event()};
+    cudaEventRecord(t.a, st);
+    launch();
+    cudaEventRecord(t.b, st);
+    timed.push_back(t);
   }
   void recycle_timed() {
     for (auto& t : timed) {
@@ -132,7 +148,9 @@ struct lbm_ctx {
   // driver pieces
   void fill_gff(int li);
   void source_moments(int li, size_t mom_off, size_t prev_off = 0);
-  void fill_gfc(int li_fine, bool two_times);
+  // all_layers false: in LINEAR mode the outer ghost layer, which no
+  // stream-collide reads, is left unwritten
+  void fill_gfc(int li_fine, bool two_times, bool all_layers = false);
   void stream_collide(int li);
   void advance(int li);
   // graph of two coarse steps from the current parity state, captured on

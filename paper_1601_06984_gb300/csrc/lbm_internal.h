@@ -23,6 +23,7 @@ constexpr uint32_t NB_FLAG30 = 0x40000000u;
 constexpr uint32_t NB_INDEX = 0x3FFFFFFFu;
 constexpr int kPad = 32;  // every level segment is padded to a multiple of this
 constexpr int32_t kBrickMissing = INT32_MIN;  // brick row entry: neighbour brick not complete
+constexpr uint8_t kGfcOuter = 0x80;  // GhostFromCoarser octant byte: ghost of the outer layer
 
 enum { K_FLUID = 0, K_GFC = 1, K_GFF = 2, K_PAD = 3 };
 
@@ -65,7 +66,8 @@ struct HostLevel {
   std::vector<int32_t> gff_child0;  // [nG1 + nG2]
   // GhostFromCoarser of this level: 4 positions in the source list of level L-1, octant bits
   std::vector<int32_t> gfc_src;  // [4][nC]
-  std::vector<uint8_t> gfc_oct;  // [nC], bit a set: ghost on the + side of its parent along a
+  std::vector<uint8_t> gfc_oct;  // [nC], bit a < 3 set: ghost on the + side of its parent along a;
+                                 // kGfcOuter: outer layer (no fluid or subdivided neighbour)
   // sources (global indices on this level) feeding the GFC of level L+1
   std::vector<int32_t> src_elem;
   // outlet links processed before this level's stream-collide: global range in the outlet list
@@ -189,6 +191,7 @@ struct GfcArgs {
   void* dst;
   int64_t Ntot;
   double omega_c, omega_f, rho_off;
+  int skip_outer;        // leave the outer-layer ghosts (oct & kGfcOuter) unwritten
 };
 
 struct GffArgs {

@@ -710,6 +710,9 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       for (int s = 0; s < 4 && ok; ++s) ok = H.gfc_src[s * H.nC + k] == H.gfc_src[s * H.nC + k0 + canon[s]];
       if (!ok) return bad(LBM_ERR_INTERNAL, "GhostFromCoarser sibling group inconsistent");
     }
+    // bit 7 marks the outer layer (no fluid or subdivided neighbour on this level)
+    for (int64_t k = 0; k < H.nC; ++k)
+      if (gfc[li][k].layer == 2) H.gfc_oct[k] |= kGfcOuter;
   }
 
   // ---- pull neighbour lists (Sec. 2.1) with boundary rules (Sec. 2.3)
@@ -839,6 +842,10 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
               const int32_t v = B.value(li, q);
               if (v >= 0) {
                 code = (uint32_t)(H.base + v);
+                // the outer GhostFromCoarser layer is not refilled by the
+                // LINEAR-mode step, so nothing processed may read it
+                if (B.mode == LBM_TIME_LINEAR && kd[v] == K_GFC && layer[v] == 2)
+                  myerr = "a processed element reads the outer GhostFromCoarser layer";
               } else if (k == K_FLUID) {
                 if (v == G_SUB || B.covered_by_coarser(li, q))
                   myerr = "neighbour on another level has no ghost element";

@@ -26,7 +26,7 @@ EXPORTS = ["lbm_build_mesh", "lbm_mesh_info", "lbm_device_bytes", "lbm_bind", "l
            "lbm_step", "lbm_fill_ghosts", "lbm_moments", "lbm_reduce", "lbm_get_state", "lbm_set_state", "lbm_ghost_count",
            "lbm_get_ghosts", "lbm_sfc_partition", "lbm_kernel_launches", "lbm_timing_enable", "lbm_timing_read",
            "lbm_reduce_noalloc", "lbm_set_params", "lbm_adjoint_bytes", "lbm_adjoint", "lbm_last_error",
-           "lbm_destroy", "lbm_obstacle_links", "lbm_set_link_q"]
+           "lbm_destroy", "lbm_obstacle_links", "lbm_set_link_q", "lbm_alu_peak"]
 
 
 class LBMError(RuntimeError):
@@ -80,6 +80,7 @@ def lib():
             "lbm_adjoint": [P, I64, I32, I32, P, U64, P, P, P, P, P],
             "lbm_obstacle_links": [P, P, P, I64, C.POINTER(I64)],
             "lbm_set_link_q": [P, P, I64],
+            "lbm_alu_peak": [I32, P, U64, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -135,6 +136,20 @@ def lbm_sfc_partition(tree_ids, d, nparts):
     part = np.zeros(n, np.int32)
     _check(None, lib().lbm_sfc_partition(_p(tid), n, d, nparts, _p(order), _p(w), _p(cum), _p(part)))
     return order, w, cum, part
+
+
+def lbm_alu_peak(precision, device="cuda"):
+    """Measured multiply-add rate (GFLOP/s) of the device for FP64 or FP32
+    (precision FP64 / FP32DEV)."""
+    import torch
+    dev = torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    scratch = torch.empty(16 * sms * 256 * 8, dtype=torch.uint8, device=dev)
+    out = C.c_double()
+    with torch.cuda.device(dev):
+        _check(None, lib().lbm_alu_peak(int(precision), C.c_void_p(scratch.data_ptr()), scratch.numel(),
+                                        C.byref(out)))
+    return float(out.value)
 
 
 def lbm_reduce_noalloc(sim):
@@ -232,15 +247,19 @@ class Sim:
     def timing_enable(self, on=True):
         _check(self.ctx, lib().lbm_timing_enable(self.ctx, int(bool(on))))
 
+    TIMED_KINDS = ("interior", "list", "boundary", "gff", "moments", "gfc", "outlet", "unused")
+
     def timing_read(self):
-        """Stream-collide launches and summed device ms since enabled, arrays
-        [level, kernel] with kernel 0 = interior bricks, 1 = neighbour list,
-        2 = boundary bricks."""
-        n = np.zeros(96, np.int64)
-        ms = np.zeros(96)
-        _check(self.ctx, lib().lbm_timing_read(self.ctx, _p(n), _p(ms), 96))
+        """Launches and summed device ms since enabled, arrays [level, kind]
+        with kind 0 = interior-brick stream-collide, 1 = neighbour-list
+        stream-collide, 2 = boundary-brick stream-collide, 3 = GhostFromFiner,
+        4 = source moments, 5 = GhostFromCoarser, 6 = outlet values."""
+        k = len(self.TIMED_KINDS)
+        n = np.zeros(16 * k, np.int64)
+        ms = np.zeros(16 * k)
+        _check(self.ctx, lib().lbm_timing_read(self.ctx, _p(n), _p(ms), 16 * k))
         nl = len(self.mesh_info())
-        return n[: 3 * nl].reshape(nl, 3), ms[: 3 * nl].reshape(nl, 3)
+        return n[: k * nl].reshape(nl, k), ms[: k * nl].reshape(nl, k)
 
     # -- state
     def init(self, rho, u, S=None, df=None):
