@@ -256,13 +256,15 @@ OUTLETS = {"linear": 0, "zero-gradient": 1}
 
 
 def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_moments=False, outlet=0,
-            kernel_timing=True, state=None):
-    """Time K coarse steps after W_ warm-up steps.  With kernel_timing the
-    library brackets every launch with CUDA events (steps are then launched
-    kernel by kernel) and the per-kernel times come from those events; without
-    it the steps replay the library's captured CUDA graphs, as a caller's
-    lbm_step(K) does.  state: post-collision pdfs [n, Q] to start from instead
-    of the fields."""
+            timing=2, breakdown=True, state=None):
+    """Time K coarse steps after W_ warm-up steps, the way a caller's
+    lbm_step(K) runs them: replaying the library's captured two-step CUDA
+    graphs.  timing=2 has those graphs record CUDA events around the finest
+    level's stream-collide launches (the roofline kernel's launch time comes
+    from the last replay of the timed region); timing=0 records none.  With
+    breakdown, K more steps follow with every kernel bracketed by events
+    (launched kernel by kernel) for the per-kind and per-level times.
+    state: post-collision pdfs [n, Q] to start from instead of the fields."""
     import numpy as np
     import torch
 
@@ -276,11 +278,12 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
         sim.init(rho, u, S)
     else:
         sim.set_state(state)
+    sim.timing_enable(timing)
     sim.step(W_)
+    sim.step(2)  # captures the graph of the parity state the timed region starts from
     info = sim.mesh_info()
     stream = sim.stream
-    torch.cuda.synchronize(device)
-    sim.timing_enable(kernel_timing)
+    sim.timing_read()  # clears the warm-up record
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(device)
@@ -296,7 +299,6 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     ms = ev0.elapsed_time(ev1)
     launches = sim.kernel_launches() - n0
     nl, kms = sim.timing_read()
-    sim.timing_enable(False)
     ms = max_over_ranks(ms, dist, device)
     finest = len(info) - 1
     nlev = len(info)
@@ -304,7 +306,8 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     # (the neighbour-list kernel when the level has no interior bricks)
     kb = 0 if info[finest, 8] > 0 else 1
     units = int(64 * info[finest, 8]) if kb == 0 else int(info[finest, 1])
-    avg_ms = kms[finest, kb] / max(nl[finest, kb], 1) if kernel_timing else float("nan")
+    timed = timing == 2 and nl[finest, kb] > 0
+    avg_ms = kms[finest, kb] / nl[finest, kb] if timed else float("nan")
     bpu = bytes_per_update(Q, prec, brick=kb == 0)
     list_units = int(info[finest, 1] - 64 * (info[finest, 8] + info[finest, 9]))
     list_ms = kms[finest, 1] / max(nl[finest, 1], 1)
@@ -320,7 +323,7 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     res = {"ms_total": ms, "ms_per_step": ms / K, "mlups": K * U / (ms * 1e-3) / 1e6, "launches": launches,
            "finest_kernel": "k_stream_collide_brick" if kb == 0 else "k_stream_collide",
            "finest_launch_ms": avg_ms, "finest_launches": int(nl[finest, kb]), "finest_units": units,
-           "finest_bytes": units * bpu, "finest_gbs": units * bpu / (avg_ms * 1e-3) / 1e9 if kernel_timing else None,
+           "finest_bytes": units * bpu, "finest_gbs": units * bpu / (avg_ms * 1e-3) / 1e9 if timed else None,
            "finest_list_units": list_units, "finest_list_launch_ms": list_ms,
            "finest_boundary_units": bnd_units, "finest_boundary_launch_ms": bnd_ms,
            "finest_boundary_gbs": (bnd_units * bytes_per_update(Q, prec, brick=True) / (bnd_ms * 1e-3) / 1e9
@@ -330,38 +333,38 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
            "interior_fraction": float(64 * info[:, 8].sum() / info[:, 1].sum()),
            "brick_fraction": float(64 * (info[:, 8] + info[:, 9]).sum() / info[:, 1].sum()),
            "step_bytes": step_bytes, "bytes_per_update": bpu, "build_s": t_build,
-           "device_gb": sim.device_bytes() / 1e9, "reduce": sim.reduce().tolist()}
-    if kernel_timing:
-        per_kind = {k: float(kms[:, i].sum() / K) for i, k in enumerate(KINDS)}
-        res["breakdown_ms_per_step"] = dict(per_kind, between_kernels=ms / K - sum(per_kind.values()))
-        res["level_ms_per_step"] = {f"L{int(info[li, 0])}": {k: round(float(kms[li, i] / K), 4)
-                                                            for i, k in enumerate(KINDS) if nl[li, i] > 0}
+           "device_gb": sim.device_bytes() / 1e9}
+    if breakdown:
+        sim.timing_enable(1)
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        ms1 = e0.elapsed_time(e1)
+        nl1, kms1 = sim.timing_read()
+        per_kind = {k: float(kms1[:, i].sum() / K) for i, k in enumerate(KINDS)}
+        res["breakdown"] = {"ms_per_step": ms1 / K,
+                            "kinds_ms_per_step": dict(per_kind, between_kernels=ms1 / K - sum(per_kind.values())),
+                            "note": "K further steps with every kernel bracketed by CUDA events, launched kernel "
+                                    "by kernel (the events add about 2 us per launch)"}
+        res["level_ms_per_step"] = {f"L{int(info[li, 0])}": {k: round(float(kms1[li, i] / K), 4)
+                                                            for i, k in enumerate(KINDS) if nl1[li, i] > 0}
                                     for li in range(nlev)}
         # every level's brick stream-collide against the HBM roofline
         res["level_brick_gbs"] = {}
         for li in range(nlev):
             for i, key in ((0, "interior"), (2, "boundary")):
                 n_ = int(64 * info[li, 8 if i == 0 else 9])
-                if nl[li, i] > 0 and n_ > 0:
+                if nl1[li, i] > 0 and n_ > 0:
                     res["level_brick_gbs"][f"L{int(info[li, 0])}_{key}"] = round(
-                        n_ * bytes_per_update(Q, prec, brick=True) / (kms[li, i] / nl[li, i] * 1e-3) / 1e9, 1)
+                        n_ * bytes_per_update(Q, prec, brick=True) / (kms1[li, i] / nl1[li, i] * 1e-3) / 1e9, 1)
+    sim.timing_enable(0)
+    res["reduce"] = sim.reduce().tolist()
     if want_moments:
         res["moments"] = sim.moments()
     return sim, res
-
-
-def graph_replay(sim, K, device):
-    """K coarse steps on the same context through lbm_step's captured graphs
-    (no per-kernel events), timed with CUDA events on the bound stream."""
-    import torch
-    sim.step(2)  # capture both parity states' graphs outside the timed region
-    torch.cuda.synchronize(device)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(sim.stream)
-    sim.step(K)
-    ev1.record(sim.stream)
-    torch.cuda.synchronize(device)
-    return ev0.elapsed_time(ev1) / K
 
 
 def adjoint_run(device):
@@ -470,13 +473,16 @@ def precision_study(mesh, Q, om, uin, fields, K, W_, device, outlet, develop, pe
     for name, prec in (("fp64", lbm.FP64), ("fp32dev", lbm.FP32DEV), ("bf16dev", lbm.BF16DEV)):
         s, r = run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, None, want_moments=True, outlet=outlet,
                        state=f_dev)
+        # the precision's own steps from the developed state: W_ + 2 warm-up, K
+        # timed, K with per-kernel events (moments after all of them)
+        steps_run = W_ + 2 + 2 * K
         _, u, S = r.pop("moments")
         mom[name] = (u, S * sc)
         red[name] = np.asarray(r["reduce"])
         rec[name] = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "finest_kernel_gbs": r["finest_gbs"],
                      "finest_kernel_frac": r["finest_gbs"] / peak, "bytes_per_update": r["bytes_per_update"],
                      "device_gb": r["device_gb"], "step_gbs_algorithmic": r["step_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9,
-                     "breakdown_ms_per_step": r["breakdown_ms_per_step"], "finest_units": r["finest_units"],
+                     "breakdown": r["breakdown"], "finest_units": r["finest_units"],
                      "finest_launch_ms": r["finest_launch_ms"], "reduce": r["reduce"]}
         s.close()
         del s
@@ -495,7 +501,7 @@ def precision_study(mesh, Q, om, uin, fields, K, W_, device, outlet, develop, pe
                         "lift_z_vs_fp64_rel_to_drag": float(abs(rp[6] - rf[6]) / abs(rf[4])) if rf[4] else None,
                         "mass_rel_vs_fp64": float(abs(rp[0] - rf[0]) / rf[0])}
     errors["state"] = (f"flow developed for {done + develop} coarse steps from rest (uniform u_in) in FP32-deviation storage, "
-                       f"then each precision runs {W_ + K} coarse steps from that state; fp64 drag "
+                       f"then each precision runs {steps_run} coarse steps from that state; fp64 drag "
                        f"{rf[4]:.6g}, lift {rf[5]:.3g}, {rf[6]:.3g} (finest-level lattice units)")
     errors["develop_seconds"] = round(t_dev, 1)
     return rec, errors
@@ -511,12 +517,12 @@ def side_workload(mesh, Q, om, uin, fields, precs, steps, device, outlet=0, ref=
     out = {}
     for name, prec in precs:
         s, r = run_gpu(mesh, Q, om, uin, fields, prec, steps, 3, device, None, want_moments=ref is not None,
-                       outlet=outlet, kernel_timing=False)
+                       outlet=outlet, timing=0, breakdown=False)
         rec = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"],
                "hbm_gbs_algorithmic": r["step_bytes"] / (r["ms_per_step"] * 1e-3) / 1e9}
         if ref is not None:
             _, u, _ = r.pop("moments")
-            ua = ref(mesh, steps + 3)
+            ua = ref(mesh, steps + 5)  # 3 + 2 warm-up steps, then the timed ones
             rec["u_l2_rel_vs_closed_form"] = float(np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum()))
         out[name] = rec
         s.close()
@@ -574,7 +580,6 @@ def main():
     outlet = OUTLETS.get(desc.get("outlet"), 0)
     sim, r = run_gpu(mesh, Q, om, uin, fields, lbm.FP32DEV, K, W_, device, dist, outlet=outlet)
     clocks = clk.stop()
-    graph_ms = graph_replay(sim, K, device)
     e2e = e2e_run(sim, mesh, fields, K)
     if dist is not None:
         e2e["value"] = job_throughput(K * U, e2e["seconds"], world, dist, device)
@@ -602,7 +607,8 @@ def main():
             "fp64_inst_per_update": irec["fp64_inst_per_unit"], "flops_per_update": irec["flops_per_unit"],
             "peak_source": "measured: lbm_alu_peak(LBM_FP64) in this run"}
         # the paper's own 3D stencil on the same mesh, FP32 deviation storage
-        s27, r27 = run_gpu(mesh, 27, om, uin, fields, lbm.FP32DEV, K, W_, device, None, outlet=outlet)
+        s27, r27 = run_gpu(mesh, 27, om, uin, fields, lbm.FP32DEV, K, W_, device, None, outlet=outlet,
+                           breakdown=False)
         variants["d3q27_fp32dev"] = {
             "mlups": r27["mlups"], "ms_per_step": r27["ms_per_step"], "kernel": r27["finest_kernel"],
             "finest_kernel_gbs": r27["finest_gbs"], "finest_kernel_frac": r27["finest_gbs"] / peak,
@@ -654,7 +660,9 @@ def main():
         "config": dict(desc, elements=mesh.n, updates_per_coarse_step=U, storage="fp32 deviation g=f-w*rho0",
                        time_mode="linear", parallelism="replicas" if world > 1 else "single GPU",
                        l2="inputs larger than L2 (%.1f GB workspace)" % r["device_gb"],
-                       timing="every kernel bracketed by CUDA events on the bound stream, launched kernel by kernel"),
+                       timing="K coarse steps through lbm_step's captured two-step CUDA graphs, CUDA events on the "
+                              "bound stream around the region; the graphs also record events around the finest "
+                              "level's stream-collide launches (roofline: the last replay's launches)"),
         "roofline": {"bound": "hbm", "achieved": r["finest_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": r["finest_gbs"] / peak,
                      "traffic": None if traffic_per_unit is None else traffic_per_unit * r["finest_units"],
@@ -662,17 +670,16 @@ def main():
                                        "(profiles/stream_collide_brick_fp32_sphere.md)",
                      "kernel": r["finest_kernel"] + "<19,float> on the finest level",
                      "units_per_launch": r["finest_units"], "bytes_per_unit": r["bytes_per_update"],
-                     "avg_launch_ms": r["finest_launch_ms"], "peak_source": peak_src,
+                     "avg_launch_ms": r["finest_launch_ms"], "launches_averaged": r["finest_launches"],
+                     "peak_source": peak_src,
                      "step": {"achieved": step_gbs, "frac_of_measured": step_gbs / peak,
                               "frac_of_nominal": step_gbs / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                               "bytes_per_step": r["step_bytes"],
                               "meaning": "algorithmic bytes of every level's stream-collide per coarse step "
                                          "over the whole step's time (ghost fills count as time, not bytes)"}},
-        "breakdown_ms_per_step": r["breakdown_ms_per_step"],
+        "breakdown": r["breakdown"],
         "level_ms_per_step": r["level_ms_per_step"],
         "level_brick_gbs": r["level_brick_gbs"],
-        "graph_replay": {"ms_per_step": graph_ms, "mlups": U / (graph_ms * 1e-3) / 1e6,
-                         "note": "same context, lbm_step(K) through the captured graphs, no per-kernel events"},
         "interior_brick_fraction": r["interior_fraction"],
         "brick_fraction": r["brick_fraction"],
         "finest_boundary_brick_kernel": {"units_per_launch": r["finest_boundary_units"],

@@ -308,9 +308,15 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, int64_t n_coarse, int32_t K, int32_t object
 /* Launches of library kernels enqueued by this context since it was bound. */
 lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
 
-/* Device timing of the step's kernels: while enabled, every launch of
- * lbm_step is bracketed by CUDA events recorded on the bound stream (and the
- * steps are launched kernel by kernel, not replayed from graphs).
+/* Device timing of the step's kernels with CUDA events on the bound stream.
+ *  mode 0: off.
+ *  mode 1: every launch of lbm_step is bracketed by events, and the steps are
+ *          launched kernel by kernel, not replayed from graphs.
+ *  mode 2: lbm_step keeps replaying its captured two-step graphs, which then
+ *          also record events around the finest level's stream-collide
+ *          launches (kinds 0-2); lbm_timing_read returns those of the most
+ *          recent replay (its two coarse steps), if not read before.
+ * Changing between mode 2 and the others drops the captured graphs.
  * lbm_timing_read synchronises the stream and returns, in row 8 L + k for level
  * index L (coarsest 0) and kernel kind k, the number of timed launches and
  * their summed device time in milliseconds (rows 0..cap-1), then clears the
@@ -318,8 +324,9 @@ lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
  * bricks, 1 stream-collide through the neighbour list, 2 stream-collide of the
  * boundary bricks, 3 GhostFromFiner (L: the coarse level holding the ghosts),
  * 4 source moments (L: the coarse level), 5 GhostFromCoarser (L: the fine
- * level holding the ghosts), 6 outlet values, 7 unused. */
-lbm_status lbm_timing_enable(lbm_ctx* ctx, int32_t on);
+ * level holding the ghosts), 6 outlet values, 7 unused.  Other modes:
+ * LBM_ERR_ARG. */
+lbm_status lbm_timing_enable(lbm_ctx* ctx, int32_t mode);
 lbm_status lbm_timing_read(lbm_ctx* ctx, int64_t* launches, double* ms, int32_t cap);
 
 /* Measured fused multiply-add rate of the current CUDA device in GFLOP/s

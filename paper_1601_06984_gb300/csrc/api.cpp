@@ -257,16 +257,27 @@ const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
   // stream, which cannot be captured); host bookkeeping is restored afterwards
   const std::vector<int> p0 = parity;
   const int64_t l0 = launches;
+  if (timing == 2) {
+    // events for the finest level's stream-collide launches (up to three per
+    // substep, 2^(nlev-1) substeps per coarse step, two coarse steps), made
+    // before the capture begins
+    for (int k = 0; k < 2 * 3 * 2 * (1 << (nlev - 1)); ++k) event_pool.push_back(get_event());
+  }
+  const size_t t0 = timed.size();
   cudaStream_t user = st;
   st = cap_stream;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
+    capturing = true;
     advance(0);
     advance(0);
+    capturing = false;
     e = cudaStreamEndCapture(cap_stream, &graph);
   }
   st = user;
+  std::vector<Timed> gt(timed.begin() + t0, timed.end());
+  timed.resize(t0);
   const int64_t nl = launches - l0;
   launches = l0;
   const bool same = parity == p0;
@@ -276,10 +287,14 @@ const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess || !exec || !same) {
     cudaGetLastError();
+    for (auto& t : gt) {
+      event_pool.push_back(t.a);
+      event_pool.push_back(t.b);
+    }
     graphs_on = false;
     return nullptr;
   }
-  graphs.push_back({p0, exec, nl});
+  graphs.push_back({p0, exec, nl, std::move(gt)});
   return &graphs.back();
 }
 
@@ -617,13 +632,15 @@ static lbm_status step_run(lbm_ctx* c, int64_t n_coarse) {
   int64_t k = 0;
   // pairs of coarse steps replay a captured graph; a single step, timed
   // steps and the adjoint's recorded steps are issued one kernel at a time
-  if (c->graphs_on && !c->timing && !c->hook && !c->dry) {
+  if (c->graphs_on && c->timing != 1 && !c->hook && !c->dry) {
     while (n_coarse - k >= 2) {
       const lbm_ctx::StepGraph* g = c->step_graph();
       if (!g) break;
       lbm_status s = c->cuda_check(cudaGraphLaunch(g->exec, c->st), "graph launch");
       if (s != LBM_OK) return s;
       c->launches += g->launches;
+      c->last_graph = (int)(g - c->graphs.data());
+      c->graph_unread = true;
       k += 2;
     }
   }
@@ -808,12 +825,16 @@ lbm_status lbm_kernel_launches(const lbm_ctx* c, int64_t* count) {
   return LBM_OK;
 }
 
-lbm_status lbm_timing_enable(lbm_ctx* c, int32_t on) {
+lbm_status lbm_timing_enable(lbm_ctx* c, int32_t mode) {
   if (!c) return LBM_ERR_ARG;
+  if (mode < 0 || mode > 2) return c->fail(LBM_ERR_ARG, "timing mode must be 0, 1 or 2");
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_timing_enable before lbm_bind");
   lbm_status s = c->cuda_check(cudaStreamSynchronize(c->st), "timing sync");
   c->recycle_timed();
-  c->timing = on != 0;
+  // graphs captured with events (mode 2) and without them are not interchangeable
+  if ((mode == 2) != (c->timing == 2)) c->drop_graphs();
+  c->graph_unread = false;
+  c->timing = mode;
   return s;
 }
 
@@ -826,16 +847,19 @@ lbm_status lbm_timing_read(lbm_ctx* c, int64_t* launches, double* ms, int32_t ca
     launches[k] = 0;
     ms[k] = 0.0;
   }
-  for (auto& t : c->timed) {
+  auto add = [&](const lbm_ctx::Timed& t) {
     float e = 0.f;
-    s = c->cuda_check(cudaEventElapsedTime(&e, t.a, t.b), "timing read");
-    if (s != LBM_OK) break;
+    if (s == LBM_OK) s = c->cuda_check(cudaEventElapsedTime(&e, t.a, t.b), "timing read");
     const int row = kTimedKinds * t.li + t.kernel;
-    if (row < cap) {
+    if (s == LBM_OK && row < cap) {
       launches[row] += 1;
       ms[row] += e;
     }
-  }
+  };
+  for (auto& t : c->timed) add(t);
+  if (c->graph_unread && c->last_graph >= 0)
+    for (auto& t : c->graphs[c->last_graph].timed) add(t);
+  c->graph_unread = false;
   c->recycle_timed();
   return s;
 }

@@ -150,7 +150,9 @@ __device__ __forceinline__ void raw_moments(const R* g, R& rp, R* j) {
 
 // Pre-collision moments from a stored post-collision set: u = (j - F/2)/rho,
 // f^neq = (g - g^eq - F_i) / (1 - omega), S_ab = -(3 omega / 2 rho) sum c_a c_b f^neq.
-template <int Q, class R, bool WANT_S>
+// g^eq per pair of opposite velocities (c.u changes sign: the even part is
+// shared); without FORCE the forcing terms are left out at compile time.
+template <int Q, class R, bool WANT_S, bool FORCE = true>
 __device__ __forceinline__ void post_moments(const R* g, R omega, R rho_off, const R* F, R& rp, R* u,
                                              R* fneq, R* S) {
   using LT = Lat<Q>;
@@ -161,13 +163,36 @@ __device__ __forceinline__ void post_moments(const R* g, R omega, R rho_off, con
   const R inv = R(1) / rho;
   u[0] = u[1] = u[2] = R(0);
 #pragma unroll
-  for (int a = 0; a < D; ++a) u[a] = (j[a] - R(0.5) * F[a]) * inv;
+  for (int a = 0; a < D; ++a) u[a] = (FORCE ? j[a] - R(0.5) * F[a] : j[a]) * inv;
   R usq = R(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) usq += u[a] * u[a];
   const R r1w = R(1) / (R(1) - omega);
+  const R base = rp - R(1.5) * rho * usq;
+  {
+    R f0 = g[0] - R(LT::w(0)) * base;
+    if (FORCE) f0 -= guo<Q, R>(0, omega, u, F);
+    fneq[0] = f0 * r1w;
+  }
 #pragma unroll
-  for (int i = 0; i < Q; ++i) fneq[i] = (g[i] - geq<Q, R>(i, rp, rho, u, usq) - guo<Q, R>(i, omega, u, F)) * r1w;
+  for (int i = 1; i < Q; i += 2) {
+    R cu = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (LT::c(i, a) > 0) cu += u[a];
+      if (LT::c(i, a) < 0) cu -= u[a];
+    }
+    const R w = R(LT::w(i));
+    const R even = w * (base + R(4.5) * rho * cu * cu);
+    const R odd = w * R(3) * rho * cu;
+    R fa = g[i] - (even + odd), fb = g[i + 1] - (even - odd);
+    if (FORCE) {
+      fa -= guo<Q, R>(i, omega, u, F);
+      fb -= guo<Q, R>(i + 1, omega, u, F);
+    }
+    fneq[i] = fa * r1w;
+    fneq[i + 1] = fb * r1w;
+  }
   if (WANT_S) {
     const R pre = -R(1.5) * omega * inv;
 #pragma unroll
@@ -390,9 +415,14 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
 // link is not complete; those links (row entry kBrickMissing) take the
 // element's neighbour-list code like k_stream_collide: a pull, the element's
 // own opposite slot (bounce-back), plus the inlet term, or a boundary value.
-// Four blocks per SM (64 registers) where that fits without spills: D3Q19 and
-// D2Q9 with 4-byte or narrower storage; three otherwise.
-#define LBM_BR_BND_MINB(Q, S) ((Q) > 19 || sizeof(S) > 4 ? 3 : 4)
+// Every link is first resolved to one 32-bit offset, so the gathers need no
+// branch.  Five blocks per SM (48 registers, no spills) for D3Q19 and D2Q9
+// with 4-byte or narrower storage (measured: 4.66 against 4.38 TB/s at four);
+// three where more registers are needed (D3Q27, FP64).
+#ifndef LBM_BR_BND_MINB_NARROW
+#define LBM_BR_BND_MINB_NARROW 5
+#endif
+#define LBM_BR_BND_MINB(Q, S) ((Q) > 19 || sizeof(S) > 4 ? 3 : LBM_BR_BND_MINB_NARROW)
 // Interior bricks: BF16 storage moves half the bytes per element, so it needs
 // more elements in flight; five blocks per SM (48 registers, no spills) for
 // D3Q19 / D2Q9 BF16, measured faster than four or six.
@@ -429,36 +459,55 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : LB
       g[i] = Sto<S>::ld(src + (int64_t)(i * N) + r + (v & 63));
     }
   } else {
-    // phase 1: the neighbour-list codes of links through missing bricks, all
-    // issued before any gather (kNoCode: the link stays in the brick tables)
-    constexpr uint32_t kNoCode = 0xffffffffu;
+    // phase 1: every link's pull source as one 32-bit offset from src + i N
+    // (src starts at the brick's first element): the brick-table entry, or,
+    // through a missing neighbour brick, the element's neighbour-list code
+    // resolved to a pull (n - first), to its own opposite slot (bounce-back,
+    // and the inlet's base value: (opp(i) - i) N + l), or, for a boundary
+    // value, to that same valid slot, the value being substituted below.
+    // |offsets| < 2^30 + 64 since Ntot < 2^30.  Links whose value gets an
+    // inlet term or a substitute are marked in `patch`.
     const int64_t e = first + l;
-    uint32_t code[Q];
+    int32_t off[Q];
+    uint32_t miss = 0, patch = 0;
+    off[0] = 0;
+    // 1a: brick-table offsets; the codes of links through missing bricks are
+    // loaded, all before any of them is used
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
       const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
-      code[i] = r == kBrickMissing ? __ldg(a.nbr + (size_t)(i - 1) * N + e) : kNoCode;
-    }
-    // phase 2: the gathers
-    const S* base = static_cast<const S*>(a.src);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
-      const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
-      const uint32_t n = code[i];
-      if (n == kNoCode) g[i] = Sto<S>::ld(src + (int64_t)(i * N) + r + (v & 63));
-      else g[i] = Sto<S>::ld(base + (n < NB_FLAG30 ? (size_t)i * N + n : (size_t)opp(i) * N + (size_t)e));
-    }
-    // phase 3: bounce-back, inlet and boundary-value links
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const uint32_t n = code[i];
-      if (n == kNoCode || n < NB_FLAG30) continue;
-      if (n & NB_BOUNCE) {
-        if (n & NB_FLAG30) g[i] += R(a.inlet[i]) * (a.inlet_s ? R(a.inlet_s[n & NB_INDEX]) : R(1));
+      if (r != kBrickMissing) {
+        off[i] = r + (int32_t)(v & 63);
       } else {
-        g[i] = static_cast<const R*>(a.side)[n & NB_INDEX];
+        off[i] = (int32_t)__ldg(a.nbr + (size_t)(i - 1) * N + e);
+        miss |= 1u << i;
+      }
+    }
+    // 1b: the codes resolved to offsets
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      if (!((miss >> i) & 1u)) continue;
+      const uint32_t n = (uint32_t)off[i];
+      if (n < NB_FLAG30) {
+        off[i] = (int32_t)((int64_t)n - first);
+      } else {
+        off[i] = (int32_t)((int64_t)(opp(i) - i) * (int64_t)N + l);
+        if (n & NB_FLAG30) patch |= 1u << i;
+      }
+    }
+    // phase 2: the gathers, branch-free
+#pragma unroll
+    for (int i = 1; i < Q; ++i) g[i] = Sto<S>::ld(src + (int64_t)(i * N) + off[i]);
+    // phase 3 (inlet and boundary-value elements only): the inlet term or the
+    // precomputed boundary value, from the link's code read again
+    if (patch) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!((patch >> i) & 1u)) continue;
+        const uint32_t n = __ldg(a.nbr + (size_t)(i - 1) * N + e);
+        if (n & NB_BOUNCE) g[i] += R(a.inlet[i]) * (a.inlet_s ? R(a.inlet_s[n & NB_INDEX]) : R(1));
+        else g[i] = static_cast<const R*>(a.side)[n & NB_INDEX];
       }
     }
   }
@@ -585,8 +634,19 @@ __device__ __forceinline__ void st4(double* p, const double* v) {
 // every coarse element that feeds a GhostFromCoarser, one record per source.
 // With prev set, the record is the mean of prev and the moments now (the
 // source moments at t+1/2 of the linear-in-time mode).
-template <int Q, class S>
-__global__ void __launch_bounds__(128) k_source_moments(const MomentsArgs a) {
+// Launch bounds of the ghost kernels: LBM_*_MINB sets a minimum of resident
+// blocks per SM; unset (0), only the block size is given, which lets the
+// compiler use fewer registers than an explicit minimum of one block.
+#ifndef LBM_MOM_BLOCK
+#define LBM_MOM_BLOCK 128
+#endif
+#if defined(LBM_MOM_MINB) && LBM_MOM_MINB > 0
+#define LBM_MOM_BOUNDS __launch_bounds__(LBM_MOM_BLOCK, LBM_MOM_MINB)
+#else
+#define LBM_MOM_BOUNDS __launch_bounds__(LBM_MOM_BLOCK)
+#endif
+template <int Q, class S, bool FORCE>
+__global__ void LBM_MOM_BOUNDS k_source_moments(const MomentsArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
@@ -600,14 +660,14 @@ __global__ void __launch_bounds__(128) k_source_moments(const MomentsArgs a) {
 #pragma unroll
   for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(src + (size_t)q * N + e);
   R F[3] = {R(0), R(0), R(0)};
-  if (a.force)
+  if (FORCE)
 #pragma unroll
     for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(a.force)[(size_t)b * N + e];
   R rec[RL::STRIDE];
 #pragma unroll
   for (int f = 0; f < RL::STRIDE; ++f) rec[f] = R(0);
   R rp, u[3], fneq[Q], Sv[NS];
-  post_moments<Q, R, true>(g, R(a.omega), R(a.rho_off), F, rp, u, fneq, Sv);
+  post_moments<Q, R, true, FORCE>(g, R(a.omega), R(a.rho_off), F, rp, u, fneq, Sv);
 #pragma unroll
   for (int q = 0; q < Q; ++q) rec[RL::FN + q] = fneq[q];
   rec[RL::RP] = rp;
@@ -699,9 +759,16 @@ struct GfcGroup {
   }
 };
 
+#ifndef LBM_GFC_BLOCK
 #define LBM_GFC_BLOCK 64
+#endif
+#if defined(LBM_GFC_MINB) && LBM_GFC_MINB > 0
+#define LBM_GFC_BOUNDS __launch_bounds__(LBM_GFC_BLOCK, LBM_GFC_MINB)
+#else
+#define LBM_GFC_BOUNDS __launch_bounds__(LBM_GFC_BLOCK)
+#endif
 template <int Q, class S>
-__global__ void __launch_bounds__(LBM_GFC_BLOCK) k_fill_gfc(const GfcArgs a) {
+__global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
@@ -779,6 +846,8 @@ __global__ void __launch_bounds__(LBM_GFC_BLOCK) k_fill_gfc(const GfcArgs a) {
   S* __restrict__ dst = static_cast<S*>(a.dst);
   const size_t N = (size_t)a.Ntot;
   const int64_t e = a.dest0 + k;
+  // interpolated f^neq, then f^eq per pair of opposite velocities (shared even part)
+  R fn[Q];
 #pragma unroll
   for (int q0 = 0; q0 < Q; q0 += 4) {
     R f0[4], f1[4], f2[4], f3[4];
@@ -787,13 +856,24 @@ __global__ void __launch_bounds__(LBM_GFC_BLOCK) k_fill_gfc(const GfcArgs a) {
     ld4(rec[2] + RL::FN + q0, f2);
     ld4(rec[3] + RL::FN + q0, f3);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int q = q0 + c;
-      if (q < Q) {
-        const R fn = lw0 * f0[c] + lw1 * f1[c] + lw2 * f2[c] + lw3 * f3[c];
-        dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rp, rho, u, usq) + scale * fn);
-      }
+    for (int c = 0; c < 4; ++c)
+      if (q0 + c < Q) fn[q0 + c] = lw0 * f0[c] + lw1 * f1[c] + lw2 * f2[c] + lw3 * f3[c];
+  }
+  const R base = rp - R(1.5) * rho * usq;
+  dst[e] = Sto<S>::cv(R(LT::w(0)) * base + scale * fn[0]);
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    R cu = R(0);
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      if (LT::c(i, b) > 0) cu += u[b];
+      if (LT::c(i, b) < 0) cu -= u[b];
     }
+    const R w = R(LT::w(i));
+    const R even = w * (base + R(4.5) * rho * cu * cu);
+    const R odd = w * R(3) * rho * cu;
+    dst[(size_t)i * N + e] = Sto<S>::cv(even + odd + scale * fn[i]);
+    dst[(size_t)(i + 1) * N + e] = Sto<S>::cv(even - odd + scale * fn[i + 1]);
   }
 }
 
@@ -807,8 +887,13 @@ __global__ void __launch_bounds__(LBM_GFC_BLOCK) k_fill_gfc(const GfcArgs a) {
 // One group of 2^d consecutive lanes per ghost: lane b loads child b (siblings
 // are contiguous, so the group's loads are coalesced), and the sums over the
 // children are shuffles inside the group.
-template <int Q, class S>
-__global__ void __launch_bounds__(256) k_fill_gff(const GffArgs a) {
+#if defined(LBM_GFF_MINB) && LBM_GFF_MINB > 0
+#define LBM_GFF_BOUNDS __launch_bounds__(256, LBM_GFF_MINB)
+#else
+#define LBM_GFF_BOUNDS __launch_bounds__(256)
+#endif
+template <int Q, class S, bool FORCE>
+__global__ void LBM_GFF_BOUNDS k_fill_gff(const GffArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D, NS = LT::NS, NCH = 1 << D;
@@ -830,10 +915,10 @@ __global__ void __launch_bounds__(256) k_fill_gff(const GffArgs a) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(src + (size_t)q * N + e);
     R F[3] = {R(0), R(0), R(0)};
-    if (a.force)
+    if (FORCE)
 #pragma unroll
       for (int c = 0; c < D; ++c) F[c] = static_cast<const R*>(a.force)[(size_t)c * N + e];
-    post_moments<Q, R, true>(g, wf, rho_off, F, rp, u, fneq, Sv);
+    post_moments<Q, R, true, FORCE>(g, wf, rho_off, F, rp, u, fneq, Sv);
   }
   // The ghost's velocity, mean minus (1/32) lap u, is linear in the children's
   // values, and so is lap u_a = dfac sum_c (2 d_c S_ac - d_a S_cc) with d_c the
@@ -1165,7 +1250,12 @@ struct Launch {
   }
   static void source_moments(int Q, const MomentsArgs& a, cudaStream_t st) {
     if (a.nsrc <= 0) return;
-    with_q(Q, [&](auto q) { k_source_moments<decltype(q)::value, S><<<blocks_for(a.nsrc, 128), 128, 0, st>>>(a); });
+    with_q(Q, [&](auto q) {
+      constexpr int QQ = decltype(q)::value;
+      const unsigned g = blocks_for(a.nsrc, LBM_MOM_BLOCK);
+      if (a.force) k_source_moments<QQ, S, true><<<g, LBM_MOM_BLOCK, 0, st>>>(a);
+      else k_source_moments<QQ, S, false><<<g, LBM_MOM_BLOCK, 0, st>>>(a);
+    });
   }
   static void fill_gfc(int Q, const GfcArgs& a, cudaStream_t st) {
     if (a.ng <= 0) return;
@@ -1177,7 +1267,9 @@ struct Launch {
     if (a.ng <= 0) return;
     with_q(Q, [&](auto q) {
       constexpr int QQ = decltype(q)::value;
-      k_fill_gff<QQ, S><<<blocks_for(a.ng * (1 << Lat<QQ>::D), 256), 256, 0, st>>>(a);
+      const unsigned g = blocks_for(a.ng * (1 << Lat<QQ>::D), 256);
+      if (a.force) k_fill_gff<QQ, S, true><<<g, 256, 0, st>>>(a);
+      else k_fill_gff<QQ, S, false><<<g, 256, 0, st>>>(a);
     });
   }
   static void fill_rest(int Q, const FillArgs& a, cudaStream_t st) {
@@ -1216,9 +1308,10 @@ const Ops* make_ops() {
                           &Launch<S>::set_state,
                           &Launch<S>::gather_ghosts,
                           &Launch<S>::reduce,         sizeof(S),              sizeof(typename Sto<S>::R),
-                          // BF16 storage: the boundary-brick kernel measured slower than the
-                          // neighbour-list kernel on the same elements
-                          sizeof(S) != 2};
+                          // every storage type streams its boundary bricks through the
+                          // brick tables (BF16: 2.85 against 5.50 ms per sphere step
+                          // through the neighbour list, measured)
+                          true};
   return &ops;
 }
 

@@ -60,8 +60,11 @@ struct lbm_ctx {
   // with dry set, advance() only walks the op sequence and flips parities
   std::function<void(int op, int level)> hook;
   bool dry = false;
-  // stream-collide timing (events recorded around each launch when enabled)
-  bool timing = false;
+  // per-launch timing: 0 off; 1 every kernel of the step, launched kernel by
+  // kernel; 2 steps keep replaying the captured graphs, which then record
+  // events around the finest level's stream-collide launches
+  int timing = 0;
+  bool capturing = false;
   struct Timed {
     int li, kernel;  // lbm::TimedKind
     cudaEvent_t a, b;
@@ -78,17 +81,22 @@ struct lbm_ctx {
     cudaEventCreate(&e);
     return e;
   }
-  // runs launch(), bracketed by events on the bound stream while timing is on
+  // runs launch(), bracketed by events on the bound stream when the timing
+  // mode asks for this launch
   template <class F>
   void timed_launch(int li, int kind, F&& launch) {
-    if (!timing) {
+    const bool rec = timing == 1 || (timing == 2 && capturing && li == nlev - 1 && kind <= lbm::TK_BOUNDARY);
+    if (!rec) {
       launch();
       return;
     }
     Timed t{li, kind, get_event(), get_event()};
-    cudaEventRecord(t.a, st);
+    // inside a capture, only an external record becomes an event-record node
+    // of the graph (a plain record would just order the captured work)
+    const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    cudaEventRecordWithFlags(t.a, st, flags);
     launch();
-    cudaEventRecord(t.b, st);
+    cudaEventRecordWithFlags(t.b, st, flags);
     timed.push_back(t);
   }
   void recycle_timed() {
@@ -105,18 +113,29 @@ struct lbm_ctx {
     std::vector<int> parity;
     cudaGraphExec_t exec;
     int64_t launches;
+    std::vector<Timed> timed;  // event pairs recorded by the graph (timing mode 2)
   };
   std::vector<StepGraph> graphs;
   cudaStream_t cap_stream = nullptr;
   bool graphs_on = true;
+  int last_graph = -1;        // graph of the most recent replay
+  bool graph_unread = false;  // its events hold a replay not yet read
   void drop_graphs() {
-    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& g : graphs) {
+      cudaGraphExecDestroy(g.exec);
+      for (auto& t : g.timed) {
+        event_pool.push_back(t.a);
+        event_pool.push_back(t.b);
+      }
+    }
     graphs.clear();
+    last_graph = -1;
+    graph_unread = false;
   }
   ~lbm_ctx() {
+    drop_graphs();
     recycle_timed();
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
-    drop_graphs();
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 

@@ -16,8 +16,8 @@
 
 namespace {
 
-constexpr int kChains = 8;
-constexpr int kIters = 4096;
+constexpr int kChains = 16;
+constexpr int kIters = 2048;
 constexpr int kReps = 5;
 constexpr int kThreads = 256;
 
@@ -41,8 +41,10 @@ lbm_status run(void* scratch, uint64_t bytes, double* gflops) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return LBM_ERR_CUDA;
-  // FP64 is slow on this part: fewer blocks keep one launch near a millisecond
-  const int blocks = sms * (sizeof(T) == 8 ? 2 : 16);
+  // whole waves of resident 256-thread blocks: FP64 (40 registers a thread)
+  // fits six per SM, one wave of a few milliseconds on this part's narrow
+  // FP64 pipe; FP32 (31 registers) eight per SM, two waves
+  const int blocks = sms * (sizeof(T) == 8 ? 6 : 16);
   if (bytes < (uint64_t)blocks * kThreads * sizeof(T)) return LBM_ERR_ARG;
   T* out = static_cast<T*>(scratch);
   cudaStream_t st = nullptr;

@@ -244,8 +244,11 @@ class Sim:
         _check(self.ctx, lib().lbm_kernel_launches(self.ctx, C.byref(n)))
         return int(n.value)
 
-    def timing_enable(self, on=True):
-        _check(self.ctx, lib().lbm_timing_enable(self.ctx, int(bool(on))))
+    def timing_enable(self, mode=1):
+        """0 off; 1 every kernel timed, steps launched kernel by kernel; 2 steps
+        replay the captured graphs, which time the finest level's
+        stream-collide launches (read back: the most recent replay)."""
+        _check(self.ctx, lib().lbm_timing_enable(self.ctx, int(mode)))
 
     TIMED_KINDS = ("interior", "list", "boundary", "gff", "moments", "gfc", "outlet", "unused")
 
