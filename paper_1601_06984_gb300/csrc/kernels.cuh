@@ -522,6 +522,84 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : LB
   for (int i = 0; i < Q; ++i) st_once(dst + i * N, Sto<S>::cv(g[i]));
 }
 
+// BF16 interior bricks, two neighbouring elements per thread: lane m of the
+// brick's warp takes z-curve positions 2m and 2m+1, which differ only in the
+// lowest x bit, so they sit next to each other in every direction array.  A
+// link with c_x = 0 pulls both sources from one brick slot at positions l'
+// and l'+1 (the mesh builder checks this on the link table), one 32-bit
+// bfloat16 pair load at an even element index; links with c_x != 0 take two
+// single loads.  The 19 results are written as bfloat16 pairs, rounded by one
+// packed conversion each.  Same pull and BGK collision as the one-element
+// kernel, element by element.
+// Four blocks per SM (64 registers) for D2Q9 / D3Q19, three for D3Q27 (which
+// spills at four).
+#define LBM_BR_PAIR_MINB(Q) ((Q) > 19 ? 3 : 4)
+template <int Q, bool FORCE>
+__global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_BR_PAIR_MINB(Q)) k_stream_collide_brick_pair(const BrickArgs a) {
+  using S = __nv_bfloat16;
+  using R = float;
+  using LT = Lat<Q>;
+  constexpr int D = LT::D;
+  constexpr int BPB = LBM_BR_BLOCK / 32;
+  const int m = threadIdx.x & 31;
+  // one brick per warp: the exit below and the shuffles run with whole warps
+  const int64_t b = (int64_t)blockIdx.x * BPB + (threadIdx.x >> 5);
+  if (b >= a.nB) return;
+  const int32_t row = m < 27 ? __ldg(a.nb + b * 27 + m) : 0;
+  const size_t N = (size_t)a.Ntot;
+  const int64_t first = a.begin + b * 64;
+  const S* __restrict__ src = static_cast<const S*>(a.src) + first;
+  S* __restrict__ dst = static_cast<S*>(a.dst) + first + 2 * m;
+  // the link-table entries of positions 2m (low half) and 2m+1 (high half)
+  const uint32_t* __restrict__ tab2 = reinterpret_cast<const uint32_t*>(a.tab);
+  R g0[Q], g1[Q];
+  {
+    const __nv_bfloat162 p = *reinterpret_cast<const __nv_bfloat162*>(src + 2 * m);
+    g0[0] = __low2float(p);
+    g1[0] = __high2float(p);
+  }
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const uint32_t tw = __ldg(tab2 + (i - 1) * 32 + m);
+    const S* base = src + (int64_t)(i * N);
+    if (LT::c(i, 0) == 0) {
+      const uint32_t v = tw & 0xffffu;
+      const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
+      const __nv_bfloat162 p = *reinterpret_cast<const __nv_bfloat162*>(base + (r + (int32_t)(v & 63)));
+      g0[i] = __low2float(p);
+      g1[i] = __high2float(p);
+    } else {
+      const uint32_t v0 = tw & 0xffffu, v1 = tw >> 16;
+      const int32_t r0 = __shfl_sync(0xffffffffu, row, (int)(v0 >> 6));
+      const int32_t r1 = __shfl_sync(0xffffffffu, row, (int)(v1 >> 6));
+      // signed sums: a neighbour brick stored before this one has r < 0
+      g0[i] = __bfloat162float(base[r0 + (int32_t)(v0 & 63)]);
+      g1[i] = __bfloat162float(base[r1 + (int32_t)(v1 & 63)]);
+    }
+  }
+  R F0[3] = {R(0), R(0), R(0)}, F1[3] = {R(0), R(0), R(0)};
+  if (FORCE) {
+    const R* __restrict__ fp = static_cast<const R*>(a.force) + first + 2 * m;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const float2 f = *reinterpret_cast<const float2*>(fp + c * N);
+      F0[c] = f.x;
+      F1[c] = f.y;
+    }
+  }
+  bgk_collide<Q, R, FORCE>(g0, R(a.omega), R(a.rho_off), F0);
+  bgk_collide<Q, R, FORCE>(g1, R(a.omega), R(a.rho_off), F1);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(g0[i], g1[i]);
+#if LBM_SC_STREAM
+    __stcs(reinterpret_cast<unsigned int*>(dst + i * N), *reinterpret_cast<const unsigned int*>(&p));
+#else
+    *reinterpret_cast<__nv_bfloat162*>(dst + i * N) = p;
+#endif
+  }
+}
+
 // ----------------------------------------------------------------- outlet values
 // Sec. 2.3 outflow: for an incoming direction i whose upstream element lies
 // beyond the outlet, either extrapolate that element's f_i linearly along -n
@@ -1223,6 +1301,15 @@ struct Launch {
     const unsigned g = blocks_for(a.nB, LBM_BR_BLOCK / 64);
     with_q(Q, [&](auto q) {
       constexpr int QQ = decltype(q)::value;
+      if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        // BF16 interior bricks: two elements per thread, one brick per warp
+        if (!boundary) {
+          const unsigned g2 = blocks_for(a.nB, LBM_BR_BLOCK / 32);
+          if (force) k_stream_collide_brick_pair<QQ, true><<<g2, LBM_BR_BLOCK, 0, st>>>(a);
+          else k_stream_collide_brick_pair<QQ, false><<<g2, LBM_BR_BLOCK, 0, st>>>(a);
+          return;
+        }
+      }
       if (boundary) {
         if (force) k_stream_collide_brick<QQ, S, true, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
         else k_stream_collide_brick<QQ, S, false, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);

@@ -599,6 +599,15 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
         }
         M.brick_tab[(size_t)(i - 1) * 64 + l] = (uint16_t)((t << 6) | (int)zkey(y, d, bshift));
       }
+    // the two-element BF16 kernel pulls both sources of positions 2m, 2m+1
+    // through a link with c_x = 0 as one pair: same slot, positions l', l'+1
+    for (int i = 1; i < Q; ++i) {
+      if (B.dr.c[i][0] != 0) continue;
+      for (int l = 0; l < 64; l += 2) {
+        const uint16_t e0 = M.brick_tab[(size_t)(i - 1) * 64 + l], e1 = M.brick_tab[(size_t)(i - 1) * 64 + l + 1];
+        if ((e0 & 1) || e1 != e0 + 1) return bad(LBM_ERR_INTERNAL, "brick link table breaks the x pairing");
+      }
+    }
   }
   // relaxation per level, Eq. (fneq_scale)
   M.lv[0].omega = p.omega_coarse;
