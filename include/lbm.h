@@ -273,6 +273,31 @@ lbm_status lbm_sfc_partition(const int64_t* tree_ids, int64_t n, int32_t d, int3
                              int64_t* order, int64_t* weights, int64_t* cumulative,
                              int32_t* part);
 
+/* Halo plan of a partitioned mesh (Sec. 3.1 weight-based decomposition along
+ * the space-filling curve, Sec. 3.2 halo elements); host only, no device work.
+ * part[n]: the owning part of every element in caller order, 0 <= part <
+ * nparts (for instance the split of lbm_sfc_partition mapped back through its
+ * order).  Part `rank` computes its own fluid elements and the ghost elements
+ * they depend on; it must receive the other parts' fluid elements that these
+ * computations read: pull sources (also the second node of interpolated
+ * bounce-back and the outlet's extrapolation sources), GhostFromCoarser
+ * sources and GhostFromFiner children of the ghosts it fills, and the pull
+ * sources of the ghost layer the time mode advances.  Each such read takes the
+ * current state of the read element's level, so exchanging a level's halo
+ * after every stream-collide of that level (and after lbm_init) keeps all
+ * reads current.
+ * Outputs: recv_count[nparts], the number of elements to receive from each
+ * part (0 for rank itself); recv, their caller indices grouped by sending part
+ * (parts ascending), ascending within a group, up to recv_cap entries (recv
+ * may be NULL with recv_cap 0); *n_ghosts, the number of ghosts the part fills
+ * itself, and ghosts, their rows in the lbm_get_ghosts order (ascending), up
+ * to ghost_cap entries.  The part sending to r sends, in r's order, the list
+ * lbm_halo_plan for r gives under the sender.  Errors: LBM_ERR_ARG (null
+ * pointers, part values outside [0, nparts), rank outside [0, nparts)). */
+lbm_status lbm_halo_plan(const lbm_ctx* ctx, const int32_t* part, int32_t nparts, int32_t rank,
+                         int64_t* recv_count, int64_t* recv, int64_t recv_cap, int64_t* n_ghosts,
+                         int64_t* ghosts, int64_t ghost_cap);
+
 /* Change the coarsest relaxation rate (finer levels follow Eq. fneq_scale) and,
  * if u_in is not NULL, the inlet velocity, without rebuilding the mesh.  The
  * state is kept. */

@@ -769,6 +769,41 @@ struct Sim {
 
   void fill_gfc(int li, const std::vector<Mom<T>>& q0, const std::vector<Mom<T>>* q1);
 
+  // The ops of advance() one at a time, for a driver that interleaves its own
+  // steps (the halo exchange of a partitioned run): source moments at t (A)
+  // and t+1 (B) are kept per level between calls.
+  std::vector<std::vector<Mom<T>>> op_qa, op_qb;
+  bool run_op(int op, int li) {
+    if (li < 0 || li >= nlev()) return false;
+    op_qa.resize(nlev());
+    op_qb.resize(nlev());
+    const bool finer = li + 1 < nlev();
+    switch (op) {
+      case 0:  // GhostFromFiner of level li
+        if (!finer) return false;
+        fill_gff(li);
+        return true;
+      case 1:  // source moments of level li at t
+        op_qa[li] = level_moments(li);
+        return true;
+      case 2:  // GhostFromCoarser of level li+1 from the moments at t
+        if (!finer || op_qa[li].size() != lv[li].e.size()) return false;
+        fill_gfc(li + 1, op_qa[li], nullptr);
+        return true;
+      case 3:  // stream + collide of level li
+        stream_collide(li);
+        return true;
+      case 4:  // source moments of level li at t+1
+        op_qb[li] = level_moments(li);
+        return true;
+      case 5:  // GhostFromCoarser of level li+1 from the mean of t and t+1
+        if (!finer || op_qa[li].size() != lv[li].e.size() || op_qb[li].size() != lv[li].e.size()) return false;
+        fill_gfc(li + 1, op_qa[li], &op_qb[li]);
+        return true;
+    }
+    return false;
+  }
+
   // ------------------------------------------------------------ driver
   // Recursive level time stepping (Sec. 2.2): one step on level L is two on
   // level L+1 (acoustic scaling); GFF is filled before GFC at the synchronous
@@ -1159,6 +1194,15 @@ int orc_fill_ghosts(void* h) {
   static_cast<Sim<double>*>(h)->fill_ghosts();
   return 0;
 }
+
+// One op of the recursive step (0 GhostFromFiner of level li, 1 / 4 source
+// moments of level li at t / t+1, 2 / 5 GhostFromCoarser of level li+1 from
+// the moments at t / their mean with t+1, 3 stream-collide of level li), for a
+// driver that runs the ops in advance()'s order with its own steps in
+// between.  Returns -1 for an op that does not apply.
+int orc_op(void* h, int op, int li) { return static_cast<Sim<double>*>(h)->run_op(op, li) ? 0 : -1; }
+
+int orc_nlev(void* h) { return static_cast<Sim<double>*>(h)->nlev(); }
 
 // rho[n], u[n][d], S[n][d(d+1)/2] (each element in its own level's lattice
 // units), user order

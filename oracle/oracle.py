@@ -72,6 +72,10 @@ def lib():
         L.orc_compact_velocity.argtypes = [I, P, P, P, P]
         L.orc_set_threads.argtypes = [I]
         L.orc_set_threads.restype = I
+        L.orc_op.argtypes = [P, I, I]
+        L.orc_op.restype = I
+        L.orc_nlev.argtypes = [P]
+        L.orc_nlev.restype = I
         _lib = L
     return _lib
 
@@ -184,6 +188,17 @@ class Oracle:
 
     def fill_ghosts(self):
         lib().orc_fill_ghosts(self.h)
+
+    OP_GFF, OP_MOM_A, OP_GFC_A, OP_SC, OP_MOM_B, OP_GFC_B = range(6)
+
+    def op(self, op, level):
+        """One op of the recursive step (see orc_op), for drivers that put
+        their own work between the ops."""
+        if lib().orc_op(self.h, int(op), int(level)) != 0:
+            raise OracleError(f"op {op} does not apply on level {level}")
+
+    def nlev(self):
+        return int(lib().orc_nlev(self.h))
 
     def moments(self):
         rho = np.zeros(self.n)

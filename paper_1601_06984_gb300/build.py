@@ -18,7 +18,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CU = ["kernels_fp64.cu", "kernels_fp32dev.cu", "kernels_bf16dev.cu", "reduce_noalloc.cu",
       "adjoint_fp64.cu", "adjoint_fp32dev.cu", "adjoint_bf16dev.cu", "probe.cu"]
-CPP = ["mesh.cpp", "api.cpp", "adjoint.cpp"]
+CPP = ["mesh.cpp", "api.cpp", "adjoint.cpp", "partition.cpp"]
 
 
 def _cuda_home() -> str:

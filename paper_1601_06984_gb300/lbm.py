@@ -26,7 +26,7 @@ EXPORTS = ["lbm_build_mesh", "lbm_mesh_info", "lbm_device_bytes", "lbm_bind", "l
            "lbm_step", "lbm_fill_ghosts", "lbm_moments", "lbm_reduce", "lbm_get_state", "lbm_set_state", "lbm_ghost_count",
            "lbm_get_ghosts", "lbm_sfc_partition", "lbm_kernel_launches", "lbm_timing_enable", "lbm_timing_read",
            "lbm_reduce_noalloc", "lbm_set_params", "lbm_adjoint_bytes", "lbm_adjoint", "lbm_last_error",
-           "lbm_destroy", "lbm_obstacle_links", "lbm_set_link_q", "lbm_alu_peak"]
+           "lbm_destroy", "lbm_obstacle_links", "lbm_set_link_q", "lbm_alu_peak", "lbm_halo_plan"]
 
 
 class LBMError(RuntimeError):
@@ -81,6 +81,7 @@ def lib():
             "lbm_obstacle_links": [P, P, P, I64, C.POINTER(I64)],
             "lbm_set_link_q": [P, P, I64],
             "lbm_alu_peak": [I32, P, U64, P],
+            "lbm_halo_plan": [P, P, I32, I32, P, P, I64, P, P, I64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -213,6 +214,22 @@ class Sim:
         self.close()
 
     # -- queries
+    def halo_plan(self, part, nparts, rank):
+        """Sec. 3.1/3.2 halo plan of part `rank` for the owner array part[n]
+        (caller order): {sending part: caller indices to receive (ascending)}
+        and the rows (lbm_get_ghosts order) of the ghosts the part fills."""
+        part = _arr(part, np.int32, (self.n,))
+        counts = np.zeros(nparts, np.int64)
+        ng = C.c_int64()
+        _check(self.ctx, lib().lbm_halo_plan(self.ctx, _p(part), int(nparts), int(rank), _p(counts), None, 0,
+                                             C.byref(ng), None, 0))
+        recv = np.zeros(int(counts.sum()), np.int64)
+        ghosts = np.zeros(ng.value, np.int64)
+        _check(self.ctx, lib().lbm_halo_plan(self.ctx, _p(part), int(nparts), int(rank), _p(counts), _p(recv),
+                                             len(recv), C.byref(ng), _p(ghosts), len(ghosts)))
+        start = np.concatenate([[0], np.cumsum(counts)])
+        return {p: recv[start[p]:start[p + 1]] for p in range(nparts) if counts[p] > 0}, ghosts
+
     def mesh_info(self):
         info = np.zeros((32, 10), np.int64)
         nl = C.c_int32()
