@@ -423,6 +423,45 @@ def adjoint_run(device):
     return out
 
 
+def sphere_adjoint_run(mesh, Q, om, uin, fields, outlet, device, n=4, K=2):
+    """Adjoint at production size: the bench sphere, FP32 deviation storage,
+    drag objective, n coarse steps with checkpoints every K, each step recorded
+    in a recompute of its own (adjoint_tape 2, the smaller workspace).  Time of
+    the adjoint (forward with checkpoints, recomputes, reverse sweep) over the
+    forward alone (n steps through lbm_step's graphs)."""
+    import torch
+    from paper_1601_06984_gb300 import lbm
+    rec = {"config": f"sphere_re100_d3q19_5level FP32 deviation, drag (F_x) objective, {n} coarse steps, K={K}, "
+                     "step-by-step recording"}
+    g = None
+    try:
+        g = lbm.Sim(mesh, Q, om, precision=lbm.FP32DEV, u_in=uin, outlet=outlet, device=device, adjoint_tape=2)
+        rho, u, S = fields(mesh)
+        g.init(rho, u, S)
+        g.step(4)
+        f0 = g.get_state()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        g.step(n)
+        g.reduce()
+        tf = time.perf_counter() - t0
+        g.set_state(f0)
+        del f0
+        rec["adjoint_workspace_gb"] = g.adjoint_bytes(n, K) / 1e9
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        J, _, dw, dU = g.adjoint(n, K, 1, want_force=False)
+        ta = time.perf_counter() - t0
+        rec.update({"forward_s": tf, "adjoint_s": ta, "adjoint_to_forward": ta / tf, "J_drag": J,
+                    "dJ_domega_c": dw, "dJ_du_in_x": float(dU[0])})
+    except Exception as ex:  # reported, not fatal: the workspace is the largest allocation of the run
+        rec["error"] = repr(ex)[:300]
+    if g is not None:
+        g.close()
+    torch.cuda.empty_cache()
+    return rec
+
+
 def e2e_run(sim, mesh, fields, K):
     """End to end through the C ABI: initial fields from pinned host memory,
     then K coarse steps each followed by the FP64 reduction (mass, momentum,
@@ -641,6 +680,7 @@ def main():
             v_["note"] = ("working set fits in the 129 MB L2 (not flushed); steps replay the library's CUDA "
                           "graphs; hbm_gbs_algorithmic counts the algorithmic bytes, most of which L2 serves")
         adj = adjoint_run(device)
+        adj["sphere"] = sphere_adjoint_run(mesh, Q, om, uin, fields, outlet, device)
 
     if rank != 0:
         if dist is not None:

@@ -114,7 +114,14 @@ enum { LBM_INLET_UNIFORM = 0, LBM_INLET_PARABOLIC = 1 };
  *                lbm_init or lbm_set_state.  The check synchronises the stream.
  *                Negative: LBM_ERR_ARG.
  *  mass_band     relative band of the mass check (0: finiteness only; negative
- *                or not finite: LBM_ERR_ARG). */
+ *                or not finite: LBM_ERR_ARG).
+ *  adjoint_tape  how lbm_adjoint records the forward steps it reverses (the
+ *                gradients are the same either way): 1 records all steps of a
+ *                checkpoint segment in one recompute (two forward passes per
+ *                step); 2 recomputes the segment, then each step once more
+ *                while recording it (three passes, less memory); 0 picks 1
+ *                when its workspace holds at most twice the states of 2 or at
+ *                most 8 GiB of states, else 2.  Other values: LBM_ERR_ARG. */
 typedef struct {
   int32_t stencil;
   int32_t precision;
@@ -131,6 +138,7 @@ typedef struct {
   int32_t n_levels;
   int32_t check_every;
   double mass_band;
+  int32_t adjoint_tape;
 } lbm_params;
 
 /* Build the multilevel mesh on the host (no device work).
@@ -326,6 +334,10 @@ lbm_status lbm_set_params(lbm_ctx* ctx, double omega_coarse, const double* u_in)
  * gradient with respect to F is that of the forced scheme (also when
  * use_force is 0, where it is taken at F = 0). */
 lbm_status lbm_adjoint_bytes(lbm_ctx* ctx, int64_t n_coarse, int32_t K, uint64_t* bytes);
+/* The workspace holds, besides the adjoint buffers, ceil(n_coarse / K)
+ * checkpoints and the final state, and (params.adjoint_tape) either K step
+ * states plus one step's snapshots, or K steps' snapshots plus two states per
+ * step but the last (each a full [Q][Ntot] state of the storage type). */
 lbm_status lbm_adjoint(lbm_ctx* ctx, int64_t n_coarse, int32_t K, int32_t objective, void* adj_ws,
                        uint64_t bytes, double* J, double* dJ_dF, double* dJ_domega, double* dJ_duin,
                        double* dJ_df0);

@@ -36,8 +36,12 @@ struct TapeOp {
 struct AdjLayout {
   size_t lamA = 0, lamB = 0, lamF = 0, side_fwd = 0, lam_side = 0, partial = 0, acc = 0, contrib = 0;
   std::vector<size_t> lam_recA, lam_recB, recA, recB, csr_off, csr_item;
-  size_t ck = 0, steps = 0, snaps = 0, fin = 0;
+  size_t ck = 0, steps = 0, snaps = 0, ends = 0, fin = 0;
   int n_ck = 0, n_steps = 0, n_snaps = 0;
+  // tape_all: a segment's recompute records every step's tape (two forward
+  // passes per step instead of three); needs K tapes' copies plus, per step but
+  // the last, copies of the states the reverse reads in place (both buffers)
+  bool tape_all = false;
   size_t state_bytes = 0, total = 0;
   int partial_rows = 0;  // running rows of the parameter sums: the largest grid of a reverse launch
 };
@@ -225,12 +229,21 @@ AdjLayout adj_layout(lbm_ctx* c, int64_t n, int K) {
   L.n_ck = (int)((n + K - 1) / K);
   L.n_steps = K;
   L.n_snaps = count_snapshots(c);
+  // workspace rule: record the whole segment when that needs at most twice the
+  // states of the step-by-step scheme, or at most 8 GiB of states
+  const size_t per_step_old = (size_t)K + (size_t)L.n_snaps;
+  const size_t per_step_new = (size_t)K * (size_t)(L.n_snaps + 2);
+  if (c->p.adjoint_tape == 1) L.tape_all = true;
+  else if (c->p.adjoint_tape == 2) L.tape_all = false;
+  else L.tape_all = per_step_new <= 2 * per_step_old || per_step_new * L.state_bytes <= ((size_t)8 << 30);
   L.ck = o;
   o += (size_t)L.n_ck * L.state_bytes;
   L.steps = o;
-  o += (size_t)L.n_steps * L.state_bytes;
+  if (!L.tape_all) o += (size_t)L.n_steps * L.state_bytes;
   L.snaps = o;
-  o += (size_t)L.n_snaps * L.state_bytes;
+  o += (size_t)L.n_snaps * L.state_bytes * (L.tape_all ? (size_t)K : 1);
+  L.ends = o;
+  if (L.tape_all) o += (size_t)2 * (size_t)(K - 1) * L.state_bytes;
   L.fin = o;
   o += L.state_bytes;
   L.total = o;
@@ -321,14 +334,26 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
       copy_level(c, src, c->cur(li), li);
     }
   };
-  // ---- forward with checkpoints
+  // ---- forward with checkpoints: the parities of every step from a dry walk,
+  // then each segment through lbm_step's path (graph replay of step pairs)
   std::vector<std::vector<int>> parity_at(n + 1);
-  for (int64_t t = 0; t < n; ++t) {
-    parity_at[t] = c->parity;
-    if (t % K == 0) save_state(W + L.ck + (size_t)(t / K) * L.state_bytes);
-    c->advance(0);
+  {
+    const std::vector<int> p0 = c->parity;
+    c->dry = true;
+    for (int64_t t = 0; t < n; ++t) {
+      parity_at[t] = c->parity;
+      c->advance(0);
+    }
+    c->dry = false;
+    parity_at[n] = c->parity;
+    c->parity = p0;
   }
-  parity_at[n] = c->parity;
+  for (int64_t t = 0; t < n && s == LBM_OK; t += K) {
+    save_state(W + L.ck + (size_t)(t / K) * L.state_bytes);
+    s = c->run_steps(std::min<int64_t>(K, n - t));
+  }
+  if (s == LBM_OK && c->parity != parity_at[n]) s = c->fail(LBM_ERR_INTERNAL, "adjoint forward parities differ");
+  if (s != LBM_OK) return s;
   save_state(W + L.fin);
   s = c->launched("adjoint forward");
   if (s != LBM_OK) return s;
@@ -387,170 +412,203 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   }
   // ---- reverse sweep
   const int nseg = L.n_ck;
-  for (int seg = nseg - 1; seg >= 0 && s == LBM_OK; --seg) {
-    const int64_t s0 = (int64_t)seg * K, s1 = std::min<int64_t>(s0 + K, n);
-    // recompute the segment keeping each step's start state; the last step's
-    // is the live state, which its tape pass starts from directly
-    restore_state(W + L.ck + (size_t)seg * L.state_bytes, parity_at[s0]);
-    for (int64_t t = s0; t + 1 < s1; ++t) {
-      save_state(W + L.steps + (size_t)(t - s0) * L.state_bytes);
-      c->advance(0);
-    }
-    for (int64_t t = s1 - 1; t >= s0 && s == LBM_OK; --t) {
-      if (t + 1 < s1) restore_state(W + L.steps + (size_t)(t - s0) * L.state_bytes, parity_at[t]);
-      Recorder r(c);
-      r.counting = false;
-      r.need_copy = plan_snapshots(c);
-      r.snap_base = W + L.snaps;
-      r.state_bytes = L.state_bytes;
-      r.max_snaps = L.n_snaps;
-      c->hook = [&](int op, int li) { r.on(op, li); };
-      c->advance(0);
-      c->hook = nullptr;
-      if (r.overflow) return c->fail(LBM_ERR_INTERNAL, "adjoint tape needs more snapshots than counted");
-      if (r.clobbered != r.need_copy) return c->fail(LBM_ERR_INTERNAL, "adjoint tape differs from its plan");
-      auto snap = [&](int id) { return r.where[id]; };
-      // forward records of an interface, recomputed from the snapshots
-      auto records = [&](int lc, int sa, int sb) {
-        const HostLevel& Hc = c->M.lv[lc];
-        MomentsArgs m{};
-        m.force = force;
-        m.elem = c->at<int32_t>(c->ld[lc].src_elem);
-        m.Ntot = (int64_t)N;
-        m.nsrc = c->ld[lc].nsrc;
-        m.omega = Hc.omega;
-        m.rho_off = c->rho_off;
-        m.src = snap(sa);
-        m.mom = W + L.recA[lc];
-        m.prev = nullptr;
-        c->ops->source_moments(c->Q, m, st);
-        if (sb < 0) return static_cast<const void*>(W + L.recA[lc]);
-        m.src = snap(sb);
-        m.mom = W + L.recB[lc];
-        m.prev = W + L.recA[lc];
-        c->ops->source_moments(c->Q, m, st);
-        return static_cast<const void*>(W + L.recB[lc]);
-      };
-      for (int k = (int)r.tape.size() - 1; k >= 0; --k) {
-        const TapeOp& t = r.tape[k];
-        const int li = t.level;
-        const HostLevel& H = c->M.lv[li];
-        if (t.op == OP_SC) {
-          const int p = t.parity[li];
-          const bool outlet = H.out_end > H.out_begin;
-          if (outlet) {
-            OutletArgs o{};
-            o.src = snap(t.snap);
-            o.side = W + L.side_fwd;
+  // records one coarse step's tape while running it (copies into snap_base)
+  auto record_step = [&](Recorder& r, char* snap_base) -> lbm_status {
+    r.counting = false;
+    r.need_copy = plan_snapshots(c);
+    r.snap_base = snap_base;
+    r.state_bytes = L.state_bytes;
+    r.max_snaps = L.n_snaps;
+    c->hook = [&](int op, int li) { r.on(op, li); };
+    c->advance(0);
+    c->hook = nullptr;
+    if (r.overflow) return c->fail(LBM_ERR_INTERNAL, "adjoint tape needs more snapshots than counted");
+    if (r.clobbered != r.need_copy) return c->fail(LBM_ERR_INTERNAL, "adjoint tape differs from its plan");
+    return LBM_OK;
+  };
+  // runs one recorded step backwards
+  auto reverse_step = [&](Recorder& r) {
+    auto snap = [&](int id) { return r.where[id]; };
+    // forward records of an interface, recomputed from the snapshots
+    auto records = [&](int lc, int sa, int sb) {
+      const HostLevel& Hc = c->M.lv[lc];
+      MomentsArgs m{};
+      m.force = force;
+      m.elem = c->at<int32_t>(c->ld[lc].src_elem);
+      m.Ntot = (int64_t)N;
+      m.nsrc = c->ld[lc].nsrc;
+      m.omega = Hc.omega;
+      m.rho_off = c->rho_off;
+      m.src = snap(sa);
+      m.mom = W + L.recA[lc];
+      m.prev = nullptr;
+      c->ops->source_moments(c->Q, m, st);
+      if (sb < 0) return static_cast<const void*>(W + L.recA[lc]);
+      m.src = snap(sb);
+      m.mom = W + L.recB[lc];
+      m.prev = W + L.recA[lc];
+      c->ops->source_moments(c->Q, m, st);
+      return static_cast<const void*>(W + L.recB[lc]);
+    };
+    for (int k = (int)r.tape.size() - 1; k >= 0; --k) {
+      const TapeOp& t = r.tape[k];
+      const int li = t.level;
+      const HostLevel& H = c->M.lv[li];
+      if (t.op == OP_SC) {
+        const int p = t.parity[li];
+        const bool outlet = H.out_end > H.out_begin;
+        if (outlet) {
+          OutletArgs o{};
+          o.src = snap(t.snap);
+          o.side = W + L.side_fwd;
+          o.elem = c->at<int32_t>(c->oOutElem);
+          o.a = c->at<int32_t>(c->oOutA);
+          o.b = c->at<int32_t>(c->oOutB);
+          o.dir = c->at<int8_t>(c->oOutDir);
+          o.kind = c->at<int8_t>(c->oOutKind);
+          o.force = force;
+          o.Ntot = (int64_t)N;
+          o.begin = H.out_begin;
+          o.end = H.out_end;
+          o.omega = H.omega;
+          o.rho_off = c->rho_off;
+          o.rho0 = c->p.rho0;
+          o.zero_gradient = c->p.outlet == LBM_OUTLET_ZERO_GRADIENT;
+          o.q = c->at<double>(c->oOutQ);
+          c->ops->outlet(c->Q, o, st);
+        }
+        AdjSCArgs a{};
+        a.c = common(snap(t.snap), lam_for(!p), lam_for(p), li);
+        a.nbr = c->at<uint32_t>(c->oNbr);
+        a.side_fwd = W + L.side_fwd;
+        a.lam_side = W + L.lam_side;
+        a.omega = H.omega;
+        std::memcpy(a.inlet, c->inlet, sizeof(a.inlet));
+        a.inlet_s = c->at<double>(c->oInletS);
+        // interior bricks (the first 64 nB fluid elements) through the brick
+        // tables, everything else through the neighbour list
+        const int64_t nbrick = 64 * H.nB;
+        AdjSCArgs ab = a;
+        ab.begin = H.base + H.oF;
+        ab.nB = H.nB;
+        ab.brick_nb = c->at<int32_t>(c->oBrickNb) + (size_t)H.brick_first * 27;
+        ab.brick_tab = c->at<uint16_t>(c->oBrickTab);
+        aops->sc_brick(c->Q, ab, st);
+        if (c->p.time_mode == LBM_TIME_TWO_LAYER) {
+          a.begin = H.base + H.oC;
+          a.end = H.base + H.oG1 - nbrick;
+          a.hole_at = H.base + H.oF;
+          a.hole_len = nbrick;
+        } else {
+          a.begin = H.base + H.oF + nbrick;
+          a.end = H.base + H.oG2;
+          a.hole_at = a.end;
+          a.hole_len = 0;
+        }
+        aops->sc(c->Q, a, st);
+        if (outlet) {
+          for (int which = 0; which < (c->p.bouzidi ? 6 : 3); ++which) {
+            AdjOutletArgs o{};
+            o.c = common(snap(t.snap), nullptr, lam_for(p), li);
             o.elem = c->at<int32_t>(c->oOutElem);
             o.a = c->at<int32_t>(c->oOutA);
             o.b = c->at<int32_t>(c->oOutB);
             o.dir = c->at<int8_t>(c->oOutDir);
             o.kind = c->at<int8_t>(c->oOutKind);
-            o.force = force;
-            o.Ntot = (int64_t)N;
+            o.lam_side = W + L.lam_side;
             o.begin = H.out_begin;
             o.end = H.out_end;
+            o.which = which;
             o.omega = H.omega;
-            o.rho_off = c->rho_off;
-            o.rho0 = c->p.rho0;
             o.zero_gradient = c->p.outlet == LBM_OUTLET_ZERO_GRADIENT;
             o.q = c->at<double>(c->oOutQ);
-            c->ops->outlet(c->Q, o, st);
+            aops->outlet(c->Q, o, st);  // pass 0 also adds d/d omega through the normal links' f^neq
           }
-          AdjSCArgs a{};
-          a.c = common(snap(t.snap), lam_for(!p), lam_for(p), li);
-          a.nbr = c->at<uint32_t>(c->oNbr);
-          a.side_fwd = W + L.side_fwd;
-          a.lam_side = W + L.lam_side;
-          a.omega = H.omega;
-          std::memcpy(a.inlet, c->inlet, sizeof(a.inlet));
-          a.inlet_s = c->at<double>(c->oInletS);
-          // interior bricks (the first 64 nB fluid elements) through the brick
-          // tables, everything else through the neighbour list
-          const int64_t nbrick = 64 * H.nB;
-          AdjSCArgs ab = a;
-          ab.begin = H.base + H.oF;
-          ab.nB = H.nB;
-          ab.brick_nb = c->at<int32_t>(c->oBrickNb) + (size_t)H.brick_first * 27;
-          ab.brick_tab = c->at<uint16_t>(c->oBrickTab);
-          aops->sc_brick(c->Q, ab, st);
-          if (c->p.time_mode == LBM_TIME_TWO_LAYER) {
-            a.begin = H.base + H.oC;
-            a.end = H.base + H.oG1 - nbrick;
-            a.hole_at = H.base + H.oF;
-            a.hole_len = nbrick;
-          } else {
-            a.begin = H.base + H.oF + nbrick;
-            a.end = H.base + H.oG2;
-            a.hole_at = a.end;
-            a.hole_len = 0;
-          }
-          aops->sc(c->Q, a, st);
-          if (outlet) {
-            for (int which = 0; which < (c->p.bouzidi ? 6 : 3); ++which) {
-              AdjOutletArgs o{};
-              o.c = common(snap(t.snap), nullptr, lam_for(p), li);
-              o.elem = c->at<int32_t>(c->oOutElem);
-              o.a = c->at<int32_t>(c->oOutA);
-              o.b = c->at<int32_t>(c->oOutB);
-              o.dir = c->at<int8_t>(c->oOutDir);
-              o.kind = c->at<int8_t>(c->oOutKind);
-              o.lam_side = W + L.lam_side;
-              o.begin = H.out_begin;
-              o.end = H.out_end;
-              o.which = which;
-              o.omega = H.omega;
-              o.zero_gradient = c->p.outlet == LBM_OUTLET_ZERO_GRADIENT;
-              o.q = c->at<double>(c->oOutQ);
-              aops->outlet(c->Q, o, st);  // pass 0 also adds d/d omega through the normal links' f^neq
-            }
-          }
-        } else if (t.op == OP_MOM_A || t.op == OP_MOM_B) {
-          if (c->ld[li].nsrc == 0) continue;
-          AdjMomArgs a{};
-          a.c = common(snap(t.snap), nullptr, lam_for(t.parity[li]), li);
-          a.elem = c->at<int32_t>(c->ld[li].src_elem);
-          a.lam_rec = W + (t.op == OP_MOM_A ? L.lam_recA[li] : L.lam_recB[li]);
-          a.lam_rec_prev = t.op == OP_MOM_B ? W + L.lam_recA[li] : nullptr;
-          a.nsrc = c->ld[li].nsrc;
-          a.omega = H.omega;
-          aops->moments(c->Q, a, st);
-        } else if (t.op == OP_GFC_A || t.op == OP_GFC_B) {
-          if (H.nC == 0) continue;
-          const int lc = li - 1;
-          const void* rec = records(lc, t.snap_a, t.op == OP_GFC_B ? t.snap_b : -1);
-          AdjGfcArgs a{};
-          a.c = common(nullptr, lam_for(t.parity[li]), nullptr, lc, li);
-          a.rec = rec;
-          a.gsrc = c->at<int32_t>(c->ld[li].gfc_src);
-          a.oct = c->at<uint8_t>(c->ld[li].gfc_oct);
-          a.contrib = W + L.contrib;
-          a.ng = H.nC;
-          a.dest0 = H.base + H.oC;
-          a.omega_c = c->M.lv[lc].omega;
-          a.omega_f = H.omega;
-          aops->gfc(c->Q, a, st);
-          AdjGatherArgs g{W + L.contrib, reinterpret_cast<const int32_t*>(W + L.csr_off[lc]),
-                          reinterpret_cast<const int32_t*>(W + L.csr_item[lc]),
-                          W + (t.op == OP_GFC_A ? L.lam_recA[lc] : L.lam_recB[lc]), c->ld[lc].nsrc,
-                          mom_stride(c->Q)};
-          launch_adj_gather(fp64, g, st);
-        } else if (t.op == OP_GFF) {
-          if (H.nG1 + H.nG2 == 0) continue;
-          AdjGffArgs a{};
-          a.c = common(snap(t.snap), lam_for(t.parity[li]), lam_for(t.parity[li + 1]), li, li + 1);
-          a.child0 = c->at<int32_t>(c->ld[li].gff_child0);
-          a.ng = H.nG1 + H.nG2;
-          a.n_inner = H.nG1;
-          a.dest0 = H.base + H.oG1;
-          a.dest_outer = H.base + H.oG2;
-          a.omega_c = H.omega;
-          a.omega_f = c->M.lv[li + 1].omega;
-          aops->gff(c->Q, a, st);
+        }
+      } else if (t.op == OP_MOM_A || t.op == OP_MOM_B) {
+        if (c->ld[li].nsrc == 0) continue;
+        AdjMomArgs a{};
+        a.c = common(snap(t.snap), nullptr, lam_for(t.parity[li]), li);
+        a.elem = c->at<int32_t>(c->ld[li].src_elem);
+        a.lam_rec = W + (t.op == OP_MOM_A ? L.lam_recA[li] : L.lam_recB[li]);
+        a.lam_rec_prev = t.op == OP_MOM_B ? W + L.lam_recA[li] : nullptr;
+        a.nsrc = c->ld[li].nsrc;
+        a.omega = H.omega;
+        aops->moments(c->Q, a, st);
+      } else if (t.op == OP_GFC_A || t.op == OP_GFC_B) {
+        if (H.nC == 0) continue;
+        const int lc = li - 1;
+        const void* rec = records(lc, t.snap_a, t.op == OP_GFC_B ? t.snap_b : -1);
+        AdjGfcArgs a{};
+        a.c = common(nullptr, lam_for(t.parity[li]), nullptr, lc, li);
+        a.rec = rec;
+        a.gsrc = c->at<int32_t>(c->ld[li].gfc_src);
+        a.oct = c->at<uint8_t>(c->ld[li].gfc_oct);
+        a.contrib = W + L.contrib;
+        a.ng = H.nC;
+        a.dest0 = H.base + H.oC;
+        a.omega_c = c->M.lv[lc].omega;
+        a.omega_f = H.omega;
+        aops->gfc(c->Q, a, st);
+        AdjGatherArgs g{W + L.contrib, reinterpret_cast<const int32_t*>(W + L.csr_off[lc]),
+                        reinterpret_cast<const int32_t*>(W + L.csr_item[lc]),
+                        W + (t.op == OP_GFC_A ? L.lam_recA[lc] : L.lam_recB[lc]), c->ld[lc].nsrc,
+                        mom_stride(c->Q)};
+        launch_adj_gather(fp64, g, st);
+      } else if (t.op == OP_GFF) {
+        if (H.nG1 + H.nG2 == 0) continue;
+        AdjGffArgs a{};
+        a.c = common(snap(t.snap), lam_for(t.parity[li]), lam_for(t.parity[li + 1]), li, li + 1);
+        a.child0 = c->at<int32_t>(c->ld[li].gff_child0);
+        a.ng = H.nG1 + H.nG2;
+        a.n_inner = H.nG1;
+        a.dest0 = H.base + H.oG1;
+        a.dest_outer = H.base + H.oG2;
+        a.omega_c = H.omega;
+        a.omega_f = c->M.lv[li + 1].omega;
+        aops->gff(c->Q, a, st);
+      }
+    }
+    return c->launched("adjoint sweep");
+  };
+  for (int seg = nseg - 1; seg >= 0 && s == LBM_OK; --seg) {
+    const int64_t s0 = (int64_t)seg * K, s1 = std::min<int64_t>(s0 + K, n);
+    restore_state(W + L.ck + (size_t)seg * L.state_bytes, parity_at[s0]);
+    if (L.tape_all) {
+      // record every step of the segment in one recompute; what a step's
+      // reverse would read in place is copied before the next step overwrites
+      // it (both buffers of a level can hold such a state)
+      std::vector<Recorder> recs;
+      recs.reserve((size_t)(s1 - s0));
+      for (int64_t t = s0; t < s1 && s == LBM_OK; ++t) {
+        recs.emplace_back(c);
+        Recorder& r = recs.back();
+        s = record_step(r, W + L.snaps + (size_t)(t - s0) * L.n_snaps * L.state_bytes);
+        if (s != LBM_OK || t + 1 == s1) continue;
+        char* ends = W + L.ends + (size_t)(t - s0) * 2 * L.state_bytes;
+        for (size_t id = 0; id < r.snap_key.size(); ++id) {
+          if (r.need_copy[id]) continue;
+          const int li = r.snap_key[id].first;
+          const int buf = r.snap_buf[id];
+          char* dst = ends + (size_t)buf * L.state_bytes;
+          copy_level(c, buf ? c->at(c->oB) : c->at(c->oA), dst, li);
+          r.where[id] = dst;
         }
       }
-      s = c->launched("adjoint sweep");
+      for (int64_t t = s1 - 1; t >= s0 && s == LBM_OK; --t) s = reverse_step(recs[t - s0]);
+    } else {
+      // recompute the segment keeping each step's start state; the last step's
+      // is the live state, which its tape pass starts from directly
+      for (int64_t t = s0; t + 1 < s1; ++t) {
+        save_state(W + L.steps + (size_t)(t - s0) * L.state_bytes);
+        c->advance(0);
+      }
+      for (int64_t t = s1 - 1; t >= s0 && s == LBM_OK; --t) {
+        if (t + 1 < s1) restore_state(W + L.steps + (size_t)(t - s0) * L.state_bytes, parity_at[t]);
+        Recorder r(c);
+        s = record_step(r, W + L.snaps);
+        if (s == LBM_OK) s = reverse_step(r);
+      }
     }
   }
   if (s != LBM_OK) return s;

@@ -368,6 +368,11 @@ lbm_status lbm_build_mesh(const int64_t* tree_ids, const int8_t* levels, int64_t
     *out = c;
     return LBM_ERR_ARG;
   }
+  if (params->adjoint_tape < 0 || params->adjoint_tape > 2) {
+    c->err = "adjoint_tape must be 0, 1 or 2";
+    *out = c;
+    return LBM_ERR_ARG;
+  }
   lbm_status s;
   try {
     s = build_host_mesh(tree_ids, levels, n, c->p, &c->M, &c->err);
@@ -579,6 +584,8 @@ lbm_status lbm_set_force(lbm_ctx* c, const double* F) {
   return s;
 }
 
+static lbm_status step_run(lbm_ctx* c, int64_t n_coarse);
+
 // the FP64 reductions of the current state into out[8] (host), synchronising
 static lbm_status reduce_to_host(lbm_ctx* c, double out[8]) {
   // the per-level arguments come from the one plan builder (also used by
@@ -628,6 +635,8 @@ static lbm_status check_mass(lbm_ctx* c, bool reference) {
 }
 
 // n_coarse coarse steps with no check in between
+lbm_status lbm_ctx::run_steps(int64_t n_coarse) { return step_run(this, n_coarse); }
+
 static lbm_status step_run(lbm_ctx* c, int64_t n_coarse) {
   int64_t k = 0;
   // pairs of coarse steps replay a captured graph; a single step, timed

@@ -175,5 +175,7 @@ struct lbm_ctx {
   // graph of two coarse steps from the current parity state, captured on
   // first use; null when capture is unavailable (the caller steps eagerly)
   const StepGraph* step_graph();
+  // n coarse steps as lbm_step issues them (graph replay for pairs of steps)
+  lbm_status run_steps(int64_t n_coarse);
 };
 

@@ -40,7 +40,8 @@ class lbm_params(C.Structure):
                 ("extent", C.c_int32 * 3), ("bc", C.c_int32 * 6), ("omega_coarse", C.c_double),
                 ("rho0", C.c_double), ("u_in", C.c_double * 3), ("use_force", C.c_int32),
                 ("outlet", C.c_int32), ("inlet_profile", C.c_int32), ("bouzidi", C.c_int32),
-                ("n_levels", C.c_int32), ("check_every", C.c_int32), ("mass_band", C.c_double)]
+                ("n_levels", C.c_int32), ("check_every", C.c_int32), ("mass_band", C.c_double),
+                ("adjoint_tape", C.c_int32)]
 
 
 _lib = None
@@ -169,7 +170,8 @@ class Sim:
 
     def __init__(self, mesh, stencil, omega_c, precision=FP64, time_mode=TIME_LINEAR, rho0=1.0,
                  u_in=(0.0, 0.0, 0.0), use_force=False, device="cuda", stream=None, outlet=OUTLET_LINEAR,
-                 inlet_profile=INLET_UNIFORM, bouzidi=False, n_levels=0, check_every=0, mass_band=0.0):
+                 inlet_profile=INLET_UNIFORM, bouzidi=False, n_levels=0, check_every=0, mass_band=0.0,
+                 adjoint_tape=0):
         self.d = 2 if stencil == 9 else 3
         self.Q = stencil
         self.ns = 3 if self.d == 2 else 6
@@ -188,6 +190,7 @@ class Sim:
         p.inlet_profile = int(inlet_profile)
         p.bouzidi = int(bool(bouzidi))
         p.n_levels, p.check_every, p.mass_band = int(n_levels), int(check_every), float(mass_band)
+        p.adjoint_tape = int(adjoint_tape)
         self.params = p
         self.ctx = lbm_build_mesh(mesh.tree_ids, mesh.levels, p)
         self.ws = None

@@ -128,6 +128,8 @@ def test_bad_arguments(lbm):
         lbm.Sim(mesh, 9, 1.6, device=None, check_every=10, mass_band=-1e-3)
     with pytest.raises(lbm.LBMError, match="mass_band"):
         lbm.Sim(mesh, 9, 1.6, device=None, check_every=10, mass_band=float("nan"))
+    with pytest.raises(lbm.LBMError, match="adjoint_tape"):
+        lbm.Sim(mesh, 9, 1.6, device=None, adjoint_tape=3)
 
 
 @pytest.mark.parametrize("mode", [0, 1])

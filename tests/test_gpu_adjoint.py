@@ -89,8 +89,9 @@ def J_of(red, objective):
     return red[7] if objective == 0 else red[3 + objective]
 
 
+@pytest.mark.parametrize("tape", [1, 2])
 @pytest.mark.parametrize("name,mode,objective", CASES)
-def test_adjoint_matches_dual_oracle(lbm, oracle_mod, name, mode, objective):
+def test_adjoint_matches_dual_oracle(lbm, oracle_mod, name, mode, objective, tape):
     m, Q, om, uin, fields, n, K = make(name)
     d = 2 if Q == 9 else 3
     rho, u, S = fields(m)
@@ -98,7 +99,7 @@ def test_adjoint_matches_dual_oracle(lbm, oracle_mod, name, mode, objective):
     out = OUTLET.get(name, 0)
     bz = name in BOUZIDI
     g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True, outlet=out, bouzidi=bz,
-                inlet_profile=1 if bz else 0)
+                inlet_profile=1 if bz else 0, adjoint_tape=tape)
     links = configure(name, m, Q, g)
     g.init(rho, u, S, W.pdf_perturbation(m, Q, 1e-5))
     g.set_force(F)
@@ -189,6 +190,28 @@ def test_adjoint_reduced_precision(lbm, prec, tol, name, mode, objective):
         # the drag of the small sphere after a few steps does not depend on u_in yet
         err["dU"] = float(np.linalg.norm(dU1 - dU0) / max(np.linalg.norm(dU0), 1e-12 * abs(J0)))
     assert all(v <= tol for v in err.values()), err
+
+
+@pytest.mark.parametrize("name,mode,objective,K", [("sphere", 0, 1, 2), ("tgv3d", 1, 0, 3), ("channel_zg", 0, 0, 4)])
+def test_adjoint_tape_schemes_agree_bitwise(lbm, name, mode, objective, K):
+    """Recording every step of a segment in one recompute (adjoint_tape 1) and
+    recomputing each step once more to record it (2) feed the same reverse
+    kernels the same states in the same order: bit-identical gradients, with
+    K not dividing n."""
+    m, Q, om, uin, fields, n, _ = make(name)
+    rho, u, S = fields(m)
+    F = W.gaussian_force(m, 1e-5)
+    out = []
+    for tape in (1, 2):
+        g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin, use_force=True, outlet=OUTLET.get(name, 0),
+                    adjoint_tape=tape)
+        g.init(rho, u, S, W.pdf_perturbation(m, Q, 1e-5))
+        g.set_force(F)
+        out.append(g.adjoint(n + 1, K, objective, want_f0=True) + (g.get_state(),))
+    (J1, dF1, dw1, dU1, f1, s1), (J2, dF2, dw2, dU2, f2, s2) = out
+    assert J1 == J2 and dw1 == dw2
+    assert np.array_equal(dF1, dF2) and np.array_equal(dU1, dU2) and np.array_equal(f1, f2)
+    assert np.array_equal(s1, s2)
 
 
 def test_adjoint_leaves_final_state_and_is_deterministic(lbm):
