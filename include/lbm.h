@@ -207,8 +207,11 @@ lbm_status lbm_set_force(lbm_ctx* ctx, const double* F);
  * two substeps of the next finer level).  Pairs of coarse steps replay a CUDA
  * graph captured on first use (one per A/B parity state; dropped by
  * lbm_set_params and lbm_bind) on the bound stream; a remaining single step,
- * and all steps while timing is enabled, are launched kernel by kernel.  Both
- * paths issue the same kernels in the same order.  With params.check_every = M
+ * and all steps in timing mode 1, are launched kernel by kernel.  Both paths
+ * issue the same kernels; in the graphs the three stream-collide kernels of a
+ * level (interior bricks, boundary bricks, neighbour list: disjoint elements,
+ * the same source state) run as parallel branches, joined before the next op,
+ * which leaves every result bitwise the same.  With params.check_every = M
  * the mass is checked after every M-th coarse step (see lbm_params); a failed
  * check returns LBM_ERR_NUMERIC right after that step, with the state left as
  * it was then (the context stays usable, e.g. for lbm_set_state). */
@@ -351,8 +354,11 @@ lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
  *          launched kernel by kernel, not replayed from graphs.
  *  mode 2: lbm_step keeps replaying its captured two-step graphs, which then
  *          also record events around the finest level's stream-collide
- *          launches (kinds 0-2); lbm_timing_read returns those of the most
- *          recent replay (its two coarse steps), if not read before.
+ *          launches (kinds 0-2) and around their whole group (kind 7: in the
+ *          graphs a level's three stream-collide kernels run as parallel
+ *          branches, so their span is the level's stream-collide time);
+ *          lbm_timing_read returns those of the most recent replay (its two
+ *          coarse steps), if not read before.
  * Changing between mode 2 and the others drops the captured graphs.
  * lbm_timing_read synchronises the stream and returns, in row 8 L + k for level
  * index L (coarsest 0) and kernel kind k, the number of timed launches and
@@ -361,8 +367,8 @@ lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
  * bricks, 1 stream-collide through the neighbour list, 2 stream-collide of the
  * boundary bricks, 3 GhostFromFiner (L: the coarse level holding the ghosts),
  * 4 source moments (L: the coarse level), 5 GhostFromCoarser (L: the fine
- * level holding the ghosts), 6 outlet values, 7 unused.  Other modes:
- * LBM_ERR_ARG. */
+ * level holding the ghosts), 6 outlet values, 7 the span of a level's
+ * stream-collide kernels (mode 2 only).  Other modes: LBM_ERR_ARG. */
 lbm_status lbm_timing_enable(lbm_ctx* ctx, int32_t mode);
 lbm_status lbm_timing_read(lbm_ctx* ctx, int64_t* launches, double* ms, int32_t cap);
 

@@ -100,8 +100,9 @@ void lbm_ctx::fill_gff(int li) {
   ++launches;
 }
 
-void lbm_ctx::source_moments(int li, size_t mom_off, size_t prev_off) {
+void lbm_ctx::source_moments(int li, size_t mom_off, size_t prev_off, cudaStream_t s) {
   if (ld[li].nsrc == 0) return;
+  if (!s) s = st;
   MomentsArgs a{};
   a.src = cur(li);
   a.force = force_ptr();
@@ -112,13 +113,14 @@ void lbm_ctx::source_moments(int li, size_t mom_off, size_t prev_off) {
   a.nsrc = ld[li].nsrc;
   a.omega = M.lv[li].omega;
   a.rho_off = rho_off;
-  timed_launch(li, TK_MOM, [&] { ops->source_moments(Q, a, st); });
+  timed_launch(li, TK_MOM, [&] { ops->source_moments(Q, a, s); }, s);
   ++launches;
 }
 
-void lbm_ctx::fill_gfc(int lf, bool two_times, bool all_layers) {
+void lbm_ctx::fill_gfc(int lf, bool two_times, bool all_layers, cudaStream_t s) {
   const HostLevel& H = M.lv[lf];
   if (H.nC == 0) return;
+  if (!s) s = st;
   const int lc = lf - 1;
   GfcArgs a{};
   a.mom = two_times ? at(ld[lc].momB) : at(ld[lc].momA);
@@ -133,11 +135,12 @@ void lbm_ctx::fill_gfc(int lf, bool two_times, bool all_layers) {
   a.omega_f = H.omega;
   a.rho_off = rho_off;
   a.skip_outer = !all_layers && p.time_mode == LBM_TIME_LINEAR;
-  timed_launch(lf, TK_GFC, [&] { ops->fill_gfc(Q, a, st); });
+  timed_launch(lf, TK_GFC, [&] { ops->fill_gfc(Q, a, s); }, s);
   ++launches;
 }
 
-void lbm_ctx::stream_collide(int li) {
+void lbm_ctx::stream_collide(int li, cudaStream_t s0) {
+  if (!s0) s0 = st;
   const HostLevel& H = M.lv[li];
   if (H.out_end > H.out_begin) {
     OutletArgs o{};
@@ -157,7 +160,7 @@ void lbm_ctx::stream_collide(int li) {
     o.rho0 = p.rho0;
     o.zero_gradient = p.outlet == LBM_OUTLET_ZERO_GRADIENT;
     o.q = at<double>(oOutQ);
-    timed_launch(li, TK_OUTLET, [&] { ops->outlet(Q, o, st); });
+    timed_launch(li, TK_OUTLET, [&] { ops->outlet(Q, o, s0); }, s0);
     ++launches;
   }
   // interior bricks, then boundary bricks (the first 64 (nB + nBb) fluid
@@ -208,16 +211,37 @@ void lbm_ctx::stream_collide(int li) {
   a.rho_off = rho_off;
   std::memcpy(a.inlet, inlet, sizeof(inlet));
   const bool use_force = p.use_force != 0;
-  auto launch = [&](int kernel) {
-    if (kernel == TK_INTERIOR) ops->stream_collide_brick(Q, use_force, false, b, st);
-    else if (kernel == TK_BOUNDARY) ops->stream_collide_brick(Q, use_force, true, bb, st);
-    else ops->stream_collide(Q, use_force, a, st);
+  auto launch = [&](int kernel, cudaStream_t s) {
+    if (kernel == TK_INTERIOR) ops->stream_collide_brick(Q, use_force, false, b, s);
+    else if (kernel == TK_BOUNDARY) ops->stream_collide_brick(Q, use_force, true, bb, s);
+    else ops->stream_collide(Q, use_force, a, s);
     ++launches;
   };
-  for (int kernel : {TK_INTERIOR, TK_BOUNDARY, TK_LIST}) {
-    if (kernel == TK_INTERIOR ? b.nB == 0 : kernel == TK_BOUNDARY ? bb.nB == 0 : a.end <= a.begin) continue;
-    timed_launch(li, kernel, [&] { launch(kernel); });
-  }
+  const bool has[3] = {b.nB > 0, a.end > a.begin, bb.nB > 0};  // by TimedKind 0..2
+  // inside a graph capture the kernels run as parallel branches (boundary
+  // bricks and neighbour list on the level's two side streams), joined before
+  // the next op; launched kernel by kernel they run one after the other
+  const bool fork = capturing && concurrent_sc && timing != 1 && !lvs.empty() && (has[TK_BOUNDARY] || has[TK_LIST]);
+  auto group = [&] {
+    if (fork) {
+      cudaEventRecord(lvs[li].fork, s0);
+      cudaStreamWaitEvent(lvs[li].side[0], lvs[li].fork, 0);
+      cudaStreamWaitEvent(lvs[li].side[1], lvs[li].fork, 0);
+    }
+    for (int kernel : {TK_INTERIOR, TK_BOUNDARY, TK_LIST}) {
+      if (!has[kernel]) continue;
+      cudaStream_t s = !fork || kernel == TK_INTERIOR ? s0 : lvs[li].side[kernel == TK_BOUNDARY ? 0 : 1];
+      timed_launch(li, kernel, [&] { launch(kernel, s); }, s);
+    }
+    if (fork) {
+      for (int k = 0; k < 2; ++k) {
+        cudaEventRecord(lvs[li].join[k], lvs[li].side[k]);
+        cudaStreamWaitEvent(s0, lvs[li].join[k], 0);
+      }
+    }
+  };
+  // the whole level's stream-collide (fork to join) as one timed span
+  timed_launch(li, TK_SC_SPAN, group, s0);
   parity[li] ^= 1;
 }
 
@@ -227,15 +251,37 @@ void lbm_ctx::advance(int li) {
     if (hook) hook(kind, level);
     return !dry;
   };
+  // In a graph capture the level's stream-collide becomes a branch of its
+  // own, forked after the GhostFromFiner fill (the last op it needs) and joined
+  // before the first op that reads its result (the source moments at t+1, or
+  // the finer level's second substep); meanwhile the source moments at t, the
+  // finer level's GhostFromCoarser fill and its first substep run on the main
+  // branch (they read this level's current buffer or other levels only).
+  // Measured: the ghost ops of the second substep kept off the branch (beside
+  // the finest level's stream-collide they slowed it by a quarter).
+  const bool branch = has_finer && capturing && concurrent_sc && timing != 1 && !lvs.empty() && !dry;
   if (has_finer) {
     if (op(OP_GFF, li)) fill_gff(li);
+    if (branch) cudaEventRecord(lvs[li].fork_sc, st);
     if (op(OP_MOM_A, li)) source_moments(li, ld[li].momA);
     if (op(OP_GFC_A, li + 1)) fill_gfc(li + 1, false);
   }
-  if (op(OP_SC, li)) stream_collide(li);
-  else parity[li] ^= 1;
+  if (op(OP_SC, li)) {
+    if (branch) {
+      cudaStreamWaitEvent(lvs[li].sc, lvs[li].fork_sc, 0);
+      stream_collide(li, lvs[li].sc);
+    } else {
+      stream_collide(li);
+    }
+  } else {
+    parity[li] ^= 1;
+  }
   if (has_finer) {
     advance(li + 1);
+    if (branch) {
+      cudaEventRecord(lvs[li].done_sc, lvs[li].sc);
+      cudaStreamWaitEvent(st, lvs[li].done_sc, 0);
+    }
     if (p.time_mode == LBM_TIME_LINEAR) {
       // source moments at t+1/2: mean of those at t (momA) and at t+1
       if (op(OP_MOM_B, li)) source_moments(li, ld[li].momB, ld[li].momA);
@@ -243,6 +289,21 @@ void lbm_ctx::advance(int li) {
     }
     advance(li + 1);
   }
+}
+
+bool lbm_ctx::make_level_streams() {
+  if (!lvs.empty()) return true;
+  std::vector<LevelStreams> v(nlev);
+  bool ok = true;
+  for (auto& L : v) {
+    for (cudaStream_t* s : {&L.sc, &L.side[0], &L.side[1]})
+      ok = ok && cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t* e : {&L.fork_sc, &L.done_sc, &L.fork, &L.join[0], &L.join[1]})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+  }
+  lvs.swap(v);  // created handles are released by the destructor either way
+  if (!ok) cudaGetLastError();
+  return ok;
 }
 
 const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
@@ -253,15 +314,17 @@ const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
     graphs_on = false;
     return nullptr;
   }
+  // no branch streams: the captured steps stay sequential
+  if (concurrent_sc && !make_level_streams()) concurrent_sc = false;
   // capture on a private stream (the bound stream may be the legacy default
   // stream, which cannot be captured); host bookkeeping is restored afterwards
   const std::vector<int> p0 = parity;
   const int64_t l0 = launches;
   if (timing == 2) {
-    // events for the finest level's stream-collide launches (up to three per
-    // substep, 2^(nlev-1) substeps per coarse step, two coarse steps), made
-    // before the capture begins
-    for (int k = 0; k < 2 * 3 * 2 * (1 << (nlev - 1)); ++k) event_pool.push_back(get_event());
+    // events for the finest level's stream-collide launches and their span
+    // (up to four pairs per substep, 2^(nlev-1) substeps per coarse step, two
+    // coarse steps), made before the capture begins
+    for (int k = 0; k < 2 * 4 * 2 * (1 << (nlev - 1)); ++k) event_pool.push_back(get_event());
   }
   const size_t t0 = timed.size();
   cudaStream_t user = st;

@@ -14,7 +14,8 @@ namespace lbm {
 // Ops of the recursive level step, in the order lbm_ctx::advance issues them.
 enum StepOp { OP_GFF = 0, OP_MOM_A = 1, OP_GFC_A = 2, OP_SC = 3, OP_MOM_B = 4, OP_GFC_B = 5 };
 // Kernel kinds of the per-launch timing (lbm_timing_read row kTimedKinds * L + kind)
-enum TimedKind { TK_INTERIOR = 0, TK_LIST = 1, TK_BOUNDARY = 2, TK_GFF = 3, TK_MOM = 4, TK_GFC = 5, TK_OUTLET = 6 };
+enum TimedKind { TK_INTERIOR = 0, TK_LIST = 1, TK_BOUNDARY = 2, TK_GFF = 3, TK_MOM = 4, TK_GFC = 5, TK_OUTLET = 6,
+                 TK_SC_SPAN = 7 };
 constexpr int kTimedKinds = 8;
 
 struct LevelDev {
@@ -81,22 +82,24 @@ struct lbm_ctx {
     cudaEventCreate(&e);
     return e;
   }
-  // runs launch(), bracketed by events on the bound stream when the timing
-  // mode asks for this launch
+  // runs launch(), bracketed by events on stream s (default: the bound
+  // stream) when the timing mode asks for this launch
   template <class F>
-  void timed_launch(int li, int kind, F&& launch) {
-    const bool rec = timing == 1 || (timing == 2 && capturing && li == nlev - 1 && kind <= lbm::TK_BOUNDARY);
+  void timed_launch(int li, int kind, F&& launch, cudaStream_t s = nullptr) {
+    const bool finest_sc = li == nlev - 1 && (kind <= lbm::TK_BOUNDARY || kind == lbm::TK_SC_SPAN);
+    const bool rec = (timing == 1 && kind != lbm::TK_SC_SPAN) || (timing == 2 && capturing && finest_sc);
     if (!rec) {
       launch();
       return;
     }
+    if (!s) s = st;
     Timed t{li, kind, get_event(), get_event()};
     // inside a capture, only an external record becomes an event-record node
     // of the graph (a plain record would just order the captured work)
     const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    cudaEventRecordWithFlags(t.a, st, flags);
+    cudaEventRecordWithFlags(t.a, s, flags);
     launch();
-    cudaEventRecordWithFlags(t.b, st, flags);
+    cudaEventRecordWithFlags(t.b, s, flags);
     timed.push_back(t);
   }
   void recycle_timed() {
@@ -117,6 +120,21 @@ struct lbm_ctx {
   };
   std::vector<StepGraph> graphs;
   cudaStream_t cap_stream = nullptr;
+  // branch streams and fork/join events of the captured graphs, per level:
+  // the level's stream-collide runs on branch `sc` (forked after its
+  // GhostFromFiner, joined before the ops that read its result), and its three
+  // kernels (disjoint elements, same source buffer) on `sc` and the two `side`
+  // streams
+  struct LevelStreams {
+    cudaStream_t sc = nullptr, side[2] = {nullptr, nullptr};
+    cudaEvent_t fork_sc = nullptr, done_sc = nullptr, fork = nullptr, join[2] = {nullptr, nullptr};
+  };
+  std::vector<LevelStreams> lvs;
+  bool make_level_streams();
+#ifndef LBM_CONCURRENT_SC
+#define LBM_CONCURRENT_SC 1
+#endif
+  bool concurrent_sc = LBM_CONCURRENT_SC != 0;
   bool graphs_on = true;
   int last_graph = -1;        // graph of the most recent replay
   bool graph_unread = false;  // its events hold a replay not yet read
@@ -137,6 +155,12 @@ struct lbm_ctx {
     recycle_timed();
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (auto& L : lvs) {
+      for (cudaStream_t s : {L.sc, L.side[0], L.side[1]})
+        if (s) cudaStreamDestroy(s);
+      for (cudaEvent_t e : {L.fork_sc, L.done_sc, L.fork, L.join[0], L.join[1]})
+        if (e) cudaEventDestroy(e);
+    }
   }
 
   template <class T = void>
@@ -166,11 +190,12 @@ struct lbm_ctx {
   void layout();
   // driver pieces
   void fill_gff(int li);
-  void source_moments(int li, size_t mom_off, size_t prev_off = 0);
+  void source_moments(int li, size_t mom_off, size_t prev_off = 0, cudaStream_t s = nullptr);
   // all_layers false: in LINEAR mode the outer ghost layer, which no
   // stream-collide reads, is left unwritten
-  void fill_gfc(int li_fine, bool two_times, bool all_layers = false);
-  void stream_collide(int li);
+  void fill_gfc(int li_fine, bool two_times, bool all_layers = false, cudaStream_t s = nullptr);
+  // launches on stream s (default: the bound stream)
+  void stream_collide(int li, cudaStream_t s = nullptr);
   void advance(int li);
   // graph of two coarse steps from the current parity state, captured on
   // first use; null when capture is unavailable (the caller steps eagerly)

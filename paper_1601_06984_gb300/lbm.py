@@ -270,7 +270,7 @@ class Sim:
         stream-collide launches (read back: the most recent replay)."""
         _check(self.ctx, lib().lbm_timing_enable(self.ctx, int(mode)))
 
-    TIMED_KINDS = ("interior", "list", "boundary", "gff", "moments", "gfc", "outlet", "unused")
+    TIMED_KINDS = ("interior", "list", "boundary", "gff", "moments", "gfc", "outlet", "sc_span")
 
     def timing_read(self):
         """Launches and summed device ms since enabled, arrays [level, kind]
