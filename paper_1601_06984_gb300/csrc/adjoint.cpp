@@ -268,6 +268,7 @@ lbm_status lbm_set_params(lbm_ctx* c, double omega_coarse, const double* u_in) {
   for (int li = 0; li < c->nlev; ++li)
     if (std::fabs(1.0 - om[li]) < 1e-3) return c->fail(LBM_ERR_ARG, "omega too close to 1 on some level");
   c->drop_graphs();  // captured steps carry the old omega and inlet values
+  c->recs_valid = false;  // the source records depend on omega
   for (int li = 0; li < c->nlev; ++li) c->M.lv[li].omega = om[li];
   c->p.omega_coarse = omega_coarse;
   if (u_in) {
@@ -333,6 +334,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
       c->parity[li] = par[li];
       copy_level(c, src, c->cur(li), li);
     }
+    c->recs_valid = false;
   };
   // ---- forward with checkpoints: the parities of every step from a dry walk,
   // then each segment through lbm_step's path (graph replay of step pairs)
@@ -419,6 +421,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
     r.snap_base = snap_base;
     r.state_bytes = L.state_bytes;
     r.max_snaps = L.n_snaps;
+    c->ensure_records();  // before the hook: the tape holds the step's own ops only
     c->hook = [&](int op, int li) { r.on(op, li); };
     c->advance(0);
     c->hook = nullptr;
@@ -601,7 +604,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
       // is the live state, which its tape pass starts from directly
       for (int64_t t = s0; t + 1 < s1; ++t) {
         save_state(W + L.steps + (size_t)(t - s0) * L.state_bytes);
-        c->advance(0);
+        c->coarse_step();
       }
       for (int64_t t = s1 - 1; t >= s0 && s == LBM_OK; --t) {
         if (t + 1 < s1) restore_state(W + L.steps + (size_t)(t - s0) * L.state_bytes, parity_at[t]);

@@ -56,8 +56,12 @@ void lbm_ctx::layout() {
     L.gfc_oct = take(H.gfc_oct.size());
     L.src_elem = take(H.src_elem.size() * 4);
     L.nsrc = (int64_t)H.src_elem.size();
-    L.momA = take(M_ * L.nsrc * cb);
-    L.momB = take(M_ * L.nsrc * cb);
+    L.gsrc_elem = take(H.gsrc_elem.size() * 4);
+    L.gsrc_rec = take(H.gsrc_rec.size() * 4);
+    L.n_gsrc = (int64_t)H.gsrc_elem.size();
+    L.n_gsrc_inner = H.n_gsrc_inner;
+    L.momA[0] = take(M_ * L.nsrc * cb);
+    L.momA[1] = take(M_ * L.nsrc * cb);
   }
   const size_t nout = m.out_elem.size(), nobs = m.obs_elem.size();
   oOutElem = take(nout * 4);
@@ -71,6 +75,8 @@ void lbm_ctx::layout() {
   oUslot = take((size_t)m.n_user * 4);
   oUlev = take((size_t)m.n_user);
   oSlotUser = take((size_t)N * 4);
+  oSrcMask = take(m.src_mask.size() * 4);
+  oSrcFirst = take(m.src_first.size() * 4);
   chunk = std::min<int64_t>(m.n_user, (int64_t)1 << 20);
   oStage = take((size_t)chunk * (1 + d + nS + Q + Q) * 8);
   oPartial = take((size_t)nlev * kReduceBlocks * 8 * 8);
@@ -100,36 +106,47 @@ void lbm_ctx::fill_gff(int li) {
   ++launches;
 }
 
-void lbm_ctx::source_moments(int li, size_t mom_off, size_t prev_off, cudaStream_t s) {
-  if (ld[li].nsrc == 0) return;
+void lbm_ctx::source_moments(int li, size_t mom_off, size_t prev_off, cudaStream_t s, int subset) {
+  const LevelDev& L = ld[li];
+  const int64_t n = subset == SRC_ALL ? L.nsrc : subset == SRC_GFF ? L.n_gsrc : L.n_gsrc - L.n_gsrc_inner;
+  if (n == 0) return;
   if (!s) s = st;
   MomentsArgs a{};
   a.src = cur(li);
   a.force = force_ptr();
-  a.elem = at<int32_t>(ld[li].src_elem);
+  if (subset == SRC_ALL) {
+    a.elem = at<int32_t>(L.src_elem);
+  } else {
+    const int64_t skip = subset == SRC_GFF ? 0 : L.n_gsrc_inner;
+    a.elem = at<int32_t>(L.gsrc_elem) + skip;
+    a.rec = at<int32_t>(L.gsrc_rec) + skip;
+  }
   a.mom = at(mom_off);
   a.prev = prev_off ? at(prev_off) : nullptr;
   a.Ntot = M.Ntot;
-  a.nsrc = ld[li].nsrc;
+  a.nsrc = n;
   a.omega = M.lv[li].omega;
   a.rho_off = rho_off;
   timed_launch(li, TK_MOM, [&] { ops->source_moments(Q, a, s); }, s);
   ++launches;
 }
 
-void lbm_ctx::fill_gfc(int lf, bool two_times, bool all_layers, cudaStream_t s) {
+void lbm_ctx::fill_gfc(int lf, bool two_times, bool all_layers, cudaStream_t s, bool next_buffer) {
   const HostLevel& H = M.lv[lf];
   if (H.nC == 0) return;
   if (!s) s = st;
   const int lc = lf - 1;
   GfcArgs a{};
-  a.mom = two_times ? at(ld[lc].momB) : at(ld[lc].momA);
+  // at t + 1/2 (after the coarse stream-collide): the means of the records
+  // at t and t + 1, which the two buffers hold
+  a.mom = at(ld[lc].momA[parity[lc] ^ (two_times ? 1 : 0)]);
+  a.mom2 = two_times ? at(ld[lc].momA[parity[lc]]) : nullptr;
   a.nsrc = ld[lc].nsrc;
   a.gsrc = at<int32_t>(ld[lf].gfc_src);
   a.oct = at<uint8_t>(ld[lf].gfc_oct);
   a.ng = H.nC;
   a.dest0 = H.base + H.oC;
-  a.dst = cur(lf);
+  a.dst = next_buffer ? nxt(lf) : cur(lf);
   a.Ntot = M.Ntot;
   a.omega_c = M.lv[lc].omega;
   a.omega_f = H.omega;
@@ -182,6 +199,14 @@ void lbm_ctx::stream_collide(int li, cudaStream_t s0) {
   b.side = at(oSide);
   b.inlet_s = at<double>(oInletS);
   std::memcpy(b.inlet, inlet, sizeof(inlet));
+  // the level's GFC source records at t + 1 from the new state
+  SourceOut so{};
+  if (li + 1 < nlev && ld[li].nsrc > 0) {
+    so.mask = at<uint32_t>(oSrcMask);
+    so.first = at<int32_t>(oSrcFirst);
+    so.rec_out = at(ld[li].momA[parity[li] ^ 1]);
+  }
+  b.so = so;
   BrickArgs bb = b;
   bb.nb = b.nb + (size_t)H.nB * 27;
   bb.begin = b.begin + 64 * H.nB;
@@ -210,6 +235,7 @@ void lbm_ctx::stream_collide(int li, cudaStream_t s0) {
   a.omega = H.omega;
   a.rho_off = rho_off;
   std::memcpy(a.inlet, inlet, sizeof(inlet));
+  a.so = so;
   const bool use_force = p.use_force != 0;
   auto launch = [&](int kernel, cudaStream_t s) {
     if (kernel == TK_INTERIOR) ops->stream_collide_brick(Q, use_force, false, b, s);
@@ -245,31 +271,53 @@ void lbm_ctx::stream_collide(int li, cudaStream_t s0) {
   parity[li] ^= 1;
 }
 
+void lbm_ctx::ensure_records() {
+  if (recs_valid || dry) return;
+  for (int li = 0; li + 1 < nlev; ++li) source_moments(li, ld[li].momA[parity[li]]);
+  recs_valid = true;
+}
+
 void lbm_ctx::advance(int li) {
   const bool has_finer = li + 1 < nlev;
+  const bool linear = p.time_mode == LBM_TIME_LINEAR;
   auto op = [&](int kind, int level) {
     if (hook) hook(kind, level);
     return !dry;
   };
+  // Source records (interpolation step 1), two buffers per level: momA[parity]
+  // holds those of the current state.  The stream-collide writes the records
+  // of the sources it updates into the other buffer (their state at t + 1);
+  // the GhostFromFiner sources get theirs at t after their fill, and in
+  // LINEAR mode the outer GhostFromFiner layer, which no stream-collide
+  // updates, at t + 1 from its stored state.  The fill at t + 1/2 takes the
+  // means of the two buffers.
   // In a graph capture the level's stream-collide becomes a branch of its
-  // own, forked after the GhostFromFiner fill (the last op it needs) and joined
-  // before the first op that reads its result (the source moments at t+1, or
-  // the finer level's second substep); meanwhile the source moments at t, the
-  // finer level's GhostFromCoarser fill and its first substep run on the main
-  // branch (they read this level's current buffer or other levels only).
-  // Measured: the ghost ops of the second substep kept off the branch (beside
-  // the finest level's stream-collide they slowed it by a quarter).
-  const bool branch = has_finer && capturing && concurrent_sc && timing != 1 && !lvs.empty() && !dry;
+  // own, forked after the GhostFromFiner fill (the last op it needs) and
+  // joined before the finer level's second substep; meanwhile the records at
+  // t, the finer level's GhostFromCoarser fill and its first substep run on
+  // the main branch (they read this level's current buffer, its records at t
+  // or other levels only).  With gfc_b_branch the finer level's fill at
+  // t + 1/2 follows the stream-collide on its branch (forked after the
+  // records at t), into the fine buffer that the first substep's
+  // stream-collide writes, whose ghost slots nothing touches before the
+  // second substep.
+  const bool branch = has_finer && capturing && concurrent_sc && level_branch && timing != 1 && !lvs.empty() && !dry;
+  const bool gfc_b_on_branch = branch && linear && gfc_b_branch;
   if (has_finer) {
     if (op(OP_GFF, li)) fill_gff(li);
-    if (branch) cudaEventRecord(lvs[li].fork_sc, st);
-    if (op(OP_MOM_A, li)) source_moments(li, ld[li].momA);
+    if (branch && !gfc_b_on_branch) cudaEventRecord(lvs[li].fork_sc, st);
+    if (op(OP_MOM_A, li)) source_moments(li, ld[li].momA[parity[li]], 0, nullptr, SRC_GFF);
+    if (gfc_b_on_branch) cudaEventRecord(lvs[li].fork_sc, st);
     if (op(OP_GFC_A, li + 1)) fill_gfc(li + 1, false);
   }
   if (op(OP_SC, li)) {
     if (branch) {
       cudaStreamWaitEvent(lvs[li].sc, lvs[li].fork_sc, 0);
       stream_collide(li, lvs[li].sc);
+      if (gfc_b_on_branch) {
+        source_moments(li, ld[li].momA[parity[li]], 0, lvs[li].sc, SRC_GFF_OUTER);
+        fill_gfc(li + 1, true, false, lvs[li].sc, true);
+      }
     } else {
       stream_collide(li);
     }
@@ -282,10 +330,10 @@ void lbm_ctx::advance(int li) {
       cudaEventRecord(lvs[li].done_sc, lvs[li].sc);
       cudaStreamWaitEvent(st, lvs[li].done_sc, 0);
     }
-    if (p.time_mode == LBM_TIME_LINEAR) {
-      // source moments at t+1/2: mean of those at t (momA) and at t+1
-      if (op(OP_MOM_B, li)) source_moments(li, ld[li].momB, ld[li].momA);
-      if (op(OP_GFC_B, li + 1)) fill_gfc(li + 1, true);
+    if (linear) {
+      if (op(OP_MOM_B, li) && !gfc_b_on_branch)
+        source_moments(li, ld[li].momA[parity[li]], 0, nullptr, SRC_GFF_OUTER);
+      if (op(OP_GFC_B, li + 1) && !gfc_b_on_branch) fill_gfc(li + 1, true);
     }
     advance(li + 1);
   }
@@ -546,7 +594,11 @@ lbm_status lbm_bind(lbm_ctx* c, void* ws, uint64_t bytes, void* stream) {
     if (s == LBM_OK) s = up(c->ld[li].gfc_src, H.gfc_src.data(), H.gfc_src.size() * 4);
     if (s == LBM_OK) s = up(c->ld[li].gfc_oct, H.gfc_oct.data(), H.gfc_oct.size());
     if (s == LBM_OK) s = up(c->ld[li].src_elem, H.src_elem.data(), H.src_elem.size() * 4);
+    if (s == LBM_OK) s = up(c->ld[li].gsrc_elem, H.gsrc_elem.data(), H.gsrc_elem.size() * 4);
+    if (s == LBM_OK) s = up(c->ld[li].gsrc_rec, H.gsrc_rec.data(), H.gsrc_rec.size() * 4);
   }
+  if (s == LBM_OK) s = up(c->oSrcMask, m.src_mask.data(), m.src_mask.size() * 4);
+  if (s == LBM_OK) s = up(c->oSrcFirst, m.src_first.data(), m.src_first.size() * 4);
   if (s == LBM_OK) s = up(c->oOutElem, m.out_elem.data(), m.out_elem.size() * 4);
   if (s == LBM_OK) s = up(c->oOutA, m.out_a.data(), m.out_a.size() * 4);
   if (s == LBM_OK) s = up(c->oOutB, m.out_b.data(), m.out_b.size() * 4);
@@ -642,6 +694,7 @@ lbm_status lbm_set_force(lbm_ctx* c, const double* F) {
     launch_scatter_force(c->p.precision == LBM_FP64, a, c->st);
     ++c->launches;
   }
+  c->recs_valid = false;
   lbm_status s = c->launched("set_force");
   if (s == LBM_OK) s = c->cuda_check(cudaStreamSynchronize(c->st), "force sync");
   return s;
@@ -702,6 +755,7 @@ lbm_status lbm_ctx::run_steps(int64_t n_coarse) { return step_run(this, n_coarse
 
 static lbm_status step_run(lbm_ctx* c, int64_t n_coarse) {
   int64_t k = 0;
+  if (n_coarse > 0) c->ensure_records();  // outside any capture
   // pairs of coarse steps replay a captured graph; a single step, timed
   // steps and the adjoint's recorded steps are issued one kernel at a time
   if (c->graphs_on && c->timing != 1 && !c->hook && !c->dry) {
@@ -716,7 +770,7 @@ static lbm_status step_run(lbm_ctx* c, int64_t n_coarse) {
       k += 2;
     }
   }
-  for (; k < n_coarse; ++k) c->advance(0);
+  for (; k < n_coarse; ++k) c->coarse_step();
   return c->launched("step");
 }
 
@@ -755,9 +809,10 @@ lbm_status lbm_fill_ghosts(lbm_ctx* c) {
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_fill_ghosts before lbm_bind");
   for (int li = 0; li + 1 < c->nlev; ++li) {
     c->fill_gff(li);
-    c->source_moments(li, c->ld[li].momA);
+    c->source_moments(li, c->ld[li].momA[c->parity[li]]);
     c->fill_gfc(li + 1, false, true);
   }
+  c->recs_valid = true;  // every record now holds the current state's moments
   return c->launched("fill_ghosts");
 }
 

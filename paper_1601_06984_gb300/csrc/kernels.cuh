@@ -213,6 +213,109 @@ __device__ __forceinline__ void post_moments(const R* g, R omega, R rho_off, con
   }
 }
 
+// ----------------------------------------------------------------- GFC source records
+// Record of one source (compute type, mom_stride(Q) values, 16-byte aligned
+// groups): f^neq[Q] padded to a multiple of 4, then rho - rho_off, u[D], S[nS],
+// padding.  Vector loads/stores move a record in 8 (float) or 16 (double) pieces.
+template <int Q>
+struct RecLayout {
+  static constexpr int D = Lat<Q>::D, NS = Lat<Q>::NS;
+  static constexpr int FN = 0;
+  static constexpr int RP = (Q + 3) / 4 * 4;
+  static constexpr int U = RP + 1;
+  static constexpr int SS = U + D;
+  static constexpr int END = SS + NS;
+  static constexpr int STRIDE = mom_stride(Q);
+  static_assert(END <= STRIDE && STRIDE % 4 == 0, "moment record too long");
+};
+
+__device__ __forceinline__ void ld4(const float* p, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* o) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = b.x;
+  o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Interpolation step 1 (Sec. 2.2) for one source: its record from its stored
+// (post-collision) pdfs g.
+template <int Q, class R, bool FORCE>
+__device__ __forceinline__ void source_record(const R (&g)[Q], R omega, R rho_off, const R* F,
+                                              R (&rec)[RecLayout<Q>::STRIDE]) {
+  using RL = RecLayout<Q>;
+  constexpr int D = Lat<Q>::D, NS = Lat<Q>::NS;
+#pragma unroll
+  for (int f = 0; f < RL::STRIDE; ++f) rec[f] = R(0);
+  R rp, u[3], fneq[Q], Sv[NS];
+  post_moments<Q, R, true, FORCE>(g, omega, rho_off, F, rp, u, fneq, Sv);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) rec[RL::FN + q] = fneq[q];
+  rec[RL::RP] = rp;
+#pragma unroll
+  for (int b = 0; b < D; ++b) rec[RL::U + b] = u[b];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) rec[RL::SS + s] = Sv[s];
+}
+
+// rec := (prev + rec) / 2; the whole previous record is read before the
+// caller's first store (the compiler cannot tell the records apart and would
+// otherwise serialise loads and stores)
+template <int Q, class R>
+__device__ __forceinline__ void mean_record(const R* __restrict__ prev, R (&rec)[RecLayout<Q>::STRIDE]) {
+  using RL = RecLayout<Q>;
+  R pv[RL::STRIDE];
+#pragma unroll
+  for (int f = 0; f < RL::END; f += 4) ld4(prev + f, pv + f);
+#pragma unroll
+  for (int f = 0; f < RL::END; ++f) rec[f] = R(0.5) * (pv[f] + rec[f]);
+}
+
+template <int Q, class R>
+__device__ __forceinline__ void store_record(R* __restrict__ out, const R (&rec)[RecLayout<Q>::STRIDE]) {
+#pragma unroll
+  for (int f = 0; f < RecLayout<Q>::END; f += 4) st4(out + f, rec + f);
+}
+
+// Stream-collide epilogue for a GhostFromCoarser source among the processed
+// elements: g are the element's new values before rounding to storage; the
+// record is taken from the values as stored, so it equals what
+// k_source_moments computes from the stored state.  Mask words are per 32
+// slots: one broadcast load for a warp of consecutive elements.
+template <int Q, class S, bool FORCE>
+__device__ __forceinline__ void source_out(const SourceOut& so, int64_t e, const typename Sto<S>::R (&g)[Q],
+                                           typename Sto<S>::R omega, typename Sto<S>::R rho_off,
+                                           const typename Sto<S>::R* F) {
+  using R = typename Sto<S>::R;
+  using RL = RecLayout<Q>;
+  const uint32_t m = __ldg(so.mask + (e >> 5));
+  const uint32_t bit = (uint32_t)e & 31u;
+  if (!((m >> bit) & 1u)) return;
+  const int64_t k = (int64_t)__ldg(so.first + (e >> 5)) + __popc(m & ((1u << bit) - 1u));
+  R gs[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const S v = Sto<S>::cv(g[q]);
+    gs[q] = Sto<S>::ld(&v);
+  }
+  R rec[RL::STRIDE];
+  source_record<Q, R, FORCE>(gs, omega, rho_off, F, rec);
+  store_record<Q, R>(static_cast<R*>(so.rec_out) + k * RL::STRIDE, rec);
+}
+
 // ----------------------------------------------------------------- stream + collide
 // Tuning knobs of the hot kernel (compile-time; the defaults are the measured
 // best on GB300).  LBM_SC_EPT: elements per thread; LBM_SC_BLOCK: threads per
@@ -325,7 +428,7 @@ __device__ __forceinline__ void bgk_collide(R (&g)[Q], R om, R rho_off, const R*
 // a plain pull read the element's own opposite slot, which is the bounce-back
 // value), and patches the rare inlet / outlet values afterwards, so that up to
 // 2(Q-1) independent loads per element are in flight.
-template <int Q, class S, bool FORCE, int EPT>
+template <int Q, class S, bool FORCE, int EPT, bool MOMS>
 __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(const StreamCollideArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
@@ -390,6 +493,7 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
     bgk_collide<Q, R, FORCE>(g[k], R(a.omega), R(a.rho_off), F);
 #pragma unroll
     for (int i = 0; i < Q; ++i) st_once(dst + (size_t)i * N + e, Sto<S>::cv(g[k][i]));
+    if (MOMS) source_out<Q, S, FORCE>(a.so, e, g[k], R(a.omega), R(a.rho_off), F);
   }
 }
 
@@ -427,8 +531,10 @@ __global__ void __launch_bounds__(LBM_SC_BLOCK, LBM_SC_MINB) k_stream_collide(co
 // more elements in flight; five blocks per SM (48 registers, no spills) for
 // D3Q19 / D2Q9 BF16, measured faster than four or six.
 #define LBM_BR_INT_MINB(Q, S) ((Q) <= 19 && sizeof(S) == 2 ? 5 : LBM_BR_MINB)
-template <int Q, class S, bool FORCE, bool BND>
-__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : LBM_BR_INT_MINB(Q, S)) k_stream_collide_brick(const BrickArgs a) {
+#define LBM_BR_MOMS_MINB(Q, S) ((Q) <= 19 && sizeof(S) <= 4 ? 5 : LBM_BR_MINB)
+
+template <int Q, class S, bool FORCE, bool BND, bool MOMS>
+__global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : (MOMS ? LBM_BR_MOMS_MINB(Q, S) : LBM_BR_INT_MINB(Q, S))) k_stream_collide_brick(const BrickArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -520,6 +626,7 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : LB
   bgk_collide<Q, R, FORCE>(g, R(a.omega), R(a.rho_off), F);
 #pragma unroll
   for (int i = 0; i < Q; ++i) st_once(dst + i * N, Sto<S>::cv(g[i]));
+  if (MOMS) source_out<Q, S, FORCE>(a.so, first + l, g, R(a.omega), R(a.rho_off), F);
 }
 
 // BF16 interior bricks, two neighbouring elements per thread: lane m of the
@@ -671,47 +778,13 @@ __global__ void k_outlet(const OutletArgs a) {
 }
 
 // ----------------------------------------------------------------- GFC source moments
-// Record of one source (compute type, mom_stride(Q) values, 16-byte aligned
-// groups): f^neq[Q] padded to a multiple of 4, then rho - rho_off, u[D], S[nS],
-// padding.  Vector loads/stores move a record in 8 (float) or 16 (double) pieces.
-template <int Q>
-struct RecLayout {
-  static constexpr int D = Lat<Q>::D, NS = Lat<Q>::NS;
-  static constexpr int FN = 0;
-  static constexpr int RP = (Q + 3) / 4 * 4;
-  static constexpr int U = RP + 1;
-  static constexpr int SS = U + D;
-  static constexpr int END = SS + NS;
-  static constexpr int STRIDE = mom_stride(Q);
-  static_assert(END <= STRIDE && STRIDE % 4 == 0, "moment record too long");
-};
-
-__device__ __forceinline__ void ld4(const float* p, float* o) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  o[0] = v.x;
-  o[1] = v.y;
-  o[2] = v.z;
-  o[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double* o) {
-  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
-  o[0] = a.x;
-  o[1] = a.y;
-  o[2] = b.x;
-  o[3] = b.y;
-}
-__device__ __forceinline__ void st4(float* p, const float* v) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-__device__ __forceinline__ void st4(double* p, const double* v) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-}
-
-// Interpolation step 1 (Sec. 2.2): density, velocity, strain rate and f^neq of
-// every coarse element that feeds a GhostFromCoarser, one record per source.
+// Interpolation step 1 (Sec. 2.2) as a kernel of its own: density, velocity,
+// strain rate and f^neq of the listed sources (elem[k], record rec[k] or k).
 // With prev set, the record is the mean of prev and the moments now (the
-// source moments at t+1/2 of the linear-in-time mode).
+// source moments at t+1/2 of the linear-in-time mode).  During the steps the
+// stream-collide writes the records of the sources it updates (source_out);
+// this kernel takes the GhostFromFiner sources after their fill and every
+// source when the records have to be rebuilt from a new state.
 // Launch bounds of the ghost kernels: LBM_*_MINB sets a minimum of resident
 // blocks per SM; unset (0), only the block size is given, which lets the
 // compiler use fewer registers than an explicit minimum of one block.
@@ -726,14 +799,14 @@ __device__ __forceinline__ void st4(double* p, const double* v) {
 template <int Q, class S, bool FORCE>
 __global__ void LBM_MOM_BOUNDS k_source_moments(const MomentsArgs a) {
   using R = typename Sto<S>::R;
-  using LT = Lat<Q>;
   using RL = RecLayout<Q>;
-  constexpr int D = LT::D, NS = LT::NS;
+  constexpr int D = Lat<Q>::D;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.nsrc) return;
   const S* __restrict__ src = static_cast<const S*>(a.src);
   const size_t N = (size_t)a.Ntot;
   const int64_t e = a.elem[k];
+  const int64_t r = a.rec ? (int64_t)a.rec[k] : k;
   R g[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) g[q] = Sto<S>::ld(src + (size_t)q * N + e);
@@ -742,30 +815,9 @@ __global__ void LBM_MOM_BOUNDS k_source_moments(const MomentsArgs a) {
 #pragma unroll
     for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(a.force)[(size_t)b * N + e];
   R rec[RL::STRIDE];
-#pragma unroll
-  for (int f = 0; f < RL::STRIDE; ++f) rec[f] = R(0);
-  R rp, u[3], fneq[Q], Sv[NS];
-  post_moments<Q, R, true, FORCE>(g, R(a.omega), R(a.rho_off), F, rp, u, fneq, Sv);
-#pragma unroll
-  for (int q = 0; q < Q; ++q) rec[RL::FN + q] = fneq[q];
-  rec[RL::RP] = rp;
-#pragma unroll
-  for (int b = 0; b < D; ++b) rec[RL::U + b] = u[b];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) rec[RL::SS + s] = Sv[s];
-  R* __restrict__ out = static_cast<R*>(a.mom) + (size_t)k * RL::STRIDE;
-  if (a.prev) {
-    // the whole previous record is read before the first store (the compiler
-    // cannot tell the two records apart and would otherwise serialise them)
-    const R* __restrict__ prev = static_cast<const R*>(a.prev) + (size_t)k * RL::STRIDE;
-    R pv[RL::STRIDE];
-#pragma unroll
-    for (int f = 0; f < RL::END; f += 4) ld4(prev + f, pv + f);
-#pragma unroll
-    for (int f = 0; f < RL::END; ++f) rec[f] = R(0.5) * (pv[f] + rec[f]);
-  }
-#pragma unroll
-  for (int f = 0; f < RL::END; f += 4) st4(out + f, rec + f);
+  source_record<Q, R, FORCE>(g, R(a.omega), R(a.rho_off), F, rec);
+  if (a.prev) mean_record<Q, R>(static_cast<const R*>(a.prev) + (size_t)r * RL::STRIDE, rec);
+  store_record<Q, R>(static_cast<R*>(a.mom) + (size_t)r * RL::STRIDE, rec);
 }
 
 // Compact quadratic velocity at the ghost in the octant's local frame, a linear
@@ -845,7 +897,7 @@ struct GfcGroup {
 #else
 #define LBM_GFC_BOUNDS __launch_bounds__(LBM_GFC_BLOCK)
 #endif
-template <int Q, class S>
+template <int Q, class S, bool TWO>
 __global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
@@ -865,6 +917,7 @@ __global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) src[s] = a.gsrc[(size_t)s * a.ng + k];
   const R* __restrict__ mom = static_cast<const R*>(a.mom);
+  const R* __restrict__ mom2 = static_cast<const R*>(a.mom2);
   R* sg_base = stage + grp * NSLOT * PSTR;
 #pragma unroll
   for (int t = 0; t < NSLOT; ++t) {
@@ -874,6 +927,13 @@ __global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
       for (int c = oct; c < RL::STRIDE / 4; c += G) {
         R v[4];
         ld4(mom + (size_t)r * RL::STRIDE + 4 * c, v);
+        if (TWO) {
+          // the records at t + 1/2: mean of those at t and t + 1
+          R w[4];
+          ld4(mom2 + (size_t)r * RL::STRIDE + 4 * c, w);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) v[j] = R(0.5) * (v[j] + w[j]);
+        }
         st4(sg_base + t * PSTR + 4 * c, v);
       }
   }
@@ -1301,21 +1361,30 @@ struct Launch {
     const unsigned g = blocks_for(a.nB, LBM_BR_BLOCK / 64);
     with_q(Q, [&](auto q) {
       constexpr int QQ = decltype(q)::value;
+      const bool moms = a.so.mask != nullptr;
       if constexpr (std::is_same<S, __nv_bfloat16>::value) {
         // BF16 interior bricks: two elements per thread, one brick per warp
-        if (!boundary) {
+        // (on levels without GFC sources; the others take the one-element
+        // kernel with its record epilogue)
+        if (!boundary && !moms) {
           const unsigned g2 = blocks_for(a.nB, LBM_BR_BLOCK / 32);
           if (force) k_stream_collide_brick_pair<QQ, true><<<g2, LBM_BR_BLOCK, 0, st>>>(a);
           else k_stream_collide_brick_pair<QQ, false><<<g2, LBM_BR_BLOCK, 0, st>>>(a);
           return;
         }
       }
+      auto go = [&](auto F, auto B, auto M) {
+        k_stream_collide_brick<QQ, S, decltype(F)::value, decltype(B)::value, decltype(M)::value>
+            <<<g, LBM_BR_BLOCK, 0, st>>>(a);
+      };
+      using T = std::true_type;
+      using U = std::false_type;
       if (boundary) {
-        if (force) k_stream_collide_brick<QQ, S, true, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
-        else k_stream_collide_brick<QQ, S, false, true><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+        if (force) moms ? go(T{}, T{}, T{}) : go(T{}, T{}, U{});
+        else moms ? go(U{}, T{}, T{}) : go(U{}, T{}, U{});
       } else {
-        if (force) k_stream_collide_brick<QQ, S, true, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
-        else k_stream_collide_brick<QQ, S, false, false><<<g, LBM_BR_BLOCK, 0, st>>>(a);
+        if (force) moms ? go(T{}, U{}, T{}) : go(T{}, U{}, U{});
+        else moms ? go(U{}, U{}, T{}) : go(U{}, U{}, U{});
       }
     });
   }
@@ -1326,8 +1395,14 @@ struct Launch {
     const unsigned g = blocks_for(n, LBM_SC_BLOCK * EPT);
     with_q(Q, [&](auto q) {
       constexpr int QQ = decltype(q)::value;
-      if (force) k_stream_collide<QQ, S, true, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
-      else k_stream_collide<QQ, S, false, EPT><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+      const bool moms = a.so.mask != nullptr;
+      if (force) {
+        if (moms) k_stream_collide<QQ, S, true, EPT, true><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+        else k_stream_collide<QQ, S, true, EPT, false><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+      } else {
+        if (moms) k_stream_collide<QQ, S, false, EPT, true><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+        else k_stream_collide<QQ, S, false, EPT, false><<<g, LBM_SC_BLOCK, 0, st>>>(a);
+      }
     });
   }
   static void outlet(int Q, const OutletArgs& a, cudaStream_t st) {
@@ -1347,7 +1422,10 @@ struct Launch {
   static void fill_gfc(int Q, const GfcArgs& a, cudaStream_t st) {
     if (a.ng <= 0) return;
     with_q(Q, [&](auto q) {
-      k_fill_gfc<decltype(q)::value, S><<<blocks_for(a.ng, LBM_GFC_BLOCK), LBM_GFC_BLOCK, 0, st>>>(a);
+      constexpr int QQ = decltype(q)::value;
+      const unsigned g = blocks_for(a.ng, LBM_GFC_BLOCK);
+      if (a.mom2) k_fill_gfc<QQ, S, true><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
+      else k_fill_gfc<QQ, S, false><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
     });
   }
   static void fill_gff(int Q, const GffArgs& a, cudaStream_t st) {

@@ -19,8 +19,12 @@ enum TimedKind { TK_INTERIOR = 0, TK_LIST = 1, TK_BOUNDARY = 2, TK_GFF = 3, TK_M
 constexpr int kTimedKinds = 8;
 
 struct LevelDev {
-  size_t gff_child0 = 0, gfc_src = 0, gfc_oct = 0, src_elem = 0, momA = 0, momB = 0;
-  int64_t nsrc = 0;
+  size_t gff_child0 = 0, gfc_src = 0, gfc_oct = 0, src_elem = 0, gsrc_elem = 0, gsrc_rec = 0;
+  // source records of the two pdf buffers: momA[parity] those of the current
+  // state (a stream-collide writes those of its new state into the other one
+  // while the GhostFromCoarser fill may still read these)
+  size_t momA[2] = {0, 0};
+  int64_t nsrc = 0, n_gsrc = 0, n_gsrc_inner = 0;
 };
 
 }  // namespace lbm
@@ -35,7 +39,8 @@ struct lbm_ctx {
   double inlet[lbm::kQmax] = {};
   // layout (byte offsets into the workspace)
   size_t oA = 0, oB = 0, oNbr = 0, oBrickNb = 0, oBrickTab = 0, oInletS = 0, oOutQ = 0, oObsA = 0, oObsQ = 0, oF = 0, oOutElem = 0, oOutA = 0, oOutB = 0, oOutDir = 0, oOutKind = 0,
-         oSide = 0, oObsElem = 0, oObsDir = 0, oUslot = 0, oUlev = 0, oSlotUser = 0, oStage = 0, oPartial = 0, oRed = 0;
+         oSide = 0, oObsElem = 0, oObsDir = 0, oUslot = 0, oUlev = 0, oSlotUser = 0, oStage = 0, oPartial = 0, oRed = 0,
+         oSrcMask = 0, oSrcFirst = 0;
   std::vector<lbm::LevelDev> ld;
   size_t bytes = 0;
   int64_t chunk = 0;
@@ -56,7 +61,14 @@ struct lbm_ctx {
     steps_since_check = 0;
     mass_ref_valid = false;
     steps_done = 0;
+    recs_valid = false;
   }
+  // the source records momA[parity] of every level hold the moments of the
+  // current state (kept by the stream-collide epilogue from one step to the
+  // next); cleared by anything else that changes the state, the force or the
+  // relaxation rates, and restored by ensure_records()
+  bool recs_valid = false;
+  void ensure_records();
   // observer called before every op of advance() (records the adjoint tape);
   // with dry set, advance() only walks the op sequence and flips parities
   std::function<void(int op, int level)> hook;
@@ -135,6 +147,14 @@ struct lbm_ctx {
 #define LBM_CONCURRENT_SC 1
 #endif
   bool concurrent_sc = LBM_CONCURRENT_SC != 0;
+#ifndef LBM_GFC_B_BRANCH
+#define LBM_GFC_B_BRANCH 0
+#endif
+  bool gfc_b_branch = LBM_GFC_B_BRANCH != 0;
+#ifndef LBM_LEVEL_BRANCH
+#define LBM_LEVEL_BRANCH 1
+#endif
+  bool level_branch = LBM_LEVEL_BRANCH != 0;
   bool graphs_on = true;
   int last_graph = -1;        // graph of the most recent replay
   bool graph_unread = false;  // its events hold a replay not yet read
@@ -190,13 +210,25 @@ struct lbm_ctx {
   void layout();
   // driver pieces
   void fill_gff(int li);
-  void source_moments(int li, size_t mom_off, size_t prev_off = 0, cudaStream_t s = nullptr);
+  // records of the level's sources into mom_off: subset SRC_ALL every
+  // source, SRC_GFF the GhostFromFiner ones, SRC_GFF_OUTER those of the outer
+  // GhostFromFiner layer
+  void source_moments(int li, size_t mom_off, size_t prev_off = 0, cudaStream_t s = nullptr, int subset = 0);
+  enum { SRC_ALL = 0, SRC_GFF = 1, SRC_GFF_OUTER = 2 };
   // all_layers false: in LINEAR mode the outer ghost layer, which no
   // stream-collide reads, is left unwritten
-  void fill_gfc(int li_fine, bool two_times, bool all_layers = false, cudaStream_t s = nullptr);
+  // next_buffer: write the ghosts into the fine level's other buffer (the
+  // one its next stream-collide writes, issued before that stream-collide)
+  void fill_gfc(int li_fine, bool two_times, bool all_layers = false, cudaStream_t s = nullptr,
+                bool next_buffer = false);
   // launches on stream s (default: the bound stream)
   void stream_collide(int li, cudaStream_t s = nullptr);
   void advance(int li);
+  // one coarse step from the top: ensure_records(), then advance(0)
+  void coarse_step() {
+    ensure_records();
+    advance(0);
+  }
   // graph of two coarse steps from the current parity state, captured on
   // first use; null when capture is unavailable (the caller steps eagerly)
   const StepGraph* step_graph();

@@ -22,6 +22,7 @@ constexpr uint32_t NB_BOUNCE = 0x80000000u;
 constexpr uint32_t NB_FLAG30 = 0x40000000u;
 constexpr uint32_t NB_INDEX = 0x3FFFFFFFu;
 constexpr int kPad = 32;  // every level segment is padded to a multiple of this
+static_assert(kPad % 32 == 0, "source masks take 32-slot blocks inside one level");
 constexpr int32_t kBrickMissing = INT32_MIN;  // brick row entry: neighbour brick not complete
 constexpr uint8_t kGfcOuter = 0x80;  // GhostFromCoarser octant byte: ghost of the outer layer
 
@@ -70,6 +71,10 @@ struct HostLevel {
                                  // kGfcOuter: outer layer (no fluid or subdivided neighbour)
   // sources (global indices on this level) feeding the GFC of level L+1
   std::vector<int32_t> src_elem;
+  // sources that are GhostFromFiner ghosts (their records follow the ghost
+  // fill): element and record index, the inner layer first
+  std::vector<int32_t> gsrc_elem, gsrc_rec;
+  int64_t n_gsrc_inner = 0;
   // outlet links processed before this level's stream-collide: global range in the outlet list
   int64_t out_begin = 0, out_end = 0;
   // obstacle links of this level: global range in the obstacle list
@@ -111,6 +116,11 @@ struct HostMesh {
   // the pull source f*_i(x - c_i) at first + brick_nb[t] + l'
   std::vector<int32_t> brick_nb;    // [sum nB][27]
   std::vector<uint16_t> brick_tab;  // [Q-1][64]
+  // GhostFromCoarser sources, per 32 slots (level segments are 32-aligned, so
+  // a block lies in one level): bit j set if slot 32 blk + j is a source of
+  // its level, and the record index of the block's first source
+  std::vector<uint32_t> src_mask;  // [Ntot / 32]
+  std::vector<int32_t> src_first;  // [Ntot / 32]
 };
 
 // Build the mesh tables; returns LBM_OK or LBM_ERR_MESH / LBM_ERR_ARG with msg.
@@ -124,6 +134,15 @@ lbm_status sfc_partition(const int64_t* tree_ids, int64_t n, int d, int nparts, 
 // ----------------------------------------------------------------- kernels
 // Launch arguments are plain data; pointers are device pointers into the
 // workspace.  "src"/"dst" are pdf arrays [Q][Ntot] of the storage type.
+// GFC source records written by a stream-collide (interpolation step 1 of
+// Sec. 2.2 fused into the kernel that produces the source state): for every
+// processed element marked in mask, the record of its new state goes to
+// rec_out.  mask null: no records.
+struct SourceOut {
+  const uint32_t* mask;  // [Ntot / 32] source bits per 32 slots
+  const int32_t* first;  // [Ntot / 32] record index of each block's first source
+  void* rec_out;         // [nsrc][mom_stride(Q)] records of the new state
+};
 struct StreamCollideArgs {
   const void* src;
   void* dst;
@@ -135,6 +154,7 @@ struct StreamCollideArgs {
   int64_t hole_at, hole_len;  // interior bricks skipped by this kernel (0 length: none)
   double omega, rho_off;
   double inlet[kQmax];  // 6 w_i rho0 (c_i . u_in)
+  SourceOut so;
 };
 
 // Stream-collide of the interior bricks of one level: nB bricks of 64
@@ -154,6 +174,7 @@ struct BrickArgs {
   const void* side;
   const double* inlet_s;
   double inlet[kQmax];
+  SourceOut so;
 };
 
 struct OutletArgs {
@@ -178,12 +199,14 @@ struct MomentsArgs {
   const int32_t* elem;
   void* mom;         // [nsrc][mom_stride(Q)]
   const void* prev;  // if set: mom = (prev + moments now) / 2 (mean of two time levels)
+  const int32_t* rec;  // record index of elem[k] (null: k)
   int64_t Ntot, nsrc;
   double omega, rho_off;
 };
 
 struct GfcArgs {
   const void* mom;       // [nsrc][mom_stride(Q)] source records
+  const void* mom2;      // if set: the records are the means of mom and mom2 (t + 1/2)
   int64_t nsrc;
   const int32_t* gsrc;   // [4][ng]
   const uint8_t* oct;    // [ng]

@@ -723,6 +723,31 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     for (int64_t k = 0; k < H.nC; ++k)
       if (gfc[li][k].layer == 2) H.gfc_oct[k] |= kGfcOuter;
   }
+  // source bits per 32 slots (records written by the stream-collide) and the
+  // GhostFromFiner sources (records written after the ghost fill)
+  M.src_mask.assign((size_t)(M.Ntot / 32), 0u);
+  M.src_first.assign((size_t)(M.Ntot / 32), 0);
+  for (int li = 0; li < nlev; ++li) {
+    HostLevel& H = M.lv[li];
+    std::vector<int32_t> outer_e, outer_r;
+    for (int64_t k = 0; k < (int64_t)H.src_elem.size(); ++k) {
+      const int64_t e = H.src_elem[k];
+      const size_t blk = (size_t)(e >> 5);
+      if (!M.src_mask[blk]) M.src_first[blk] = (int32_t)k;
+      M.src_mask[blk] |= 1u << (e & 31);
+      if (M.kind[e] != K_GFF) continue;
+      if (e - H.base < H.oG2) {
+        H.gsrc_elem.push_back((int32_t)e);
+        H.gsrc_rec.push_back((int32_t)k);
+      } else {
+        outer_e.push_back((int32_t)e);
+        outer_r.push_back((int32_t)k);
+      }
+    }
+    H.n_gsrc_inner = (int64_t)H.gsrc_elem.size();
+    H.gsrc_elem.insert(H.gsrc_elem.end(), outer_e.begin(), outer_e.end());
+    H.gsrc_rec.insert(H.gsrc_rec.end(), outer_r.begin(), outer_r.end());
+  }
 
   // ---- pull neighbour lists (Sec. 2.1) with boundary rules (Sec. 2.3)
   M.nbr.assign((size_t)(Q - 1) * M.Ntot, 0);
