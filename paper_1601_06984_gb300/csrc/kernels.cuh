@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <type_traits>
 #include <cuda_runtime.h>
 
@@ -75,6 +76,30 @@ struct Lat<27> {
 };
 
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// Run-time lookup of c_{i,a} and w_i for a velocity index known only at run
+// time (a lane's share of the directions): c_{i,a} + 1 packed in two bits per
+// velocity; the weights depend on |c_i|^2, i.e. on the index range (every
+// lattice lists its velocities by increasing length).
+template <int Q>
+struct LatRt {
+  __host__ __device__ static constexpr uint64_t pack(int a) {
+    uint64_t m = 0;
+    for (int i = 0; i < Q; ++i) m |= (uint64_t)(Lat<Q>::c(i, a) + 1) << (2 * i);
+    return m;
+  }
+  __device__ static __forceinline__ int c(int i, int a) {
+    constexpr uint64_t X = pack(0), Y = pack(1), Z = pack(2);
+    const uint64_t m = a == 0 ? X : (a == 1 ? Y : Z);
+    return (int)((m >> (2 * i)) & 3u) - 1;
+  }
+  template <class R>
+  __device__ static __forceinline__ R w(int i) {
+    constexpr int D = Lat<Q>::D;
+    return i == 0 ? R(Lat<Q>::w(0))
+                  : (i <= 2 * D ? R(Lat<Q>::w(1)) : ((Q == 27 && i > 18) ? R(Lat<Q>::w(19)) : R(Lat<Q>::w(2 * D + 1))));
+  }
+};
 
 // index of S_ab in the packed strain-rate vector (xx,yy,xy | xx,yy,zz,xy,yz,xz)
 template <int D>
@@ -889,57 +914,16 @@ struct GfcGroup {
   }
 };
 
-#ifndef LBM_GFC_BLOCK
-#define LBM_GFC_BLOCK 64
-#endif
-#if defined(LBM_GFC_MINB) && LBM_GFC_MINB > 0
-#define LBM_GFC_BOUNDS __launch_bounds__(LBM_GFC_BLOCK, LBM_GFC_MINB)
-#else
-#define LBM_GFC_BOUNDS __launch_bounds__(LBM_GFC_BLOCK)
-#endif
-template <int Q, class S, bool TWO>
-__global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
+// Interpolation steps 2-5 for ghost k (octant oct) from its group's staged
+// records (sg_base: NSLOT padded records), written into a.dst.
+template <int Q, class S>
+__device__ __forceinline__ void gfc_ghost(const GfcArgs& a, const typename Sto<S>::R* sg_base, int oct, int64_t k) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
   using GG = GfcGroup<LT::D>;
-  constexpr int D = LT::D, NS = LT::NS, G = GG::G, NSLOT = GG::NSLOT;
-  constexpr int PSTR = RL::STRIDE + 4;  // padded record: sibling lanes' reads fall in distinct banks
-  constexpr int NGRP = LBM_GFC_BLOCK / G;
-  __shared__ __align__(16) R stage[NGRP * NSLOT * PSTR];
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int oct = threadIdx.x & (G - 1);  // octant of the ghost
-  const int grp = threadIdx.x / G;
-  const bool active = k < a.ng;                   // ng is a multiple of G: whole groups
-  const unsigned lane0 = (threadIdx.x & 31) & ~(unsigned)(G - 1);
-  int32_t src[4] = {0, 0, 0, 0};
-  if (active)
-#pragma unroll
-    for (int s = 0; s < 4; ++s) src[s] = a.gsrc[(size_t)s * a.ng + k];
-  const R* __restrict__ mom = static_cast<const R*>(a.mom);
-  const R* __restrict__ mom2 = static_cast<const R*>(a.mom2);
-  R* sg_base = stage + grp * NSLOT * PSTR;
-#pragma unroll
-  for (int t = 0; t < NSLOT; ++t) {
-    const int r = __shfl_sync(0xffffffffu, src[GG::src_of(t)], lane0 + GG::lane_of(t));
-    if (active)
-#pragma unroll
-      for (int c = oct; c < RL::STRIDE / 4; c += G) {
-        R v[4];
-        ld4(mom + (size_t)r * RL::STRIDE + 4 * c, v);
-        if (TWO) {
-          // the records at t + 1/2: mean of those at t and t + 1
-          R w[4];
-          ld4(mom2 + (size_t)r * RL::STRIDE + 4 * c, w);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) v[j] = R(0.5) * (v[j] + w[j]);
-        }
-        st4(sg_base + t * PSTR + 4 * c, v);
-      }
-  }
-  __syncwarp();
-  // outer-layer ghosts are staged with their group but, when skipped, not written
-  if (!active || (a.skip_outer && (a.oct[k] & kGfcOuter))) return;
+  constexpr int D = LT::D, NS = LT::NS;
+  constexpr int PSTR = RL::STRIDE + 4;
   const R* rec[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) rec[s] = sg_base + GG::slot(s, oct) * PSTR;
@@ -1013,6 +997,144 @@ __global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
     dst[(size_t)i * N + e] = Sto<S>::cv(even + odd + scale * fn[i]);
     dst[(size_t)(i + 1) * N + e] = Sto<S>::cv(even - odd + scale * fn[i + 1]);
   }
+}
+
+
+#ifndef LBM_GFC_BLOCK
+#define LBM_GFC_BLOCK 64
+#endif
+#ifndef LBM_GFC_PIPE
+#define LBM_GFC_PIPE 0
+#endif
+#if defined(LBM_GFC_MINB) && LBM_GFC_MINB > 0
+#define LBM_GFC_BOUNDS __launch_bounds__(LBM_GFC_BLOCK, LBM_GFC_MINB)
+#else
+#define LBM_GFC_BOUNDS __launch_bounds__(LBM_GFC_BLOCK)
+#endif
+template <int Q, class S, bool TWO>
+__global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  using RL = RecLayout<Q>;
+  using GG = GfcGroup<LT::D>;
+  constexpr int G = GG::G, NSLOT = GG::NSLOT;
+  constexpr int PSTR = RL::STRIDE + 4;  // padded record: sibling lanes' reads fall in distinct banks
+  constexpr int NGRP = LBM_GFC_BLOCK / G;
+  __shared__ __align__(16) R stage[NGRP * NSLOT * PSTR];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int oct = threadIdx.x & (G - 1);  // octant of the ghost
+  const int grp = threadIdx.x / G;
+  const bool active = k < a.ng;                   // ng is a multiple of G: whole groups
+  const unsigned lane0 = (threadIdx.x & 31) & ~(unsigned)(G - 1);
+  int32_t src[4] = {0, 0, 0, 0};
+  if (active)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) src[s] = a.gsrc[(size_t)s * a.ng + k];
+  const R* __restrict__ mom = static_cast<const R*>(a.mom);
+  const R* __restrict__ mom2 = static_cast<const R*>(a.mom2);
+  R* sg_base = stage + grp * NSLOT * PSTR;
+#pragma unroll
+  for (int t = 0; t < NSLOT; ++t) {
+    const int r = __shfl_sync(0xffffffffu, src[GG::src_of(t)], lane0 + GG::lane_of(t));
+    if (active)
+#pragma unroll
+      for (int c = oct; c < RL::STRIDE / 4; c += G) {
+        R v[4];
+        ld4(mom + (size_t)r * RL::STRIDE + 4 * c, v);
+        if (TWO) {
+          // the records at t + 1/2: mean of those at t and t + 1
+          R w[4];
+          ld4(mom2 + (size_t)r * RL::STRIDE + 4 * c, w);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) v[j] = R(0.5) * (v[j] + w[j]);
+        }
+        st4(sg_base + t * PSTR + 4 * c, v);
+      }
+  }
+  __syncwarp();
+  // outer-layer ghosts are staged with their group but, when skipped, not written
+  if (!active || (a.skip_outer && (a.oct[k] & kGfcOuter))) return;
+  gfc_ghost<Q, S>(a, sg_base, oct, k);
+}
+
+// Asynchronous global -> shared copies of 16 bytes (cached in L2 only), in
+// commit groups; wait_group N returns once at most N of this thread's groups
+// are still in flight.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The same fill with persistent blocks and a two-stage pipeline: while a
+// block's lanes interpolate one tile of ghosts (BLK per tile), the records of
+// its next tile are already on their way into the other stage (asynchronous
+// copies), and the source positions of the tile after that into registers.
+// The groups of a tile lie inside one warp, so warp barriers order the
+// stages.  Records at t only (the fill at t + 1/2 keeps the one-tile kernel).
+template <class R>
+struct GfcPipe {
+  static constexpr int BLK = sizeof(R) == 8 ? 32 : 64;
+};
+template <int Q, class S>
+__global__ void __launch_bounds__(GfcPipe<typename Sto<S>::R>::BLK) k_fill_gfc_pipe(const GfcArgs a) {
+  using R = typename Sto<S>::R;
+  using LT = Lat<Q>;
+  using RL = RecLayout<Q>;
+  using GG = GfcGroup<LT::D>;
+  constexpr int G = GG::G, NSLOT = GG::NSLOT;
+  constexpr int BLK = GfcPipe<R>::BLK;
+  constexpr int PSTR = RL::STRIDE + 4;
+  constexpr int NGRP = BLK / G;
+  constexpr int CH = RL::STRIDE * (int)sizeof(R) / 16;  // 16-byte chunks per record
+  constexpr int RPC = 16 / (int)sizeof(R);              // values per chunk
+  constexpr int BUF = NGRP * NSLOT * PSTR;
+  __shared__ __align__(16) R stage[2][BUF];
+  const int oct = threadIdx.x & (G - 1), grp = threadIdx.x / G;
+  const unsigned lane0 = (threadIdx.x & 31) & ~(unsigned)(G - 1);
+  const int64_t ntile = (a.ng + BLK - 1) / BLK;
+  const R* __restrict__ mom = static_cast<const R*>(a.mom);
+  auto load_src = [&](int64_t tile, int32_t (&src)[4]) {
+    const int64_t k = tile * BLK + threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) src[q] = k < a.ng ? a.gsrc[(size_t)q * a.ng + k] : 0;
+  };
+  // every lane takes part in the shuffles; only lanes of ghosts copy
+  auto stage_tile = [&](int64_t tile, const int32_t (&src)[4], R* buf) {
+    const bool act = tile * BLK + threadIdx.x < a.ng;
+#pragma unroll
+    for (int t = 0; t < NSLOT; ++t) {
+      const int r = __shfl_sync(0xffffffffu, src[GG::src_of(t)], lane0 + GG::lane_of(t));
+      if (act)
+#pragma unroll
+        for (int c = oct; c < CH; c += G)
+          cp_async16(buf + (grp * NSLOT + t) * PSTR + c * RPC, mom + (size_t)r * RL::STRIDE + c * RPC);
+    }
+    cp_async_commit();
+  };
+  int64_t tile = blockIdx.x;
+  int32_t nxt[4], after[4];
+  load_src(tile, nxt);
+  stage_tile(tile, nxt, stage[0]);
+  load_src(tile + gridDim.x, nxt);
+  for (int it = 0; tile < ntile; ++it, tile += gridDim.x) {
+    const int cur = it & 1;
+    stage_tile(tile + gridDim.x, nxt, stage[cur ^ 1]);
+    load_src(tile + 2 * (int64_t)gridDim.x, after);
+    cp_async_wait<1>();  // this tile's copies have landed
+    __syncwarp();
+    const int64_t k = tile * BLK + threadIdx.x;
+    if (k < a.ng && !(a.skip_outer && (a.oct[k] & kGfcOuter)))
+      gfc_ghost<Q, S>(a, stage[cur] + grp * NSLOT * PSTR, oct, k);
+    __syncwarp();  // the stage is refilled in the next iteration
+#pragma unroll
+    for (int q = 0; q < 4; ++q) nxt[q] = after[q];
+  }
+  cp_async_wait<0>();
 }
 
 // ----------------------------------------------------------------- GhostFromFiner
@@ -1114,10 +1236,20 @@ __global__ void LBM_GFF_BOUNDS k_fill_gff(const GffArgs a) {
   const R scale = (R(1) - wc) * R(2) * wf / wc * inv;
   S* __restrict__ dst = static_cast<S*>(a.dst);
   const int64_t e = k < a.n_inner ? a.dest0 + k : a.dest_outer + (k - a.n_inner);
-  // the group's lanes share the Q stores
+  // the group's lanes share the Q stores: lane b the directions j 2^d + b,
+  // whose c_i it looks up at run time (a compile-time loop over all Q would
+  // issue every direction's arithmetic in every lane)
 #pragma unroll
-  for (int q = 0; q < Q; ++q)
-    if (q % NCH == b) dst[(size_t)q * N + e] = Sto<S>::cv(geq<Q, R>(q, rpm, rho, uP, usq) + scale * W[q / NCH][0]);
+  for (int j = 0; j < NR; ++j) {
+    const int q = j * NCH + b;
+    if (q < Q) {
+      R cu = R(0);
+#pragma unroll
+      for (int aa = 0; aa < D; ++aa) cu += R(LatRt<Q>::c(q, aa)) * uP[aa];
+      const R feq = LatRt<Q>::template w<R>(q) * (rpm + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
+      dst[(size_t)q * N + e] = Sto<S>::cv(feq + scale * W[j][0]);
+    }
+  }
 }
 
 // ----------------------------------------------------------------- set-up (compute type) / output (FP64)
@@ -1424,8 +1556,25 @@ struct Launch {
     with_q(Q, [&](auto q) {
       constexpr int QQ = decltype(q)::value;
       const unsigned g = blocks_for(a.ng, LBM_GFC_BLOCK);
-      if (a.mom2) k_fill_gfc<QQ, S, true><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
-      else k_fill_gfc<QQ, S, false><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
+      if (a.mom2) {
+        k_fill_gfc<QQ, S, true><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
+      } else if (LBM_GFC_PIPE) {
+        // persistent: as many blocks as fit on the device at once
+        constexpr int BLK = GfcPipe<typename Sto<S>::R>::BLK;
+        static int per_sm = 0, sms = 0;
+        if (!per_sm) {
+          int dev = 0;
+          cudaGetDevice(&dev);
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fill_gfc_pipe<QQ, S>, BLK, 0);
+          if (per_sm < 1) per_sm = 1;
+        }
+        const int64_t tiles = (a.ng + BLK - 1) / BLK;
+        const unsigned gp = (unsigned)std::min<int64_t>(tiles, (int64_t)per_sm * sms);
+        k_fill_gfc_pipe<QQ, S><<<gp, BLK, 0, st>>>(a);
+      } else {
+        k_fill_gfc<QQ, S, false><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
+      }
     });
   }
   static void fill_gff(int Q, const GffArgs& a, cudaStream_t st) {
