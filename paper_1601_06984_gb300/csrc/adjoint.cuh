@@ -22,6 +22,39 @@
 namespace lbm {
 namespace dev {
 
+// Minimum resident blocks per SM of the reverse kernels (0: only the block
+// size is given to __launch_bounds__).
+#ifndef LBM_ADJ_SC_MINB
+#define LBM_ADJ_SC_MINB 2
+#endif
+#ifndef LBM_ADJ_BRICK_MINB
+#define LBM_ADJ_BRICK_MINB 2
+#endif
+#ifndef LBM_ADJ_MOM_MINB
+#define LBM_ADJ_MOM_MINB 0
+#endif
+#ifndef LBM_ADJ_GFC_MINB
+#define LBM_ADJ_GFC_MINB 0
+#endif
+#ifndef LBM_ADJ_GFF_MINB
+#define LBM_ADJ_GFF_MINB 0
+#endif
+#if LBM_ADJ_MOM_MINB > 0
+#define LBM_ADJ_MOM_BOUNDS __launch_bounds__(128, LBM_ADJ_MOM_MINB)
+#else
+#define LBM_ADJ_MOM_BOUNDS __launch_bounds__(128)
+#endif
+#if LBM_ADJ_GFC_MINB > 0
+#define LBM_ADJ_GFC_BOUNDS __launch_bounds__(128, LBM_ADJ_GFC_MINB)
+#else
+#define LBM_ADJ_GFC_BOUNDS __launch_bounds__(128)
+#endif
+#if LBM_ADJ_GFF_MINB > 0
+#define LBM_ADJ_GFF_BOUNDS __launch_bounds__(256, LBM_ADJ_GFF_MINB)
+#else
+#define LBM_ADJ_GFF_BOUNDS __launch_bounds__(256)
+#endif
+
 // ----------------------------------------------------------------- reverse helpers
 // Reverse of g^eq_i(rp, rho = rho_off + rp, u) for all i, weighted by lam[i]:
 // adds to lam_rp and lam_u.
@@ -356,7 +389,7 @@ __global__ void __launch_bounds__(256) k_adj_seed(const AdjSeedArgs a) {
 // is added to the slot the forward pulled from (a conflict-free scatter: each
 // slot has one reader), or to the adjoint of the outlet value it came from.
 template <int Q, class S>
-__global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
+__global__ void __launch_bounds__(256, LBM_ADJ_SC_MINB) k_adj_sc(const AdjSCArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -445,7 +478,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_sc(const AdjSCArgs a) {
 // row b.
 static_assert(LBM_BR_BLOCK / 64 == LBM_BRICKS_PER_BLOCK, "host sizes the running rows by this many bricks per block");
 template <int Q, class S>
-__global__ void __launch_bounds__(LBM_BR_BLOCK, 2) k_adj_sc_brick(const AdjSCArgs a) {
+__global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_ADJ_BRICK_MINB) k_adj_sc_brick(const AdjSCArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -578,7 +611,7 @@ __global__ void __launch_bounds__(256) k_adj_outlet(const AdjOutletArgs a) {
 
 // ----------------------------------------------------------------- source moments
 template <int Q, class S>
-__global__ void __launch_bounds__(128) k_adj_moments(const AdjMomArgs a) {
+__global__ void LBM_ADJ_MOM_BOUNDS k_adj_moments(const AdjMomArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
@@ -636,7 +669,7 @@ __global__ void __launch_bounds__(128) k_adj_moments(const AdjMomArgs a) {
 
 // ----------------------------------------------------------------- GhostFromCoarser
 template <int Q, class S>
-__global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
+__global__ void LBM_ADJ_GFC_BOUNDS k_adj_gfc(const AdjGfcArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
@@ -771,7 +804,7 @@ __global__ void __launch_bounds__(128) k_adj_gather(const AdjGatherArgs a) {
 
 // ----------------------------------------------------------------- GhostFromFiner
 template <int Q, class S>
-__global__ void __launch_bounds__(256) k_adj_gff(const AdjGffArgs a) {
+__global__ void LBM_ADJ_GFF_BOUNDS k_adj_gff(const AdjGffArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D, NS = LT::NS, NCH = 1 << D;

@@ -15,7 +15,6 @@
 #pragma once
 
 #include <cuda_bf16.h>
-#include <algorithm>
 #include <type_traits>
 #include <cuda_runtime.h>
 
@@ -665,7 +664,10 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : (M
 // kernel, element by element.
 // Four blocks per SM (64 registers) for D2Q9 / D3Q19, three for D3Q27 (which
 // spills at four).
-#define LBM_BR_PAIR_MINB(Q) ((Q) > 19 ? 3 : 4)
+#ifndef LBM_BR_PAIR_MINB_Q19
+#define LBM_BR_PAIR_MINB_Q19 4
+#endif
+#define LBM_BR_PAIR_MINB(Q) ((Q) > 19 ? 3 : LBM_BR_PAIR_MINB_Q19)
 template <int Q, bool FORCE>
 __global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_BR_PAIR_MINB(Q)) k_stream_collide_brick_pair(const BrickArgs a) {
   using S = __nv_bfloat16;
@@ -1003,9 +1005,6 @@ __device__ __forceinline__ void gfc_ghost(const GfcArgs& a, const typename Sto<S
 #ifndef LBM_GFC_BLOCK
 #define LBM_GFC_BLOCK 64
 #endif
-#ifndef LBM_GFC_PIPE
-#define LBM_GFC_PIPE 0
-#endif
 #if defined(LBM_GFC_MINB) && LBM_GFC_MINB > 0
 #define LBM_GFC_BOUNDS __launch_bounds__(LBM_GFC_BLOCK, LBM_GFC_MINB)
 #else
@@ -1055,86 +1054,6 @@ __global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
   // outer-layer ghosts are staged with their group but, when skipped, not written
   if (!active || (a.skip_outer && (a.oct[k] & kGfcOuter))) return;
   gfc_ghost<Q, S>(a, sg_base, oct, k);
-}
-
-// Asynchronous global -> shared copies of 16 bytes (cached in L2 only), in
-// commit groups; wait_group N returns once at most N of this thread's groups
-// are still in flight.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// The same fill with persistent blocks and a two-stage pipeline: while a
-// block's lanes interpolate one tile of ghosts (BLK per tile), the records of
-// its next tile are already on their way into the other stage (asynchronous
-// copies), and the source positions of the tile after that into registers.
-// The groups of a tile lie inside one warp, so warp barriers order the
-// stages.  Records at t only (the fill at t + 1/2 keeps the one-tile kernel).
-template <class R>
-struct GfcPipe {
-  static constexpr int BLK = sizeof(R) == 8 ? 32 : 64;
-};
-template <int Q, class S>
-__global__ void __launch_bounds__(GfcPipe<typename Sto<S>::R>::BLK) k_fill_gfc_pipe(const GfcArgs a) {
-  using R = typename Sto<S>::R;
-  using LT = Lat<Q>;
-  using RL = RecLayout<Q>;
-  using GG = GfcGroup<LT::D>;
-  constexpr int G = GG::G, NSLOT = GG::NSLOT;
-  constexpr int BLK = GfcPipe<R>::BLK;
-  constexpr int PSTR = RL::STRIDE + 4;
-  constexpr int NGRP = BLK / G;
-  constexpr int CH = RL::STRIDE * (int)sizeof(R) / 16;  // 16-byte chunks per record
-  constexpr int RPC = 16 / (int)sizeof(R);              // values per chunk
-  constexpr int BUF = NGRP * NSLOT * PSTR;
-  __shared__ __align__(16) R stage[2][BUF];
-  const int oct = threadIdx.x & (G - 1), grp = threadIdx.x / G;
-  const unsigned lane0 = (threadIdx.x & 31) & ~(unsigned)(G - 1);
-  const int64_t ntile = (a.ng + BLK - 1) / BLK;
-  const R* __restrict__ mom = static_cast<const R*>(a.mom);
-  auto load_src = [&](int64_t tile, int32_t (&src)[4]) {
-    const int64_t k = tile * BLK + threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) src[q] = k < a.ng ? a.gsrc[(size_t)q * a.ng + k] : 0;
-  };
-  // every lane takes part in the shuffles; only lanes of ghosts copy
-  auto stage_tile = [&](int64_t tile, const int32_t (&src)[4], R* buf) {
-    const bool act = tile * BLK + threadIdx.x < a.ng;
-#pragma unroll
-    for (int t = 0; t < NSLOT; ++t) {
-      const int r = __shfl_sync(0xffffffffu, src[GG::src_of(t)], lane0 + GG::lane_of(t));
-      if (act)
-#pragma unroll
-        for (int c = oct; c < CH; c += G)
-          cp_async16(buf + (grp * NSLOT + t) * PSTR + c * RPC, mom + (size_t)r * RL::STRIDE + c * RPC);
-    }
-    cp_async_commit();
-  };
-  int64_t tile = blockIdx.x;
-  int32_t nxt[4], after[4];
-  load_src(tile, nxt);
-  stage_tile(tile, nxt, stage[0]);
-  load_src(tile + gridDim.x, nxt);
-  for (int it = 0; tile < ntile; ++it, tile += gridDim.x) {
-    const int cur = it & 1;
-    stage_tile(tile + gridDim.x, nxt, stage[cur ^ 1]);
-    load_src(tile + 2 * (int64_t)gridDim.x, after);
-    cp_async_wait<1>();  // this tile's copies have landed
-    __syncwarp();
-    const int64_t k = tile * BLK + threadIdx.x;
-    if (k < a.ng && !(a.skip_outer && (a.oct[k] & kGfcOuter)))
-      gfc_ghost<Q, S>(a, stage[cur] + grp * NSLOT * PSTR, oct, k);
-    __syncwarp();  // the stage is refilled in the next iteration
-#pragma unroll
-    for (int q = 0; q < 4; ++q) nxt[q] = after[q];
-  }
-  cp_async_wait<0>();
 }
 
 // ----------------------------------------------------------------- GhostFromFiner
@@ -1556,25 +1475,8 @@ struct Launch {
     with_q(Q, [&](auto q) {
       constexpr int QQ = decltype(q)::value;
       const unsigned g = blocks_for(a.ng, LBM_GFC_BLOCK);
-      if (a.mom2) {
-        k_fill_gfc<QQ, S, true><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
-      } else if (LBM_GFC_PIPE) {
-        // persistent: as many blocks as fit on the device at once
-        constexpr int BLK = GfcPipe<typename Sto<S>::R>::BLK;
-        static int per_sm = 0, sms = 0;
-        if (!per_sm) {
-          int dev = 0;
-          cudaGetDevice(&dev);
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fill_gfc_pipe<QQ, S>, BLK, 0);
-          if (per_sm < 1) per_sm = 1;
-        }
-        const int64_t tiles = (a.ng + BLK - 1) / BLK;
-        const unsigned gp = (unsigned)std::min<int64_t>(tiles, (int64_t)per_sm * sms);
-        k_fill_gfc_pipe<QQ, S><<<gp, BLK, 0, st>>>(a);
-      } else {
-        k_fill_gfc<QQ, S, false><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
-      }
+      if (a.mom2) k_fill_gfc<QQ, S, true><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
+      else k_fill_gfc<QQ, S, false><<<g, LBM_GFC_BLOCK, 0, st>>>(a);
     });
   }
   static void fill_gff(int Q, const GffArgs& a, cudaStream_t st) {

@@ -311,6 +311,64 @@ def test_graph_steps_match_eager_steps(lbm, precision, mode):
     assert np.array_equal(a.get_state(), b.get_state())
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_records_follow_state_changes(lbm, mode):
+    """The stream-collide keeps the GhostFromCoarser source records of the
+    state it writes; anything else that changes the state, the force or the
+    relaxation rates must make the next step rebuild them.  A context that has
+    been stepping (records current) and then takes lbm_set_state,
+    lbm_set_force or lbm_set_params continues bit for bit like a fresh context
+    given the same state and parameters, through the eager and the graph path
+    (FP64, whose state round trip is exact)."""
+    precision = 0
+    m = W.config_tgv3d(16)
+    rho, u, S = W.tgv_fields(m, 0.01)
+    df = W.pdf_perturbation(m, 19)
+    F1, F2 = W.gaussian_force(m, 1e-5), 2.0 * W.gaussian_force(m, 1e-5)
+
+    def sim(om=1.6):
+        s_ = lbm.Sim(m, 19, om, precision=precision, time_mode=mode, use_force=True)
+        s_.set_force(F1)
+        return s_
+
+    a = sim()
+    a.init(rho, u, S, df)
+    a.step(3)
+    other = sim()
+    other.init(rho, -u, S, df)
+    other.step(2)
+    y = other.get_state()
+    # a new state
+    a.set_state(y)
+    a.step(1)
+    a.step(2)
+    b = sim()
+    b.set_state(y)
+    b.step(1)
+    b.step(2)
+    assert np.array_equal(a.get_state(), b.get_state())
+    # a new force
+    x = a.get_state()
+    a.set_force(F2)
+    a.step(2)
+    a.step(1)
+    c = sim()
+    c.set_state(x)
+    c.set_force(F2)
+    c.step(2)
+    c.step(1)
+    assert np.array_equal(a.get_state(), c.get_state())
+    # new relaxation rates
+    x = a.get_state()
+    a.set_params(1.5)
+    a.step(2)
+    d = sim(1.5)
+    d.set_state(x)
+    d.set_force(F2)
+    d.step(2)
+    assert np.array_equal(a.get_state(), d.get_state())
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 def test_q27_reduced_precision_tracks_fp64(lbm, oracle_mod, precision):
     """D3Q27 with FP32 / BF16 deviation storage on the two-level 16^3 Taylor-Green
