@@ -664,17 +664,23 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, BND ? LBM_BR_BND_MINB(Q, S) : (M
 // kernel, element by element.
 // Four blocks per SM (64 registers) for D2Q9 / D3Q19, three for D3Q27 (which
 // spills at four).
+#ifndef LBM_PAIR_STCS
+#define LBM_PAIR_STCS 1
+#endif
+#ifndef LBM_BR_PAIR_BLOCK
+#define LBM_BR_PAIR_BLOCK 256
+#endif
 #ifndef LBM_BR_PAIR_MINB_Q19
 #define LBM_BR_PAIR_MINB_Q19 4
 #endif
 #define LBM_BR_PAIR_MINB(Q) ((Q) > 19 ? 3 : LBM_BR_PAIR_MINB_Q19)
 template <int Q, bool FORCE>
-__global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_BR_PAIR_MINB(Q)) k_stream_collide_brick_pair(const BrickArgs a) {
+__global__ void __launch_bounds__(LBM_BR_PAIR_BLOCK, LBM_BR_PAIR_MINB(Q)) k_stream_collide_brick_pair(const BrickArgs a) {
   using S = __nv_bfloat16;
   using R = float;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
-  constexpr int BPB = LBM_BR_BLOCK / 32;
+  constexpr int BPB = LBM_BR_PAIR_BLOCK / 32;
   const int m = threadIdx.x & 31;
   // one brick per warp: the exit below and the shuffles run with whole warps
   const int64_t b = (int64_t)blockIdx.x * BPB + (threadIdx.x >> 5);
@@ -726,7 +732,7 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_BR_PAIR_MINB(Q)) k_stream_co
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(g0[i], g1[i]);
-#if LBM_SC_STREAM
+#if LBM_SC_STREAM && LBM_PAIR_STCS
     __stcs(reinterpret_cast<unsigned int*>(dst + i * N), *reinterpret_cast<const unsigned int*>(&p));
 #else
     *reinterpret_cast<__nv_bfloat162*>(dst + i * N) = p;
@@ -1418,9 +1424,9 @@ struct Launch {
         // (on levels without GFC sources; the others take the one-element
         // kernel with its record epilogue)
         if (!boundary && !moms) {
-          const unsigned g2 = blocks_for(a.nB, LBM_BR_BLOCK / 32);
-          if (force) k_stream_collide_brick_pair<QQ, true><<<g2, LBM_BR_BLOCK, 0, st>>>(a);
-          else k_stream_collide_brick_pair<QQ, false><<<g2, LBM_BR_BLOCK, 0, st>>>(a);
+          const unsigned g2 = blocks_for(a.nB, LBM_BR_PAIR_BLOCK / 32);
+          if (force) k_stream_collide_brick_pair<QQ, true><<<g2, LBM_BR_PAIR_BLOCK, 0, st>>>(a);
+          else k_stream_collide_brick_pair<QQ, false><<<g2, LBM_BR_PAIR_BLOCK, 0, st>>>(a);
           return;
         }
       }
