@@ -24,6 +24,9 @@ namespace dev {
 
 // Minimum resident blocks per SM of the reverse kernels (0: only the block
 // size is given to __launch_bounds__).
+#ifndef LBM_ADJ_PHASES
+#define LBM_ADJ_PHASES 0
+#endif
 #ifndef LBM_ADJ_SC_MINB
 #define LBM_ADJ_SC_MINB 2
 #endif
@@ -434,6 +437,17 @@ __global__ void __launch_bounds__(256, LBM_ADJ_SC_MINB) k_adj_sc(const AdjSCArgs
     bgk_rev<Q, R>(g, lo, F, om, rho_off, base, sa, lF, lom);
     part[0] += lom;
     add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
+    // the adjoints of the pulled pdfs replace lo (which nothing reads after)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      R lg = (R(1) - om) * lo[i] + base;
+#pragma unroll
+      for (int b = 0; b < D; ++b) lg += sa[b] * R(LT::c(i, b));
+      lo[i] = lg;
+    }
+#if LBM_ADJ_PHASES
+    asm volatile("" ::: "memory");
+#endif
     // reverse streaming
     auto target = [&](int i) -> size_t {
       const uint32_t n = nb[i];
@@ -447,9 +461,7 @@ __global__ void __launch_bounds__(256, LBM_ADJ_SC_MINB) k_adj_sc(const AdjSCArgs
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      R lg = (R(1) - om) * lo[i] + base;
-#pragma unroll
-      for (int b = 0; b < D; ++b) lg += sa[b] * R(LT::c(i, b));
+      const R lg = lo[i];
       const uint32_t n = nb[i];
       lam_out[(size_t)i * N + e] = R(0);
       if (i > 0 && n >= NB_FLAG30 && !(n & NB_BOUNCE)) {
@@ -500,16 +512,18 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_ADJ_BRICK_MINB) k_adj_sc_bri
     const S* __restrict__ x = static_cast<const S*>(a.c.fsrc) + first;
     R* __restrict__ lam_out = static_cast<R*>(a.c.lam_a);
     R* __restrict__ lam_in = static_cast<R*>(a.c.lam_b) + first;
-    // pull source of link i, relative to the brick's first element
-    auto src_of = [&](int i) -> int64_t {
-      if (i == 0) return l;
+    // pull source of link i: row i of the state, at this 32-bit offset from
+    // the brick's first element (kept, not the 64-bit addresses)
+    int32_t off[Q];
+    off[0] = l;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
       const uint32_t v = (tw[(i - 1) >> 1] >> (((i - 1) & 1) * 16)) & 0xffffu;
-      const int32_t r = __shfl_sync(0xffffffffu, row, (int)(v >> 6));
-      return (int64_t)(i * N) + r + (v & 63);
-    };
+      off[i] = __shfl_sync(0xffffffffu, row, (int)(v >> 6)) + (int32_t)(v & 63);
+    }
     R g[Q], lo[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = Sto<S>::ld(x + src_of(i));
+    for (int i = 0; i < Q; ++i) g[i] = Sto<S>::ld(x + (int64_t)(i * N) + off[i]);
 #pragma unroll
     for (int i = 0; i < Q; ++i) lo[i] = lam_out[(size_t)i * N + e];
     R F[3];
@@ -519,16 +533,25 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_ADJ_BRICK_MINB) k_adj_sc_bri
     bgk_rev<Q, R>(g, lo, F, om, R(a.c.rho_off), base, sa, lF, lom);
     part[0] += lom;
     add_force<R>(a.c.lam_force, a.c.Ntot, e, lF, D);
-    R cur[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) cur[i] = lam_in[src_of(i)];
+    // the adjoints of the pulled pdfs replace lo (which nothing reads after)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       R lg = (R(1) - om) * lo[i] + base;
 #pragma unroll
       for (int b = 0; b < D; ++b) lg += sa[b] * R(LT::c(i, b));
+      lo[i] = lg;
+    }
+#if LBM_ADJ_PHASES
+    // keep the read-modify-write loads after the reverse collision
+    asm volatile("" ::: "memory");
+#endif
+    R cur[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) cur[i] = lam_in[(int64_t)(i * N) + off[i]];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
       lam_out[(size_t)i * N + e] = R(0);
-      lam_in[src_of(i)] = cur[i] + lg;
+      lam_in[(int64_t)(i * N) + off[i]] = cur[i] + lo[i];
     }
   }
   store_partials<R, 1>(part, a.c);
