@@ -22,41 +22,25 @@
 namespace lbm {
 namespace dev {
 
-// Minimum resident blocks per SM of the reverse kernels (0: only the block
-// size is given to __launch_bounds__).
-#ifndef LBM_ADJ_PHASES
-#define LBM_ADJ_PHASES 0
-#endif
+// Minimum resident blocks per SM of the reverse kernels with 4-byte compute
+// type (FP64 keeps the lower counts, its registers being twice as many).
+// Measured on the two-level TGV adjoint (FP32 deviation, 400 steps): three
+// blocks of brick reverse (80 registers), two of GhostFromFiner reverse and
+// four of moments reverse (128 registers, small spills) 0.214 s against
+// 0.219 s with the compiler's choice; the list reverse spills 600 B at three.
 #ifndef LBM_ADJ_SC_MINB
 #define LBM_ADJ_SC_MINB 2
 #endif
 #ifndef LBM_ADJ_BRICK_MINB
-#define LBM_ADJ_BRICK_MINB 2
+#define LBM_ADJ_BRICK_MINB 3
 #endif
 #ifndef LBM_ADJ_MOM_MINB
-#define LBM_ADJ_MOM_MINB 0
-#endif
-#ifndef LBM_ADJ_GFC_MINB
-#define LBM_ADJ_GFC_MINB 0
+#define LBM_ADJ_MOM_MINB 4
 #endif
 #ifndef LBM_ADJ_GFF_MINB
-#define LBM_ADJ_GFF_MINB 0
+#define LBM_ADJ_GFF_MINB 2
 #endif
-#if LBM_ADJ_MOM_MINB > 0
-#define LBM_ADJ_MOM_BOUNDS __launch_bounds__(128, LBM_ADJ_MOM_MINB)
-#else
-#define LBM_ADJ_MOM_BOUNDS __launch_bounds__(128)
-#endif
-#if LBM_ADJ_GFC_MINB > 0
-#define LBM_ADJ_GFC_BOUNDS __launch_bounds__(128, LBM_ADJ_GFC_MINB)
-#else
-#define LBM_ADJ_GFC_BOUNDS __launch_bounds__(128)
-#endif
-#if LBM_ADJ_GFF_MINB > 0
-#define LBM_ADJ_GFF_BOUNDS __launch_bounds__(256, LBM_ADJ_GFF_MINB)
-#else
-#define LBM_ADJ_GFF_BOUNDS __launch_bounds__(256)
-#endif
+#define LBM_ADJ_MINB(S, M, M64) (sizeof(typename Sto<S>::R) == 8 ? (M64) : (M))
 
 // ----------------------------------------------------------------- reverse helpers
 // Reverse of g^eq_i(rp, rho = rho_off + rp, u) for all i, weighted by lam[i]:
@@ -392,7 +376,7 @@ __global__ void __launch_bounds__(256) k_adj_seed(const AdjSeedArgs a) {
 // is added to the slot the forward pulled from (a conflict-free scatter: each
 // slot has one reader), or to the adjoint of the outlet value it came from.
 template <int Q, class S>
-__global__ void __launch_bounds__(256, LBM_ADJ_SC_MINB) k_adj_sc(const AdjSCArgs a) {
+__global__ void __launch_bounds__(256, LBM_ADJ_MINB(S, LBM_ADJ_SC_MINB, 2)) k_adj_sc(const AdjSCArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -445,9 +429,6 @@ __global__ void __launch_bounds__(256, LBM_ADJ_SC_MINB) k_adj_sc(const AdjSCArgs
       for (int b = 0; b < D; ++b) lg += sa[b] * R(LT::c(i, b));
       lo[i] = lg;
     }
-#if LBM_ADJ_PHASES
-    asm volatile("" ::: "memory");
-#endif
     // reverse streaming
     auto target = [&](int i) -> size_t {
       const uint32_t n = nb[i];
@@ -490,7 +471,7 @@ __global__ void __launch_bounds__(256, LBM_ADJ_SC_MINB) k_adj_sc(const AdjSCArgs
 // row b.
 static_assert(LBM_BR_BLOCK / 64 == LBM_BRICKS_PER_BLOCK, "host sizes the running rows by this many bricks per block");
 template <int Q, class S>
-__global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_ADJ_BRICK_MINB) k_adj_sc_brick(const AdjSCArgs a) {
+__global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_ADJ_MINB(S, LBM_ADJ_BRICK_MINB, 2)) k_adj_sc_brick(const AdjSCArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D;
@@ -541,10 +522,6 @@ __global__ void __launch_bounds__(LBM_BR_BLOCK, LBM_ADJ_BRICK_MINB) k_adj_sc_bri
       for (int b = 0; b < D; ++b) lg += sa[b] * R(LT::c(i, b));
       lo[i] = lg;
     }
-#if LBM_ADJ_PHASES
-    // keep the read-modify-write loads after the reverse collision
-    asm volatile("" ::: "memory");
-#endif
     R cur[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) cur[i] = lam_in[(int64_t)(i * N) + off[i]];
@@ -634,7 +611,7 @@ __global__ void __launch_bounds__(256) k_adj_outlet(const AdjOutletArgs a) {
 
 // ----------------------------------------------------------------- source moments
 template <int Q, class S>
-__global__ void LBM_ADJ_MOM_BOUNDS k_adj_moments(const AdjMomArgs a) {
+__global__ void __launch_bounds__(128, LBM_ADJ_MINB(S, LBM_ADJ_MOM_MINB, 1)) k_adj_moments(const AdjMomArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
@@ -692,7 +669,7 @@ __global__ void LBM_ADJ_MOM_BOUNDS k_adj_moments(const AdjMomArgs a) {
 
 // ----------------------------------------------------------------- GhostFromCoarser
 template <int Q, class S>
-__global__ void LBM_ADJ_GFC_BOUNDS k_adj_gfc(const AdjGfcArgs a) {
+__global__ void __launch_bounds__(128) k_adj_gfc(const AdjGfcArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   using RL = RecLayout<Q>;
@@ -827,7 +804,7 @@ __global__ void __launch_bounds__(128) k_adj_gather(const AdjGatherArgs a) {
 
 // ----------------------------------------------------------------- GhostFromFiner
 template <int Q, class S>
-__global__ void LBM_ADJ_GFF_BOUNDS k_adj_gff(const AdjGffArgs a) {
+__global__ void __launch_bounds__(256, LBM_ADJ_MINB(S, LBM_ADJ_GFF_MINB, 1)) k_adj_gff(const AdjGffArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
   constexpr int D = LT::D, NS = LT::NS, NCH = 1 << D;
