@@ -205,9 +205,10 @@ lbm_status lbm_set_force(lbm_ctx* ctx, const double* F);
 /* Advance n_coarse coarse time steps (Sec. 2.2 recursive level stepping:
  * GhostFromFiner, then GhostFromCoarser, then stream+collide on the level, then
  * two substeps of the next finer level).  Pairs of coarse steps replay a CUDA
- * graph captured on first use (one per A/B parity state; dropped by
- * lbm_set_params and lbm_bind) on the bound stream; a remaining single step,
- * and all steps in timing mode 1, are launched kernel by kernel.  Both paths
+ * graph captured on first use, a remaining single step a one-step graph (one
+ * of each per A/B parity state; dropped by lbm_set_params and lbm_bind), on
+ * the bound stream; in timing mode 1 every step is launched kernel by kernel
+ * (the adjoint's recomputed steps too).  Both paths
  * issue the same kernels; in the graphs the three stream-collide kernels of a
  * level (interior bricks, boundary bricks, neighbour list: disjoint elements,
  * the same source state) run as parallel branches, joined before the next op,
@@ -352,7 +353,7 @@ lbm_status lbm_kernel_launches(const lbm_ctx* ctx, int64_t* count);
  *  mode 0: off.
  *  mode 1: every launch of lbm_step is bracketed by events, and the steps are
  *          launched kernel by kernel, not replayed from graphs.
- *  mode 2: lbm_step keeps replaying its captured two-step graphs, which then
+ *  mode 2: lbm_step keeps replaying its captured graphs, which then
  *          also record events around the finest level's stream-collide
  *          launches (kinds 0-2) and around their whole group (kind 7: in the
  *          graphs a level's three stream-collide kernels run as parallel

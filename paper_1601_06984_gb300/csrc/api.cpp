@@ -354,9 +354,9 @@ bool lbm_ctx::make_level_streams() {
   return ok;
 }
 
-const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
+const lbm_ctx::StepGraph* lbm_ctx::step_graph(int nsteps) {
   for (const StepGraph& g : graphs)
-    if (g.parity == parity) return &g;
+    if (g.parity == parity && g.steps == nsteps) return &g;
   if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     graphs_on = false;
@@ -370,9 +370,9 @@ const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
   const int64_t l0 = launches;
   if (timing == 2) {
     // events for the finest level's stream-collide launches and their span
-    // (up to four pairs per substep, 2^(nlev-1) substeps per coarse step, two
-    // coarse steps), made before the capture begins
-    for (int k = 0; k < 2 * 4 * 2 * (1 << (nlev - 1)); ++k) event_pool.push_back(get_event());
+    // (up to four pairs per substep, 2^(nlev-1) substeps per coarse step),
+    // made before the capture begins
+    for (int k = 0; k < nsteps * 4 * 2 * (1 << (nlev - 1)); ++k) event_pool.push_back(get_event());
   }
   const size_t t0 = timed.size();
   cudaStream_t user = st;
@@ -381,8 +381,7 @@ const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
   cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     capturing = true;
-    advance(0);
-    advance(0);
+    for (int k = 0; k < nsteps; ++k) advance(0);
     capturing = false;
     e = cudaStreamEndCapture(cap_stream, &graph);
   }
@@ -391,7 +390,12 @@ const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
   timed.resize(t0);
   const int64_t nl = launches - l0;
   launches = l0;
-  const bool same = parity == p0;
+  // two steps bring every level back to its buffer; one step flips the
+  // coarsest level's (the finer levels take an even number of substeps)
+  std::vector<int> expect = p0;
+  if (nsteps == 1) expect[0] ^= 1;
+  const std::vector<int> p1 = parity;
+  const bool same = p1 == expect;
   parity = p0;
   cudaGraphExec_t exec = nullptr;
   if (e == cudaSuccess && graph && same) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -405,7 +409,7 @@ const lbm_ctx::StepGraph* lbm_ctx::step_graph() {
     graphs_on = false;
     return nullptr;
   }
-  graphs.push_back({p0, exec, nl, std::move(gt)});
+  graphs.push_back({p0, p1, nsteps, exec, nl, std::move(gt)});
   return &graphs.back();
 }
 
@@ -756,18 +760,20 @@ lbm_status lbm_ctx::run_steps(int64_t n_coarse) { return step_run(this, n_coarse
 static lbm_status step_run(lbm_ctx* c, int64_t n_coarse) {
   int64_t k = 0;
   if (n_coarse > 0) c->ensure_records();  // outside any capture
-  // pairs of coarse steps replay a captured graph; a single step, timed
-  // steps and the adjoint's recorded steps are issued one kernel at a time
+  // pairs of coarse steps replay a captured two-step graph and a remaining
+  // single step a one-step graph; timed steps (mode 1) and the adjoint's
+  // recorded steps are issued one kernel at a time
   if (c->graphs_on && c->timing != 1 && !c->hook && !c->dry) {
-    while (n_coarse - k >= 2) {
-      const lbm_ctx::StepGraph* g = c->step_graph();
+    while (k < n_coarse) {
+      const lbm_ctx::StepGraph* g = c->step_graph(n_coarse - k >= 2 ? 2 : 1);
       if (!g) break;
       lbm_status s = c->cuda_check(cudaGraphLaunch(g->exec, c->st), "graph launch");
       if (s != LBM_OK) return s;
       c->launches += g->launches;
+      c->parity = g->end;
       c->last_graph = (int)(g - c->graphs.data());
       c->graph_unread = true;
-      k += 2;
+      k += g->steps;
     }
   }
   for (; k < n_coarse; ++k) c->coarse_step();

@@ -122,10 +122,12 @@ struct lbm_ctx {
     timed.clear();
   }
   // CUDA graphs of two coarse steps (every level's A/B parity is back where it
-  // started after two coarse steps), one per starting parity state; kernel
-  // arguments are baked in, so any change of them drops the graphs
+  // started after two coarse steps) or of one, per starting parity state;
+  // kernel arguments are baked in, so any change of them drops the graphs
   struct StepGraph {
-    std::vector<int> parity;
+    std::vector<int> parity;  // at the start
+    std::vector<int> end;     // after the replay
+    int steps;
     cudaGraphExec_t exec;
     int64_t launches;
     std::vector<Timed> timed;  // event pairs recorded by the graph (timing mode 2)
@@ -229,9 +231,10 @@ struct lbm_ctx {
     ensure_records();
     advance(0);
   }
-  // graph of two coarse steps from the current parity state, captured on
-  // first use; null when capture is unavailable (the caller steps eagerly)
-  const StepGraph* step_graph();
+  // graph of nsteps (1 or 2) coarse steps from the current parity state,
+  // captured on first use; null when capture is unavailable (the caller
+  // steps eagerly)
+  const StepGraph* step_graph(int nsteps);
   // n coarse steps as lbm_step issues them (graph replay for pairs of steps)
   lbm_status run_steps(int64_t n_coarse);
 };

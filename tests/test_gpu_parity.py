@@ -284,7 +284,8 @@ def test_checkpoint_restart(lbm, precision):
 
 @pytest.mark.parametrize("precision,mode", [(0, 0), (1, 1), (2, 0)])
 def test_graph_steps_match_eager_steps(lbm, precision, mode):
-    """lbm_step(n >= 2) replays captured two-step graphs; one step at a time is
+    """lbm_step replays captured graphs (two-step graphs for pairs of steps, a
+    one-step graph for a remaining step); in timing mode 1 every step is
     launched kernel by kernel.  Same kernels, same order: bitwise equal states
     and equal launch counts, from either parity state, and after set_params
     (which must drop the captured steps)."""
@@ -295,10 +296,11 @@ def test_graph_steps_match_eager_steps(lbm, precision, mode):
     b = lbm.Sim(m, 19, 1.6, precision=precision, time_mode=mode)
     for s_ in (a, b):
         s_.init(rho, u, S, df)
+    b.timing_enable(1)  # kernel by kernel
     na, nb = a.kernel_launches(), b.kernel_launches()
-    a.step(1)
-    a.step(5)       # graph from the odd parity state, then one eager step
-    a.step(4)       # graph from the even parity state
+    a.step(1)       # one-step graph from the even parity state
+    a.step(5)       # two-step graphs from the odd parity state, then a one-step graph
+    a.step(4)       # two-step graphs from the even parity state
     for _ in range(10):
         b.step(1)
     assert np.array_equal(a.get_state(), b.get_state())
