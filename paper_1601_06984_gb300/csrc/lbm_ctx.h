@@ -149,10 +149,16 @@ struct lbm_ctx {
 #define LBM_CONCURRENT_SC 1
 #endif
   bool concurrent_sc = LBM_CONCURRENT_SC != 0;
+  // the finer level's GhostFromCoarser fill at t + 1/2 on the coarse level's
+  // stream-collide branch, beside the finer level's first substep (off:
+  // measured 35.5 against 32.8 ms per sphere step, the finest stream-collide
+  // slowed by its neighbour)
 #ifndef LBM_GFC_B_BRANCH
 #define LBM_GFC_B_BRANCH 0
 #endif
   bool gfc_b_branch = LBM_GFC_B_BRANCH != 0;
+  // a level's stream-collide as a graph branch of its own (on: 33.06 against
+  // 33.14 ms per sphere step with the level's three kernels forked either way)
 #ifndef LBM_LEVEL_BRANCH
 #define LBM_LEVEL_BRANCH 1
 #endif
@@ -235,7 +241,7 @@ struct lbm_ctx {
   // captured on first use; null when capture is unavailable (the caller
   // steps eagerly)
   const StepGraph* step_graph(int nsteps);
-  // n coarse steps as lbm_step issues them (graph replay for pairs of steps)
+  // n coarse steps as lbm_step issues them (graph replay unless timing mode 1)
   lbm_status run_steps(int64_t n_coarse);
 };
 
