@@ -636,27 +636,46 @@ lbm_status lbm_bind(lbm_ctx* c, void* ws, uint64_t bytes, void* stream) {
 lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* S, const double* df) {
   if (!c || !rho || !u) return LBM_ERR_ARG;
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_init before lbm_bind");
-  const int64_t n = c->M.n_user, CH = c->chunk;
+  const int64_t n = c->M.n_user;
   const int d = c->d, nS = c->nS, Q = c->Q;
-  double* sr = c->at<double>(c->oStage);
-  double* su = sr + CH;
-  double* sS = su + CH * d;
-  double* sdf = sS + CH * nS;
   // Every level starts in A.  The chunks are computed in caller order into B
   // (coalesced writes, B holds nothing that survives an init), then placed
   // into the element slots of A in slot order, and B is reset to rest.
+  // The staging area is used as two halves: the host copies of one half-chunk
+  // (on the context's copy stream) overlap the init kernel of the other.
   std::fill(c->parity.begin(), c->parity.end(), 0);
   c->reset_check();
-  for (int64_t first = 0; first < n; first += CH) {
+  const bool two = c->copy_stream_ready();
+  const int64_t CH = two ? (c->chunk + 1) / 2 : c->chunk;
+  const int64_t per = 1 + d + nS + Q;  // staged doubles per element
+  cudaStream_t cs = two ? c->copy_st : c->st;
+  if (two) {
+    // the staging area may still be read by earlier work on the bound stream
+    cudaEventRecord(c->copy_ev[2], c->st);
+    cudaStreamWaitEvent(cs, c->copy_ev[2], 0);
+  }
+  int64_t i = 0;
+  for (int64_t first = 0; first < n; first += CH, ++i) {
     const int64_t cnt = std::min(CH, n - first);
-    lbm_status s = c->cuda_check(cudaMemcpyAsync(sr, rho + first, cnt * 8, cudaMemcpyHostToDevice, c->st), "init copy");
+    const int half = two ? (int)(i & 1) : 0;
+    double* sr = c->at<double>(c->oStage) + (size_t)half * CH * per;
+    double* su = sr + CH;
+    double* sS = su + CH * d;
+    double* sdf = sS + CH * nS;
+    // this half's previous init kernel has read it
+    if (two && i >= 2) cudaStreamWaitEvent(cs, c->copy_ev[half], 0);
+    lbm_status s = c->cuda_check(cudaMemcpyAsync(sr, rho + first, cnt * 8, cudaMemcpyHostToDevice, cs), "init copy");
     if (s == LBM_OK)
-      s = c->cuda_check(cudaMemcpyAsync(su, u + first * d, cnt * d * 8, cudaMemcpyHostToDevice, c->st), "init copy");
+      s = c->cuda_check(cudaMemcpyAsync(su, u + first * d, cnt * d * 8, cudaMemcpyHostToDevice, cs), "init copy");
     if (s == LBM_OK && S)
-      s = c->cuda_check(cudaMemcpyAsync(sS, S + first * nS, cnt * nS * 8, cudaMemcpyHostToDevice, c->st), "init copy");
+      s = c->cuda_check(cudaMemcpyAsync(sS, S + first * nS, cnt * nS * 8, cudaMemcpyHostToDevice, cs), "init copy");
     if (s == LBM_OK && df)
-      s = c->cuda_check(cudaMemcpyAsync(sdf, df + first * Q, cnt * Q * 8, cudaMemcpyHostToDevice, c->st), "init copy");
+      s = c->cuda_check(cudaMemcpyAsync(sdf, df + first * Q, cnt * Q * 8, cudaMemcpyHostToDevice, cs), "init copy");
     if (s != LBM_OK) return s;
+    if (two) {
+      cudaEventRecord(c->copy_ev[3], cs);
+      cudaStreamWaitEvent(c->st, c->copy_ev[3], 0);
+    }
     InitArgs a{};
     a.temp = c->at(c->oB);
     a.ulev = c->at<uint8_t>(c->oUlev);
@@ -671,6 +690,7 @@ lbm_status lbm_init(lbm_ctx* c, const double* rho, const double* u, const double
     a.rho_off = c->rho_off;
     c->ops->init(Q, a, c->st);
     ++c->launches;
+    if (two) cudaEventRecord(c->copy_ev[half], c->st);
   }
   PlaceArgs pl{c->at(c->oB), c->at(c->oA), c->at<int32_t>(c->oSlotUser), n, c->M.Ntot};
   c->ops->init_place(Q, pl, c->st);

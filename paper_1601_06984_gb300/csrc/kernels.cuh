@@ -1339,8 +1339,26 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
   }
 }
 
+// Running sum of FP32 values kept as an unevaluated pair hi + lo (Knuth's
+// two-sum: hi + x is split exactly into its rounded value and the rounding
+// error, which lo collects): about twice the FP32 precision on the FP32
+// pipe, converted to FP64 once at the end.
+struct SumF2 {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // mass, momentum, obstacle force (momentum exchange, Sec. 2.3) and kinetic energy
 // of one level; one partial row per block, fixed grid -> deterministic order.
+// A thread sums its elements' moments (FP32 compute type: as two-float sums,
+// which keeps the FP64 pipe, GB300's narrow one, out of the per-element work;
+// FP64 storage: in FP64), then the block and grid sums are FP64.
 template <int Q, class S>
 __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
   using LT = Lat<Q>;
@@ -1353,6 +1371,8 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
   // stored values); the accumulation over elements in FP64
   // (the level volume and rho_off are applied once per thread below)
   using R = typename Sto<S>::R;
+  constexpr bool F2 = sizeof(R) == 4;
+  SumF2 sf[5];  // rp, rho u, kinetic energy (FP32 compute type)
   int64_t cnt = 0;
   for (int64_t e = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.end; e += stride) {
     R g[Q];
@@ -1365,15 +1385,31 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
       for (int b = 0; b < D; ++b) F[b] = static_cast<const R*>(a.force)[(size_t)b * N + e];
     const R rho = R(a.rho_off) + rp;
     R uu = R(0);
-    acc[0] += (double)rp;
+    R m[3] = {R(0), R(0), R(0)};
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-      const R m = j[b] - R(0.5) * F[b];  // rho u
-      acc[1 + b] += (double)m;
-      uu += m * m;
+      m[b] = j[b] - R(0.5) * F[b];  // rho u
+      uu += m[b] * m[b];
     }
-    acc[7] += (double)(R(0.5) * uu / rho);
+    const R ke = R(0.5) * uu / rho;
+    if constexpr (F2) {
+      sf[0].add(rp);
+#pragma unroll
+      for (int b = 0; b < D; ++b) sf[1 + b].add(m[b]);
+      sf[4].add(ke);
+    } else {
+      acc[0] += (double)rp;
+#pragma unroll
+      for (int b = 0; b < D; ++b) acc[1 + b] += (double)m[b];
+      acc[7] += (double)ke;
+    }
     ++cnt;
+  }
+  if constexpr (F2) {
+    acc[0] = sf[0].value();
+#pragma unroll
+    for (int b = 0; b < 3; ++b) acc[1 + b] = sf[1 + b].value();
+    acc[7] = sf[4].value();
   }
   acc[0] = a.vol * (acc[0] + (double)cnt * a.rho_off);
 #pragma unroll

@@ -145,6 +145,28 @@ struct lbm_ctx {
   };
   std::vector<LevelStreams> lvs;
   bool make_level_streams();
+  // copy stream of lbm_init's double-buffered host uploads: copy_ev[0..1]
+  // mark each staging half free again, [2] the bound stream's earlier work,
+  // [3] a half-chunk's copies done (made on first use; false if unavailable)
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool copy_tried = false;
+  bool copy_stream_ready() {
+    if (!copy_tried) {
+      copy_tried = true;
+      bool ok = cudaStreamCreateWithFlags(&copy_st, cudaStreamNonBlocking) == cudaSuccess;
+      for (cudaEvent_t& e : copy_ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        if (copy_st) cudaStreamDestroy(copy_st);
+        for (cudaEvent_t& e : copy_ev)
+          if (e) cudaEventDestroy(e);
+        copy_st = nullptr;
+        for (cudaEvent_t& e : copy_ev) e = nullptr;
+      }
+    }
+    return copy_st != nullptr;
+  }
 #ifndef LBM_CONCURRENT_SC
 #define LBM_CONCURRENT_SC 1
 #endif
@@ -183,6 +205,9 @@ struct lbm_ctx {
     recycle_timed();
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (copy_st) cudaStreamDestroy(copy_st);
+    for (cudaEvent_t e : copy_ev)
+      if (e) cudaEventDestroy(e);
     for (auto& L : lvs) {
       for (cudaStream_t s : {L.sc, L.side[0], L.side[1]})
         if (s) cudaStreamDestroy(s);
