@@ -232,7 +232,10 @@ lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* S);
  * out[0] mass sum rho vol, out[1..3] momentum sum rho u vol, out[4..6] force on
  * solid obstacles by momentum exchange (Sec. 2.3, half-way bounce-back: each
  * link carries 2 c f*), in finest-level lattice units, out[7] kinetic energy
- * sum rho |u|^2 vol / 2; vol = 2^{-d (L - Lmin)}. */
+ * sum rho |u|^2 vol / 2; vol = 2^{-d (L - Lmin)}.  Each element's moments are
+ * formed in the storage's compute type; with FP32 compute (FP32 and BF16
+ * deviation storage) a thread's sum over its elements is kept as a two-float
+ * pair (about 48 bits), everything after that in FP64. */
 lbm_status lbm_reduce(lbm_ctx* ctx, double out[8]);
 
 /* lbm_reduce_noalloc: the same eight FP64 values as lbm_reduce, computed by the
