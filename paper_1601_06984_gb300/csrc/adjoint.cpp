@@ -16,6 +16,12 @@
 #include <vector>
 
 #include "lbm_ctx.h"
+
+// run the brick and neighbour-list reverse stream-collide of a level
+// concurrently (disjoint elements and scatter targets, rows of their own)
+#ifndef LBM_ADJ_CONCURRENT
+#define LBM_ADJ_CONCURRENT 1
+#endif
 #include "lbm_internal.h"
 
 using namespace lbm;
@@ -44,6 +50,7 @@ struct AdjLayout {
   bool tape_all = false;
   size_t state_bytes = 0, total = 0;
   int partial_rows = 0;  // running rows of the parameter sums: the largest grid of a reverse launch
+  int side_row0 = 0;     // first row of the neighbour-list reverse, which runs beside the brick reverse
 };
 
 // Copies the rows of level li's segment of a [Q][Ntot] state.
@@ -209,6 +216,10 @@ AdjLayout adj_layout(lbm_ctx* c, int64_t n, int K) {
   L.partial_rows = kAdjBlocks;
   for (int li = 0; li < c->nlev; ++li)
     L.partial_rows = std::max<int>(L.partial_rows, (int)((c->M.lv[li].nB + LBM_BRICKS_PER_BLOCK - 1) / LBM_BRICKS_PER_BLOCK));
+  // the neighbour-list reverse runs concurrently with the brick reverse, so
+  // its blocks add to rows of their own
+  L.side_row0 = LBM_ADJ_CONCURRENT ? L.partial_rows : 0;
+  if (LBM_ADJ_CONCURRENT) L.partial_rows += kAdjBlocks;
   L.partial = take((size_t)L.partial_rows * kAccCols * 8);
   L.acc = take(32 * 8);
   int64_t max_contrib = 0;
@@ -256,6 +267,26 @@ const AdjOps* adj_ops_for(int precision) {
   return adj_ops_bf16dev();
 }
 
+// side stream and fork/join events of the concurrent reverse kernels (ok
+// false: not available, everything runs on the bound stream); released when
+// the adjoint returns (the driver releases pending resources when done)
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool ok = false;
+  SideStream() {
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+  }
+  ~SideStream() {
+    if (s) cudaStreamDestroy(s);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+  }
+};
+
 }  // namespace
 
 extern "C" {
@@ -302,6 +333,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
   if (reinterpret_cast<uintptr_t>(adj_ws) % kAlign) return c->fail(LBM_ERR_ARG, "adjoint workspace not aligned");
   char* W = static_cast<char*>(adj_ws);
   cudaStream_t st = c->st;
+  SideStream side;
   const AdjOps* aops = adj_ops_for(c->p.precision);
   const bool fp64 = c->p.precision == LBM_FP64;
   const size_t N = (size_t)c->M.Ntot;
@@ -496,6 +528,12 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
         ab.nB = H.nB;
         ab.brick_nb = c->at<int32_t>(c->oBrickNb) + (size_t)H.brick_first * 27;
         ab.brick_tab = c->at<uint16_t>(c->oBrickTab);
+        // the neighbour-list reverse on the side stream, beside the brick reverse
+        const bool fork = LBM_ADJ_CONCURRENT && side.ok;
+        if (fork) {
+          cudaEventRecord(side.fork, st);
+          cudaStreamWaitEvent(side.s, side.fork, 0);
+        }
         aops->sc_brick(c->Q, ab, st);
         if (c->p.time_mode == LBM_TIME_TWO_LAYER) {
           a.begin = H.base + H.oC;
@@ -508,7 +546,12 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
           a.hole_at = a.end;
           a.hole_len = 0;
         }
-        aops->sc(c->Q, a, st);
+        a.c.partial = partial + (size_t)L.side_row0 * kAccCols;
+        aops->sc(c->Q, a, fork ? side.s : st);
+        if (fork) {
+          cudaEventRecord(side.join, side.s);
+          cudaStreamWaitEvent(st, side.join, 0);
+        }
         if (outlet) {
           for (int which = 0; which < (c->p.bouzidi ? 6 : 3); ++which) {
             AdjOutletArgs o{};
