@@ -144,7 +144,7 @@ Lattice make_lattice(int q) {
 }
 
 // ---------------------------------------------------------------- constants
-enum { TIME_LINEAR = 0, TIME_TWO_LAYER = 1 };
+enum { TIME_LINEAR = 0, TIME_TWO_LAYER = 1, TIME_DIFFUSIVE = 2 };
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY_IN = 2, BC_PRESSURE_OUT = 3 };
 enum Kind { FLUID = 0, GFC = 1, GFF = 2 };
 enum LinkKind { LK_SELF, LK_PULL, LK_BOUNCE, LK_INLET, LK_OUT_NORMAL, LK_OUT_EXTRAP };
@@ -187,6 +187,7 @@ template <class T>
 struct Level {
   int L = 0;
   T omega = T(0.0);
+  double uin_scale = 1.0;  // inlet velocity of this level per unit of the coarsest level's
   std::vector<Elem<T>> e;
   std::unordered_map<int64_t, int> at;
   std::unordered_set<int64_t> leaf, sub;
@@ -205,6 +206,10 @@ template <class T>
 struct Sim {
   Lattice lat;
   int d = 0, Q = 0, mode = TIME_LINEAR;
+  // time-step ratio dt_c / dt_f of a level interface: 2 with acoustic scaling
+  // (dt proportional to dx), 4 with the diffusive scaling (dt proportional to
+  // dx^2) that Sec. 2.2 mentions for the multi-layer scheme
+  double mt() const { return mode == TIME_DIFFUSIVE ? 4.0 : kM; }
   int64_t ext0[3] = {1, 1, 1};
   int bc[6] = {0, 0, 0, 0, 0, 0};
   double rho0 = 1.0;
@@ -371,9 +376,12 @@ struct Sim {
     lv.assign(Lmax - Lmin + 1, Level<T>());
     for (int li = 0; li < nlev(); ++li) lv[li].L = Lmin + li;
     // relaxation per level, Eq. (fneq_scale): 1/w_f - 1/2 = m (1/w_c - 1/2)
+    // (acoustic scaling).  Diffusive scaling keeps the lattice viscosity, so
+    // omega is the same on every level: the factor is dx_c^2 dt_f / (dx_f^2 dt_c)
     lv[0].omega = omega_c;
     for (int li = 1; li < nlev(); ++li)
-      lv[li].omega = T(1.0) / (T(0.5) + T(kM) * (T(1.0) / lv[li - 1].omega - T(0.5)));
+      lv[li].omega = T(1.0) / (T(0.5) + T(kM * kM / mt()) * (T(1.0) / lv[li - 1].omega - T(0.5)));
+    for (int li = 0; li < nlev(); ++li) lv[li].uin_scale = std::pow(kM / mt(), li);
     for (int64_t k = 0; k < n; ++k) {
       int li = L[k] - Lmin;
       for (int a = 0; a < d; ++a)
@@ -445,17 +453,19 @@ struct Sim {
         lv[li].e.push_back(std::move(g));
       }
     }
-    // GhostFromCoarser: all children of level L-1 fluid parents that touch the
-    // refined region; two fine layers around the fine fluid.
+    // GhostFromCoarser: all children of level L-1 fluid parents within R coarse
+    // cells of the refined region: two fine layers around the fine fluid
+    // (R = 1), four with diffusive scaling (R = 2), Sec. 2.2.
+    const int R = mode == TIME_DIFFUSIVE ? 2 : 1;
     for (int li = 1; li < nlev(); ++li) {
       int nparent = (int)lv[li - 1].e.size();
       for (int k = 0; k < nparent; ++k) {
         if (lv[li - 1].e[k].kind != FLUID) continue;
         const Coord P = lv[li - 1].e[k].x;
         bool touches = false;
-        for (int oz = (d == 3 ? -1 : 0); oz <= (d == 3 ? 1 : 0) && !touches; ++oz)
-          for (int oy = -1; oy <= 1 && !touches; ++oy)
-            for (int ox = -1; ox <= 1 && !touches; ++ox) {
+        for (int oz = (d == 3 ? -R : 0); oz <= (d == 3 ? R : 0) && !touches; ++oz)
+          for (int oy = -R; oy <= R && !touches; ++oy)
+            for (int ox = -R; ox <= R && !touches; ++ox) {
               Coord p{P[0] + ox, P[1] + oy, P[2] + oz};
               if (cell_state(li - 1, p, nullptr, nullptr) == CS_SUB) touches = true;
             }
@@ -466,12 +476,17 @@ struct Sim {
           int bit[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
           g.x = {2 * P[0] + bit[0], 2 * P[1] + bit[1], d == 3 ? 2 * P[2] + bit[2] : 0};
           for (int a = 0; a < 3; ++a) g.sgn[a] = (a < d && bit[a]) ? 1 : -1;
-          g.layer = 2;
-          for (int oz = (d == 3 ? -1 : 0); oz <= (d == 3 ? 1 : 0); ++oz)
-            for (int oy = -1; oy <= 1; ++oy)
-              for (int ox = -1; ox <= 1; ++ox) {
+          // layer: the Chebyshev distance to the nearest fine fluid (or more
+          // refined) cell, the outermost layer (2, or 4) also for farther ghosts
+          const int nlay = 2 * R;
+          g.layer = nlay;
+          for (int oz = (d == 3 ? -(nlay - 1) : 0); oz <= (d == 3 ? nlay - 1 : 0); ++oz)
+            for (int oy = -(nlay - 1); oy <= nlay - 1; ++oy)
+              for (int ox = -(nlay - 1); ox <= nlay - 1; ++ox) {
+                const int dist = std::max(std::abs(ox), std::max(std::abs(oy), std::abs(oz)));
+                if (dist == 0 || dist >= g.layer) continue;
                 int st = cell_state(li, Coord{g.x[0] + ox, g.x[1] + oy, g.x[2] + oz}, nullptr, nullptr);
-                if (st == CS_LEAF || st == CS_SUB) g.layer = 1;
+                if (st == CS_LEAF || st == CS_SUB) g.layer = dist;
               }
           // sources on level L-1 (Sec. 2.2): the parent H and, in the octant of
           // the ghost, K=(1,1,0), M=(1,0,1), N=(0,1,1) in 3D; in 2D the square
@@ -499,6 +514,7 @@ struct Sim {
     for (int li = 0; li < nlev(); ++li)
       for (auto& e : lv[li].e)
         e.processed = e.kind == FLUID || (e.kind == GFC && e.layer == 1 && mode == TIME_TWO_LAYER) ||
+                      (e.kind == GFC && e.layer <= 3 && mode == TIME_DIFFUSIVE) ||
                       (e.kind == GFF && e.layer == 1 && mode == TIME_LINEAR);
     // pull links (Sec. 2.1 streaming, Sec. 2.3 boundaries)
     for (int li = 0; li < nlev(); ++li) {
@@ -636,7 +652,7 @@ struct Sim {
         // velocity bounce-back (Ladd): f_i = f*_ib + 2 w_i rho0 (c_i.U) / c_s^2,
         // U = u_in times the profile factor at the boundary point
         T cu = T(0.0);
-        for (int a = 0; a < d; ++a) cu += T((double)lat.c[i][a]) * uinT[a];
+        for (int a = 0; a < d; ++a) cu += T((double)lat.c[i][a]) * uinT[a] * T(l.uin_scale);
         return e.f[ib] + T(6.0 * lat.w[i] * rho0 * lk.s) * cu;
       }
       case LK_OUT_NORMAL: {
@@ -719,7 +735,14 @@ struct Sim {
       }
       rho = rho / T((double)nch);
       for (int a = 0; a < d; ++a) u[a] = u[a] / T((double)nch);
-      // strain rate of every child in coarse lattice units: S_c = m S_f
+      if (mode == TIME_DIFFUSIVE) {
+        // to coarse lattice units: u_c = (dt_c / dt_f) / (dx_c / dx_f) u_f, and
+        // the density deviation (a pressure) scales with the square of that
+        const double us = mt() / kM;
+        rho = T(rho0) + T(us * us) * (rho - T(rho0));
+        for (int a = 0; a < d; ++a) u[a] = T(us) * u[a];
+      }
+      // strain rate of every child in coarse lattice units: S_c = (dt_c/dt_f) S_f
       auto S_c = [&](int b, int a1, int a2) {
         int idx;
         if (a1 == a2) idx = a1;
@@ -728,7 +751,7 @@ struct Sim {
           int lo = std::min(a1, a2), hi = std::max(a1, a2);
           idx = lo == 0 ? (hi == 1 ? 3 : 5) : 4;  // xy, xz, yz
         }
-        return T(kM) * mk[b].S[idx];
+        return T(mt()) * mk[b].S[idx];
       };
       // d/dx_c of a child quantity: (mean over children on the + side minus
       // mean on the - side) / (1/2)
@@ -747,7 +770,7 @@ struct Sim {
         }
         u[a] = u[a] - lap / T(32.0);
       }
-      const T scale = T(kM) * lf.omega / lc.omega;
+      const T scale = T(mt()) * lf.omega / lc.omega;
       for (int i = 0; i < Q; ++i) {
         T fn = scale * fneq[i] / T((double)nch);
         g.f[i] = feq(i, rho, u) + (T(1.0) - lc.omega) * fn;
@@ -819,6 +842,11 @@ struct Sim {
       fill_gfc(li + 1, qt, nullptr);
     }
     stream_collide(li);
+    if (li + 1 < nlev() && mode == TIME_DIFFUSIVE) {
+      // four fine substeps on the four ghost layers filled above
+      for (int k = 0; k < 4; ++k) advance(li + 1);
+      return;
+    }
     if (li + 1 < nlev()) {
       advance(li + 1);
       if (mode == TIME_LINEAR) {
@@ -980,8 +1008,15 @@ void Sim<T>::fill_gfc(int li, const std::vector<Mom<T>>& q0, const std::vector<M
       compact_velocity_2d<T>(g.sgn, us, Ss, u);
     T rho = T(0.0);
     for (int k = 0; k < 4; ++k) rho += T(lw[k]) * m[k].rho;
-    // step 4: rescale f^neq, omega_c f^neq_c / m = omega_f f^neq_f
-    const T scale = lc.omega / (T(kM) * lf.omega);
+    if (mode == TIME_DIFFUSIVE) {
+      // to fine lattice units (inverse of the GhostFromFiner conversion)
+      const double us = kM / mt();
+      rho = T(rho0) + T(us * us) * (rho - T(rho0));
+      for (int a = 0; a < d; ++a) u[a] = T(us) * u[a];
+    }
+    // step 4: rescale f^neq, omega_c f^neq_c / m = omega_f f^neq_f (m the
+    // time-step ratio)
+    const T scale = lc.omega / (T(mt()) * lf.omega);
     for (int i = 0; i < Q; ++i) {
       T fn = T(0.0);
       for (int k = 0; k < 4; ++k) fn += T(lw[k]) * m[k].fneq[i];
@@ -1008,7 +1043,7 @@ Sim<T>* create_sim(int stencil, int time_mode, const int* extent, const int* bc,
     return nullptr;
   };
   if (stencil != 9 && stencil != 19 && stencil != 27) return bail("stencil must be 9, 19 or 27");
-  if (time_mode != TIME_LINEAR && time_mode != TIME_TWO_LAYER) return bail("bad time mode");
+  if (time_mode != TIME_LINEAR && time_mode != TIME_TWO_LAYER && time_mode != TIME_DIFFUSIVE) return bail("bad time mode");
   s->lat = make_lattice(stencil);
   s->d = s->lat.d;
   s->Q = s->lat.Q;
@@ -1078,17 +1113,34 @@ void reduce_sim(const Sim<T>* s, T out[8]) {
     const auto& l = s->lv[li];
     const double vol = std::ldexp(1.0, -d * li);
     const double fscale = std::ldexp(1.0, (d - 1) * (s->nlev() - 1 - li));
+    // diffusive scaling: density deviation, momentum and kinetic energy in the
+    // coarsest level's lattice units, forces in the finest level's (the level's
+    // velocity unit is (mt/2)^li of the coarsest's; a force unit scales with
+    // dx^(d+1) / dt^2)
+    const bool dif = s->mode == TIME_DIFFUSIVE;
+    const double us = dif ? std::pow(s->mt() / kM, li) : 1.0;
+    const double fs = dif ? std::ldexp(1.0, (d - 3) * (s->nlev() - 1 - li)) : fscale;
     for (const auto& e : l.e) {
       if (e.kind != FLUID) continue;
       Mom<T> m;
       s->moments(e, l.omega, &m);
-      out[0] += T(vol) * m.rho;
-      T uu = T(0.0);
-      for (int a = 0; a < d; ++a) {
-        out[1 + a] += T(vol) * m.rho * m.u[a];
-        uu += m.u[a] * m.u[a];
+      if (dif) {
+        out[0] += T(vol) * (T(s->rho0) + T(us * us) * (m.rho - T(s->rho0)));
+        T uu = T(0.0);
+        for (int a = 0; a < d; ++a) {
+          out[1 + a] += T(vol * us) * m.rho * m.u[a];
+          uu += m.u[a] * m.u[a];
+        }
+        out[7] += T(0.5 * vol * us * us) * m.rho * uu;
+      } else {
+        out[0] += T(vol) * m.rho;
+        T uu = T(0.0);
+        for (int a = 0; a < d; ++a) {
+          out[1 + a] += T(vol) * m.rho * m.u[a];
+          uu += m.u[a] * m.u[a];
+        }
+        out[7] += T(0.5 * vol) * m.rho * uu;
       }
-      out[7] += T(0.5 * vol) * m.rho * uu;
       // momentum exchange on obstacle links (Sec. 2.3): the pdf f*_ib(x_b)
       // leaves toward the body and f_i(x_b) (the bounce-back value of the next
       // step) returns, so the link carries c_ib (f*_ib + f_i) to the body; with
@@ -1098,7 +1150,7 @@ void reduce_sim(const Sim<T>* s, T out[8]) {
         int ib = s->lat.opp[i];
         const T back = s->pull(l, e, i);
         for (int a = 0; a < d; ++a)
-          out[4 + a] += T(fscale * s->lat.c[ib][a]) * (e.f[ib] + back);
+          out[4 + a] += T(fs * s->lat.c[ib][a]) * (e.f[ib] + back);
       }
     }
   }

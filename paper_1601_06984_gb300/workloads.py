@@ -88,10 +88,11 @@ class Mesh:
         lv, cnt = np.unique(self.levels, return_counts=True)
         return {int(a): int(b) for a, b in zip(lv, cnt)}
 
-    def updates_per_coarse_step(self) -> int:
-        """Fine-substep weighted element updates, sum_L N_L 2^{L-Lmin}
-        (the workload weights of Sec. 3.1, Eq. weight)."""
-        return int(sum(c << (lv - self.lmin) for lv, c in self.level_counts().items()))
+    def updates_per_coarse_step(self, substeps: int = 2) -> int:
+        """Fine-substep weighted element updates, sum_L N_L m^{L-Lmin} (the
+        workload weights of Sec. 3.1, Eq. weight), m = 2 fine substeps per
+        coarse step (acoustic scaling) or 4 (diffusive scaling)."""
+        return int(sum(c * substeps ** (lv - self.lmin) for lv, c in self.level_counts().items()))
 
 
 def _grid(lo, hi):
@@ -313,6 +314,20 @@ def tgv_fields(mesh: Mesh, u0: float, rho0: float = 1.0, t: float = 0.0, nu: flo
         u = np.stack([ux, uy, np.zeros(n)], axis=1)
         S = np.stack([sxx, -sxx, np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)], axis=1)
     S = S * lvl_scale[:, None]
+    return rho, u, S
+
+
+def diffusive_units(mesh: Mesh, rho, u, S, rho0: float = 1.0):
+    """Fields given as the generators above return them (rho and u in the
+    coarsest level's lattice units, S in each level's units of acoustic
+    scaling, dt ~ dx) converted to each level's lattice units of diffusive
+    scaling (dt ~ dx^2): per level below the coarsest, velocity / 2, strain
+    rate / 4 (one more factor 1/2 here) and density deviation / 4."""
+    l = (mesh.levels.astype(np.int64) - mesh.lmin)
+    h = np.ldexp(1.0, -l)
+    rho = rho0 + (np.asarray(rho) - rho0) * h * h
+    u = np.asarray(u) * h[:, None]
+    S = None if S is None else np.asarray(S) * h[:, None]
     return rho, u, S
 
 
