@@ -259,7 +259,7 @@ OUTLETS = {"linear": 0, "zero-gradient": 1}
 
 
 def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_moments=False, outlet=0,
-            timing=2, breakdown=True, state=None):
+            timing=2, breakdown=True, state=None, time_mode=0):
     """Time K coarse steps after W_ warm-up steps, the way a caller's
     lbm_step(K) runs them: replaying the library's captured two-step CUDA
     graphs.  timing=2 has those graphs record CUDA events around the finest
@@ -267,14 +267,16 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     from the last replay of the timed region); timing=0 records none.  With
     breakdown, K more steps follow with every kernel bracketed by events
     (launched kernel by kernel) for the per-kind and per-level times.
-    state: post-collision pdfs [n, Q] to start from instead of the fields."""
+    state: post-collision pdfs [n, Q] to start from instead of the fields.
+    time_mode 2 (diffusive scaling) takes four substeps per coarser step."""
     import numpy as np
     import torch
 
     from paper_1601_06984_gb300 import lbm
-    U = mesh.updates_per_coarse_step()
+    msub = 4 if time_mode == 2 else 2
+    U = mesh.updates_per_coarse_step(msub)
     t_build = time.perf_counter()
-    sim = lbm.Sim(mesh, Q, om, precision=prec, u_in=uin, device=device, outlet=outlet)
+    sim = lbm.Sim(mesh, Q, om, precision=prec, u_in=uin, device=device, outlet=outlet, time_mode=time_mode)
     t_build = time.perf_counter() - t_build
     if state is None:
         rho, u, S = fields(mesh)
@@ -320,7 +322,7 @@ def run_gpu(mesh, Q, om, uin, fields, prec, K, W_, device, dist=None, want_momen
     # bricks at the brick rate, the rest at the neighbour-list rate, times its
     # substeps per coarse step
     brick_units = [int(64 * (info[li, 8] + info[li, 9])) for li in range(nlev)]
-    step_bytes = float(sum((1 << li) * (brick_units[li] * bytes_per_update(Q, prec, brick=True)
+    step_bytes = float(sum(msub ** li * (brick_units[li] * bytes_per_update(Q, prec, brick=True)
                                         + (info[li, 1] - brick_units[li]) * bytes_per_update(Q, prec))
                            for li in range(nlev)))
     # the finest level's stream-collide as one op: its three kernels run as
@@ -682,6 +684,26 @@ def main():
             "interior_fraction": r27["interior_fraction"], "reduce": r27["reduce"]}
         s27.close()
         del s27
+        torch.cuda.empty_cache()
+        # diffusive scaling (dt ~ dx^2) on the same mesh: four substeps per
+        # coarser step (256 on the finest level per coarse step), four
+        # GhostFromCoarser layers, omega 1.8 on every level, the inlet velocity
+        # halved per level; FP32 deviation storage
+        from paper_1601_06984_gb300 import workloads as Wk
+        sd, rd = run_gpu(mesh, Q, 1.8, uin, lambda m: Wk.diffusive_units(m, *fields(m)), lbm.FP32DEV, 2, 3,
+                         device, None, outlet=outlet, breakdown=False, time_mode=2)
+        fsc = rd["finest_sc"]
+        variants["diffusive_fp32dev"] = {
+            "mlups": rd["mlups"], "ms_per_step": rd["ms_per_step"], "steps": 2, "warmup": 3,
+            "updates_per_coarse_step": mesh.updates_per_coarse_step(4), "omega_all_levels": 1.8,
+            "kernel": rd["finest_kernel"], "finest_kernel_gbs": rd["finest_gbs"],
+            "finest_kernel_frac": None if rd["finest_gbs"] is None else rd["finest_gbs"] / peak,
+            "finest_sc_gbs": fsc["gbs"], "finest_sc_frac": None if fsc["gbs"] is None else fsc["gbs"] / peak,
+            "step_gbs_algorithmic": rd["step_bytes"] / (rd["ms_per_step"] * 1e-3) / 1e9,
+            "step_frac": rd["step_bytes"] / (rd["ms_per_step"] * 1e-3) / 1e9 / peak,
+            "device_gb": rd["device_gb"], "launches_per_step": rd["launches"] / 2, "reduce": rd["reduce"]}
+        sd.close()
+        del sd
         torch.cuda.empty_cache()
         # side workloads (working sets that fit in L2: launch- and latency-bound sizes)
         from paper_1601_06984_gb300 import workloads as Wk

@@ -59,7 +59,7 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_FP64 = 0, LBM_FP32DEV = 1, LBM_BF16DEV = 2 };
-enum { LBM_TIME_LINEAR = 0, LBM_TIME_TWO_LAYER = 1 };
+enum { LBM_TIME_LINEAR = 0, LBM_TIME_TWO_LAYER = 1, LBM_TIME_DIFFUSIVE = 2 };
 enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_VELOCITY_IN = 2, LBM_BC_PRESSURE_OUT = 3 };
 enum { LBM_OUTLET_LINEAR = 0, LBM_OUTLET_ZERO_GRADIENT = 1 };
 enum { LBM_INLET_UNIFORM = 0, LBM_INLET_PARABOLIC = 1 };
@@ -76,6 +76,15 @@ enum { LBM_INLET_UNIFORM = 0, LBM_INLET_PARABOLIC = 1 };
  *                from the mean of the coarse source moments at t and t+1.
  *                LBM_TIME_TWO_LAYER: two fine ghost layers filled at the synchronous
  *                step and advanced by the fine kernel (Sec. 2.2, last paragraph).
+ *                LBM_TIME_DIFFUSIVE: diffusive scaling, dt proportional to dx^2
+ *                (Sec. 2.2 names it as the case for more than two layers): four
+ *                fine substeps per coarse step, four fine ghost layers filled at
+ *                the synchronous step (the inner three advanced by the fine
+ *                kernel), omega the same on every level, and each level in its
+ *                own lattice units: for the same flow its velocity is 2^-l,
+ *                its density deviation and strain rate 4^-l times the coarsest
+ *                level's (l the level index from the coarsest).  The ghost
+ *                fills convert between them.
  *  extent        domain box in elements of the coarsest level present (unused axes 1).
  *  bc            per face x-, x+, y-, y+, z-, z+; PERIODIC must be set on both faces of
  *                an axis.  WALL = half-way bounce-back, VELOCITY_IN = velocity
@@ -83,9 +92,11 @@ enum { LBM_INLET_UNIFORM = 0, LBM_INLET_PARABOLIC = 1 };
  *                normal pdf pressure-corrected to rho0: f_i = f^eq_i(rho0, u) +
  *                f^neq_opp(i), f^neq the pre-collision non-equilibrium part (Sec. 2.3).
  *  omega_coarse  BGK relaxation rate on the coarsest level, in (0,2); finer levels
- *                follow 1/omega_f - 1/2 = 2 (1/omega_c - 1/2) (Sec. 2.2, Eq. fneq_scale).
+ *                follow 1/omega_f - 1/2 = 2 (1/omega_c - 1/2) (Sec. 2.2, Eq. fneq_scale),
+ *                except in LBM_TIME_DIFFUSIVE, where every level has omega_coarse.
  *  rho0          reference density (outlet density, deviation offset).
- *  u_in          inlet velocity (lattice units).
+ *  u_in          inlet velocity (lattice units of the coarsest level; in
+ *                LBM_TIME_DIFFUSIVE a level l inlet applies u_in 2^-l).
  *  use_force     nonzero: a per-element body force (Guo forcing) is applied.
  *  outlet        extrapolation of the outlet's tangential and oblique pdfs:
  *                LBM_OUTLET_LINEAR (0): 2 f(x - n) - f(x - 2n), as in Sec. 2.3;
@@ -232,7 +243,10 @@ lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* S);
  * out[0] mass sum rho vol, out[1..3] momentum sum rho u vol, out[4..6] force on
  * solid obstacles by momentum exchange (Sec. 2.3, half-way bounce-back: each
  * link carries 2 c f*), in finest-level lattice units, out[7] kinetic energy
- * sum rho |u|^2 vol / 2; vol = 2^{-d (L - Lmin)}.  Each element's moments are
+ * sum rho |u|^2 vol / 2; vol = 2^{-d (L - Lmin)}.  In LBM_TIME_DIFFUSIVE the
+ * mass, momentum and kinetic energy are in the coarsest level's lattice units
+ * (rho0 + 4^l (rho - rho0), 2^l rho u, 4^l rho |u|^2 / 2 per element of level
+ * index l) and the force in the finest level's.  Each element's moments are
  * formed in the storage's compute type; with FP32 compute (FP32 and BF16
  * deviation storage) a thread's sum over its elements is kept as a two-float
  * pair (about 48 bits), everything after that in FP64. */
@@ -313,7 +327,8 @@ lbm_status lbm_halo_plan(const lbm_ctx* ctx, const int32_t* part, int32_t nparts
                          int64_t* recv_count, int64_t* recv, int64_t recv_cap, int64_t* n_ghosts,
                          int64_t* ghosts, int64_t ghost_cap);
 
-/* Change the coarsest relaxation rate (finer levels follow Eq. fneq_scale) and,
+/* Change the coarsest relaxation rate (finer levels follow Eq. fneq_scale, or
+ * keep it in LBM_TIME_DIFFUSIVE) and,
  * if u_in is not NULL, the inlet velocity, without rebuilding the mesh.  The
  * state is kept. */
 lbm_status lbm_set_params(lbm_ctx* ctx, double omega_coarse, const double* u_in);
@@ -339,7 +354,8 @@ lbm_status lbm_set_params(lbm_ctx* ctx, double omega_coarse, const double* u_in)
  * lbm_adjoint_bytes(n_coarse, K) bytes owned by the caller.  Afterwards the
  * simulation is at the final state, as after lbm_step(n_coarse).  The
  * gradient with respect to F is that of the forced scheme (also when
- * use_force is 0, where it is taken at F = 0). */
+ * use_force is 0, where it is taken at F = 0).  LBM_TIME_DIFFUSIVE has no
+ * adjoint: both calls return LBM_ERR_STATE there. */
 lbm_status lbm_adjoint_bytes(lbm_ctx* ctx, int64_t n_coarse, int32_t K, uint64_t* bytes);
 /* The workspace holds, besides the adjoint buffers, ceil(n_coarse / K)
  * checkpoints and the final state, and (params.adjoint_tape) either K step

@@ -295,7 +295,7 @@ lbm_status lbm_set_params(lbm_ctx* c, double omega_coarse, const double* u_in) {
   if (!c || !(omega_coarse > 0.0 && omega_coarse < 2.0)) return LBM_ERR_ARG;
   std::vector<double> om(c->nlev);
   om[0] = omega_coarse;
-  for (int li = 1; li < c->nlev; ++li) om[li] = 1.0 / (0.5 + 2.0 * (1.0 / om[li - 1] - 0.5));
+  for (int li = 1; li < c->nlev; ++li) om[li] = finer_omega(om[li - 1], c->p.time_mode);
   for (int li = 0; li < c->nlev; ++li)
     if (std::fabs(1.0 - om[li]) < 1e-3) return c->fail(LBM_ERR_ARG, "omega too close to 1 on some level");
   c->drop_graphs();  // captured steps carry the old omega and inlet values
@@ -319,6 +319,7 @@ lbm_status lbm_set_params(lbm_ctx* c, double omega_coarse, const double* u_in) {
 lbm_status lbm_adjoint_bytes(lbm_ctx* c, int64_t n_coarse, int32_t K, uint64_t* bytes) {
   if (!c || !bytes || n_coarse < 1 || K < 1) return LBM_ERR_ARG;
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_adjoint_bytes before lbm_bind");
+  if (c->p.time_mode == LBM_TIME_DIFFUSIVE) return c->fail(LBM_ERR_STATE, "no adjoint in LBM_TIME_DIFFUSIVE");
   *bytes = adj_layout(c, n_coarse, K).total;
   return LBM_OK;
 }
@@ -327,6 +328,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int64_t n, int32_t K, int32_t objective, void
                        double* J, double* dJ_dF, double* dJ_domega, double* dJ_duin, double* dJ_df0) {
   if (!c || !adj_ws || n < 1 || K < 1 || objective < 0 || objective > 3) return LBM_ERR_ARG;
   if (!c->bound) return c->fail(LBM_ERR_STATE, "lbm_adjoint before lbm_bind");
+  if (c->p.time_mode == LBM_TIME_DIFFUSIVE) return c->fail(LBM_ERR_STATE, "no adjoint in LBM_TIME_DIFFUSIVE");
   if (objective > c->d) return c->fail(LBM_ERR_ARG, "force component beyond the dimension");
   const AdjLayout L = adj_layout(c, n, K);
   if (bytes < L.total) return c->fail(LBM_ERR_ARG, "adjoint workspace too small");

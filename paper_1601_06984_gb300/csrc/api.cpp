@@ -102,6 +102,12 @@ void lbm_ctx::fill_gff(int li) {
   a.omega_c = H.omega;
   a.omega_f = Hf.omega;
   a.rho_off = rho_off;
+  // fine -> coarse lattice units: u_c = (dt_c / dt_f) / 2 u_f, the density
+  // deviation with the square of that factor (1 in acoustic scaling)
+  a.tratio = time_ratio(p.time_mode);
+  a.u_scale = a.tratio / 2.0;
+  a.r_scale = a.u_scale * a.u_scale;
+  a.r_shift = (1.0 - a.r_scale) * (p.rho0 - rho_off);
   timed_launch(li, TK_GFF, [&] { ops->fill_gff(Q, a, st); });
   ++launches;
 }
@@ -152,6 +158,11 @@ void lbm_ctx::fill_gfc(int lf, bool two_times, bool all_layers, cudaStream_t s, 
   a.omega_f = H.omega;
   a.rho_off = rho_off;
   a.skip_outer = !all_layers && p.time_mode == LBM_TIME_LINEAR;
+  // coarse -> fine lattice units, the inverse of the GhostFromFiner conversion
+  a.tratio = time_ratio(p.time_mode);
+  a.u_scale = 2.0 / a.tratio;
+  a.r_scale = a.u_scale * a.u_scale;
+  a.r_shift = (1.0 - a.r_scale) * (p.rho0 - rho_off);
   timed_launch(lf, TK_GFC, [&] { ops->fill_gfc(Q, a, s); }, s);
   ++launches;
 }
@@ -198,7 +209,9 @@ void lbm_ctx::stream_collide(int li, cudaStream_t s0) {
   b.nbr = at<uint32_t>(oNbr);
   b.side = at(oSide);
   b.inlet_s = at<double>(oInletS);
-  std::memcpy(b.inlet, inlet, sizeof(inlet));
+  // the inlet velocity in this level's lattice units
+  const double uin_unit = level_velocity_ratio(li, p.time_mode);
+  for (int i = 0; i < kQmax; ++i) b.inlet[i] = inlet[i] * uin_unit;
   // the level's GFC source records at t + 1 from the new state
   SourceOut so{};
   if (li + 1 < nlev && ld[li].nsrc > 0) {
@@ -211,8 +224,8 @@ void lbm_ctx::stream_collide(int li, cudaStream_t s0) {
   bb.nb = b.nb + (size_t)H.nB * 27;
   bb.begin = b.begin + 64 * H.nB;
   bb.nB = nbnd;
-  // the rest through the neighbour list; processed range: TWO_LAYER [GFC |
-  // fluid], LINEAR [fluid | GFF inner], minus the bricks
+  // the rest through the neighbour list; processed range: TWO_LAYER and
+  // DIFFUSIVE [GFC | fluid], LINEAR [fluid | GFF inner], minus the bricks
   StreamCollideArgs a{};
   a.src = cur(li);
   a.dst = nxt(li);
@@ -221,7 +234,7 @@ void lbm_ctx::stream_collide(int li, cudaStream_t s0) {
   a.side = at(oSide);
   a.inlet_s = at<double>(oInletS);
   a.Ntot = M.Ntot;
-  if (p.time_mode == LBM_TIME_TWO_LAYER) {
+  if (p.time_mode != LBM_TIME_LINEAR) {
     a.begin = H.base + H.oC;
     a.end = H.base + H.oG1 - nbrick;
     a.hole_at = H.base + H.oF;
@@ -234,7 +247,7 @@ void lbm_ctx::stream_collide(int li, cudaStream_t s0) {
   }
   a.omega = H.omega;
   a.rho_off = rho_off;
-  std::memcpy(a.inlet, inlet, sizeof(inlet));
+  std::memcpy(a.inlet, b.inlet, sizeof(a.inlet));
   a.so = so;
   const bool use_force = p.use_force != 0;
   auto launch = [&](int kernel, cudaStream_t s) {
@@ -335,7 +348,9 @@ void lbm_ctx::advance(int li) {
         source_moments(li, ld[li].momA[parity[li]], 0, nullptr, SRC_GFF_OUTER);
       if (op(OP_GFC_B, li + 1) && !gfc_b_on_branch) fill_gfc(li + 1, true);
     }
-    advance(li + 1);
+    // the remaining substeps (one in acoustic scaling; three with diffusive
+    // scaling, whose four ghost layers filled at t last all four)
+    for (int k = 1; k < time_ratio(p.time_mode); ++k) advance(li + 1);
   }
 }
 
@@ -370,9 +385,12 @@ const lbm_ctx::StepGraph* lbm_ctx::step_graph(int nsteps) {
   const int64_t l0 = launches;
   if (timing == 2) {
     // events for the finest level's stream-collide launches and their span
-    // (up to four pairs per substep, 2^(nlev-1) substeps per coarse step),
-    // made before the capture begins
-    for (int k = 0; k < nsteps * 4 * 2 * (1 << (nlev - 1)); ++k) event_pool.push_back(get_event());
+    // (up to four pairs per substep, m^(nlev-1) substeps per coarse step, m
+    // the time-step ratio), made before the capture begins (at most 2^16;
+    // further ones are made as they are needed)
+    int64_t nev = (int64_t)nsteps * 4 * 2;
+    for (int li = 1; li < nlev && nev < (1 << 16); ++li) nev *= time_ratio(p.time_mode);
+    for (int64_t k = 0; k < std::min<int64_t>(nev, 1 << 16); ++k) event_pool.push_back(get_event());
   }
   const size_t t0 = timed.size();
   cudaStream_t user = st;
@@ -436,6 +454,15 @@ lbm_status reduce_plan(lbm_ctx* c, ReducePlan* plan) {
     a.omega = H.omega;
     a.rho_off = c->rho_off;
     a.vol = std::ldexp(1.0, -d * li);
+    // diffusive scaling: mass, momentum and kinetic energy in the coarsest
+    // level's units (a lattice velocity of level li is 2^li of the
+    // coarsest's), forces in the finest level's (a force unit goes with
+    // dx^(d+1) / dt^2)
+    const double us = 1.0 / level_velocity_ratio(li, c->p.time_mode);
+    a.vol_m = a.vol * us;
+    a.vol_k = a.vol * us * us;
+    a.r_scale = us * us;
+    a.rho0 = c->p.rho0;
     a.partial = nullptr;
     a.nblocks = kReduceBlocks;
     a.obs_elem = c->at<int32_t>(c->oObsElem) + H.obs_begin;
@@ -443,7 +470,7 @@ lbm_status reduce_plan(lbm_ctx* c, ReducePlan* plan) {
     a.obs_a = c->at<int32_t>(c->oObsA) + H.obs_begin;
     a.obs_q = c->at<double>(c->oObsQ) + H.obs_begin;
     a.obs_n = H.obs_end - H.obs_begin;
-    a.fscale = std::ldexp(1.0, (d - 1) * (c->nlev - 1 - li));
+    a.fscale = std::ldexp(1.0, (c->p.time_mode == LBM_TIME_DIFFUSIVE ? d - 3 : d - 1) * (c->nlev - 1 - li));
     plan->levels.push_back(a);
   }
   return LBM_OK;

@@ -900,8 +900,10 @@ __device__ __forceinline__ void compact_uloc(const R (&ul)[4][3], const R (&Sl)[
 //   u_a = 1/2 u_H + 1/4 (u_E + u_N) - 3/16 (q_xx + q_yy)_a + 1/16 q_xy,a,
 // the least-squares linear part over the square.  Density and f^neq are
 // linear (weights 5/8,1/8,1/8,1/8 resp. 9/16,3/16,3/16,1/16), f^neq is
-// rescaled by omega_c / (m omega_f), and f = f^eq + (1 - omega_f) f^neq is
-// stored as the ghost's post-collision state.
+// rescaled by omega_c / (m omega_f) (m = dt_c / dt_f), and f = f^eq +
+// (1 - omega_f) f^neq is stored as the ghost's post-collision state.  With
+// diffusive scaling the velocity and density deviation are converted to the
+// fine level's lattice units first.
 // Ghosts come in groups of 2^d consecutive siblings (the children of one
 // coarse parent, octant b = k mod 2^d), and their 4 x 2^d source records are
 // 13 distinct ones in 3D (the parent and its 12 edge neighbours), 9 in 2D.  A
@@ -963,19 +965,20 @@ __device__ __forceinline__ void gfc_ghost(const GfcArgs& a, const typename Sto<S
   compact_uloc<Q, R>(ul, Sl, uloc);
   R u[3] = {R(0), R(0), R(0)};
   R usq = R(0);
+  const R us = R(a.u_scale);  // to fine lattice units (1 in acoustic scaling)
 #pragma unroll
   for (int b = 0; b < D; ++b) {
-    u[b] = sg[b] * uloc[b];
+    u[b] = sg[b] * uloc[b] * us;
     usq += u[b] * u[b];
   }
   const R lw0 = D == 3 ? R(0.625) : R(0.5625);
   const R lw1 = D == 3 ? R(0.125) : R(0.1875);
   const R lw2 = D == 3 ? R(0.125) : R(0.1875);
   const R lw3 = D == 3 ? R(0.125) : R(0.0625);
-  const R rp = lw0 * rps[0] + lw1 * rps[1] + lw2 * rps[2] + lw3 * rps[3];
+  const R rp = R(a.r_scale) * (lw0 * rps[0] + lw1 * rps[1] + lw2 * rps[2] + lw3 * rps[3]) + R(a.r_shift);
   const R rho = R(a.rho_off) + rp;
   const R wf = R(a.omega_f);
-  const R scale = (R(1) - wf) * R(a.omega_c) / (R(2) * wf);
+  const R scale = (R(1) - wf) * R(a.omega_c) / (R(a.tratio) * wf);
   S* __restrict__ dst = static_cast<S*>(a.dst);
   const size_t N = (size_t)a.Ntot;
   const int64_t e = a.dest0 + k;
@@ -1071,7 +1074,9 @@ __global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
 // Density and f^neq: the children's mean.  Velocity: the children's mean minus
 // (1/32) lap u, with lap u_a = 2 d_c S_ac - d_a S_cc from the children's strain
 // rates (differences across the children's cube).  f^neq is rescaled by
-// m omega_f / omega_c; f = f^eq + (1 - omega_c) f^neq.
+// m omega_f / omega_c (m = dt_c / dt_f); f = f^eq + (1 - omega_c) f^neq.  With
+// diffusive scaling the mean velocity and density deviation are converted to
+// the coarse level's lattice units.
 // One group of 2^d consecutive lanes per ghost: lane b loads child b (siblings
 // are contiguous, so the group's loads are coalesced), and the sums over the
 // children are shuffles inside the group.
@@ -1112,10 +1117,13 @@ __global__ void LBM_GFF_BOUNDS k_fill_gff(const GffArgs a) {
   // values, and so is lap u_a = dfac sum_c (2 d_c S_ac - d_a S_cc) with d_c the
   // difference across the cube (+ for children with bit c set, - otherwise):
   // each lane forms its child's share and the group sums d + 1 values.
-  // d_c S (coarse units): S_coarse = 2 S_fine; difference of the two half-cubes
-  // over a distance of 1/2 coarse cell -> factor 2 * 2^{2-D}
+  // d_c S (coarse units): S_coarse = m S_fine (m = dt_c / dt_f); difference of
+  // the two half-cubes over a distance of 1/2 coarse cell -> factor m 2^{2-D}.
+  // The mean velocity goes to coarse units with u_scale (a power of two, so
+  // inv_u is exact).
   const R inv = R(1) / R(NCH);
-  const R dfac = R(2) * R(D == 3 ? 0.5 : 1.0);
+  const R inv_u = inv * R(a.u_scale);
+  const R dfac = R(a.tratio) * R(D == 3 ? 0.5 : 1.0);
   R rpm = rp * inv, uP[3] = {R(0), R(0), R(0)};
 #pragma unroll
   for (int aa = 0; aa < D; ++aa) {
@@ -1126,7 +1134,7 @@ __global__ void LBM_GFF_BOUNDS k_fill_gff(const GffArgs a) {
       const R sc = ((b >> c) & 1) ? R(1) : R(-1);
       lap += dfac * (R(2) * sc * Sv[sidx<D>(aa, c)] - sa * Sv[sidx<D>(c, c)]);
     }
-    uP[aa] = u[aa] * inv - lap * R(1.0 / 32.0);
+    uP[aa] = u[aa] * inv_u - lap * R(1.0 / 32.0);
   }
 #pragma unroll
   for (int o = 1; o < NCH; o <<= 1) {
@@ -1160,8 +1168,9 @@ __global__ void LBM_GFF_BOUNDS k_fill_gff(const GffArgs a) {
 #pragma unroll
   for (int aa = 0; aa < D; ++aa) usq += uP[aa] * uP[aa];
   const R wc = R(a.omega_c);
+  rpm = R(a.r_scale) * rpm + R(a.r_shift);  // to coarse units (unchanged in acoustic scaling)
   const R rho = rho_off + rpm;
-  const R scale = (R(1) - wc) * R(2) * wf / wc * inv;
+  const R scale = (R(1) - wc) * R(a.tratio) * wf / wc * inv;
   S* __restrict__ dst = static_cast<S*>(a.dst);
   const int64_t e = k < a.n_inner ? a.dest0 + k : a.dest_outer + (k - a.n_inner);
   // the group's lanes share the Q stores: lane b the directions j 2^d + b,
@@ -1411,10 +1420,13 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
     for (int b = 0; b < 3; ++b) acc[1 + b] = sf[1 + b].value();
     acc[7] = sf[4].value();
   }
-  acc[0] = a.vol * (acc[0] + (double)cnt * a.rho_off);
+  if (a.r_scale == 1.0)
+    acc[0] = a.vol * (acc[0] + (double)cnt * a.rho_off);
+  else  // density deviations in another level's units
+    acc[0] = a.vol * ((double)cnt * a.rho0 + a.r_scale * (acc[0] + (double)cnt * (a.rho_off - a.rho0)));
 #pragma unroll
-  for (int b = 0; b < 3; ++b) acc[1 + b] *= a.vol;
-  acc[7] *= a.vol;
+  for (int b = 0; b < 3; ++b) acc[1 + b] *= a.vol_m;
+  acc[7] *= a.vol_k;
   // momentum exchange (Sec. 2.3): the link carries c_ib (f*_ib(x) + f_i(x)) to
   // the body, f_i the bounce-back value of the next step (interpolated with
   // the wall distance q; q = 1/2 gives 2 c_ib f*_ib)

@@ -5,6 +5,7 @@
 #include <cuda_runtime_api.h>
 
 #include <climits>
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -52,6 +53,20 @@ inline void host_lattice(int Q, int c[kQmax][3], double w[kQmax]) {
   }
 }
 enum { OUT_NORMAL = 0, OUT_EXTRAP = 1, OUT_BOUZIDI = 2 };
+
+// Time scaling of a level interface (Sec. 2.2).  Acoustic scaling (LINEAR and
+// TWO_LAYER modes): dt_c / dt_f = 2, two fine substeps, and the relaxation
+// follows Eq. (fneq_scale), 1/w_f - 1/2 = 2 (1/w_c - 1/2).  Diffusive scaling
+// (dt proportional to dx^2): dt_c / dt_f = 4, four fine substeps, the lattice
+// viscosity and so omega the same on every level; a level's lattice velocity
+// is (dt/dx) times the physical one, so u_c = 2 u_f for the same flow, the
+// density deviation (a pressure) goes with u^2, and the strain rate with dt.
+inline int time_ratio(int mode) { return mode == LBM_TIME_DIFFUSIVE ? 4 : 2; }
+inline double finer_omega(double omega_c, int mode) {
+  return mode == LBM_TIME_DIFFUSIVE ? omega_c : 1.0 / (0.5 + 2.0 * (1.0 / omega_c - 0.5));
+}
+// the same flow's lattice velocity on level index li over that on the coarsest level
+inline double level_velocity_ratio(int li, int mode) { return mode == LBM_TIME_DIFFUSIVE ? std::ldexp(1.0, -li) : 1.0; }
 
 struct HostLevel {
   int L = 0;
@@ -215,6 +230,9 @@ struct GfcArgs {
   int64_t Ntot;
   double omega_c, omega_f, rho_off;
   int skip_outer;        // leave the outer-layer ghosts (oct & kGfcOuter) unwritten
+  // unit conversion coarse -> fine: dt_c / dt_f, u_f = u_scale u_c and the
+  // density deviation rho'_f = r_scale rho'_c + r_shift (relative to rho_off)
+  double tratio, u_scale, r_scale, r_shift;
 };
 
 struct GffArgs {
@@ -226,6 +244,9 @@ struct GffArgs {
   void* dst;             // pdfs holding the coarse ghosts
   int64_t Ntot;
   double omega_c, omega_f, rho_off;
+  // unit conversion fine -> coarse: dt_c / dt_f, u_c = u_scale u_f and the
+  // density deviation rho'_c = r_scale rho'_f + r_shift (relative to rho_off)
+  double tratio, u_scale, r_scale, r_shift;
 };
 
 struct FillArgs {  // rest equilibrium everywhere
@@ -303,6 +324,9 @@ struct ReduceArgs {
   const double* obs_q;    // wall distance (1/2: half-way bounce-back)
   int64_t obs_n;
   double fscale;
+  // mass vol (cnt rho0 + r_scale sum (rho - rho0)) (r_scale 1: vol sum rho),
+  // momentum vol_m sum rho u, kinetic energy vol_k sum rho |u|^2 / 2
+  double vol_m, vol_k, r_scale, rho0;
 };
 
 struct FinalArgs {

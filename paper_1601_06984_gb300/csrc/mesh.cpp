@@ -155,7 +155,7 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
   };
   if (!tid || n <= 0) return bad(LBM_ERR_ARG, "empty mesh");
   if (p.stencil != 9 && p.stencil != 19 && p.stencil != 27) return bad(LBM_ERR_ARG, "stencil must be 9, 19 or 27");
-  if (p.time_mode != LBM_TIME_LINEAR && p.time_mode != LBM_TIME_TWO_LAYER)
+  if (p.time_mode != LBM_TIME_LINEAR && p.time_mode != LBM_TIME_TWO_LAYER && p.time_mode != LBM_TIME_DIFFUSIVE)
     return bad(LBM_ERR_ARG, "bad time mode");
   if (p.inlet_profile != LBM_INLET_UNIFORM && p.inlet_profile != LBM_INLET_PARABOLIC)
     return bad(LBM_ERR_ARG, "bad inlet profile");
@@ -480,7 +480,11 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
     });
   }
 
-  // ---- GhostFromCoarser: all children of level L-1 fluid touching a subdivided cell
+  // ---- GhostFromCoarser: all children of level L-1 fluid within R coarse cells
+  // of a subdivided cell: two fine layers (R = 1), or four with diffusive
+  // scaling (R = 2), whose four substeps per coarse step eat one layer each
+  const int R = B.mode == LBM_TIME_DIFFUSIVE ? 2 : 1;
+  const int nlay = 2 * R;
   for (int li = 1; li < nlev; ++li) {
     const auto& parents = fl[li - 1];
     const int64_t np = (int64_t)parents.size();
@@ -488,9 +492,9 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
 #pragma omp parallel for schedule(static)
     for (int64_t r = 0; r < np; ++r) {
       const int64_t* P = &X[3 * parents[r].second];
-      for (int oz = -zr; oz <= zr && !touch[r]; ++oz)
-        for (int oy = -1; oy <= 1 && !touch[r]; ++oy)
-          for (int ox = -1; ox <= 1; ++ox) {
+      for (int oz = -R * zr; oz <= R * zr && !touch[r]; ++oz)
+        for (int oy = -R; oy <= R && !touch[r]; ++oy)
+          for (int ox = -R; ox <= R; ++ox) {
             int64_t q[3] = {P[0] + ox, P[1] + oy, P[2] + oz};
             if (B.wrap(li - 1, q)) continue;
             if (B.value(li - 1, q) == G_SUB) {
@@ -510,24 +514,25 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
         g.x[2] = d == 3 ? 2 * P[2] + ((b >> 2) & 1) : 0;
         g.oct = (uint8_t)b;
         g.key = zkey(g.x, d, B.Lmin + li);
-        g.layer = 2;
+        g.layer = nlay;
         gfc[li].push_back(g);
       }
     }
-    // layer: 1 if any neighbour of the ghost is fluid or subdivided on this level
+    // layer: the Chebyshev distance to the nearest fluid or subdivided cell of
+    // this level, nlay for farther ghosts too
+    const int sr = nlay - 1;
 #pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < (int64_t)gfc[li].size(); ++k) {
       Ghost& g = gfc[li][k];
-      for (int oz = -zr; oz <= zr && g.layer == 2; ++oz)
-        for (int oy = -1; oy <= 1 && g.layer == 2; ++oy)
-          for (int ox = -1; ox <= 1; ++ox) {
+      for (int oz = -sr * zr; oz <= sr * zr; ++oz)
+        for (int oy = -sr; oy <= sr; ++oy)
+          for (int ox = -sr; ox <= sr; ++ox) {
+            const int dist = std::max(std::abs(ox), std::max(std::abs(oy), std::abs(oz)));
+            if (dist == 0 || dist >= g.layer) continue;
             int64_t q[3] = {g.x[0] + ox, g.x[1] + oy, g.x[2] + oz};
             if (B.wrap(li, q)) continue;
             int32_t v = B.value(li, q);
-            if (v >= 0 || v == G_SUB) {
-              g.layer = 1;
-              break;
-            }
+            if (v >= 0 || v == G_SUB) g.layer = dist;
           }
     }
   }
@@ -611,7 +616,7 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
   }
   // relaxation per level, Eq. (fneq_scale)
   M.lv[0].omega = p.omega_coarse;
-  for (int li = 1; li < nlev; ++li) M.lv[li].omega = 1.0 / (0.5 + 2.0 * (1.0 / M.lv[li - 1].omega - 0.5));
+  for (int li = 1; li < nlev; ++li) M.lv[li].omega = finer_omega(M.lv[li - 1].omega, B.mode);
   for (int li = 0; li < nlev; ++li)
     if (std::fabs(1.0 - M.lv[li].omega) < 1e-3) return bad(LBM_ERR_ARG, "omega too close to 1 on some level");
 
@@ -719,9 +724,10 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       for (int s = 0; s < 4 && ok; ++s) ok = H.gfc_src[s * H.nC + k] == H.gfc_src[s * H.nC + k0 + canon[s]];
       if (!ok) return bad(LBM_ERR_INTERNAL, "GhostFromCoarser sibling group inconsistent");
     }
-    // bit 7 marks the outer layer (no fluid or subdivided neighbour on this level)
+    // bit 7 marks the outer layer (no fluid or subdivided cell on this level
+    // within nlay - 1 cells)
     for (int64_t k = 0; k < H.nC; ++k)
-      if (gfc[li][k].layer == 2) H.gfc_oct[k] |= kGfcOuter;
+      if (gfc[li][k].layer == nlay) H.gfc_oct[k] |= kGfcOuter;
   }
   // source bits per 32 slots (records written by the stream-collide) and the
   // GhostFromFiner sources (records written after the ghost fill)
@@ -802,11 +808,14 @@ lbm_status build_host_mesh(const int64_t* tid, const int8_t* levels, int64_t n, 
       for (int64_t e = 0; e < H.N; ++e) {
         const uint8_t k = kd[e];
         const int64_t ge = H.base + e;
-        // processed: fluid always; GFC (both layers) in TWO_LAYER mode; inner GFF in LINEAR mode
-        const bool proc = k == K_FLUID || (k == K_GFC && B.mode == LBM_TIME_TWO_LAYER) ||
+        // processed: fluid always; GFC (all layers) in TWO_LAYER and DIFFUSIVE
+        // modes; inner GFF in LINEAR mode
+        const bool proc = k == K_FLUID || (k == K_GFC && B.mode != LBM_TIME_LINEAR) ||
                           (k == K_GFF && layer[e] == 1 && B.mode == LBM_TIME_LINEAR);
-        // ghosts whose pulled values reach fluid must find every neighbour
-        const bool strict_ghost = (k == K_GFC && layer[e] == 1) || k == K_GFF;
+        // ghosts whose pulled values reach fluid must find every neighbour: the
+        // GFC layers before the outermost (whose processed values reach no
+        // fluid before the next fill) and the GFF ghosts
+        const bool strict_ghost = (k == K_GFC && layer[e] < nlay) || k == K_GFF;
         for (int i = 1; i < Q; ++i) {
           // default for links whose value never reaches a fluid element: read the
           // element's own opposite slot (each pdf slot keeps a single reader, so

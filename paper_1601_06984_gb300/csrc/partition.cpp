@@ -9,7 +9,8 @@
 // the outlet's extrapolation sources), the GhostFromCoarser sources and the
 // GhostFromFiner children of the ghosts it fills, and the pull sources of the
 // ghosts the time mode advances (the inner GhostFromFiner layer in
-// LBM_TIME_LINEAR, the inner GhostFromCoarser layer in LBM_TIME_TWO_LAYER).
+// LBM_TIME_LINEAR, the inner GhostFromCoarser layer in LBM_TIME_TWO_LAYER, the
+// inner three of the four GhostFromCoarser layers in LBM_TIME_DIFFUSIVE).
 // Every such read takes the current state of the read element's level, so one
 // exchange of a level's halo after each stream-collide of that level (and one
 // after lbm_init) keeps every read current.  Ghosts are computed by every
@@ -34,6 +35,8 @@ extern "C" lbm_status lbm_halo_plan(const lbm_ctx* c, const int32_t* part, int32
   for (int64_t u = 0; u < n; ++u)
     if (part[u] < 0 || part[u] >= nparts) return LBM_ERR_ARG;
   const bool linear = c->p.time_mode == LBM_TIME_LINEAR;
+  // GhostFromCoarser layers whose advanced values reach fluid
+  const int gfc_adv = c->p.time_mode == LBM_TIME_DIFFUSIVE ? 3 : 1;
   // per slot: level index, position within its level's ghost rows (-1: not a ghost)
   std::vector<int8_t> lev(Ntot, -1);
   std::vector<int64_t> ghost_row(Ntot, -1);
@@ -87,7 +90,7 @@ extern "C" lbm_status lbm_halo_plan(const lbm_ctx* c, const int32_t* part, int32
       const int64_t k = e - H.oC;
       const HostLevel& Hc = M.lv[lev[g] - 1];
       for (int s = 0; s < 4; ++s) read(Hc.src_elem[H.gfc_src[(size_t)s * H.nC + k]]);
-      if (!linear && H.ghost_layer[k] == 1) pulls(g);  // advanced by the fine stream-collide
+      if (!linear && H.ghost_layer[k] <= gfc_adv) pulls(g);  // advanced by the fine stream-collide
     } else {
       const bool inner = e >= H.oG1 && e < H.oG1 + H.nG1;
       const int64_t k = inner ? e - H.oG1 : H.nG1 + (e - H.oG2);

@@ -19,7 +19,7 @@ LBM_OK = 0
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_MESH", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_OOM",
           -5: "LBM_ERR_STATE", -6: "LBM_ERR_NUMERIC", -7: "LBM_ERR_INTERNAL"}
 FP64, FP32DEV, BF16DEV = 0, 1, 2
-TIME_LINEAR, TIME_TWO_LAYER = 0, 1
+TIME_LINEAR, TIME_TWO_LAYER, TIME_DIFFUSIVE = 0, 1, 2
 OUTLET_LINEAR, OUTLET_ZERO_GRADIENT = 0, 1
 INLET_UNIFORM, INLET_PARABOLIC = 0, 1
 EXPORTS = ["lbm_build_mesh", "lbm_mesh_info", "lbm_device_bytes", "lbm_bind", "lbm_init", "lbm_set_force",

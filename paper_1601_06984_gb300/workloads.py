@@ -24,7 +24,7 @@ import math
 import numpy as np
 
 BC_PERIODIC, BC_WALL, BC_VELOCITY_IN, BC_PRESSURE_OUT = 0, 1, 2, 3
-TIME_LINEAR, TIME_TWO_LAYER = 0, 1
+TIME_LINEAR, TIME_TWO_LAYER, TIME_DIFFUSIVE = 0, 1, 2
 SEED = 20160127
 
 

@@ -43,7 +43,7 @@ MESHES = [
 
 
 @pytest.mark.parametrize("name,make,Q,omega", MESHES)
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_mesh_counts_match_oracle(lbm, oracle_mod, name, make, Q, omega, mode):
     """Level-wise fluid / GhostFromCoarser / GhostFromFiner counts of the
     library's builder equal those of the oracle's independent mesh code."""

@@ -92,9 +92,18 @@ OUTLET = {"channel_zg": 1, "sphere5": 1}  # zero-gradient outlet extrapolation
 BOUZIDI = {"schafer20": (20, (40.0, 40.0), 10.0)}
 
 
+def case_fields(m, fields, mode):
+    """The case's fields, converted to each level's lattice units in the
+    diffusive mode (the generators give coarsest-level velocities)."""
+    rho, u, S, df = fields(m)
+    if mode == 2:
+        rho, u, S = W.diffusive_units(m, rho, u, S)
+    return rho, u, S, df
+
+
 def run_both(lbm, oracle_mod, name, mode, precision=0):
     m, Q, om, uin, fields, force, steps = make_case(name)
-    rho, u, S, df = fields(m)
+    rho, u, S, df = case_fields(m, fields, mode)
     out = OUTLET.get(name, 0)
     bz = BOUZIDI.get(name)
     o = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin, use_force=force is not None, outlet=out,
@@ -121,7 +130,7 @@ CASES = ["tgv2d", "tgv2d_half", "tgv3d", "tgv3d_force", "cylinder", "channel_zg"
 
 
 @pytest.mark.parametrize("name", CASES)
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_fp64_matches_oracle(lbm, oracle_mod, name, mode):
     m, o, g = run_both(lbm, oracle_mod, name, mode)
     assert rel(g.get_state(), o.get_f()) < TOL
@@ -140,11 +149,13 @@ def test_fp64_matches_oracle(lbm, oracle_mod, name, mode):
 
 
 @pytest.mark.parametrize("name", ["tgv2d", "tgv3d", "sphere_small", "tgv3d_q27", "sphere5"])
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_ghost_fill_matches_oracle(lbm, oracle_mod, name, mode):
-    """GhostFromFiner and GhostFromCoarser values after one synchronous fill."""
+    """GhostFromFiner and GhostFromCoarser values after one synchronous fill
+    (in the diffusive mode four GhostFromCoarser layers, with the unit
+    conversions of both fills)."""
     m, Q, om, uin, fields, force, _ = make_case(name)
-    rho, u, S, df = fields(m)
+    rho, u, S, df = case_fields(m, fields, mode)
     o = oracle_mod.Oracle(m, Q, om, time_mode=mode, u_in=uin)
     g = lbm.Sim(m, Q, om, time_mode=mode, u_in=uin)
     o.init(rho, u, S, df)
@@ -223,13 +234,15 @@ def test_deterministic(lbm, precision):
     assert np.array_equal(out[0][1], out[1][1])
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_precision_variants_error(lbm, oracle_mod, mode):
     """FP32-deviation and BF16-deviation storage against the FP64 oracle on the
     2D two-level Taylor-Green (200 coarse steps, u0 = 0.01): velocity l2 error
     and mass drift stay within the stated bounds."""
     m = W.config_tgv2d()
     rho, u, S = W.tgv_fields(m, 0.01)
+    if mode == 2:
+        rho, u, S = W.diffusive_units(m, rho, u, S)
     o = oracle_mod.Oracle(m, 9, 1.6, time_mode=mode)
     o.init(rho, u, S)
     o.step(200)
@@ -282,7 +295,7 @@ def test_checkpoint_restart(lbm, precision):
         assert rel(b.get_state(), a.get_state()) < 1e-6
 
 
-@pytest.mark.parametrize("precision,mode", [(0, 0), (1, 1), (2, 0)])
+@pytest.mark.parametrize("precision,mode", [(0, 0), (1, 1), (2, 0), (1, 2)])
 def test_graph_steps_match_eager_steps(lbm, precision, mode):
     """lbm_step replays captured graphs (two-step graphs for pairs of steps, a
     one-step graph for a remaining step); in timing mode 1 every step is
@@ -313,7 +326,7 @@ def test_graph_steps_match_eager_steps(lbm, precision, mode):
     assert np.array_equal(a.get_state(), b.get_state())
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_records_follow_state_changes(lbm, mode):
     """The stream-collide keeps the GhostFromCoarser source records of the
     state it writes; anything else that changes the state, the force or the
@@ -391,7 +404,7 @@ def test_q27_reduced_precision_tracks_fp64(lbm, oracle_mod, precision):
 
 
 @pytest.mark.parametrize("d", [2, 3])
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_empty_refined_region_is_identity(lbm, oracle_mod, d, mode):
     """Sec. 2.2 recursive stepping with nothing to couple: one more declared
     level without elements (an empty refined region) leaves the FP64 result of
@@ -490,3 +503,43 @@ def test_mass_check_leaves_clean_runs_unchanged(lbm, precision):
             g.step(n)
         res.append(g.get_state())
     assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
+
+
+def test_diffusive_mode_has_no_adjoint(lbm):
+    """The adjoint covers the acoustic-scaling modes only; in the diffusive
+    mode both adjoint calls fail with LBM_ERR_STATE and leave the context usable."""
+    m = W.config_tgv2d()
+    g = lbm.Sim(m, 9, 1.6, time_mode=2)
+    g.init(*W.diffusive_units(m, *W.tgv_fields(m, 0.01)))
+    with pytest.raises(lbm.LBMError) as ex:
+        g.adjoint_bytes(2, 1)
+    assert ex.value.status == -5
+    g.step(1)
+    assert np.isfinite(g.get_state()).all()
+
+
+def test_diffusive_tgv_converges_at_second_order(lbm):
+    """Taylor-Green vortex on the half-refined square in the diffusive mode
+    (u0 ~ 1/N at fixed omega), through the C ABI in FP64 at N = 32, 64, 128, 256:
+    the strain-rate error at t_D / 4 in coarsest-level units falls at second
+    order (local slopes in [1.8, 2.2]), as the oracle's does at N = 16..128."""
+    from conv_fit import local_slopes
+    res = (32, 64, 128, 256)
+    errs = []
+    for N in res:
+        mesh = W.half_refined_2d(N)
+        omega = 1.6
+        nu = (1 / omega - 0.5) / 3
+        k = 2 * math.pi / N
+        steps = int(round(0.25 / (2 * nu * k * k)))
+        u0 = 0.0025 * 16 / N
+        g = lbm.Sim(mesh, 9, omega, time_mode=2)
+        g.init(*W.diffusive_units(mesh, *W.tgv_fields(mesh, u0)))
+        g.step(steps)
+        _, u1, S1 = g.moments()
+        _, ua, Sa = W.diffusive_units(mesh, *W.tgv_fields(mesh, u0, t=steps, nu=nu))
+        l = mesh.levels.astype(np.int64) - mesh.lmin
+        sS = np.ldexp(1.0, 2 * l)
+        errs.append(math.sqrt((((S1[:, 0] - Sa[:, 0]) * sS) ** 2).sum() / ((Sa[:, 0] * sS) ** 2).sum()))
+    sl = local_slopes(res, np.array(errs))
+    assert np.all((sl >= 1.8) & (sl <= 2.2)), (sl, errs)

@@ -122,7 +122,8 @@ def _distributed(name, mode, rank, world, dist):
             if mode == 0:
                 loc.op(loc.OP_MOM_B, li)
                 loc.op(loc.OP_GFC_B, li)
-            advance(li + 1)
+            for _ in range(3 if mode == 2 else 1):  # four substeps with diffusive scaling
+                advance(li + 1)
 
     exchange(list(range(nlev)))  # the initial state's halo
     for _ in range(steps):
@@ -134,7 +135,8 @@ def _distributed(name, mode, rank, world, dist):
             "ghosts": int(len(ghosts)), "exchanges": exchanges[0], "n": int(m.n)}
 
 
-CASES = [("tgv2d", 0), ("tgv2d", 1), ("tgv3d", 0), ("tgv3d", 1), ("schafer20", 0), ("sphere5", 0)]
+CASES = [("tgv2d", 0), ("tgv2d", 1), ("tgv2d", 2), ("tgv3d", 0), ("tgv3d", 1), ("tgv3d", 2), ("schafer20", 0),
+         ("schafer20", 2), ("sphere5", 0)]
 
 
 def _worker(rank, world, port, cases, q):
@@ -188,7 +190,7 @@ def test_distributed_run_with_halo_exchange_two_ranks():
 
 
 def test_distributed_run_three_ranks():
-    res = _run(3, [("tgv2d", 0), ("sphere5", 0)], 700)
+    res = _run(3, [("tgv2d", 0), ("sphere5", 0), ("sphere5", 2)], 700)
     for rank, out in res.items():
         assert "error" not in out, out.get("error")
         for key, r in out.items():
