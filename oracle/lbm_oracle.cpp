@@ -32,6 +32,9 @@
 //                                    rescale includes the factor 1/m implied by
 //                                    acoustic scaling and the strain-rate eq.
 //   GFF before GFC, two ghost layers  Sec. 2.2 (closing paragraphs)
+//   diffusive scaling, four layers . Sec. 2.2 (named there only; time-step
+//                                    ratio 4, omega equal on all levels and
+//                                    the unit conversions are readings)
 //   inlet / outlet / wall / force .. Sec. 2.3
 //   treeID, z-curve, weights ....... Sec. 3.1, Eq. (weight)
 //   initial f^neq .................. Sec. 4.1 (prefactor chosen so that the
