@@ -5,7 +5,8 @@
 
 Coefficients follow Sec. 4.2 / 4.3 of arXiv:1601.06984: c_D = 2 F_x / (rho
 U^2 A), c_L = 2 F_y / (rho U^2 A), A = D (2D) or pi D^2 / 4 (3D), St = f D / U
-with f the lift oscillation frequency.  Forces come from the FP64
+with f the lift oscillation frequency, and the sphere's recirculation length
+L_r / D.  Forces come from the FP64
 momentum-exchange reduction (lbm_reduce), in finest-level lattice units; D
 and U are in those units too.  The geometries are the synthetic cylinder
 channel and sphere box of workloads.py.
@@ -129,11 +130,41 @@ def schafer(Re=20.0, precision="fp32dev", steps=20000, window=5000, D=40, U=0.05
             "samples_every_coarse_steps": chunk}
 
 
+def recirculation_length(mesh, u, center, D):
+    """Length of the recirculation zone behind a body centred on the x axis
+    through `center` (finest-level cell units, a corner of the cells around
+    the axis on every level), in diameters D: from the body's rear point
+    center[0] + D/2 to the first point where the axial velocity u_x turns
+    from negative to positive (Sec. 4.3, L_r).  u_x on the axis is the mean of
+    the four cells around it at each cell-centre position x, linearly
+    interpolated between positions.  None when the flow behind the body is not
+    reversed."""
+    lv = mesh.levels.astype(np.int64)
+    h = np.ldexp(1.0, int(lv.max()) - lv)  # cell size in finest units
+    cen = (np.asarray(mesh.coords, float) + 0.5) * h[:, None]
+    on = ((np.abs(np.abs(cen[:, 1] - center[1]) - 0.5 * h) < 1e-9)
+          & (np.abs(np.abs(cen[:, 2] - center[2]) - 0.5 * h) < 1e-9))
+    x0 = center[0] + 0.5 * D
+    sel = on & (cen[:, 0] > x0)
+    if not sel.any():
+        return None
+    xs, inv = np.unique(cen[sel, 0], return_inverse=True)
+    ux = np.bincount(inv, weights=np.asarray(u)[sel, 0]) / np.bincount(inv)
+    if ux[0] >= 0.0:
+        return None
+    k = int(np.argmax(ux >= 0.0))
+    if ux[k] < 0.0:
+        return None  # reversed up to the last axis cell
+    xc = xs[k - 1] + (0.0 - ux[k - 1]) * (xs[k] - xs[k - 1]) / (ux[k] - ux[k - 1])
+    return float((xc - x0) / D)
+
+
 def sphere(precision="fp32dev", steps=2000, window=200, U=0.04, Re=100.0, outlet="auto", Q=19, bouzidi=False,
            device="cuda"):
     """The bench's sphere (D = 64 finest cells, 5 levels), D3Q19 or the paper's
     D3Q27, half-way or interpolated bounce-back with the sphere's wall
-    distances.  c_D = 2 F_x / (rho U^2 pi D^2 / 4)."""
+    distances.  c_D = 2 F_x / (rho U^2 pi D^2 / 4); L_r / D from the final
+    state's axial velocity (recirculation_length)."""
     mesh = W.config_sphere(1)
     D = 64.0
     om_f = W.omega_for_re(U, D, Re)
@@ -153,11 +184,13 @@ def sphere(precision="fp32dev", steps=2000, window=200, U=0.04, Re=100.0, outlet
         if k >= steps - window:
             cd.append(2.0 * sim.reduce()[4] / (U * U * A))
     wall = time.perf_counter() - t0
+    _, u, _ = sim.moments()
+    lr = recirculation_length(mesh, u, (8 * D,) * 3, D)
     return {"case": "sphere", "Re": Re, "precision": precision, "stencil": f"D3Q{Q}",
             "walls": "interpolated bounce-back" if bouzidi else "half-way bounce-back", "outlet": outlet,
             "coarse_steps": steps,
             "omega_coarsest": om_c, "c_D_last": cd[-1],
-            "c_D_mean": float(np.mean(cd)), "seconds": wall}
+            "c_D_mean": float(np.mean(cd)), "L_r_over_D": lr, "seconds": wall}
 
 
 def main():
