@@ -1201,8 +1201,10 @@ __global__ void k_fill_rest(const FillArgs a) {
 }
 
 // Initial state, Sec. 4.1: f = f^eq + (1 - omega) f^neq + df with
-// f^neq_i = -(3 w_i rho / omega) (c_i c_i - I/3) : S.
-template <int Q, class S>
+// f^neq_i = -(3 w_i rho / omega) (c_i c_i - I/3) : S.  HAS_S: a strain rate is
+// given (a template flag, so that the loop over the directions has no branch
+// on it and unrolls into compile-time lattice constants).
+template <int Q, class S, bool HAS_S>
 __global__ void k_init(const InitArgs a) {
   using R = typename Sto<S>::R;
   using LT = Lat<Q>;
@@ -1221,23 +1223,25 @@ __global__ void k_init(const InitArgs a) {
     u[b] = R(a.u[t * D + b]);
     usq += u[b] * u[b];
   }
-  const double* Sv = a.S ? a.S + t * NS : nullptr;
+  R sv[NS], tr = R(0);
+  if (HAS_S) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j) sv[j] = R(a.S[t * NS + j]);
+#pragma unroll
+    for (int b = 0; b < D; ++b) tr += sv[sidx<D>(b, b)];
+  }
   const double* df = a.df ? a.df + t * Q : nullptr;
   const R om = R(a.omega[li]);
   S* out = static_cast<S*>(a.temp) + k;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     R g = geq<Q, R>(q, rp, rho, u, usq);
-    if (Sv) {
-      R qs = R(0), tr = R(0);
+    if (HAS_S) {
+      R qs = R(0);
 #pragma unroll
       for (int b = 0; b < D; ++b)
 #pragma unroll
-        for (int c = b; c < D; ++c) {
-          const R sv = R(Sv[sidx<D>(b, c)]);
-          qs += R((b == c ? 1 : 2) * LT::c(q, b) * LT::c(q, c)) * sv;
-          if (b == c) tr += sv;
-        }
+        for (int c = b; c < D; ++c) qs += R((b == c ? 1 : 2) * LT::c(q, b) * LT::c(q, c)) * sv[sidx<D>(b, c)];
       // post-collision non-equilibrium part (1 - omega) f^neq of the strain rate
       g += (R(1) - om) * (-(R(3.0 * LT::w(q)) * rho / om) * (qs - tr / R(3)));
     }
@@ -1550,7 +1554,10 @@ struct Launch {
   }
   static void init(int Q, const InitArgs& a, cudaStream_t st) {
     if (a.cnt <= 0) return;
-    with_q(Q, [&](auto q) { k_init<decltype(q)::value, S><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a); });
+    with_q(Q, [&](auto q) {
+      if (a.S) k_init<decltype(q)::value, S, true><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+      else k_init<decltype(q)::value, S, false><<<blocks_for(a.cnt, 128), 128, 0, st>>>(a);
+    });
   }
   static void init_place(int Q, const PlaceArgs& a, cudaStream_t st) {
     with_q(Q, [&](auto q) { k_init_place<decltype(q)::value, S><<<blocks_for(a.Ntot, 256), 256, 0, st>>>(a); });
