@@ -260,3 +260,25 @@ def test_obstacle_links_and_link_q(lbm):
     hb = lbm.Sim(m, 9, 1.6, u_in=(0.05, 0, 0), device=None)
     with pytest.raises(lbm.LBMError, match="bouzidi"):
         hb.set_link_q(q)
+
+
+def test_diffusive_mode_needs_wider_level_margins(lbm, oracle_mod):
+    """Four GhostFromCoarser layers reach one coarse cell further than two: a
+    three-level mesh whose finest box sits two level-1 cells inside the level-1
+    box builds in the two-layer mode, but in the diffusive mode a ghost's coarse
+    source would itself be a ghost, and the oracle and the library both reject
+    it; four cells of margin build in every mode."""
+    def mesh(margin):
+        lo, hi = 32 + 2 * margin, 96 - 2 * margin
+        return W.nested_boxes(2, 5, (32, 32), [((16, 16), (48, 48)), ((lo, lo), (hi, hi))], (0,) * 4)
+    thin, wide = mesh(2), mesh(4)
+    lbm.Sim(thin, 9, 1.7, time_mode=1, device=None)
+    oracle_mod.Oracle(thin, 9, 1.7, time_mode=1)
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.Oracle(thin, 9, 1.7, time_mode=2)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.Sim(thin, 9, 1.7, time_mode=2, device=None)
+    assert ei.value.status == -2 and "source" in str(ei.value)
+    for mode in (0, 1, 2):
+        lbm.Sim(wide, 9, 1.7, time_mode=mode, device=None)
+        oracle_mod.Oracle(wide, 9, 1.7, time_mode=mode)
