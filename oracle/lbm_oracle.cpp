@@ -213,6 +213,30 @@ struct Sim {
   // (dt proportional to dx), 4 with the diffusive scaling (dt proportional to
   // dx^2) that Sec. 2.2 mentions for the multi-layer scheme
   double mt() const { return mode == TIME_DIFFUSIVE ? 4.0 : kM; }
+  // f^neq has an even part in c (first order in the Chapman-Enskog
+  // expansion: the viscous stress, proportional to tau dt S) and an odd part
+  // (a vector flux, proportional to tau dt^2 / dx: dt^2 / dx (rho d_t u +
+  // grad p) from the first-order term, and tau^2 dx dt grad^2 u from the
+  // second-order one, which is of the same order when dt ~ dx^2).  Eq.
+  // (fneq_scale) carries the even part from one level to the next by the
+  // ratio of tau dt.  With acoustic scaling dt / dx is the same on both
+  // levels, so the odd part takes the same ratio.  With diffusive scaling its
+  // ratio is smaller by (dt_f / dt_c) / (dx_f / dx_c) = 1/2 from coarse to
+  // fine (2 from fine to coarse): odd_ratio, the extra factor.
+  double odd_ratio(bool to_coarse) const {
+    if (mode != TIME_DIFFUSIVE) return 1.0;
+    return to_coarse ? mt() / kM : kM / mt();
+  }
+  // f^neq_i -> even_i + r odd_i, even / odd the halves of f^neq_i +- f^neq_opp(i)
+  void odd_rescale(T* fn, double r) const {
+    if (r == 1.0) return;
+    T out[kQmax];
+    for (int i = 0; i < Q; ++i) {
+      const T ev = (fn[i] + fn[lat.opp[i]]) / T(2.0), od = (fn[i] - fn[lat.opp[i]]) / T(2.0);
+      out[i] = ev + T(r) * od;
+    }
+    for (int i = 0; i < Q; ++i) fn[i] = out[i];
+  }
   int64_t ext0[3] = {1, 1, 1};
   int bc[6] = {0, 0, 0, 0, 0, 0};
   double rho0 = 1.0;
@@ -774,6 +798,7 @@ struct Sim {
         u[a] = u[a] - lap / T(32.0);
       }
       const T scale = T(mt()) * lf.omega / lc.omega;
+      odd_rescale(fneq, odd_ratio(true));
       for (int i = 0; i < Q; ++i) {
         T fn = scale * fneq[i] / T((double)nch);
         g.f[i] = feq(i, rho, u) + (T(1.0) - lc.omega) * fn;
@@ -1020,12 +1045,15 @@ void Sim<T>::fill_gfc(int li, const std::vector<Mom<T>>& q0, const std::vector<M
     // step 4: rescale f^neq, omega_c f^neq_c / m = omega_f f^neq_f (m the
     // time-step ratio)
     const T scale = lc.omega / (T(mt()) * lf.omega);
+    T fn[kQmax];
     for (int i = 0; i < Q; ++i) {
-      T fn = T(0.0);
-      for (int k = 0; k < 4; ++k) fn += T(lw[k]) * m[k].fneq[i];
-      fn = scale * fn;
+      fn[i] = T(0.0);
+      for (int k = 0; k < 4; ++k) fn[i] += T(lw[k]) * m[k].fneq[i];
+    }
+    odd_rescale(fn, odd_ratio(false));
+    for (int i = 0; i < Q; ++i) {
       // steps 3 and 5: f = f^eq + f^neq, stored post-collision
-      g.f[i] = feq(i, rho, u) + (T(1.0) - lf.omega) * fn;
+      g.f[i] = feq(i, rho, u) + (T(1.0) - lf.omega) * (scale * fn[i]);
     }
   }
 }

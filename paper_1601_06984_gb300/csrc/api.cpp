@@ -108,6 +108,7 @@ void lbm_ctx::fill_gff(int li) {
   a.u_scale = a.tratio / 2.0;
   a.r_scale = a.u_scale * a.u_scale;
   a.r_shift = (1.0 - a.r_scale) * (p.rho0 - rho_off);
+  a.odd_ratio = odd_fneq_ratio(p.time_mode, true);
   timed_launch(li, TK_GFF, [&] { ops->fill_gff(Q, a, st); });
   ++launches;
 }
@@ -163,6 +164,7 @@ void lbm_ctx::fill_gfc(int lf, bool two_times, bool all_layers, cudaStream_t s, 
   a.u_scale = 2.0 / a.tratio;
   a.r_scale = a.u_scale * a.u_scale;
   a.r_shift = (1.0 - a.r_scale) * (p.rho0 - rho_off);
+  a.odd_ratio = odd_fneq_ratio(p.time_mode, false);
   timed_launch(lf, TK_GFC, [&] { ops->fill_gfc(Q, a, s); }, s);
   ++launches;
 }

@@ -903,7 +903,8 @@ __device__ __forceinline__ void compact_uloc(const R (&ul)[4][3], const R (&Sl)[
 // rescaled by omega_c / (m omega_f) (m = dt_c / dt_f), and f = f^eq +
 // (1 - omega_f) f^neq is stored as the ghost's post-collision state.  With
 // diffusive scaling the velocity and density deviation are converted to the
-// fine level's lattice units first.
+// fine level's lattice units first, and f^neq's odd part (a flux of order
+// tau dt^2 / dx) takes an extra factor 1/2 beside its even part's.
 // Ghosts come in groups of 2^d consecutive siblings (the children of one
 // coarse parent, octant b = k mod 2^d), and their 4 x 2^d source records are
 // 13 distinct ones in 3D (the parent and its 12 edge neighbours), 9 in 2D.  A
@@ -997,6 +998,9 @@ __device__ __forceinline__ void gfc_ghost(const GfcArgs& a, const typename Sto<S
   }
   const R base = rp - R(1.5) * rho * usq;
   dst[e] = Sto<S>::cv(R(LT::w(0)) * base + scale * fn[0]);
+  // diffusive scaling: f^neq's odd part takes an extra factor (odd_ratio)
+  const bool odd_rescale = a.odd_ratio != 1.0;
+  const R ro = R(a.odd_ratio);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     R cu = R(0);
@@ -1008,8 +1012,14 @@ __device__ __forceinline__ void gfc_ghost(const GfcArgs& a, const typename Sto<S
     const R w = R(LT::w(i));
     const R even = w * (base + R(4.5) * rho * cu * cu);
     const R odd = w * R(3) * rho * cu;
-    dst[(size_t)i * N + e] = Sto<S>::cv(even + odd + scale * fn[i]);
-    dst[(size_t)(i + 1) * N + e] = Sto<S>::cv(even - odd + scale * fn[i + 1]);
+    R fa = fn[i], fb = fn[i + 1];
+    if (odd_rescale) {
+      const R fe = R(0.5) * (fa + fb), fo = R(0.5) * (fa - fb) * ro;
+      fa = fe + fo;
+      fb = fe - fo;
+    }
+    dst[(size_t)i * N + e] = Sto<S>::cv(even + odd + scale * fa);
+    dst[(size_t)(i + 1) * N + e] = Sto<S>::cv(even - odd + scale * fb);
   }
 }
 
@@ -1076,7 +1086,8 @@ __global__ void LBM_GFC_BOUNDS k_fill_gfc(const GfcArgs a) {
 // rates (differences across the children's cube).  f^neq is rescaled by
 // m omega_f / omega_c (m = dt_c / dt_f); f = f^eq + (1 - omega_c) f^neq.  With
 // diffusive scaling the mean velocity and density deviation are converted to
-// the coarse level's lattice units.
+// the coarse level's lattice units, and f^neq's odd part takes an extra
+// factor 2.
 // One group of 2^d consecutive lanes per ghost: lane b loads child b (siblings
 // are contiguous, so the group's loads are coalesced), and the sums over the
 // children are shuffles inside the group.
@@ -1112,6 +1123,17 @@ __global__ void LBM_GFF_BOUNDS k_fill_gff(const GffArgs a) {
 #pragma unroll
       for (int c = 0; c < D; ++c) F[c] = static_cast<const R*>(a.force)[(size_t)c * N + e];
     post_moments<Q, R, true, FORCE>(g, wf, rho_off, F, rp, u, fneq, Sv);
+    if (a.odd_ratio != 1.0) {
+      // diffusive scaling: f^neq's odd part takes an extra factor (the sum
+      // over the children is linear, so each child's share is rescaled)
+      const R ro = R(a.odd_ratio);
+#pragma unroll
+      for (int i = 1; i < Q; i += 2) {
+        const R fe = R(0.5) * (fneq[i] + fneq[i + 1]), fo = R(0.5) * (fneq[i] - fneq[i + 1]) * ro;
+        fneq[i] = fe + fo;
+        fneq[i + 1] = fe - fo;
+      }
+    }
   }
   // The ghost's velocity, mean minus (1/32) lap u, is linear in the children's
   // values, and so is lap u_a = dfac sum_c (2 d_c S_ac - d_a S_cc) with d_c the

@@ -65,6 +65,14 @@ inline int time_ratio(int mode) { return mode == LBM_TIME_DIFFUSIVE ? 4 : 2; }
 inline double finer_omega(double omega_c, int mode) {
   return mode == LBM_TIME_DIFFUSIVE ? omega_c : 1.0 / (0.5 + 2.0 * (1.0 / omega_c - 0.5));
 }
+// f^neq's odd part in c (a flux of order tau dt^2 / dx) changes between levels
+// by (dt_f / dt_c) / (dx_f / dx_c) more than its even part (the stress, of
+// order tau dt) that Eq. (fneq_scale) rescales: the extra factor, 1 with
+// acoustic scaling, 1/2 coarse to fine and 2 fine to coarse with diffusive
+// scaling
+inline double odd_fneq_ratio(int mode, bool to_coarse) {
+  return mode != LBM_TIME_DIFFUSIVE ? 1.0 : to_coarse ? 2.0 : 0.5;
+}
 // the same flow's lattice velocity on level index li over that on the coarsest level
 inline double level_velocity_ratio(int li, int mode) { return mode == LBM_TIME_DIFFUSIVE ? std::ldexp(1.0, -li) : 1.0; }
 
@@ -231,8 +239,9 @@ struct GfcArgs {
   double omega_c, omega_f, rho_off;
   int skip_outer;        // leave the outer-layer ghosts (oct & kGfcOuter) unwritten
   // unit conversion coarse -> fine: dt_c / dt_f, u_f = u_scale u_c and the
-  // density deviation rho'_f = r_scale rho'_c + r_shift (relative to rho_off)
-  double tratio, u_scale, r_scale, r_shift;
+  // density deviation rho'_f = r_scale rho'_c + r_shift (relative to rho_off);
+  // odd_ratio: the extra factor of f^neq's odd part (odd_fneq_ratio)
+  double tratio, u_scale, r_scale, r_shift, odd_ratio;
 };
 
 struct GffArgs {
@@ -245,8 +254,9 @@ struct GffArgs {
   int64_t Ntot;
   double omega_c, omega_f, rho_off;
   // unit conversion fine -> coarse: dt_c / dt_f, u_c = u_scale u_f and the
-  // density deviation rho'_c = r_scale rho'_f + r_shift (relative to rho_off)
-  double tratio, u_scale, r_scale, r_shift;
+  // density deviation rho'_c = r_scale rho'_f + r_shift (relative to rho_off);
+  // odd_ratio: the extra factor of f^neq's odd part (odd_fneq_ratio)
+  double tratio, u_scale, r_scale, r_shift, odd_ratio;
 };
 
 struct FillArgs {  // rest equilibrium everywhere

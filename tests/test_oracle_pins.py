@@ -791,21 +791,22 @@ def tgv_errors_diffusive(oracle_mod, N, frac, omega=1.6, u0_16=0.0025):
 def test_diffusive_tgv_second_order(oracle_mod):
     """The Taylor-Green vortex on the half-refined square (Sec. 4.1 layout) in
     the diffusive mode, L = 4..7 (N = 16..128) with u0 ~ 1/N and omega fixed,
-    which is the diffusive limit itself.  At t = t_D/4 every local slope of
-    S_xx lies in [1.8, 2.2] (1.92, 1.91, 1.93) and every local slope of u_x is
-    at least 1.8 (2.65, 2.85, 2.58).  At t = t_D the strain-rate slopes are
-    lower (1.86, 1.75 for N = 16..64; 1.74 to N = 128), so there they are only
-    bounded below by 1.7; the paper reports no diffusive-scaling result to
-    compare with.  A first-order interface fails both.  The range stops at
-    N = 128: beyond it (GPU, same arithmetic) the velocity error of this
-    coupling levels off near 2e-6 relative at omega 1.6."""
+    which is the diffusive limit itself.  At t = t_D/4 and at t = t_D every
+    local slope of S_xx lies in [1.8, 2.2] (1.94, 1.94, 1.97 and 1.91, 1.85,
+    1.91) and every local slope of u_x is at least 1.8 (2.53, 2.53, 2.28 and
+    2.74, 2.58, 2.39, falling toward 2 as in the acoustic modes).  Both need
+    f^neq's odd part carried between levels by its own factor: with the
+    even part's factor alone the t_D strain-rate slopes are 1.86, 1.75, 1.74
+    (and the velocity error levels off from N = 256 on).  The paper reports no
+    diffusive-scaling result to compare with.  A first-order interface fails
+    both."""
     from conv_fit import local_slopes
     res = (16, 32, 64, 128)
     e = np.array([tgv_errors_diffusive(oracle_mod, N, 0.25) for N in res])
     sS, su = local_slopes(res, e[:, 1]), local_slopes(res, e[:, 0])
     assert np.all((sS >= 1.8) & (sS <= 2.2)), (sS, e)
     assert np.all(su >= 1.8), (su, e)
-    res = (16, 32, 64)
+    res = (16, 32, 64, 128)
     e = np.array([tgv_errors_diffusive(oracle_mod, N, 1.0) for N in res])
     sS, su = local_slopes(res, e[:, 1]), local_slopes(res, e[:, 0])
-    assert np.all(sS >= 1.7) and np.all(su >= 1.8), (sS, su, e)
+    assert np.all((sS >= 1.8) & (sS <= 2.2)) and np.all(su >= 1.8), (sS, su, e)
