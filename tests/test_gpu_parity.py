@@ -2,7 +2,7 @@
 
 FP64 must match the oracle to 1e-11 relative max-norm on the post-collision
 pdfs and on the moments, element by element, on meshes that span several
-levels, ghost layers, boundaries and forces, in both time-coupling modes.
+levels, ghost layers, boundaries and forces, in all three time-coupling modes.
 """
 import math
 
